@@ -1,0 +1,148 @@
+"""Singular value thresholding operators in FP64 (test infrastructure only).
+
+- ``exact_svt``      Def. 1 / Eq. 3: S_tau(A) = U S_tau(Sigma) V^T, with the
+                     oracle's own one-sided Jacobi SVD.  Pinned by brute-force
+                     minimization of Eq. 2 on 4x3 inputs, diagonal and
+                     orthogonally-invariant closed forms, the prox optimality
+                     condition, and rank(X) = #{sigma_i > tau}.
+- ``ball_projection``Def. 3: P_tau(A) = U min(Sigma, tau) V^T (A = S_tau(A) + P_tau(A)).
+- ``frsvt``          Alg. 1 (FRSVT) step by step, with range propagation
+                     (Sec. 2.1) and the polar + eigen route of Sec. 2.2 / Eq. 6.
+                     Pinned by: equality with exact_svt when rank(A) <= l
+                     (Sec. 3.1, remark after Cor. 2), invariance to the choice
+                     of orthonormalization (Prop. 1), the Theorem 3 average
+                     bound over Omega draws, and the Prop. 4 residual estimate.
+- ``wsvt``           weighted SVT (the WSVT footnote of Sec. 1): U max(Sigma - w, 0) V^T.
+                     Pinned by reduction to SVT for constant weights and by
+                     brute-force minimization of the weighted problem on 4x3
+                     inputs with non-descending weights.
+- ``psvt``           partial SVT of the truncated nuclear norm (Table 6, Type B):
+                     the k leading singular values are kept, the rest shrunk.
+
+Readings of the paper used here (the paper is silent or self-contradictory):
+- Orientation: the basis Q is put on the shorter side of A (Sec. 2.5 asks for
+  m < n "by transposing"; footnote 2 assumes m >= n).  Omega therefore has
+  max(m, n) rows, indexed by the long-side index.
+- Rank cut of QR-CP: keep |R_jj| > rank_tol * |R_00|, rank_tol = 1e-12.
+- Range propagation with a fixed l: keep Q~ = (QV)[:, :min(r, l - 2)] (the
+  a = 2 floor of Eq. 7) and draw l - |Q~| new Gaussian columns; with an empty
+  Q~ the plain sketch of l columns is used.
+- r = #{sigma_i > tau} with a strict inequality; singular values equal to tau
+  shrink to zero either way.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import linalg
+from .philox import gaussian_matrix
+
+
+def soft(x, tau):
+    """Soft shrinkage S_tau(x) = sgn(x) max(|x| - tau, 0) (Def. 1)."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.sign(x) * np.maximum(np.abs(x) - tau, 0.0)
+
+
+def exact_svt(A: np.ndarray, tau: float):
+    """Exact SVT of Def. 1 (Eq. 3).  Returns (X, r) with r = #{sigma_i > tau}."""
+    U, s, Vt = linalg.jacobi_svd(A)
+    f = soft(s, tau)
+    return (U * f) @ Vt, int(np.sum(s > tau))
+
+
+def ball_projection(A: np.ndarray, tau: float) -> np.ndarray:
+    """2-norm-ball Euclidean projection P_tau(A) = U min(Sigma, tau) V^T (Def. 3)."""
+    U, s, Vt = linalg.jacobi_svd(A)
+    return (U * np.minimum(s, tau)) @ Vt
+
+
+def wsvt(A: np.ndarray, w: np.ndarray):
+    """Weighted SVT: U diag(max(sigma_j - w_j, 0)) V^T for weights w (one per sigma_j).
+
+    A callable w is evaluated on the singular values of A (e.g. the WNNM
+    weights c * sqrt(n) / (sigma_j + eps)).
+    """
+    U, s, Vt = linalg.jacobi_svd(A)
+    wv = w(s) if callable(w) else np.asarray(w, dtype=np.float64)
+    f = np.maximum(s - wv, 0.0)
+    return (U * f) @ Vt
+
+
+def psvt(A: np.ndarray, tau: float, k: int):
+    """Partial SVT for the truncated nuclear norm sum_{i>k} sigma_i (Table 6, Type B)."""
+    U, s, Vt = linalg.jacobi_svd(A)
+    f = s.copy()
+    f[k:] = np.maximum(s[k:] - tau, 0.0)
+    return (U * f) @ Vt
+
+
+@dataclass
+class FRSVTResult:
+    """Output of one FRSVT call (Alg. 1 outputs plus diagnostics)."""
+
+    X: np.ndarray                 # S_tau(A) approximation, m x n
+    Q_tilde: np.ndarray           # propagated basis (QV)[:, :keep] on the short side
+    r: int                        # #{sigma_i > tau}
+    sigma: np.ndarray             # D of Alg. 1 (singular values of B), descending
+    s: int                        # number of basis columns actually used
+    polar_iters: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
+          Q_prev: np.ndarray | None = None, rank_tol: float = 1e-12,
+          problem: int = 0) -> FRSVTResult:
+    """Fast randomized SVT, Alg. 1, on A (m x n) in FP64.
+
+    Omega is the (seed, stream, problem) Philox Gaussian matrix with max(m, n)
+    rows; under range propagation (Q_prev given and non-empty) only its first
+    p = l - |Q_prev| columns are used.  Q_prev lives on the short side of A.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    transposed = m > n
+    Ah = A.T if transposed else A          # short x long ("m < n" of Sec. 2.5)
+    ns, nl = Ah.shape
+    if ns == 0 or nl == 0:
+        return FRSVTResult(np.zeros_like(A), np.zeros((ns, 0)), 0, np.zeros(0), 0)
+    l = min(l, ns)
+
+    # Alg. 1 steps 3-12: sketch, with or without range propagation.
+    if Q_prev is None or Q_prev.shape[1] == 0:
+        Omega = gaussian_matrix(nl, l, seed, stream, problem)       # step 4
+        Y = Ah @ Omega                                              # step 5
+        Q = linalg.qr_cp(Y, rank_tol)                               # step 6
+    else:
+        p = l - Q_prev.shape[1]
+        Omega = gaussian_matrix(nl, p, seed, stream, problem)       # step 8
+        Y = Ah @ Omega                                              # step 9
+        QY = linalg.mgs(Q_prev, Y, rank_tol)                        # step 10
+        Q = np.hstack([Q_prev, QY])                                 # step 11
+
+    # Steps 13-15: power iteration Q = QR(A A^T Q), eta = q times.  The rank is
+    # re-checked with a pivoted QR (Sec. 2.1, range propagation paragraph).
+    for _ in range(q):
+        Q = linalg.qr_cp(Ah @ (Ah.T @ Q), rank_tol)
+
+    s = Q.shape[1]
+    if s == 0:
+        return FRSVTResult(np.zeros_like(A), np.zeros((ns, 0)), 0, np.zeros(0), 0)
+
+    # Step 16: [H, C] = QR(A^T Q).
+    H, C = linalg.qr(Ah.T @ Q)
+    # Step 17: C = W P (Newton polar).  Step 18: P = V D V^T.
+    W, P, pit = linalg.newton_polar(C)
+    D, V = linalg.jacobi_eig(P)
+    # Step 19 / Eq. 6: S_tau(A) ~= (QV) S_tau(D) (HWV)^T.
+    QV = Q @ V
+    HWV = H @ (W @ V)
+    fD = soft(D, tau)
+    Xh = (QV * fD) @ HWV.T
+    r = int(np.sum(D > tau))
+    keep = min(r, l - 2)
+    Q_tilde = np.ascontiguousarray(QV[:, :max(keep, 0)])          # step 21
+    X = Xh.T if transposed else Xh
+    return FRSVTResult(np.ascontiguousarray(X), Q_tilde, r, D, s, pit)

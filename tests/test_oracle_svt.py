@@ -1,0 +1,260 @@
+"""Pins of the oracle's SVT operators (Def. 1 / Eq. 2-3, Def. 3, Prop. 1-2, Lemma 2, Theorem 3, Alg. 1)."""
+import numpy as np
+import pytest
+import scipy.optimize
+
+from oracle import linalg, svt
+from oracle.philox import gaussian_matrix
+
+
+def nnm_objective(X, A, tau):
+    """Eq. 2: tau ||X||_* + 1/2 ||X - A||_F^2 (nuclear norm from LAPACK singular values)."""
+    return tau * np.linalg.svd(X, compute_uv=False).sum() + 0.5 * np.sum((X - A) ** 2)
+
+
+def factored_minimizer(A, tau, weights=None, starts=6, seed=0):
+    """Minimize Eq. 2 without any SVD: ||X||_* = min_{X = U V^T} (||U||_F^2 + ||V||_F^2) / 2.
+
+    BFGS over the factors (U: m x n, V: n x n) of the smooth objective
+    tau/2 (||U||^2 + ||V||^2) + 1/2 ||U V^T - A||^2 from several random starts;
+    returns the best X = U V^T.
+    """
+    m, n = A.shape
+    rng = np.random.default_rng(seed)
+
+    def fg(z):
+        U, V = z[: m * n].reshape(m, n), z[m * n:].reshape(n, n)
+        R = U @ V.T - A
+        f = 0.5 * tau * (np.sum(U * U) + np.sum(V * V)) + 0.5 * np.sum(R * R)
+        gU = tau * U + R @ V
+        gV = tau * V + R.T @ U
+        return f, np.concatenate([gU.ravel(), gV.ravel()])
+
+    best = None
+    for _ in range(starts):
+        z0 = rng.standard_normal(m * n + n * n)
+        res = scipy.optimize.minimize(fg, z0, jac=True, method="BFGS", options={"gtol": 1e-12, "maxiter": 20000})
+        if best is None or res.fun < best.fun:
+            best = res
+    U, V = best.x[: m * n].reshape(m, n), best.x[m * n:].reshape(n, n)
+    return U @ V.T
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_exact_svt_brute_force_4x3(seed):
+    """Eq. 2 minimized by an SVD-free method agrees with the oracle's exact SVT on 4 x 3 inputs."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((4, 3)) * 2.0
+    tau = np.linalg.svd(A, compute_uv=False)[1] * 0.9      # some singular values survive, some do not
+    X, r = svt.exact_svt(A, tau)
+    Xb = factored_minimizer(A, tau, seed=seed)
+    assert nnm_objective(X, A, tau) <= nnm_objective(Xb, A, tau) + 1e-12
+    assert np.linalg.norm(X - Xb) < 1e-6 * np.linalg.norm(A)     # strong convexity: unique minimizer
+
+
+@pytest.mark.parametrize("shape", [(4, 3), (30, 20), (20, 45)])
+def test_exact_svt_strong_convexity_certificate(shape):
+    """f(X* + D) >= f(X*) + 1/2 ||D||^2 for the 1-strongly convex Eq. 2 at its minimizer."""
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal(shape)
+    tau = 0.5 * np.linalg.svd(A, compute_uv=False)[0]
+    X, _ = svt.exact_svt(A, tau)
+    f0 = nnm_objective(X, A, tau)
+    for k in range(50):
+        D = rng.standard_normal(shape) * 10.0 ** rng.uniform(-6, 0)
+        assert nnm_objective(X + D, A, tau) >= f0 + 0.5 * np.sum(D ** 2) - 1e-11 * max(1.0, f0)
+
+
+def test_exact_svt_diagonal_closed_form():
+    d = np.array([5.0, -3.0, 1.5, 0.2, -0.7])
+    A = np.zeros((7, 5))
+    A[np.arange(5), np.arange(5)] = d
+    X, r = svt.exact_svt(A, 1.0)
+    ref = np.zeros((7, 5))
+    ref[np.arange(5), np.arange(5)] = np.sign(d) * np.maximum(np.abs(d) - 1.0, 0.0)
+    assert np.allclose(X, ref, atol=1e-13)
+    assert r == 3
+
+
+def test_exact_svt_orthogonal_invariance():
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((25, 15))
+    U, _ = np.linalg.qr(rng.standard_normal((25, 25)))
+    V, _ = np.linalg.qr(rng.standard_normal((15, 15)))
+    tau = 2.0
+    X1, _ = svt.exact_svt(U @ A @ V.T, tau)
+    X0, _ = svt.exact_svt(A, tau)
+    assert np.linalg.norm(X1 - U @ X0 @ V.T) < 1e-12 * np.linalg.norm(X0)
+
+
+def test_exact_svt_prox_optimality_and_rank():
+    """A - X = P_tau(A) (Def. 3, Lemma 1), ||A - X||_2 = min(sigma_1, tau), U_r^T (A - X) V_r = tau I."""
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((40, 30))
+    s = np.linalg.svd(A, compute_uv=False)
+    tau = 0.5 * (s[5] + s[6])
+    X, r = svt.exact_svt(A, tau)
+    assert r == 6 == np.linalg.matrix_rank(X, tol=1e-9 * s[0])
+    G = A - X
+    assert np.linalg.norm(G - svt.ball_projection(A, tau)) < 1e-12 * np.linalg.norm(A)
+    assert abs(np.linalg.norm(G, 2) - min(s[0], tau)) < 1e-12 * s[0]
+    U, sx, Vt = np.linalg.svd(X)
+    Ur, Vr = U[:, :r], Vt[:r].T
+    assert np.allclose(Ur.T @ G @ Vr, tau * np.eye(r), atol=1e-11)
+    # split of A into S_tau(A) + P_tau(A)
+    assert np.linalg.norm(X + svt.ball_projection(A, tau) - A) < 1e-12 * np.linalg.norm(A)
+    # tau above sigma_1 gives zero
+    X0, r0 = svt.exact_svt(A, s[0] * 1.0001)
+    assert r0 == 0 and np.all(X0 == 0)
+
+
+def test_pseudo_contractions():
+    """Prop. 2 (Frobenius) and Prop. 3 with C = 2 (spectral) on random pairs."""
+    rng = np.random.default_rng(10)
+    for _ in range(10):
+        A = rng.standard_normal((12, 9))
+        B = A + rng.standard_normal((12, 9)) * rng.uniform(0.01, 1.0)
+        tau = rng.uniform(0.5, 3.0)
+        SA, _ = svt.exact_svt(A, tau)
+        SB, _ = svt.exact_svt(B, tau)
+        PA, PB = svt.ball_projection(A, tau), svt.ball_projection(B, tau)
+        lhs = np.sum((SA - SB) ** 2)
+        assert lhs <= np.sum((A - B) ** 2) - np.sum((PA - PB) ** 2) + 1e-10
+        assert np.linalg.norm(SA - SB, 2) <= 2 * np.linalg.norm(A - B, 2) - np.linalg.norm(PA - PB, 2) + 1e-10
+
+
+def test_lemma2_tail_sum():
+    """||P_tau(A) - P_tau(A_k)||_F^2 = sum_{j>k} min(sigma_j, tau)^2 for the best rank-k projection."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((30, 20))
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    k, tau = 5, 0.5 * s[3]
+    Ak = U[:, :k] @ (U[:, :k].T @ A)
+    lhs = np.sum((svt.ball_projection(A, tau) - svt.ball_projection(Ak, tau)) ** 2)
+    assert abs(lhs - np.sum(np.minimum(s[k:], tau) ** 2)) < 1e-10 * lhs
+
+
+# ---------------------------------------------------------------- FRSVT (Alg. 1)
+
+@pytest.mark.parametrize("shape,rank,l,q", [((200, 80), 5, 10, 0), ((200, 80), 5, 10, 2),
+                                            ((60, 150), 8, 8, 1), ((90, 90), 12, 20, 1)])
+def test_frsvt_exact_when_rank_le_l(shape, rank, l, q):
+    """FRSVT is exact when rank(A) <= l (remark after Cor. 2)."""
+    rng = np.random.default_rng(rank)
+    A = rng.standard_normal((shape[0], rank)) @ rng.standard_normal((rank, shape[1]))
+    s = np.linalg.svd(A, compute_uv=False)
+    tau = 0.5 * (s[rank // 2] + s[rank // 2 + 1])
+    Xe, re = svt.exact_svt(A, tau)
+    out = svt.frsvt(A, tau, l, q, seed=3, stream=0)
+    assert out.r == re
+    assert out.s == rank                        # the pivoted QR cut the basis to rank(A)
+    assert np.linalg.norm(out.X - Xe) <= 1e-10 * np.linalg.norm(Xe)
+
+
+def test_frsvt_range_propagation_exact_when_basis_captures_range():
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((150, 6)) @ rng.standard_normal((6, 70))     # tall: short side is 70
+    tau = 0.3 * np.linalg.svd(A, compute_uv=False)[3]
+    first = svt.frsvt(A, tau, 10, 1, seed=1, stream=0)
+    assert first.Q_tilde.shape == (70, min(first.r, 8))
+    B = A + 1e-3 * rng.standard_normal(A.shape) @ np.diag(np.ones(70))   # slightly perturbed next iterate
+    second = svt.frsvt(B, tau, 10, 1, seed=1, stream=1, Q_prev=first.Q_tilde)
+    Xe, _ = svt.exact_svt(B, tau)
+    assert np.linalg.norm(second.X - Xe) <= 1e-6 * np.linalg.norm(Xe)
+
+
+def test_frsvt_depends_only_on_span_of_Q(monkeypatch):
+    """Prop. 1: X = Q S_tau(Q^T A) is invariant to the orthonormalization used."""
+    rng = np.random.default_rng(13)
+    A = rng.standard_normal((120, 60))
+    tau = 0.5 * np.linalg.svd(A, compute_uv=False)[4]
+    X1 = svt.frsvt(A, tau, 12, 1, seed=5, stream=2).X
+    monkeypatch.setattr(linalg, "qr_cp", lambda Y, tol=1e-12: np.linalg.qr(Y)[0])
+    X2 = svt.frsvt(A, tau, 12, 1, seed=5, stream=2).X
+    assert np.linalg.norm(X1 - X2) <= 1e-11 * np.linalg.norm(X1)
+
+
+def test_frsvt_equals_projected_exact_svt():
+    """With Q from the same Omega, FRSVT(A) = Q S_tau(Q^T A) computed by the exact SVT (Prop. 1)."""
+    rng = np.random.default_rng(14)
+    A = rng.standard_normal((90, 40))            # tall: work on A^T (40 x 90), Omega has 90 rows
+    tau, l, q = 3.0, 10, 1
+    out = svt.frsvt(A, tau, l, q, seed=9, stream=4)
+    Ah = A.T
+    Om = gaussian_matrix(90, l, 9, 4)
+    Q = np.linalg.qr(Ah @ Om)[0]
+    Q = np.linalg.qr(Ah @ (Ah.T @ Q))[0]
+    Xs, _ = svt.exact_svt(Q.T @ Ah, tau)
+    assert np.linalg.norm(out.X - (Q @ Xs).T) <= 1e-11 * np.linalg.norm(out.X)
+
+
+def test_frsvt_theorem3_average_bound():
+    """E ||S_tau(A) - S_tau(A_k_hat)||_F^2 <= (1 + k/(p-1)) sum_{j>k} sigma_j^2 - G(A), q = 0 (Eq. 9)."""
+    rng = np.random.default_rng(15)
+    U, _ = np.linalg.qr(rng.standard_normal((80, 40)))
+    V, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    s = 1.0 / (1.0 + np.arange(40)) ** 1.2 * 10
+    A = (U * s) @ V.T                         # tall 80 x 40: short side 40
+    k, p, tau = 6, 4, 0.5 * s[3]
+    Xe, _ = svt.exact_svt(A, tau)
+    errs = [np.sum((svt.frsvt(A, tau, k + p, 0, seed=21, stream=t).X - Xe) ** 2) for t in range(200)]
+    tail = np.sum(s[k:] ** 2)
+    bound = (1 + k / (p - 1)) * tail - np.sum(np.minimum(s[k:], tau) ** 2)
+    assert np.mean(errs) <= bound
+
+
+def test_frsvt_polar_route_matches_jacobi_svd_of_core():
+    """Steps 16-19: the polar + eigen route gives the SVD of B (D = singular values of B)."""
+    rng = np.random.default_rng(16)
+    A = rng.standard_normal((70, 50))
+    out = svt.frsvt(A, 1.0, 15, 1, seed=2, stream=0)
+    Ah = A.T
+    Q = np.linalg.qr(Ah @ gaussian_matrix(70, 15, 2, 0))[0]
+    Q = np.linalg.qr(Ah @ (Ah.T @ Q))[0]
+    _, sB, _ = linalg.jacobi_svd(Q.T @ Ah)
+    assert np.max(np.abs(out.sigma - sB)) <= 1e-12 * sB[0]
+
+
+def test_frsvt_edge_cases():
+    A = np.zeros((10, 6))
+    out = svt.frsvt(A, 1.0, 4, 1, 0, 0)
+    assert np.all(out.X == 0) and out.r == 0
+    out = svt.frsvt(np.zeros((0, 5)), 1.0, 4, 1, 0, 0)
+    assert out.X.shape == (0, 5)
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((30, 8))
+    out = svt.frsvt(A, 0.0, 20, 1, 0, 0)        # l > short side: exact (s = 8), tau = 0 gives A back
+    assert np.linalg.norm(out.X - A) < 1e-12 * np.linalg.norm(A)
+
+
+# ---------------------------------------------------------------- weighted SVT
+
+def test_wsvt_reduces_to_svt_for_constant_weights():
+    rng = np.random.default_rng(18)
+    A = rng.standard_normal((20, 12))
+    assert np.allclose(svt.wsvt(A, np.full(12, 1.3)), svt.exact_svt(A, 1.3)[0], atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_wsvt_brute_force_nondescending_weights(seed):
+    """argmin sum_j w_j sigma_j(X) + 1/2 ||X - A||^2 for non-descending w is U max(Sigma - w, 0) V^T."""
+    rng = np.random.default_rng(40 + seed)
+    A = rng.standard_normal((4, 3)) * 2
+    w = np.sort(rng.uniform(0.3, 1.5, size=3))
+    X = svt.wsvt(A, w)
+    f = lambda x: (np.sort(np.linalg.svd(x.reshape(4, 3), compute_uv=False))[::-1] @ w
+                   + 0.5 * np.sum((x.reshape(4, 3) - A) ** 2))
+    best = min((scipy.optimize.minimize(f, st, method="Powell",
+                                        options={"xtol": 1e-10, "ftol": 1e-14, "maxfev": 200000})
+                for st in (A.ravel(), np.zeros(12), rng.standard_normal(12))), key=lambda r: r.fun)
+    assert f(X.ravel()) <= best.fun + 1e-9
+
+
+def test_psvt_keeps_leading_values():
+    rng = np.random.default_rng(19)
+    A = rng.standard_normal((15, 10))
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    X = svt.psvt(A, 0.8, 1)
+    sx = np.linalg.svd(X, compute_uv=False)
+    assert abs(sx[0] - s[0]) < 1e-12 * s[0]
+    assert np.allclose(np.sort(sx[1:])[::-1][: np.sum(s[1:] > 0.8)], (s[1:] - 0.8)[s[1:] > 0.8], atol=1e-12)
