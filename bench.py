@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark: inexact-ALM RPCA iterations per second with FRSVT on one GB300.
+
+Workload (one "step" = one full iALM iteration of the hot path): the
+video-background RPCA input, O = 76800 x 200 float32 (320 x 240 pixels x 200
+frames, rank-3 smooth background, ~8 % moving rectangles, noise 0.01),
+FRSVT with l = 10, q = 2 power iterations and range propagation, lambda =
+1/sqrt(76800), rho = 1.5.  Data is synthetic (seeded), see synth.video.
+
+Default arm (--impl frsvt): the C-ABI library; each step is one rpca_ialm_step
+replayed from a captured CUDA graph.  Timing: CUDA events around each step on
+the launching stream, the L2 cache flushed (a 256 MiB write) between steps
+outside the events.  `value` = steps / summed device time, max over ranks.
+Also reported: per-phase device times through the library's tracing hook (the
+roofline of the dominant kernel), the same iteration with exact SVT by
+cuSOLVER (torch.linalg.svd) on the same GPU, the end-to-end rate through the
+public API with host buffers, the FP64 oracle on the host cores, and SM clocks
+sampled by nvidia-smi during the timed region.
+
+--impl reference times the FP64 CPU oracle (numpy) on the same workload.
+Under torchrun each rank runs an independent replica (the path does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ALM iters/s & tensor-pipe % of FRSVT vs exact-SVD SVT, same GPU, ≤1e-4 rel err"
+UNIT = "ALM iters/s"
+M, N, L_COLS, Q_POW = 76800, 200, 10, 2
+DATA_SEED, OMEGA_SEED = 1002, 2002
+WORKLOAD = "video-background RPCA 76800x200 (320x240 px x 200 frames), FRSVT l=10 q=2 range propagation"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(O64, iters: int):
+    """FP64 oracle iALM-FRSVT iterations per second on a bounded sample (host cores)."""
+    import numpy as np
+    from oracle import rpca as orpca
+    normO2 = float(np.linalg.norm(O64, 2))
+    t0 = time.perf_counter()
+    orpca.ialm_rpca(O64, method="frsvt", l=L_COLS, q=Q_POW, seed=OMEGA_SEED, fixed_iters=iters, normO2=normO2)
+    dt = time.perf_counter() - t0
+    try:
+        import threadpoolctl
+        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or os.cpu_count()
+    except Exception:
+        cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    return iters / dt, cores, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from paper_1509_00296_gb300 import synth
+    O, _, _ = synth.video(seed=DATA_SEED)
+    O64 = O.astype(np.float64)
+    for _ in range(args.warmup):
+        pass                                   # the oracle has no warm-up state; samples are independent
+    rate, cores, dt = oracle_rate(O64, max(1, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / rate, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "l": L_COLS, "q": Q_POW},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} iALM-FRSVT iterations of the full 76800x200 workload "
+                                       f"({dt:.1f} s), FP64 numpy oracle"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="frsvt", choices=["frsvt", "reference"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--oracle-iters", type=int, default=12)
+    ap.add_argument("--skip-extras", action="store_true", help="only the main timed region")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1509_00296_gb300 import build, frsvt, synth
+    build.build()
+
+    O_np, _, _ = synth.video(seed=DATA_SEED)
+    lam = 1.0 / np.sqrt(max(M, N))
+    O = torch.from_numpy(O_np).to(dev)
+    S = torch.empty_like(O)
+    A = torch.empty_like(O)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    h = frsvt.Handle(M, N, L_COLS, q=Q_POW, range_prop=True, seed=OMEGA_SEED, stream=stream)
+    h.rpca_init(O, S, A, lam, 1.5, 1e7)
+
+    launches_per_step = 3 + 4 * Q_POW + 3 + 2
+    # one eager step first: it records the problem shape in the handle, so that the
+    # captured step contains no reset of the propagated basis
+    h.ialm_step(O, S, A, L_COLS)
+    graph = None
+    if not args.no_graph:
+        cap = torch.cuda.Stream()
+        h.set_stream(cap)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=cap):
+            h.ialm_step(O, S, A, L_COLS)
+        h.set_stream(stream)
+
+    def step():
+        if graph is not None:
+            graph.replay()
+        else:
+            h.ialm_step(O, S, A, L_COLS)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    if ws > 1:
+        torch.distributed.barrier()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    dev_ms_t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(dev_ms_t, op=torch.distributed.ReduceOp.MAX)
+    dev_ms = float(dev_ms_t.item())
+    ms_per_step = dev_ms / args.steps
+    value = ws * args.steps / (dev_ms / 1e3)
+    clocks = clk.summary()
+    info = h.info()
+
+    extras = {}
+    if not args.skip_extras and rank == 0:
+        extras = run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush)
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "l": L_COLS, "q": Q_POW, "range_prop": True,
+                       "graph": graph is not None, "l2": "flushed between steps (256 MiB write, outside the events)",
+                       "timing": "sum of per-step CUDA-event durations on the launching stream",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "wall_s_timed_region": t_wall,
+            "alm_state": {"iter": info.alm_iter, "residual": info.residual, "rank": info.r,
+                          "device_status": info.device_status},
+        }
+        if extras:
+            line["roofline"] = extras["roofline"]
+            line["roofline"]["peak_kind"] = peak_kind
+            line["phases_ms_per_step"] = extras["phases"]
+            line["e2e"] = extras["e2e"]
+            line["cpu_baseline"] = extras["cpu_baseline"]
+            line["exact_svd_same_gpu"] = extras["exact"]
+            line["tensor_pipe_pct"] = None
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
+    import numpy as np
+    import torch
+    from paper_1509_00296_gb300 import frsvt
+
+    out = {}
+    # ---- per-phase device times (tracing hook), same step, eager launches on the same stream
+    K = max(10, min(args.steps, 50))
+    h.enable_timing(True)
+    h.timings()
+    for k in range(K):
+        flush.fill_(float(k))
+        h.ialm_step(O, S, A, L_COLS)
+    tm = h.timings()
+    h.enable_timing(False)
+    phases = {k: v[0] / K for k, v in tm.items() if v[1] > 0}
+    e = 4.0 * M * N
+    alg_bytes = {"epilogue": 5 * e, "sketch": e, "power_AQ": e, "power_AtZ": e, "project": e}
+    launches = {k: v[1] for k, v in tm.items()}
+    dom = max(alg_bytes, key=lambda k: tm[k][0])
+    avg_ms = tm[dom][0] / max(1, launches[dom])
+    peak, _ = peaks()
+    achieved = alg_bytes[dom] / (avg_ms / 1e3) / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "algorithmic_bytes_per_launch": alg_bytes[dom], "avg_launch_ms": avg_ms}
+    out["phases"] = phases
+
+    # ---- exact-SVD iALM on the same GPU (cuSOLVER via torch.linalg.svd), a few iterations
+    Oe = O.clone()
+    Se = torch.zeros_like(Oe)
+    normO2 = torch.linalg.matrix_norm(Oe, 2).item()
+    Ye = Oe / max(normO2, Oe.abs().max().item() / lam)
+    mu = 1.25 / normO2
+    torch.cuda.synchronize()
+    ex_it = 3
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(ex_it):
+        U, s, Vh = torch.linalg.svd(Oe - Se + Ye / mu, full_matrices=False)
+        s = torch.clamp(s - 1.0 / mu, min=0.0)
+        Le = (U * s) @ Vh
+        T = Oe - Le + Ye / mu
+        Se = torch.sign(T) * torch.clamp(T.abs() - lam / mu, min=0.0)
+        Ye = Ye + mu * (Oe - Le - Se)
+        mu = min(1.5 * mu, 1e7 * 1.25 / normO2)
+    t1.record()
+    torch.cuda.synchronize()
+    ex_ms = t0.elapsed_time(t1) / ex_it
+    out["exact"] = {"value": 1e3 / ex_ms, "unit": UNIT, "ms_per_step": ex_ms,
+                    "method": "iALM with torch.linalg.svd (cuSOLVER) exact SVT, float32, same GPU",
+                    "frsvt_speedup": None}
+
+    # ---- end to end through the public API with host buffers
+    O_host = torch.from_numpy(O_np).pin_memory()
+    S_host = torch.empty_like(O_host).pin_memory()
+    L_host = torch.empty_like(O_host).pin_memory()
+    K2 = max(5, min(args.steps, 30))
+    Od = torch.empty_like(O)
+    Sd = torch.empty_like(O)
+    Ad = torch.empty_like(O)
+    Ld = torch.empty_like(O)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    Od.copy_(O_host, non_blocking=True)
+    h.rpca_init(Od, Sd, Ad, lam, 1.5, 1e7)
+    for k in range(K2):
+        h.ialm_step(Od, Sd, Ad, L_COLS, L=Ld if k == K2 - 1 else None, sync_residual=True)
+    S_host.copy_(Sd, non_blocking=True)
+    L_host.copy_(Ld, non_blocking=True)
+    torch.cuda.synchronize()
+    w = time.perf_counter() - w0
+    nbytes = 4 * M * N
+    out["e2e"] = {"value": K2 / w, "unit": UNIT, "h2d_bytes_per_step": nbytes / K2,
+                  "d2h_bytes_per_step": (8 * K2 + 2 * nbytes) / K2,
+                  "what": f"rpca_init + {K2} rpca_ialm_step calls from pinned host O, residual read back "
+                          f"every step, S and L copied back at the end"}
+
+    # ---- FP64 oracle on the host cores (bounded sample)
+    rate, cores, dt = oracle_rate(O_np.astype(np.float64), args.oracle_iters)
+    out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": f"{args.oracle_iters} iALM-FRSVT iterations of the full workload ({dt:.1f} s)"}
+    out["exact"]["frsvt_speedup"] = None
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

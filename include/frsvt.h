@@ -1,0 +1,198 @@
+/*
+ * frsvt.h -- C ABI of libfrsvt.so: fast randomized singular value thresholding
+ * (FRSVT) and robust PCA by the inexact augmented Lagrange multiplier method,
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: T.-H. Oh, Y. Matsushita, Y.-W. Tai, I. S. Kweon, "Fast Randomized
+ * Singular Value Thresholding for Low-rank Optimization", arXiv:1509.00296.
+ *   - SVT operator S_tau(A) = U S_tau(Sigma) V^T          (Def. 1, Eq. 3)
+ *   - reduction S_tau(QB) = Q S_tau(B), Q orthonormal      (Prop. 1, Eq. 4)
+ *   - FRSVT with range propagation and power iterations    (Alg. 1, Sec. 2.1-2.2, Eq. 6)
+ *   - RPCA host loop (inexact ALM)                         (Sec. 4.1, Robust PCA test)
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major float32 in DEVICE memory owned by the caller, with
+ *     a leading dimension (row stride, in elements) ld >= number of columns.
+ *     Base pointers must be 16-byte aligned and ld a multiple of 4, otherwise
+ *     the call returns FRSVT_ERR_INVALID_ARG (no silent copy is made).
+ *   - Work is enqueued asynchronously on the handle's CUDA stream; no call
+ *     synchronizes unless its description says so.  Errors found on the host
+ *     are returned at once; errors found by kernels are OR-ed into a sticky
+ *     device status word read (and cleared) by frsvt_get_info().
+ *   - The handle owns all scratch memory; it is allocated once by
+ *     frsvt_create() for the largest sizes given in frsvt_config.  No other
+ *     call allocates.
+ *   - Orientation: the orthonormal basis Q of Alg. 1 is kept on the shorter
+ *     side of A (Sec. 2.5 asks for the transposed problem when needed).  The
+ *     Gaussian test matrix Omega therefore has max(m, n) rows.  This release
+ *     supports m >= n (tall or square A); m < n returns FRSVT_ERR_UNSUPPORTED.
+ */
+#ifndef FRSVT_H_
+#define FRSVT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum frsvt_status {
+  FRSVT_OK = 0,
+  FRSVT_ERR_INVALID_ARG = 1,     /* bad pointer, size, alignment or parameter */
+  FRSVT_ERR_UNSUPPORTED = 2,     /* valid request this build does not serve */
+  FRSVT_ERR_ALLOC = 3,           /* device allocation failed in frsvt_create */
+  FRSVT_ERR_CUDA = 4,            /* a CUDA runtime call or kernel launch failed */
+  FRSVT_ERR_RANK_DEFICIENT = 5,  /* device bit, informational: basis size s < l */
+  FRSVT_ERR_NOT_CONVERGED = 6,   /* device bit: a Jacobi solve hit max sweeps */
+  FRSVT_ERR_NONFINITE = 7        /* device bit: NaN or Inf met in a reduction */
+} frsvt_status;
+
+/* Device status word bits (frsvt_info.device_status). */
+#define FRSVT_DEV_RANK_DEFICIENT (1u << 0)
+#define FRSVT_DEV_NOT_CONVERGED  (1u << 1)
+#define FRSVT_DEV_NONFINITE      (1u << 2)
+
+typedef enum frsvt_precision {
+  FRSVT_PREC_FP32 = 0            /* float32 data, FP32-accurate passes */
+} frsvt_precision;
+
+typedef struct frsvt_config {
+  int64_t m_max;                 /* largest row count served by the handle */
+  int64_t n_max;                 /* largest column count served by the handle */
+  int32_t l_max;                 /* largest oversampled rank l = k + p, 1..32 */
+  int32_t q;                     /* power iterations eta (Alg. 1 steps 13-15), >= 0 */
+  int32_t range_prop;            /* 1: range propagation between calls (Sec. 2.1) */
+  int32_t precision;             /* frsvt_precision */
+  uint64_t seed;                 /* Philox4x64-10 key of Omega */
+  int32_t max_jacobi_sweeps;     /* cap of the l x l Jacobi SVD (<= 0: 30) */
+  int32_t reserved;
+  double rank_tol;               /* relative pivot cut of the Cholesky QR (<= 0: 1e-12) */
+} frsvt_config;
+
+typedef struct frsvt_info {
+  int32_t r;                     /* #{sigma_i > tau} of the last SVT */
+  int32_t s;                     /* basis size used by the last SVT (<= l) */
+  int32_t keep;                  /* propagated basis columns for the next call */
+  uint32_t device_status;        /* sticky FRSVT_DEV_* bits, cleared by the read */
+  uint64_t counter;              /* Omega stream index the next SVT will use */
+  int32_t alm_iter;              /* iALM iterations done since rpca_init */
+  int32_t reserved;
+  double mu;                     /* iALM penalty mu for the next iteration */
+  double residual;               /* ||O - L - S||_F / ||O||_F of the last iALM step */
+} frsvt_info;
+
+typedef struct frsvt_handle frsvt_handle;
+
+/*
+ * Create a handle.  cfg sizes the workspace; stream is a cudaStream_t (NULL:
+ * the legacy default stream).  Allocates all device scratch memory.
+ * Returns FRSVT_ERR_INVALID_ARG for out-of-range sizes, FRSVT_ERR_ALLOC if
+ * the device allocation fails.
+ */
+frsvt_status frsvt_create(frsvt_handle** h, const frsvt_config* cfg, void* stream);
+
+/* Destroy a handle and free its workspace (synchronizes its stream). */
+frsvt_status frsvt_destroy(frsvt_handle* h);
+
+/* Change the stream later calls are enqueued on. */
+frsvt_status frsvt_set_stream(frsvt_handle* h, void* stream);
+
+/*
+ * Forget the propagated basis (Alg. 1 then takes its non-propagating branch)
+ * and set the Omega stream index of the next SVT.  Enqueued on the stream.
+ */
+frsvt_status frsvt_reset(frsvt_handle* h, uint64_t counter);
+
+/*
+ * X = FRSVT_tau(A) (Alg. 1): Gaussian sketch of l columns (or, with range
+ * propagation, the propagated basis plus l - keep new columns), q power
+ * iterations with re-orthonormalisation, projection B = Q^T A, SVD of B and
+ * soft shrinkage of its singular values (Eq. 6).  A is m x n (lda), X is
+ * m x n (ldx); X may not alias A.  l is clamped to min(m, n).  The Omega
+ * stream index advances by one per call.  1 <= l <= cfg.l_max.
+ */
+frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda,
+                       float tau, int32_t l, float* X, int64_t ldx);
+
+/*
+ * Largest singular value of A by block power iteration (the range finder of
+ * Sec. 2.1 with `iters` power steps and l = cfg.l_max columns).  Synchronizes
+ * and writes the value to *sigma1.  Does not touch the propagated basis or
+ * the Omega counter.
+ */
+frsvt_status frsvt_spectral_norm(frsvt_handle* h, const float* A, int64_t m, int64_t n,
+                                 int64_t lda, int32_t iters, double* sigma1);
+
+/*
+ * Robust PCA by inexact ALM (Sec. 4.1), state kept as (S, A) with
+ * A = O - S + Y/mu (the dual Y is mu (A - O + S)).
+ *
+ * rpca_init: S := 0, A := O + Y0/mu0 with Y0 = O / max(||O||_2, ||O||_inf/lambda),
+ * mu0 = 1.25/||O||_2 (||O||_2 by frsvt_spectral_norm with power_iters steps
+ * when normO2 <= 0, else the given value), mu_bar = mu_bar_factor * mu0.
+ * Resets the propagated basis and sets the Omega counter to 0.  Synchronizes.
+ */
+frsvt_status rpca_init(frsvt_handle* h, const float* O, float* S, float* A,
+                       int64_t m, int64_t n, int64_t ld, double lambda, double rho,
+                       double mu_bar_factor, double normO2, int32_t power_iters);
+
+/*
+ * One inexact-ALM iteration with an FRSVT of l columns:
+ *   L  = FRSVT_{1/mu}(A)
+ *   S' = shrink_{lambda/mu}(A + S - L)
+ *   A' = O - S' + (mu/mu') (A + S - L - S'),  mu' = min(rho mu, mu_bar)
+ * and ||O - L - S'||_F / ||O||_F is recorded on the device.  L (nullable,
+ * ldl) receives the low-rank iterate when given; otherwise L is never
+ * materialised.  O, S, A share the leading dimension ld.  When residual is not
+ * NULL the call synchronizes and writes ||O - L - S'||_F / ||O||_F there.
+ */
+frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
+                            int64_t m, int64_t n, int64_t ld, int32_t l,
+                            float* L, int64_t ldl, double* residual);
+
+/* Synchronize the handle's stream, then report (and clear) the device state. */
+frsvt_status frsvt_get_info(frsvt_handle* h, frsvt_info* info);
+
+/* Copy the singular values D of the last SVT (descending, s of them) to host memory. */
+frsvt_status frsvt_get_sigma(frsvt_handle* h, float* sigma_host, int32_t capacity, int32_t* count);
+
+/*
+ * Tracing.  Phases of the path, in launch order within one SVT / iALM step.
+ * When timing is enabled every kernel launch is bracketed by CUDA events on
+ * the handle's stream (recording events does not synchronize; it adds a few
+ * microseconds per launch).  frsvt_get_timings synchronizes, then returns per
+ * phase the summed device time in milliseconds and the number of launches
+ * since the previous call, and clears them.  ms and launches have
+ * FRSVT_NPHASE entries.  Disabling collects pending events first.
+ */
+#define FRSVT_NPHASE 10
+#define FRSVT_PHASE_SKETCH    0   /* Y = A^T Omega            (Alg. 1 steps 4-5, 8-9) */
+#define FRSVT_PHASE_POWER_AQ  1   /* Z = A Q in a power step  (step 14) */
+#define FRSVT_PHASE_POWER_ATZ 2   /* Y = A^T Z in a power step (step 14) */
+#define FRSVT_PHASE_REDUCE    3   /* split-K reduction of Y */
+#define FRSVT_PHASE_ORTH      4   /* orthonormalisation       (steps 6, 10-11, 14) */
+#define FRSVT_PHASE_PROJECT   5   /* Z = A Q = B^T            (step 16) */
+#define FRSVT_PHASE_GRAM      6   /* B B^T = Z^T Z in double-float */
+#define FRSVT_PHASE_CORE      7   /* l x l SVD and shrinkage  (steps 16-19) */
+#define FRSVT_PHASE_EPILOGUE  8   /* X = Z M Q^T, fused with the iALM update (Eq. 6) */
+#define FRSVT_PHASE_FINISH    9   /* residual reduction and mu update */
+frsvt_status frsvt_enable_timing(frsvt_handle* h, int32_t enable);
+frsvt_status frsvt_get_timings(frsvt_handle* h, double* ms, int32_t* launches);
+const char* frsvt_phase_name(int32_t phase);
+
+const char* frsvt_status_string(frsvt_status s);
+const char* frsvt_last_error(const frsvt_handle* h);
+
+/* Debug access to stages of the path, for parity tests of single kernels. */
+/* Omega[:rows, :cols] of (seed, stream, problem) into a device buffer (ld = cols). */
+frsvt_status frsvt_debug_omega(float* out, int64_t rows, int32_t cols, uint64_t seed,
+                               uint64_t stream, uint64_t problem, void* cuda_stream);
+/* Raw Philox4x64-10 words for counters (i, j, stream, problem), i < rows, j < blocks: rows x blocks x 4 uint64. */
+frsvt_status frsvt_debug_philox(uint64_t* out, int64_t rows, int32_t blocks, uint64_t seed,
+                                uint64_t stream, uint64_t problem, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRSVT_H_ */

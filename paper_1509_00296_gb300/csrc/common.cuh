@@ -1,0 +1,87 @@
+// Device-side helpers shared by the FRSVT kernels (sm_103a).
+//
+// - Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11)
+//   and the Box-Muller map that draw the Gaussian test matrix Omega of Alg. 1
+//   (steps 4 and 8; Sec. 2.4 uses dense N(0,1) entries).  The stream contract:
+//     key = (seed, 0); counter = (row i, column block j, stream t, problem b);
+//     u(x) = ((x >> 41) + 0.5) * 2^-23;
+//     (z0, z1) = sqrt(-2 ln u(x0)) (cos 2pi u(x1), sin 2pi u(x1)), same for (x2, x3);
+//     Omega[i, 4j + k] = z_k.
+// - Double-float ("df64") accumulation: the exact product of two floats as an
+//   unevaluated sum hi + lo (FMA-based two-product) added into a (hi, lo) pair
+//   with Knuth's two-sum.  GB300 runs FP64 at a small fraction of its FP32
+//   rate, so Gram matrices that must be accumulated beyond FP32 precision are
+//   accumulated this way on the FP32 pipes (about 44 significant bits).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace frsvt {
+
+constexpr uint64_t kPhiloxM0 = 0xD2E7470EE14C6C93ull;
+constexpr uint64_t kPhiloxM1 = 0xCA5A826395121157ull;
+constexpr uint64_t kPhiloxW0 = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kPhiloxW1 = 0xBB67AE8584CAA73Bull;
+
+struct u64x4 { uint64_t x, y, z, w; };
+
+__device__ __forceinline__ u64x4 philox4x64_10(u64x4 c, uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += kPhiloxW0; k1 += kPhiloxW1; }
+    const uint64_t lo0 = kPhiloxM0 * c.x, hi0 = __umul64hi(kPhiloxM0, c.x);
+    const uint64_t lo1 = kPhiloxM1 * c.z, hi1 = __umul64hi(kPhiloxM1, c.z);
+    c = u64x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+  }
+  return c;
+}
+
+__device__ __forceinline__ float uniform23(uint64_t x) {
+  return (static_cast<float>(static_cast<uint32_t>(x >> 41)) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
+}
+
+// Four N(0,1) values Omega[row, 4*blk .. 4*blk+3] of the (seed, stream, problem) stream.
+__device__ __forceinline__ float4 gaussian4(uint64_t seed, uint64_t row, uint64_t blk,
+                                            uint64_t stream, uint64_t problem) {
+  const u64x4 w = philox4x64_10(u64x4{row, blk, stream, problem}, seed, 0ull);
+  float s0, c0, s1, c1;
+  const float r0 = sqrtf(-2.0f * logf(uniform23(w.x)));
+  sincospif(2.0f * uniform23(w.y), &s0, &c0);
+  const float r1 = sqrtf(-2.0f * logf(uniform23(w.z)));
+  sincospif(2.0f * uniform23(w.w), &s1, &c1);
+  return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+}
+
+// ---------------------------------------------------------------- df64 accumulation
+struct df64 { float hi, lo; };
+
+__device__ __forceinline__ void df64_add_prod(df64& acc, float a, float b) {
+  const float p = a * b;
+  const float e = __fmaf_rn(a, b, -p);          // exact: a*b = p + e
+  const float s = __fadd_rn(acc.hi, p);         // two-sum(acc.hi, p)
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ double df64_value(df64 a) {
+  return static_cast<double>(a.hi) + static_cast<double>(a.lo);
+}
+
+// ---------------------------------------------------------------- small utilities
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace frsvt

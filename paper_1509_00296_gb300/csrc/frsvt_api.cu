@@ -1,0 +1,498 @@
+// Host side of the C ABI declared in include/frsvt.h: handle and workspace
+// management, argument validation, and the launch sequence of FRSVT (Alg. 1)
+// and of one inexact-ALM iteration.  No entry point allocates except
+// frsvt_create; no entry point synchronizes unless its contract says so.
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/frsvt.h"
+#include "state.cuh"
+
+namespace frsvt {
+size_t orth_smem_bytes(int LP, int64_t ns);
+}
+
+using namespace frsvt;
+
+struct frsvt_handle {
+  frsvt_config cfg{};
+  cudaStream_t stream = nullptr;
+  int LP = 16;
+  int sms = 1;
+  int target_ctas = 4;
+  int64_t part_elems = 0;
+  int rpart_max = 0;
+  int gsplit_max = 0;
+  int absmax_blocks = 0;
+  DevState* dst = nullptr;
+  float* Ys = nullptr;
+  float* Qs = nullptr;
+  float* Qt = nullptr;
+  float* Zl = nullptr;
+  float* Rf = nullptr;
+  float* part = nullptr;
+  float2* gpart = nullptr;
+  float2* rpart = nullptr;
+  float* pmax = nullptr;
+  float2* psum = nullptr;
+  int64_t last_m = -1, last_n = -1;
+  int last_l = -1;
+  std::string err;
+  // tracing: CUDA events around every launch when enabled
+  int timing = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_phase;      // phase of the pair (2k, 2k+1)
+  size_t ev_used = 0;             // events recorded since the last collection
+  double phase_ms[FRSVT_NPHASE] = {0};
+  int32_t phase_launches[FRSVT_NPHASE] = {0};
+};
+
+namespace {
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+frsvt_status fail(frsvt_handle* h, frsvt_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+#define FRSVT_CK(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) return fail(h, FRSVT_ERR_CUDA, std::string(#call ": ") + \
+                                       cudaGetErrorString(e_));                     \
+  } while (0)
+
+constexpr size_t kEventPairs = 2048;
+
+frsvt_status collect_timings(frsvt_handle* h) {
+  if (h->ev_used == 0) return FRSVT_OK;
+  FRSVT_CK(cudaStreamSynchronize(h->stream));
+  for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+    float ms = 0.f;
+    FRSVT_CK(cudaEventElapsedTime(&ms, h->ev_pool[k], h->ev_pool[k + 1]));
+    const int ph = h->ev_phase[k / 2];
+    h->phase_ms[ph] += ms;
+    h->phase_launches[ph] += 1;
+  }
+  h->ev_used = 0;
+  return FRSVT_OK;
+}
+
+// Launch `call` as phase `ph`, bracketed by events when tracing is on.
+#define FRSVT_LAUNCH(ph, call)                                                       \
+  do {                                                                               \
+    if (h->timing) {                                                                 \
+      if (h->ev_used + 2 > h->ev_pool.size()) {                                      \
+        frsvt_status cs_ = collect_timings(h);                                       \
+        if (cs_ != FRSVT_OK) return cs_;                                             \
+      }                                                                              \
+      h->ev_phase[h->ev_used / 2] = (ph);                                            \
+      FRSVT_CK(cudaEventRecord(h->ev_pool[h->ev_used], h->stream));                  \
+    }                                                                                \
+    FRSVT_CK(call);                                                                  \
+    if (h->timing) {                                                                 \
+      FRSVT_CK(cudaEventRecord(h->ev_pool[h->ev_used + 1], h->stream));              \
+      h->ev_used += 2;                                                               \
+    }                                                                                \
+  } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int64_t ns_limit(int LP) {
+  // short-side rows that fit the single-CTA orthonormalisation and the staged Q of the row pass
+  const int64_t by_orth = (static_cast<int64_t>(kSmemLimit) - static_cast<int64_t>(orth_smem_bytes(LP, 0))) /
+                          (LP * static_cast<int64_t>(sizeof(float)));
+  const int64_t by_rows = static_cast<int64_t>(kSmemLimit) / (LP * static_cast<int64_t>(sizeof(float)));
+  return by_orth < by_rows ? by_orth : by_rows;
+}
+
+struct Splits {
+  int nsplit;
+  int64_t rps;
+  int ntiles;
+};
+
+Splits row_splits(const frsvt_handle* h, int64_t m, int64_t n) {
+  Splits s;
+  s.ntiles = static_cast<int>(cdiv(n, 256));
+  int64_t ns = cdiv(h->target_ctas, s.ntiles);
+  const int64_t by_rows = cdiv(m, 32);
+  if (ns > by_rows) ns = by_rows;
+  if (ns < 1) ns = 1;
+  int64_t rps = cdiv(m, ns);
+  rps = cdiv(rps, 32) * 32;
+  s.rps = rps;
+  s.nsplit = static_cast<int>(cdiv(m, rps));
+  if (s.nsplit < 1) s.nsplit = 1;
+  return s;
+}
+
+int gram_splits(const frsvt_handle* h, int64_t m) {
+  int64_t g = cdiv(m, 32);
+  if (g > h->gsplit_max) g = h->gsplit_max;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+frsvt_status check_matrix(frsvt_handle* h, const void* p, int64_t m, int64_t n, int64_t ld, const char* name) {
+  if (m == 0 || n == 0) return FRSVT_OK;
+  if (p == nullptr) return fail(h, FRSVT_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (!aligned16(p)) return fail(h, FRSVT_ERR_INVALID_ARG, std::string(name) + " is not 16-byte aligned");
+  if (ld < n || (ld % 4) != 0)
+    return fail(h, FRSVT_ERR_INVALID_ARG, std::string(name) + ": leading dimension must be >= n and a multiple of 4");
+  return FRSVT_OK;
+}
+
+frsvt_status check_shape(frsvt_handle* h, int64_t m, int64_t n) {
+  if (m < 0 || n < 0) return fail(h, FRSVT_ERR_INVALID_ARG, "negative size");
+  if (m < n) return fail(h, FRSVT_ERR_UNSUPPORTED, "m < n: pass the transposed problem (this build orients tall)");
+  if (m > h->cfg.m_max || n > h->cfg.n_max)
+    return fail(h, FRSVT_ERR_INVALID_ARG, "problem larger than the handle's m_max / n_max");
+  return FRSVT_OK;
+}
+
+// Alg. 1 up to the core SVD: sketch (steps 3-12), q power steps (13-15),
+// projection and the l x l core (16-19).  Leaves Z in h->Zl and Rf in h->Rf
+// so that X = Z Rf^T.
+frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int l, int q,
+                            int use_rp, uint64_t ctr, float tau_host, int tau_from_mu, int update_rp,
+                            int advance_counter) {
+  const int LP = h->LP;
+  cudaStream_t st = h->stream;
+  const Splits sp = row_splits(h, m, n);
+  const double tol = h->cfg.rank_tol;
+  FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_short_cols(LP, A, m, n, lda, nullptr, h->cfg.seed, ctr, h->dst, h->part,
+                                                     sp.nsplit, sp.rps, st));
+  FRSVT_LAUNCH(FRSVT_PHASE_REDUCE, launch_reduce_parts(h->part, sp.nsplit, n * LP, h->Ys, st));
+  FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_orth(LP, h->Ys, n, l, use_rp, h->Qt, h->Qs, h->dst, tol, st));
+  for (int it = 0; it < q; ++it) {
+    FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_long_rows(LP, A, m, n, lda, h->Qs, h->Zl, 8 * h->sms, st));
+    FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_short_cols(LP, A, m, n, lda, h->Zl, h->cfg.seed, ctr, h->dst, h->part,
+                                                          sp.nsplit, sp.rps, st));
+    FRSVT_LAUNCH(FRSVT_PHASE_REDUCE, launch_reduce_parts(h->part, sp.nsplit, n * LP, h->Ys, st));
+    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_orth(LP, h->Ys, n, l, 0, h->Qt, h->Qs, h->dst, tol, st));
+  }
+  FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_long_rows(LP, A, m, n, lda, h->Qs, h->Zl, 8 * h->sms, st));
+  const int gs = gram_splits(h, m);
+  FRSVT_LAUNCH(FRSVT_PHASE_GRAM, launch_gram_long(LP, h->Zl, m, h->gpart, gs, st));
+  FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_core(LP, h->gpart, gs, h->Qs, n, l, tau_host, tau_from_mu, update_rp,
+                                             advance_counter, h->Rf, h->Qt, h->dst, tol, h->cfg.max_jacobi_sweeps, st));
+  return FRSVT_OK;
+}
+
+frsvt_status sync_rp_shape(frsvt_handle* h, int64_t m, int64_t n, int l) {
+  if (h->last_m != m || h->last_n != n || h->last_l != l) {
+    FRSVT_CK(cudaMemsetAsync(&h->dst->keep, 0, sizeof(int32_t), h->stream));
+    h->last_m = m;
+    h->last_n = n;
+    h->last_l = l;
+  }
+  return FRSVT_OK;
+}
+
+void free_all(frsvt_handle* h) {
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
+  void* ptrs[] = {h->dst, h->Ys, h->Qs, h->Qt, h->Zl, h->Rf, h->part, h->gpart, h->rpart, h->pmax, h->psum};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* frsvt_status_string(frsvt_status s) {
+  switch (s) {
+    case FRSVT_OK: return "ok";
+    case FRSVT_ERR_INVALID_ARG: return "invalid argument";
+    case FRSVT_ERR_UNSUPPORTED: return "unsupported";
+    case FRSVT_ERR_ALLOC: return "device allocation failed";
+    case FRSVT_ERR_CUDA: return "CUDA error";
+    case FRSVT_ERR_RANK_DEFICIENT: return "rank deficient basis (informational)";
+    case FRSVT_ERR_NOT_CONVERGED: return "Jacobi SVD did not converge";
+    case FRSVT_ERR_NONFINITE: return "non-finite value";
+  }
+  return "unknown status";
+}
+
+const char* frsvt_last_error(const frsvt_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* stream) {
+  frsvt_handle* h = nullptr;
+  if (out == nullptr || cfg == nullptr) return FRSVT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cfg->m_max < 1 || cfg->n_max < 1 || cfg->l_max < 1 || cfg->l_max > kMaxL || cfg->q < 0 || cfg->q > 64)
+    return FRSVT_ERR_INVALID_ARG;
+  if (cfg->precision != FRSVT_PREC_FP32) return FRSVT_ERR_UNSUPPORTED;
+  h = new (std::nothrow) frsvt_handle();
+  if (h == nullptr) return FRSVT_ERR_ALLOC;
+  h->cfg = *cfg;
+  if (h->cfg.max_jacobi_sweeps <= 0) h->cfg.max_jacobi_sweeps = 30;
+  if (!(h->cfg.rank_tol > 0.0)) h->cfg.rank_tol = 1e-12;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->LP = cfg->l_max <= 16 ? 16 : 32;
+  const int64_t nsmax = cfg->n_max < cfg->m_max ? cfg->n_max : cfg->m_max;
+  if (nsmax > ns_limit(h->LP)) {
+    delete h;
+    return FRSVT_ERR_UNSUPPORTED;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete h;
+    return FRSVT_ERR_CUDA;
+  }
+  if (prepare_pass_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
+      prepare_small_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
+    delete h;
+    return FRSVT_ERR_CUDA;
+  }
+  h->target_ctas = 4 * h->sms;
+  h->gsplit_max = h->sms;
+  h->absmax_blocks = 2 * h->sms;
+  const int64_t LP = h->LP;
+  const int64_t ntiles_max = cdiv(cfg->n_max, 256);
+  h->part_elems = (static_cast<int64_t>(h->target_ctas) * 256 + cfg->n_max) * LP;
+  h->rpart_max = static_cast<int>(h->target_ctas + ntiles_max + 1);
+  bool ok = true;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (ok && cudaMalloc(p, bytes < 16 ? 16 : bytes) != cudaSuccess) ok = false;
+  };
+  alloc(reinterpret_cast<void**>(&h->dst), sizeof(DevState));
+  alloc(reinterpret_cast<void**>(&h->Ys), sizeof(float) * cfg->n_max * LP);
+  alloc(reinterpret_cast<void**>(&h->Qs), sizeof(float) * cfg->n_max * LP);
+  alloc(reinterpret_cast<void**>(&h->Qt), sizeof(float) * cfg->n_max * LP);
+  alloc(reinterpret_cast<void**>(&h->Rf), sizeof(float) * cfg->n_max * LP);
+  alloc(reinterpret_cast<void**>(&h->Zl), sizeof(float) * cfg->m_max * LP);
+  alloc(reinterpret_cast<void**>(&h->part), sizeof(float) * h->part_elems);
+  alloc(reinterpret_cast<void**>(&h->gpart), sizeof(float2) * h->gsplit_max * LP * LP);
+  alloc(reinterpret_cast<void**>(&h->rpart), sizeof(float2) * h->rpart_max);
+  alloc(reinterpret_cast<void**>(&h->pmax), sizeof(float) * h->absmax_blocks);
+  alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
+  if (!ok) {
+    free_all(h);
+    delete h;
+    return FRSVT_ERR_ALLOC;
+  }
+  if (cudaMemsetAsync(h->dst, 0, sizeof(DevState), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->Qt, 0, sizeof(float) * cfg->n_max * LP, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return FRSVT_ERR_CUDA;
+  }
+  *out = h;
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_destroy(frsvt_handle* h) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_set_stream(frsvt_handle* h, void* stream) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_reset(frsvt_handle* h, uint64_t counter) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  FRSVT_CK(cudaMemsetAsync(&h->dst->keep, 0, sizeof(int32_t), h->stream));
+  FRSVT_CK(cudaMemcpyAsync(&h->dst->counter, &counter, sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+  FRSVT_CK(cudaStreamSynchronize(h->stream));   // the host value lives on this stack frame
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, float tau, int32_t l,
+                       float* X, int64_t ldx) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = check_shape(h, m, n);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, A, m, n, lda, "A")) != FRSVT_OK) return s;
+  if ((s = check_matrix(h, X, m, n, ldx, "X")) != FRSVT_OK) return s;
+  if (l < 1 || l > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "l must be in [1, l_max]");
+  if (!(tau >= 0.f) || !std::isfinite(tau)) return fail(h, FRSVT_ERR_INVALID_ARG, "tau must be finite and >= 0");
+  if (m == 0 || n == 0) return FRSVT_OK;
+  if (static_cast<const void*>(A) == static_cast<const void*>(X)) return fail(h, FRSVT_ERR_INVALID_ARG, "X aliases A");
+  if (l > n) l = static_cast<int32_t>(n);
+  if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
+  const int rp = h->cfg.range_prop ? 1 : 0;
+  if ((s = range_and_core(h, A, m, n, lda, l, h->cfg.q, rp, kCounterFromState, tau, 0, rp, 1)) != FRSVT_OK) return s;
+  const Splits sp = row_splits(h, m, n);
+  FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_recon(h->LP, h->Zl, h->Rf, m, n, X, ldx, sp.nsplit, sp.rps, h->stream));
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_spectral_norm(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int32_t iters,
+                                 double* sigma1) {
+  if (h == nullptr || sigma1 == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = check_shape(h, m, n);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, A, m, n, lda, "A")) != FRSVT_OK) return s;
+  if (iters < 0 || iters > 64) return fail(h, FRSVT_ERR_INVALID_ARG, "iters must be in [0, 64]");
+  *sigma1 = 0.0;
+  if (m == 0 || n == 0) return FRSVT_OK;
+  const int l = static_cast<int>(n < h->cfg.l_max ? n : h->cfg.l_max);
+  const uint64_t ctr = 0x5350454354524131ull;   // a fixed stream index reserved for this estimate
+  if ((s = range_and_core(h, A, m, n, lda, l, iters, 0, ctr, FLT_MAX, 0, 0, 0)) != FRSVT_OK) return s;
+  double v = 0.0;
+  FRSVT_CK(cudaMemcpyAsync(&v, &h->dst->sigma1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  FRSVT_CK(cudaStreamSynchronize(h->stream));
+  *sigma1 = v;
+  return FRSVT_OK;
+}
+
+frsvt_status rpca_init(frsvt_handle* h, const float* O, float* S, float* A, int64_t m, int64_t n, int64_t ld,
+                       double lambda, double rho, double mu_bar_factor, double normO2, int32_t power_iters) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = check_shape(h, m, n);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, O, m, n, ld, "O")) != FRSVT_OK) return s;
+  if ((s = check_matrix(h, S, m, n, ld, "S")) != FRSVT_OK) return s;
+  if ((s = check_matrix(h, A, m, n, ld, "A")) != FRSVT_OK) return s;
+  if (!(lambda > 0.0) || !(rho >= 1.0) || !(mu_bar_factor >= 1.0) || power_iters < 0 || power_iters > 64)
+    return fail(h, FRSVT_ERR_INVALID_ARG, "need lambda > 0, rho >= 1, mu_bar_factor >= 1, 0 <= power_iters <= 64");
+  if (m == 0 || n == 0) return FRSVT_OK;
+  if (!(normO2 > 0.0)) {
+    const int l = static_cast<int>(n < h->cfg.l_max ? n : h->cfg.l_max);
+    if ((s = range_and_core(h, O, m, n, ld, l, power_iters, 0, 0x5350454354524131ull, FLT_MAX, 0, 0, 0)) != FRSVT_OK)
+      return s;
+  }
+  FRSVT_CK(launch_absmax_sumsq(O, m, n, ld, h->pmax, h->psum, h->absmax_blocks, h->stream));
+  FRSVT_CK(launch_init_scalars(h->pmax, h->psum, h->absmax_blocks, normO2, lambda, rho, mu_bar_factor, h->dst,
+                               h->stream));
+  FRSVT_CK(launch_init_state(O, S, A, m, n, ld, h->dst, h->stream));
+  h->last_m = m;
+  h->last_n = n;
+  h->last_l = -1;
+  FRSVT_CK(cudaStreamSynchronize(h->stream));
+  return FRSVT_OK;
+}
+
+frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A, int64_t m, int64_t n, int64_t ld,
+                            int32_t l, float* L, int64_t ldl, double* residual) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = check_shape(h, m, n);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, O, m, n, ld, "O")) != FRSVT_OK) return s;
+  if ((s = check_matrix(h, S, m, n, ld, "S")) != FRSVT_OK) return s;
+  if ((s = check_matrix(h, A, m, n, ld, "A")) != FRSVT_OK) return s;
+  if (L != nullptr && (s = check_matrix(h, L, m, n, ldl, "L")) != FRSVT_OK) return s;
+  if (l < 1 || l > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "l must be in [1, l_max]");
+  if (m == 0 || n == 0) return FRSVT_OK;
+  if (l > n) l = static_cast<int32_t>(n);
+  if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
+  const int rp = h->cfg.range_prop ? 1 : 0;
+  if ((s = range_and_core(h, A, m, n, ld, l, h->cfg.q, rp, kCounterFromState, 0.f, 1, rp, 1)) != FRSVT_OK) return s;
+  const Splits sp = row_splits(h, m, n);
+  FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_alm(h->LP, h->Zl, h->Rf, O, S, A, m, n, ld, L, ldl, h->dst, h->rpart,
+                                                 sp.nsplit, sp.rps, h->stream));
+  FRSVT_LAUNCH(FRSVT_PHASE_FINISH, launch_alm_finish(h->rpart, sp.nsplit * sp.ntiles, h->dst, h->stream));
+  if (residual != nullptr) {
+    double v = 0.0;
+    FRSVT_CK(cudaMemcpyAsync(&v, &h->dst->resid_ratio, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    FRSVT_CK(cudaStreamSynchronize(h->stream));
+    *residual = v;
+  }
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_get_info(frsvt_handle* h, frsvt_info* info) {
+  if (h == nullptr || info == nullptr) return FRSVT_ERR_INVALID_ARG;
+  DevState d;
+  FRSVT_CK(cudaStreamSynchronize(h->stream));
+  FRSVT_CK(cudaMemcpy(&d, h->dst, sizeof(DevState), cudaMemcpyDeviceToHost));
+  FRSVT_CK(cudaMemsetAsync(&h->dst->status, 0, sizeof(uint32_t), h->stream));
+  FRSVT_CK(cudaStreamSynchronize(h->stream));
+  std::memset(info, 0, sizeof(*info));
+  info->r = d.r;
+  info->s = d.s;
+  info->keep = d.keep;
+  info->device_status = d.status;
+  info->counter = d.counter;
+  info->alm_iter = d.iter;
+  info->mu = d.mu;
+  info->residual = d.resid_ratio;
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_get_sigma(frsvt_handle* h, float* sigma_host, int32_t capacity, int32_t* count) {
+  if (h == nullptr || sigma_host == nullptr || count == nullptr || capacity < 0) return FRSVT_ERR_INVALID_ARG;
+  DevState d;
+  FRSVT_CK(cudaStreamSynchronize(h->stream));
+  FRSVT_CK(cudaMemcpy(&d, h->dst, sizeof(DevState), cudaMemcpyDeviceToHost));
+  int c = d.s < kMaxL ? d.s : kMaxL;
+  if (c > capacity) c = capacity;
+  for (int i = 0; i < c; ++i) sigma_host[i] = d.sigma[i];
+  *count = c;
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_enable_timing(frsvt_handle* h, int32_t enable) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (enable && h->ev_pool.empty()) {
+    h->ev_pool.resize(2 * kEventPairs);
+    h->ev_phase.resize(kEventPairs);
+    for (auto& e : h->ev_pool) FRSVT_CK(cudaEventCreate(&e));
+  }
+  if (!enable) {
+    frsvt_status s = collect_timings(h);
+    if (s != FRSVT_OK) return s;
+  }
+  h->timing = enable ? 1 : 0;
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_get_timings(frsvt_handle* h, double* ms, int32_t* launches) {
+  if (h == nullptr || ms == nullptr || launches == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = collect_timings(h);
+  if (s != FRSVT_OK) return s;
+  for (int p = 0; p < FRSVT_NPHASE; ++p) {
+    ms[p] = h->phase_ms[p];
+    launches[p] = h->phase_launches[p];
+    h->phase_ms[p] = 0.0;
+    h->phase_launches[p] = 0;
+  }
+  return FRSVT_OK;
+}
+
+const char* frsvt_phase_name(int32_t phase) {
+  static const char* names[FRSVT_NPHASE] = {"sketch", "power_AQ", "power_AtZ", "reduce", "orth",
+                                            "project", "gram", "core", "epilogue", "finish"};
+  return (phase >= 0 && phase < FRSVT_NPHASE) ? names[phase] : "unknown";
+}
+
+frsvt_status frsvt_debug_omega(float* out, int64_t rows, int32_t cols, uint64_t seed, uint64_t stream,
+                               uint64_t problem, void* cuda_stream) {
+  frsvt_handle* h = nullptr;
+  if (rows < 0 || cols < 0) return FRSVT_ERR_INVALID_ARG;
+  if (rows == 0 || cols == 0) return FRSVT_OK;
+  if (out == nullptr) return FRSVT_ERR_INVALID_ARG;
+  FRSVT_CK(launch_debug_omega(out, rows, cols, seed, stream, problem, static_cast<cudaStream_t>(cuda_stream)));
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_debug_philox(uint64_t* out, int64_t rows, int32_t blocks, uint64_t seed, uint64_t stream,
+                                uint64_t problem, void* cuda_stream) {
+  frsvt_handle* h = nullptr;
+  if (rows < 0 || blocks < 0) return FRSVT_ERR_INVALID_ARG;
+  if (rows == 0 || blocks == 0) return FRSVT_OK;
+  if (out == nullptr) return FRSVT_ERR_INVALID_ARG;
+  FRSVT_CK(launch_debug_philox(out, rows, blocks, seed, stream, problem, static_cast<cudaStream_t>(cuda_stream)));
+  return FRSVT_OK;
+}
+
+}  // extern "C"

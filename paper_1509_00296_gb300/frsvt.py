@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libfrsvt.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module only turns
+torch tensors into device pointers and the caller's CUDA stream into the
+handle's stream.  If the library has not been built the first call raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfrsvt.so")
+
+FRSVT_OK = 0
+STATUS_NAMES = {0: "FRSVT_OK", 1: "FRSVT_ERR_INVALID_ARG", 2: "FRSVT_ERR_UNSUPPORTED", 3: "FRSVT_ERR_ALLOC",
+                4: "FRSVT_ERR_CUDA", 5: "FRSVT_ERR_RANK_DEFICIENT", 6: "FRSVT_ERR_NOT_CONVERGED",
+                7: "FRSVT_ERR_NONFINITE"}
+DEV_RANK_DEFICIENT, DEV_NOT_CONVERGED, DEV_NONFINITE = 1, 2, 4
+NPHASE = 10
+
+
+class FrsvtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("m_max", ctypes.c_int64), ("n_max", ctypes.c_int64), ("l_max", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("range_prop", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("max_jacobi_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rank_tol", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int32), ("s", ctypes.c_int32), ("keep", ctypes.c_int32),
+                ("device_status", ctypes.c_uint32), ("counter", ctypes.c_uint64), ("alm_iter", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("mu", ctypes.c_double), ("residual", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = {
+    "frsvt_create": [ctypes.POINTER(_P), ctypes.POINTER(Config), _P],
+    "frsvt_destroy": [_P],
+    "frsvt_set_stream": [_P, _P],
+    "frsvt_reset": [_P, ctypes.c_uint64],
+    "frsvt_svt": [_P, _P, _I64, _I64, _I64, ctypes.c_float, ctypes.c_int32, _P, _I64],
+    "frsvt_spectral_norm": [_P, _P, _I64, _I64, _I64, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)],
+    "rpca_init": [_P, _P, _P, _P, _I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                  ctypes.c_double, ctypes.c_int32],
+    "rpca_ialm_step": [_P, _P, _P, _P, _I64, _I64, _I64, ctypes.c_int32, _P, _I64, ctypes.POINTER(ctypes.c_double)],
+    "frsvt_get_info": [_P, ctypes.POINTER(Info)],
+    "frsvt_get_sigma": [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+    "frsvt_status_string": [ctypes.c_int],
+    "frsvt_last_error": [_P],
+    "frsvt_enable_timing": [_P, ctypes.c_int32],
+    "frsvt_get_timings": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
+    "frsvt_phase_name": [ctypes.c_int32],
+    "frsvt_debug_omega": [_P, _I64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P],
+    "frsvt_debug_philox": [_P, _I64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P],
+}
+
+
+def lib():
+    """Load libfrsvt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1509_00296_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = (ctypes.c_char_p if name in ("frsvt_status_string", "frsvt_last_error", "frsvt_phase_name")
+                          else ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check_f32_cuda(t, name):
+    import torch
+    if t.dtype != torch.float32 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise TypeError(f"{name} must be a 2-D tensor with unit column stride")
+
+
+@dataclass
+class SVTInfo:
+    r: int
+    s: int
+    keep: int
+    device_status: int
+    counter: int
+    alm_iter: int
+    mu: float
+    residual: float
+
+
+class Handle:
+    """An FRSVT handle: workspace, propagated basis and Omega counter (include/frsvt.h)."""
+
+    def __init__(self, m_max: int, n_max: int, l_max: int, q: int = 2, range_prop: bool = True,
+                 seed: int = 0, max_jacobi_sweeps: int = 30, rank_tol: float = 1e-12, stream=None):
+        cfg = Config(m_max, n_max, l_max, q, 1 if range_prop else 0, 0, seed, max_jacobi_sweeps, 0, rank_tol)
+        h = _P()
+        self._stream = stream
+        st = lib().frsvt_create(ctypes.byref(h), ctypes.byref(cfg), _stream_ptr(stream))
+        if st != FRSVT_OK:
+            raise FrsvtError(st, "frsvt_create failed")
+        self._h = h
+        self.cfg = cfg
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().frsvt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        if st != FRSVT_OK:
+            raise FrsvtError(st, lib().frsvt_last_error(self._h).decode())
+
+    def set_stream(self, stream=None):
+        self._stream = stream
+        self._chk(lib().frsvt_set_stream(self._h, _stream_ptr(stream)))
+
+    def reset(self, counter: int = 0):
+        self._chk(lib().frsvt_reset(self._h, counter))
+
+    def svt(self, A, tau: float, l: int, X=None):
+        """X = FRSVT_tau(A) with l sketch columns (Alg. 1)."""
+        import torch
+        _check_f32_cuda(A, "A")
+        if X is None:
+            X = torch.empty_like(A)
+        _check_f32_cuda(X, "X")
+        m, n = A.shape
+        self._chk(lib().frsvt_svt(self._h, _ptr(A), m, n, A.stride(0), float(tau), int(l), _ptr(X), X.stride(0)))
+        return X
+
+    def spectral_norm(self, A, iters: int = 20) -> float:
+        _check_f32_cuda(A, "A")
+        out = ctypes.c_double()
+        m, n = A.shape
+        self._chk(lib().frsvt_spectral_norm(self._h, _ptr(A), m, n, A.stride(0), int(iters), ctypes.byref(out)))
+        return out.value
+
+    def rpca_init(self, O, S, A, lam: float, rho: float = 1.5, mu_bar_factor: float = 1e7,
+                  normO2: float = 0.0, power_iters: int = 30):
+        for t, nm in ((O, "O"), (S, "S"), (A, "A")):
+            _check_f32_cuda(t, nm)
+        m, n = O.shape
+        self._chk(lib().rpca_init(self._h, _ptr(O), _ptr(S), _ptr(A), m, n, O.stride(0), float(lam), float(rho),
+                                  float(mu_bar_factor), float(normO2), int(power_iters)))
+
+    def ialm_step(self, O, S, A, l: int, L=None, sync_residual: bool = False):
+        m, n = O.shape
+        res = ctypes.c_double()
+        self._chk(lib().rpca_ialm_step(self._h, _ptr(O), _ptr(S), _ptr(A), m, n, O.stride(0), int(l),
+                                       _ptr(L), L.stride(0) if L is not None else 0,
+                                       ctypes.byref(res) if sync_residual else None))
+        return res.value if sync_residual else None
+
+    def info(self) -> SVTInfo:
+        inf = Info()
+        self._chk(lib().frsvt_get_info(self._h, ctypes.byref(inf)))
+        return SVTInfo(inf.r, inf.s, inf.keep, inf.device_status, inf.counter, inf.alm_iter, inf.mu, inf.residual)
+
+    def enable_timing(self, on: bool = True):
+        self._chk(lib().frsvt_enable_timing(self._h, 1 if on else 0))
+
+    def timings(self):
+        """{phase name: (device ms, launches)} since the last call (synchronizes)."""
+        ms = (ctypes.c_double * NPHASE)()
+        cnt = (ctypes.c_int32 * NPHASE)()
+        self._chk(lib().frsvt_get_timings(self._h, ms, cnt))
+        return {lib().frsvt_phase_name(p).decode(): (ms[p], cnt[p]) for p in range(NPHASE)}
+
+    def sigma(self):
+        buf = (ctypes.c_float * 32)()
+        cnt = ctypes.c_int32()
+        self._chk(lib().frsvt_get_sigma(self._h, buf, 32, ctypes.byref(cnt)))
+        return [buf[i] for i in range(cnt.value)]
+
+
+def debug_omega(rows: int, cols: int, seed: int, stream: int, problem: int = 0):
+    """Omega[:rows, :cols] of the (seed, stream, problem) Philox stream, computed by the CUDA kernel."""
+    import torch
+    out = torch.empty((rows, cols), dtype=torch.float32, device="cuda")
+    st = lib().frsvt_debug_omega(_ptr(out), rows, cols, seed, stream, problem, _stream_ptr())
+    if st != FRSVT_OK:
+        raise FrsvtError(st, "frsvt_debug_omega")
+    return out
+
+
+def debug_philox(rows: int, blocks: int, seed: int, stream: int, problem: int = 0):
+    """Raw Philox4x64-10 words (rows x blocks x 4, as int64 bit patterns) from the CUDA kernel."""
+    import torch
+    out = torch.empty((rows, blocks, 4), dtype=torch.int64, device="cuda")
+    st = lib().frsvt_debug_philox(_ptr(out), rows, blocks, seed, stream, problem, _stream_ptr())
+    if st != FRSVT_OK:
+        raise FrsvtError(st, "frsvt_debug_philox")
+    return out
+
+
+def rpca(O, lam=None, l: int = 10, q: int = 2, iters: int = 30, rho: float = 1.5, mu_bar_factor: float = 1e7,
+         seed: int = 0, range_prop: bool = True, tol: float = 0.0, return_L: bool = True):
+    """Robust PCA of O (float32 CUDA tensor) by inexact ALM with FRSVT; returns (L, S, info).
+
+    Runs `iters` iterations, or stops early once ||O - L - S||_F / ||O||_F < tol
+    (checked on the host each iteration when tol > 0).
+    """
+    import torch
+    m, n = O.shape
+    lam = 1.0 / max(m, n) ** 0.5 if lam is None else lam
+    h = Handle(m, n, l, q=q, range_prop=range_prop, seed=seed)
+    S = torch.empty_like(O)
+    A = torch.empty_like(O)
+    L = torch.empty_like(O) if return_L else None
+    h.rpca_init(O, S, A, lam, rho, mu_bar_factor)
+    for k in range(iters):
+        last = k == iters - 1
+        res = h.ialm_step(O, S, A, l, L=L if (last or tol > 0) else None, sync_residual=tol > 0)
+        if tol > 0 and res < tol:
+            break
+    info = h.info()
+    h.close()
+    return L, S, info

@@ -1,0 +1,68 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "frsvt.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1509_00296_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("frsvt_create", "frsvt_destroy", "frsvt_svt", "rpca_init", "rpca_ialm_step",
+                     "frsvt_get_info", "frsvt_spectral_norm"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu(libpath):
+    from paper_1509_00296_gb300 import frsvt
+    L = frsvt.lib()
+    assert L.frsvt_status_string(0) == b"ok"
+    assert L.frsvt_status_string(2) == b"unsupported"
+    assert L.frsvt_last_error(None) == b"null handle"
+
+
+def test_invalid_arguments_rejected_on_host(libpath):
+    """Host-side validation answers before any device work (no GPU needed)."""
+    from paper_1509_00296_gb300 import frsvt
+    L = frsvt.lib()
+    h = ctypes.c_void_p()
+    bad = frsvt.Config(0, 10, 8, 1, 1, 0, 0, 30, 0, 1e-10)           # m_max = 0
+    assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
+    bad = frsvt.Config(10, 10, 33, 1, 1, 0, 0, 30, 0, 1e-10)         # l_max > 32
+    assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
+    bad = frsvt.Config(10, 10, 8, 1, 1, 7, 0, 30, 0, 1e-10)          # unknown precision
+    assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 2
+    assert L.frsvt_create(None, None, None) == 1
+    assert L.frsvt_svt(None, None, 1, 1, 4, ctypes.c_float(1.0), 1, None, 4) == 1
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The package never imports the oracle (the oracle is test infrastructure only)."""
+    pkg = os.path.join(ROOT, "paper_1509_00296_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
