@@ -22,7 +22,8 @@
 Readings of the paper used here (the paper is silent or self-contradictory):
 - Orientation: the basis Q is put on the shorter side of A (Sec. 2.5 asks for
   m < n "by transposing"; footnote 2 assumes m >= n).  Omega therefore has
-  max(m, n) rows, indexed by the long-side index.
+  max(m, n) rows, indexed by the long-side index.  A square A is treated like
+  a tall one (the problem is transposed, Q lives on the column side).
 - Rank cut of QR-CP: keep |R_jj| > rank_tol * |R_00|, rank_tol = 1e-12.
 - Range propagation with a fixed l: keep Q~ = (QV)[:, :min(r, l - 2)] (the
   a = 2 floor of Eq. 7) and draw l - |Q~| new Gaussian columns; with an empty
@@ -103,8 +104,8 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
-    transposed = m > n
-    Ah = A.T if transposed else A          # short x long ("m < n" of Sec. 2.5)
+    transposed = m >= n
+    Ah = A.T if transposed else A          # short x long ("m < n" of Sec. 2.5); ties transpose
     ns, nl = Ah.shape
     if ns == 0 or nl == 0:
         return FRSVTResult(np.zeros_like(A), np.zeros((ns, 0)), 0, np.zeros(0), 0)

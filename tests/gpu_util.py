@@ -20,10 +20,13 @@ def spectrum_matrix(m, n, rank, decay, noise, seed):
 
 
 def to_gpu(A, ld=None):
+    """float32 CUDA copy of A; the leading dimension is ld, or n rounded up to a multiple of 4."""
     import torch
     A32 = np.asarray(A, dtype=np.float32)
     m, n = A32.shape
-    if ld is None or ld == n:
+    if ld is None:
+        ld = (n + 3) // 4 * 4
+    if ld == n:
         return torch.from_numpy(np.ascontiguousarray(A32)).cuda()
     buf = torch.zeros((m, ld), dtype=torch.float32, device="cuda")
     buf[:, :n] = torch.from_numpy(np.ascontiguousarray(A32)).cuda()

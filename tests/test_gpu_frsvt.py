@@ -56,7 +56,8 @@ def test_frsvt_matches_oracle(fr, case):
     tau = float(0.5 * (s[k - 1] + s[k]))
     ref = svt.frsvt(A, tau, l, q, seed=11, stream=0)
     h = fr.Handle(m, n, l, q=q, range_prop=False, seed=11)
-    X = h.svt(to_gpu(A, ld), tau, l).cpu().numpy()
+    Ag = to_gpu(A, ld)
+    X = h.svt(Ag, tau, l, X=to_gpu(np.zeros((m, n)), ld)).cpu().numpy()
     info = h.info()
     assert info.r == ref.r
     assert info.device_status & fr.DEV_NONFINITE == 0
@@ -101,7 +102,7 @@ def test_frsvt_range_propagation_sequence(fr):
 def test_tau_above_sigma_max_gives_zero(fr):
     A, s = spectrum_matrix(400, 50, 10, 0.8, 0.0, seed=9)
     h = fr.Handle(400, 50, 8, q=1, range_prop=False)
-    X = h.svt(to_gpu(A), float(2 * s[0]), 8).cpu().numpy()
+    X = h.svt(to_gpu(A), float(2 * s[0]), 8, X=to_gpu(np.full((400, 50), 7.0))).cpu().numpy()
     assert np.all(X == 0.0)
     assert h.info().r == 0
 
