@@ -180,6 +180,37 @@ frsvt_status frsvt_enable_timing(frsvt_handle* h, int32_t enable);
 frsvt_status frsvt_get_timings(frsvt_handle* h, double* ms, int32_t* launches);
 const char* frsvt_phase_name(int32_t phase);
 
+/*
+ * Allocation-free FRSVT (the paper has no counterpart: this is a deployment
+ * entry point, not part of the method).
+ *
+ * Some callers cannot allocate device memory: code running inside a CUDA graph
+ * capture that forbids allocation, plug-ins whose host framework owns every
+ * device allocation, real-time paths that must not enter the allocator.
+ * frsvt_svt_noalloc computes the same X = FRSVT_tau(A) as frsvt_svt (no range
+ * propagation; Omega stream index `counter`, key `seed`) without a handle and
+ * without allocating: no cudaMalloc, no cudaFree, no allocating library call.
+ * Its scratch is one static device array of FRSVT_NOALLOC_SCRATCH_BYTES (8 MiB)
+ * that every GPU which loads this library keeps until the process exits.
+ *
+ * Limits (checked; larger sizes return FRSVT_ERR_INVALID_ARG):
+ *   m <= FRSVT_NOALLOC_MAX_M, n <= FRSVT_NOALLOC_MAX_N, m >= n (m < n:
+ *   FRSVT_ERR_UNSUPPORTED), 1 <= l <= 16, 0 <= q <= 64.  A and X are
+ *   caller-owned device buffers with the alignment rules above.
+ * The first call on a device performs a one-time set-up on that device (the
+ * device address of the scratch array, kernel attributes); make that first call
+ * before any stream capture.  Every call shares the one array and keeps the
+ * previous call's contents; the call clears what must start at zero.  Calls
+ * that overlap on the GPU (different streams or host threads) race: serialize
+ * them.  Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default).
+ */
+#define FRSVT_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define FRSVT_NOALLOC_MAX_M 65536
+#define FRSVT_NOALLOC_MAX_N 256
+frsvt_status frsvt_svt_noalloc(const float* A, int64_t m, int64_t n, int64_t lda, float tau,
+                               int32_t l, int32_t q, uint64_t seed, uint64_t counter,
+                               float* X, int64_t ldx, void* stream);
+
 const char* frsvt_status_string(frsvt_status s);
 const char* frsvt_last_error(const frsvt_handle* h);
 
