@@ -51,6 +51,7 @@ typedef enum frsvt_status {
 #define FRSVT_DEV_RANK_DEFICIENT (1u << 0)
 #define FRSVT_DEV_NOT_CONVERGED  (1u << 1)
 #define FRSVT_DEV_NONFINITE      (1u << 2)
+#define FRSVT_DEV_TIMEOUT        (1u << 3)   /* a bounded wait on an asynchronous copy gave up */
 
 typedef enum frsvt_precision {
   FRSVT_PREC_FP32 = 0            /* float32 data, FP32-accurate passes */
@@ -218,6 +219,11 @@ const char* frsvt_last_error(const frsvt_handle* h);
 /* Omega[:rows, :cols] of (seed, stream, problem) into a device buffer (ld = cols). */
 frsvt_status frsvt_debug_omega(float* out, int64_t rows, int32_t cols, uint64_t seed,
                                uint64_t stream, uint64_t problem, void* cuda_stream);
+/* Z = A Q on the tensor cores (tcgen05, 3xTF32): the row pass of Alg. 1 steps 14 / 16 alone.
+ * A: m x n (lda, n <= 256), Q: n x LP row-major (LP = 16 when cfg.l_max <= 16, else 32), Z: m x LP.
+ * Enqueued on the handle's stream; device errors go to the handle's status word. */
+frsvt_status frsvt_debug_rows_tc(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda,
+                                 const float* Q, float* Z);
 /* Raw Philox4x64-10 words for counters (i, j, stream, problem), i < rows, j < blocks: rows x blocks x 4 uint64. */
 frsvt_status frsvt_debug_philox(uint64_t* out, int64_t rows, int32_t blocks, uint64_t seed,
                                 uint64_t stream, uint64_t problem, void* cuda_stream);

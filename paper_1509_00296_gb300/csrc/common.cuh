@@ -69,6 +69,46 @@ __device__ __forceinline__ double df64_value(df64 a) {
   return static_cast<double>(a.hi) + static_cast<double>(a.lo);
 }
 
+// Double-float arithmetic (Dekker / Knuth error-free transformations) with round-to-nearest
+// intrinsics, which the compiler never contracts or reassociates.  ~48 significant bits.
+__device__ __forceinline__ df64 df_quick(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  return df64{s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+
+__device__ __forceinline__ df64 df_add(df64 a, df64 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return df_quick(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df64 df_neg(df64 a) { return df64{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df64 df_mul(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_quick(p, e);
+}
+
+__device__ __forceinline__ df64 df_from_double(double x) {
+  const float hi = static_cast<float>(x);
+  return df64{hi, static_cast<float>(x - static_cast<double>(hi))};
+}
+
+// 1 / sqrt(a) for a > 0 in the float range: float seed and one Newton step in double-float,
+// y1 = y0 + y0 (1 - a y0^2) / 2 (the error squares: ~2^-46 relative).
+__device__ __forceinline__ df64 df_rsqrt(df64 a) {
+  const df64 y{rsqrtf(a.hi), 0.f};
+  const df64 r = df_add(df64{1.f, 0.f}, df_neg(df_mul(a, df_mul(y, y))));
+  df64 c = df_mul(y, r);
+  c.hi = __fmul_rn(c.hi, 0.5f);
+  c.lo = __fmul_rn(c.lo, 0.5f);
+  return df_add(y, c);
+}
+
 // ---------------------------------------------------------------- small utilities
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 

@@ -10,11 +10,55 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/frsvt.h"
 #include "state.cuh"
 
 namespace frsvt {
 size_t orth_smem_bytes(int LP, int64_t ns);
+size_t fused_orth_smem(int LP, int64_t ns);
+size_t fused_core_smem(int LP, int64_t ns);
+cudaError_t prepare_fused_kernels(int smem_limit);
+cudaError_t launch_sc_orth(int LP, const float* A, int64_t m, int64_t n, int64_t lda, const float* Zl, uint64_t seed,
+                           uint64_t ctr, DevState* dst, int nsplit, int64_t rps, float* cpart, float* Y,
+                           unsigned* tickets, int l, int use_rp, const float* Qt, float* Q, double rank_tol,
+                           cudaStream_t st);
+cudaError_t launch_lr(int LP, bool gram, const float* A, int64_t m, int64_t n, int64_t lda, const float* Q, float* Z,
+                      int nblocks, double* cpart, double* G, unsigned* tickets, int l, float tau_host,
+                      int tau_from_mu, int update_rp, int advance_counter, float* Rf, float* Qt, DevState* dst,
+                      double rank_tol, int max_sweeps, cudaStream_t st);
+cudaError_t launch_alm2(int LP, const float* Z, const float* Rf, const float* O, float* S, float* A, int64_t m,
+                        int64_t n, int64_t ld, float* L, int64_t ldl, DevState* dst, int nsplit, int64_t rps,
+                        double* cpart, double* rsum, unsigned* tickets, cudaStream_t st);
+int tma_np4(int64_t n);
+size_t tma_sc_smem(int LP, int64_t n);
+size_t tma_lr_smem(int LP, int64_t n, int nst);
+int tma_lr_stages(int LP, int64_t n, size_t limit);
+int tma_rows_per_tile_lr();
+int tma_resident_grid(int LP, int64_t n);
+size_t tma_alm_smem(int LP, int64_t n);
+int tma_rows_per_tile();
+int tma_rows_per_tile_epilogue();
+cudaError_t prepare_tma_kernels(int smem_limit);
+cudaError_t launch_tp_sc(int LP, const CUtensorMap& tmA, const CUtensorMap* tmZ, int64_t m, int64_t n, int64_t rpc,
+                         int grid, uint64_t seed, uint64_t ctr, DevState* dst, float* cpart, float* Y, unsigned* tickets,
+                         int l, int use_rp, int passes, const float* Qt, float* Q, double rank_tol, cudaStream_t st);
+cudaError_t launch_tp_lr(int LP, bool gram, const CUtensorMap& tmA, int64_t m, int64_t n, int64_t rpc, int grid,
+                         int nst, const float* Q, float* Z, double* cpart, double* G, unsigned* tickets, int l, float tau_host,
+                         int tau_from_mu, int update_rp, int advance_counter, float* Rf, float* Qt, DevState* dst,
+                         double rank_tol, int max_sweeps, cudaStream_t st);
+cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS, const CUtensorMap& tmA,
+                          const CUtensorMap& tmZ, int64_t m, int64_t n, int64_t rpc, int grid, const float* Rf,
+                          float* S, float* A, int64_t ld, float* L, int64_t ldl, DevState* dst, double* cpart,
+                          double* rsum, unsigned* tickets, cudaStream_t st);
+size_t tc_lr_smem(int LP, int64_t n);
+cudaError_t prepare_tc_kernels(int smem_limit);
+cudaError_t launch_tc_lr(int LP, const CUtensorMap& tmA, int64_t m, int64_t n, int grid, const float* Q, float* Z,
+                         DevState* dst, cudaStream_t st);
+int tc_box_cols();
+int tc_box_rows();
 }
 
 using namespace frsvt;
@@ -40,6 +84,18 @@ struct frsvt_handle {
   float2* rpart = nullptr;
   float* pmax = nullptr;
   float2* psum = nullptr;
+  // fused path (short side small enough for one CTA): cluster partials, final sums, tickets
+  bool fused = false;
+  bool tma = false;          // persistent TMA-pipelined passes (short side <= 256 columns)
+  int tma_grid = 8;
+  float* cpart_sc = nullptr;
+  double* cpart_lr = nullptr;
+  double* cpart_alm = nullptr;
+  double* Gfin = nullptr;
+  double* rsum = nullptr;
+  unsigned* tickets = nullptr;
+  int64_t cpart_sc_elems = 0, cpart_alm_elems = 0;
+  int lr_blocks = 8;
   int64_t last_m = -1, last_n = -1;
   int last_l = -1;
   std::string err;
@@ -106,6 +162,49 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D float32 tensor map of a row-major rows x cols matrix (leading dimension ld) with
+// box_rows x box_cols boxes, no swizzle, zero fill outside the matrix.
+bool make_row_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                  int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Same with 32-column (128-byte) boxes in the 128-byte swizzle read by tcgen05 as a K-major operand.
+bool make_row_map_sw128(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
+  cuuint32_t box[2] = {32u, static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int g_tc_prepared = 0;
+
 int64_t ns_limit(int LP) {
   // short-side rows that fit the single-CTA orthonormalisation and the staged Q of the row pass
   const int64_t by_orth = (static_cast<int64_t>(kSmemLimit) - static_cast<int64_t>(orth_smem_bytes(LP, 0))) /
@@ -142,6 +241,19 @@ int gram_splits(const frsvt_handle* h, int64_t m) {
   return static_cast<int>(g);
 }
 
+// Row splits of the fused passes: a multiple of the cluster size (8).
+Splits fused_splits(const frsvt_handle* h, int64_t m, int64_t n) {
+  Splits s;
+  s.ntiles = static_cast<int>(cdiv(n, 256));
+  int64_t ns = cdiv(cdiv(h->target_ctas, s.ntiles), 8) * 8;
+  const int64_t by_rows = cdiv(cdiv(m, 32), 8) * 8;
+  if (ns > by_rows) ns = by_rows;
+  if (ns < 8) ns = 8;
+  s.rps = cdiv(cdiv(m, ns), 32) * 32;
+  s.nsplit = static_cast<int>(ns);
+  return s;
+}
+
 frsvt_status check_matrix(frsvt_handle* h, const void* p, int64_t m, int64_t n, int64_t ld, const char* name) {
   if (m == 0 || n == 0) return FRSVT_OK;
   if (p == nullptr) return fail(h, FRSVT_ERR_INVALID_ARG, std::string(name) + " is NULL");
@@ -167,8 +279,55 @@ frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t 
                             int advance_counter) {
   const int LP = h->LP;
   cudaStream_t st = h->stream;
-  const Splits sp = row_splits(h, m, n);
   const double tol = h->cfg.rank_tol;
+  if (h->tma && n <= 256 && m < (int64_t(1) << 31)) {
+    CUtensorMap tmA, tmAl, tmZ;
+    if (!make_row_map(&tmA, A, m, n, lda, tma_np4(n), tma_rows_per_tile()) ||
+        !make_row_map(&tmAl, A, m, n, lda, tma_np4(n), tma_rows_per_tile_lr()) ||
+        !make_row_map(&tmZ, h->Zl, m, LP, LP, LP, tma_rows_per_tile()))
+      return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A / Z");
+    const int G = h->tma_grid;
+    const int64_t rpc = cdiv(cdiv(m, G), tma_rows_per_tile()) * tma_rows_per_tile();
+    const int64_t rpl = cdiv(cdiv(m, G), tma_rows_per_tile_lr()) * tma_rows_per_tile_lr();
+    const int nst = tma_lr_stages(LP, n, kSmemLimit - 16384);
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_tp_sc(LP, tmA, nullptr, m, n, rpc, G, h->cfg.seed, ctr, h->dst,
+                                                  h->cpart_sc, h->Ys, h->tickets, l, use_rp, q == 0 ? 2 : 1, h->Qt,
+                                                  h->Qs, tol, st));
+    CUtensorMap tmAs;                       // 128-byte swizzled boxes for the tensor-core row pass
+    if (!make_row_map_sw128(&tmAs, A, m, n, lda, tc_box_rows()))
+      return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A (swizzled)");
+    for (int it = 0; it < q; ++it) {
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_tc_lr(LP, tmAs, m, n, h->sms, h->Qs, h->Zl, h->dst, st));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_tp_sc(LP, tmA, &tmZ, m, n, rpc, G, h->cfg.seed, ctr, h->dst,
+                                                       h->cpart_sc, h->Ys, h->tickets, l, 0, it == q - 1 ? 2 : 1,
+                                                       h->Qt, h->Qs, tol, st));
+    }
+    FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_tp_lr(LP, true, tmAl, m, n, rpl, G, nst, h->Qs, h->Zl, h->cpart_lr,
+                                                   h->Gfin, h->tickets, l, tau_host, tau_from_mu, update_rp,
+                                                   advance_counter, h->Rf, h->Qt, h->dst, tol,
+                                                   h->cfg.max_jacobi_sweeps, st));
+    return FRSVT_OK;
+  }
+  if (h->fused) {
+    const Splits fs = fused_splits(h, m, n);
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_sc_orth(LP, A, m, n, lda, nullptr, h->cfg.seed, ctr, h->dst, fs.nsplit,
+                                                    fs.rps, h->cpart_sc, h->Ys, h->tickets, l, use_rp, h->Qt, h->Qs,
+                                                    tol, st));
+    for (int it = 0; it < q; ++it) {
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_lr(LP, false, A, m, n, lda, h->Qs, h->Zl, h->lr_blocks, h->cpart_lr,
+                                                   h->Gfin, h->tickets, l, 0.f, 0, 0, 0, h->Rf, h->Qt, h->dst, tol,
+                                                   h->cfg.max_jacobi_sweeps, st));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_sc_orth(LP, A, m, n, lda, h->Zl, h->cfg.seed, ctr, h->dst,
+                                                         fs.nsplit, fs.rps, h->cpart_sc, h->Ys, h->tickets, l, 0,
+                                                         h->Qt, h->Qs, tol, st));
+    }
+    FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_lr(LP, true, A, m, n, lda, h->Qs, h->Zl, h->lr_blocks, h->cpart_lr,
+                                                h->Gfin, h->tickets, l, tau_host, tau_from_mu, update_rp,
+                                                advance_counter, h->Rf, h->Qt, h->dst, tol,
+                                                h->cfg.max_jacobi_sweeps, st));
+    return FRSVT_OK;
+  }
+  const Splits sp = row_splits(h, m, n);
   FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_short_cols(LP, A, m, n, lda, nullptr, h->cfg.seed, ctr, h->dst, h->part,
                                                      sp.nsplit, sp.rps, st));
   FRSVT_LAUNCH(FRSVT_PHASE_REDUCE, launch_reduce_parts(h->part, sp.nsplit, n * LP, h->Ys, st));
@@ -201,7 +360,9 @@ frsvt_status sync_rp_shape(frsvt_handle* h, int64_t m, int64_t n, int l) {
 void free_all(frsvt_handle* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   h->ev_pool.clear();
-  void* ptrs[] = {h->dst, h->Ys, h->Qs, h->Qt, h->Zl, h->Rf, h->part, h->gpart, h->rpart, h->pmax, h->psum};
+  void* ptrs[] = {h->dst, h->Ys,       h->Qs,       h->Qt,        h->Zl,   h->Rf,   h->part,    h->gpart,
+                  h->rpart, h->pmax,   h->psum,     h->cpart_sc,  h->cpart_lr, h->cpart_alm, h->Gfin, h->rsum,
+                  h->tickets};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -252,7 +413,10 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
     return FRSVT_ERR_CUDA;
   }
   if (prepare_pass_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
-      prepare_small_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
+      prepare_small_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
+      prepare_fused_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
+      prepare_tma_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
+      prepare_tc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
     delete h;
     return FRSVT_ERR_CUDA;
   }
@@ -277,6 +441,32 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   alloc(reinterpret_cast<void**>(&h->gpart), sizeof(float2) * h->gsplit_max * LP * LP);
   alloc(reinterpret_cast<void**>(&h->rpart), sizeof(float2) * h->rpart_max);
   alloc(reinterpret_cast<void**>(&h->pmax), sizeof(float) * h->absmax_blocks);
+  // fused path: short side whose small dense work fits comfortably in one CTA
+  h->fused = fused_orth_smem(h->LP, cfg->n_max) <= 96 * 1024 && fused_core_smem(h->LP, cfg->n_max) <= 96 * 1024;
+  h->lr_blocks = 8 * h->sms;
+  {
+    const int64_t nt = cfg->n_max < 256 ? cfg->n_max : 256;
+    const int nst = tma_lr_stages(h->LP, nt, kSmemLimit - 16384);
+    h->tma = tensor_map_encoder() != nullptr && nst >= 2 &&
+             tma_sc_smem(h->LP, nt) <= kSmemLimit - 8192 &&
+             tma_lr_smem(h->LP, nt, nst) <= kSmemLimit - 8192 && tma_alm_smem(h->LP, nt) <= kSmemLimit - 8192;
+    // clusters of 8 that can be resident at once (GPCs hold a whole number of clusters)
+    h->tma_grid = h->tma ? tma_resident_grid(h->LP, nt) : 0;
+    if (h->tma_grid < 8) h->tma = false;
+  }
+  {
+    const int64_t ntl = ntiles_max;
+    const int64_t ncl_sc = cdiv(cdiv(h->target_ctas, 1), 8) + 1;          // clusters per tile, upper bound
+    h->cpart_sc_elems = ntl * ncl_sc * 256 * LP;
+    h->cpart_alm_elems = ntl * ncl_sc;
+    const int64_t np = LP * (LP + 1) / 2;
+    alloc(reinterpret_cast<void**>(&h->cpart_sc), sizeof(float) * h->cpart_sc_elems);
+    alloc(reinterpret_cast<void**>(&h->cpart_lr), sizeof(double) * (h->lr_blocks / 8) * np);
+    alloc(reinterpret_cast<void**>(&h->cpart_alm), sizeof(double) * h->cpart_alm_elems);
+    alloc(reinterpret_cast<void**>(&h->Gfin), sizeof(double) * np);
+    alloc(reinterpret_cast<void**>(&h->rsum), sizeof(double) * ntl);
+    alloc(reinterpret_cast<void**>(&h->tickets), sizeof(unsigned) * (ntl + 1));
+  }
   alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
   if (!ok) {
     free_all(h);
@@ -285,6 +475,7 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   }
   if (cudaMemsetAsync(h->dst, 0, sizeof(DevState), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->Qt, 0, sizeof(float) * cfg->n_max * LP, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * (ntiles_max + 1), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     free_all(h);
     delete h;
@@ -397,10 +588,26 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
   const int rp = h->cfg.range_prop ? 1 : 0;
   if ((s = range_and_core(h, A, m, n, ld, l, h->cfg.q, rp, kCounterFromState, 0.f, 1, rp, 1)) != FRSVT_OK) return s;
+  if (h->tma && n <= 256 && m < (int64_t(1) << 31)) {
+    CUtensorMap tO, tS, tA, tZ;
+    const int re = tma_rows_per_tile_epilogue();
+    if (!make_row_map(&tO, O, m, n, ld, tma_np4(n), re) || !make_row_map(&tS, S, m, n, ld, tma_np4(n), re) ||
+        !make_row_map(&tA, A, m, n, ld, tma_np4(n), re) || !make_row_map(&tZ, h->Zl, m, h->LP, h->LP, h->LP, re))
+      return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for O/S/A/Z");
+    const int G = h->tma_grid;
+    const int64_t rpc = cdiv(cdiv(m, G), re) * re;
+    FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_tp_alm(h->LP, tO, tS, tA, tZ, m, n, rpc, G, h->Rf, S, A, ld, L, ldl,
+                                                     h->dst, h->cpart_alm, h->rsum, h->tickets, h->stream));
+  } else if (h->fused) {
+    const Splits fs = fused_splits(h, m, n);
+    FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_alm2(h->LP, h->Zl, h->Rf, O, S, A, m, n, ld, L, ldl, h->dst, fs.nsplit,
+                                                   fs.rps, h->cpart_alm, h->rsum, h->tickets, h->stream));
+  } else {
   const Splits sp = row_splits(h, m, n);
   FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_alm(h->LP, h->Zl, h->Rf, O, S, A, m, n, ld, L, ldl, h->dst, h->rpart,
                                                  sp.nsplit, sp.rps, h->stream));
   FRSVT_LAUNCH(FRSVT_PHASE_FINISH, launch_alm_finish(h->rpart, sp.nsplit * sp.ntiles, h->dst, h->stream));
+  }
   if (residual != nullptr) {
     double v = 0.0;
     FRSVT_CK(cudaMemcpyAsync(&v, &h->dst->resid_ratio, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -492,6 +699,26 @@ frsvt_status frsvt_debug_philox(uint64_t* out, int64_t rows, int32_t blocks, uin
   if (rows == 0 || blocks == 0) return FRSVT_OK;
   if (out == nullptr) return FRSVT_ERR_INVALID_ARG;
   FRSVT_CK(launch_debug_philox(out, rows, blocks, seed, stream, problem, static_cast<cudaStream_t>(cuda_stream)));
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_debug_rows_tc(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, const float* Q,
+                                 float* Z) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = check_shape(h, m, n);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, A, m, n, lda, "A")) != FRSVT_OK) return s;
+  if (Q == nullptr || Z == nullptr) return fail(h, FRSVT_ERR_INVALID_ARG, "Q and Z are required");
+  if (n > 256) return fail(h, FRSVT_ERR_UNSUPPORTED, "the tensor-core row pass serves n <= 256");
+  if (m == 0 || n == 0) return FRSVT_OK;
+  if (!g_tc_prepared) {
+    FRSVT_CK(prepare_tc_kernels(static_cast<int>(kSmemLimit)));
+    g_tc_prepared = 1;
+  }
+  CUtensorMap tm;
+  if (!make_row_map_sw128(&tm, A, m, n, lda, tc_box_rows()))
+    return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A");
+  FRSVT_CK(launch_tc_lr(h->LP, tm, m, n, h->sms, Q, Z, h->dst, h->stream));
   return FRSVT_OK;
 }
 

@@ -1,0 +1,383 @@
+// Block-level small dense linear algebra for Alg. 1 (device functions).
+//
+// These routines run inside one CTA (any blockDim that is a multiple of 32 and
+// at least 64) and are used both by stand-alone single-CTA kernels and as the
+// "tail" of a streaming pass, executed by the CTA that finishes its split-K
+// reduction last.
+//
+// orth_block : orthonormal basis of the sketch, Alg. 1 steps 6, 10-11, 14.
+//              Cholesky QR applied twice (CholeskyQR2): Gram matrix in
+//              double-float, FP64 Cholesky with a pivot drop (s = min(l, rank)),
+//              FP32 triangular solves.  Under range propagation the new block is
+//              projected out of the propagated basis twice first (the partial
+//              orthogonalization of step 10).  Only span(Q) matters (Prop. 1).
+// core_block : singular values / vectors of B = Q^T A from B B^T = Z^T Z
+//              (Z = A Q): FP64 Cholesky R^T R = Z^T Z, FP32 one-sided Jacobi SVD
+//              of R^T (the D and V of Alg. 1 steps 16-18), soft shrinkage,
+//              M = U diag(S_tau(D) / D) U^T (Eq. 6: X = Z M Q^T), Rf = Q M and
+//              the propagated basis Q~ = Q U[:, :keep] (step 21).
+#pragma once
+#include "common.cuh"
+#include "state.cuh"
+
+namespace frsvt {
+
+// Shared-memory workspace of orth_block / core_block, carved from one buffer.
+template <int LP>
+struct SmallWs {
+  double* G;        // LP x LP
+  double* R;        // LP x LP
+  double* gdiag;    // LP (original diagonal)
+  double* gacc;     // gacc_n partial sums
+  float* Rf32;      // LP x LP  (FP32 copy of R / Jacobi columns)
+  float* rinv;      // LP       (FP32 1 / R_jj, 0 for dropped)
+  float* Cm;        // LP x LP  (projection coefficients / M)
+  float* U;         // LP x LP
+  float* vec;       // 4 * LP   (sigma, coef, ...)
+  int* iv;          // 4 * LP   (dropped, perm, flags)
+  float* W;         // ns x LP  (orth_block only)
+  int gacc_n;
+};
+
+template <int LP>
+__host__ __device__ constexpr size_t small_ws_fixed_bytes(int gacc_n) {
+  return sizeof(double) * (2 * LP * LP + LP + gacc_n) + sizeof(float) * (3 * LP * LP + LP + 4 * LP) +
+         sizeof(int) * 4 * LP;
+}
+
+template <int LP>
+__host__ __device__ constexpr size_t small_ws_bytes(int64_t ns, int gacc_n) {
+  return (small_ws_fixed_bytes<LP>(gacc_n) + 15) / 16 * 16 + static_cast<size_t>(ns) * LP * sizeof(float);
+}
+
+template <int LP>
+__device__ SmallWs<LP> carve_small_ws(unsigned char* base, int gacc_n) {
+  SmallWs<LP> w;
+  w.gacc_n = gacc_n;
+  double* d = reinterpret_cast<double*>(base);
+  w.G = d;
+  w.R = w.G + LP * LP;
+  w.gdiag = w.R + LP * LP;
+  w.gacc = w.gdiag + LP;
+  float* f = reinterpret_cast<float*>(w.gacc + gacc_n);
+  w.Rf32 = f;
+  w.rinv = w.Rf32 + LP * LP;
+  w.Cm = w.rinv + LP;
+  w.U = w.Cm + LP * LP;
+  w.vec = w.U + LP * LP;
+  w.iv = reinterpret_cast<int*>(w.vec + 4 * LP);
+  w.W = reinterpret_cast<float*>(base + (small_ws_fixed_bytes<LP>(gacc_n) + 15) / 16 * 16);
+  return w;
+}
+
+__device__ __forceinline__ void decode_pair_sym(int pr, int p, int& a, int& b) {
+  a = 0;
+  while (pr >= p - a) { pr -= p - a; ++a; }
+  b = a + pr;
+}
+
+// G[a][b] = sum_i X[i][ca + a] * X[i][cb + b] for the (a, b) pairs requested, accumulated
+// in double-float over the rows i < ns of X (row stride LP).  sym: a <= b < na (symmetric, both
+// triangles written); otherwise a < na, b < nb.  Block-wide; ends with __syncthreads.
+template <int LP>
+__device__ void block_inner(const float* X, int64_t ns, int ca, int cb, int na, int nb, bool sym, double* G,
+                            double* gacc, int gacc_n) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int np = sym ? na * (na + 1) / 2 : na * nb;
+  if (np == 0) { __syncthreads(); return; }
+  int groups = gacc_n / np;
+  if (groups > nt / np) groups = nt / np;
+  if (groups < 1) groups = 1;
+  for (int t = tid; t < np * groups; t += nt) {
+    const int pr = t % np, g = t / np;
+    int a, b;
+    if (sym) decode_pair_sym(pr, na, a, b);
+    else { a = pr / nb; b = pr % nb; }
+    df64 acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // 4 independent chains
+    int64_t i = g;
+    for (; i + 3 * groups < ns; i += 4 * groups) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        df64_add_prod(acc[u], X[(i + u * groups) * LP + ca + a], X[(i + u * groups) * LP + cb + b]);
+    }
+    for (; i < ns; i += groups) df64_add_prod(acc[0], X[i * LP + ca + a], X[i * LP + cb + b]);
+    gacc[t] = df64_value(df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3])));
+  }
+  __syncthreads();
+  for (int pr = tid; pr < np; pr += nt) {
+    int a, b;
+    if (sym) decode_pair_sym(pr, na, a, b);
+    else { a = pr / nb; b = pr % nb; }
+    double s = 0.0;
+    for (int g = 0; g < groups; ++g) s += gacc[g * np + pr];
+    G[a * LP + b] = s;
+    if (sym) G[b * LP + a] = s;
+  }
+  __syncthreads();
+}
+
+// Right-looking Cholesky G = R^T R (upper R) of the leading p x p block, by warp 0, with
+// column drops: column j is dropped (row j of R zero, rinv[j] = 0) when its pivot is not
+// above rank_tol * (original G_jj), when G_jj is below 1e-15 of the largest diagonal, or when
+// it is not a finite positive number.  G is overwritten.  Returns via iv[0..p) the drop flags.
+// Block-wide (contains __syncthreads).
+//
+// The factorization runs in double-float arithmetic on the FP32 pipes (~48 significant bits):
+// on GB300 every FP64 operation of this serial chain costs far more latency than the dozen
+// FP32 operations of its double-float counterpart.  G (double) is converted in place.
+template <int LP>
+__device__ void block_cholesky(SmallWs<LP>& w, int p, double rank_tol) {
+  const int tid = threadIdx.x;
+  df64* Gd = reinterpret_cast<df64*>(w.G);        // same 8 bytes per entry as the double
+  df64* Rd = reinterpret_cast<df64*>(w.R);
+  float* thr = w.vec + 2 * LP;                    // drop thresholds on the pivots
+  float* g0f = w.vec + 3 * LP;                    // original diagonal
+  int* dropped = w.iv;
+  if (tid < LP) {
+    const double g0 = (tid < p) ? w.G[tid * LP + tid] : 0.0;
+    thr[tid] = static_cast<float>(rank_tol * g0);
+    g0f[tid] = static_cast<float>(g0);
+  }
+  __syncthreads();
+  for (int e = tid; e < LP * LP; e += blockDim.x) {
+    const double v = w.G[e];
+    Gd[e] = df_from_double(v);
+    Rd[e] = df64{0.f, 0.f};
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    float maxdiag = 0.f;
+    for (int a = 0; a < p; ++a) maxdiag = fmaxf(maxdiag, g0f[a]);
+    for (int j = 0; j < p; ++j) {
+      const df64 d = Gd[j * LP + j];
+      const bool drop = !(d.hi > thr[j]) || !(g0f[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
+      df64 inv{0.f, 0.f}, rjj{0.f, 0.f};
+      if (!drop) {
+        inv = df_rsqrt(d);
+        rjj = df_mul(d, inv);
+      }
+      if (lane < LP) {
+        df64 v{0.f, 0.f};
+        if (lane == j) v = rjj;
+        else if (lane > j && lane < p && !drop) v = df_mul(Gd[j * LP + lane], inv);
+        Rd[j * LP + lane] = v;
+        if (lane == j) {
+          dropped[j] = drop ? 1 : 0;
+          w.rinv[j] = inv.hi;
+        }
+      }
+      __syncwarp();
+      // trailing update G[a][b] -= R[j][a] R[j][b] over the pairs j < a <= b < p, spread over the
+      // lanes: pair t of the q x q trailing triangle is (a, b) = (j + 1 + t / q', ...) decoded below
+      if (!drop) {
+        const int q = p - j - 1;
+        for (int t = lane; t < q * q; t += 32) {
+          const int a = j + 1 + t / q, b = j + 1 + t % q;
+          if (a <= b) Gd[a * LP + b] = df_add(Gd[a * LP + b], df_neg(df_mul(Rd[j * LP + a], Rd[j * LP + b])));
+        }
+      }
+      __syncwarp();
+    }
+    if (lane < LP) {
+      for (int a = 0; a < LP; ++a) w.Rf32[a * LP + lane] = Rd[a * LP + lane].hi;
+      if (lane >= p) w.rinv[lane] = 0.f;
+    }
+  }
+  __syncthreads();
+}
+
+// W[i][c0 + b] <- (W[i][c0 .. c0+p) R^{-1})_b for every row (forward substitution in FP32).
+template <int LP>
+__device__ void block_trsm_rows(SmallWs<LP>& w, float* W, int64_t ns, int c0, int p) {
+  for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+    float* row = W + i * LP + c0;
+    float x[LP];                           // fully unrolled: the solution stays in registers
+#pragma unroll
+    for (int b = 0; b < LP; ++b) {
+      if (b < p) {
+        float acc = row[b];
+#pragma unroll
+        for (int a = 0; a < b; ++a) acc = fmaf(-x[a], w.Rf32[a * LP + b], acc);
+        x[b] = acc * w.rinv[b];
+      } else {
+        x[b] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < LP; ++b)
+      if (b < p) row[b] = x[b];
+  }
+  __syncthreads();
+}
+
+// Orthonormal basis (Alg. 1 steps 6 / 10-11 / 14).  W (ns x LP, shared) holds
+// [Qt[:, :keep] | Y[:, :l - keep] | 0]; on return W holds Q.  Returns s (surviving columns).
+// passes = 2 is Cholesky QR2 (orthonormal to FP32 rounding); passes = 1 gives a basis of the
+// same span whose orthogonality error is ~u kappa(Y), enough for a basis that only feeds the
+// next power step (only its span matters there).
+template <int LP>
+__device__ int orth_block(SmallWs<LP>& w, int64_t ns, int keep, int l, double rank_tol, int passes) {
+  float* W = w.W;
+  const int p = l - keep;
+  if (keep > 0 && p > 0) {
+    for (int pass = 0; pass < 2; ++pass) {
+      block_inner<LP>(W, ns, 0, keep, keep, p, false, w.G, w.gacc, w.gacc_n);
+      for (int e = threadIdx.x; e < keep * p; e += blockDim.x) {
+        const int a = e / p, b = e % p;
+        w.Cm[a * LP + b] = static_cast<float>(w.G[a * LP + b]);
+      }
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+        float qa[LP];
+#pragma unroll
+        for (int a = 0; a < LP; ++a) qa[a] = (a < keep) ? W[i * LP + a] : 0.f;
+        for (int b = 0; b < p; ++b) {
+          float acc = W[i * LP + keep + b];
+#pragma unroll
+          for (int a = 0; a < LP; ++a)
+            if (a < keep) acc = fmaf(-qa[a], w.Cm[a * LP + b], acc);
+          W[i * LP + keep + b] = acc;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  int kept = 0;
+  for (int pass = 0; pass < passes && p > 0; ++pass) {
+    block_inner<LP>(W, ns, keep, keep, p, p, true, w.G, w.gacc, w.gacc_n);
+    block_cholesky<LP>(w, p, rank_tol);
+    block_trsm_rows<LP>(w, W, ns, keep, p);
+    kept = 0;
+    for (int c = 0; c < p; ++c) kept += w.iv[c] ? 0 : 1;
+    __syncthreads();
+  }
+  return keep + kept;
+}
+
+// Round-robin schedule: pair w of round rnd among N (even) indices.
+__device__ __forceinline__ void rr_pair(int rnd, int w, int N, int& p, int& q) {
+  if (w == 0) {
+    p = N - 1;
+    q = rnd;
+  } else {
+    p = (rnd + w) % (N - 1);
+    q = (rnd - w + (N - 1)) % (N - 1);
+  }
+  if (p > q) { const int t = p; p = q; q = t; }
+}
+
+// Core of Alg. 1 steps 16-21 from the Gram w.G = Z^T Z (LP x LP, leading l x l live).
+// Q: ns x LP (global).  Writes Rf = Q M (ns x LP), the first keep columns of Qt = Q U[:, perm],
+// and the DevState fields r, keep, sigma, status, counter.  Block-wide.
+template <int LP>
+__device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, float tau, int update_rp,
+                           int advance_counter, float* Rf, float* Qt, DevState* dst, double rank_tol,
+                           int max_sweeps) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  float* Xt = w.Rf32;          // after the Cholesky: Xt[b * LP + a] = R[b][a] (columns of R^T)
+  float* sig = w.vec;
+  float* coef = w.vec + LP;
+  int* perm = w.iv + LP;
+  int* flag = w.iv + 2 * LP;
+  block_cholesky<LP>(w, l, rank_tol);
+  const int N = (l + 1) / 2 * 2;   // even number of Jacobi columns covering the live ones
+  if (tid == 0) flag[1] = 0;
+  __syncthreads();
+  const float tol = 1e-6f;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < max_sweeps && N >= 2; ++sweep) {
+    if (tid == 0) flag[0] = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < N - 1; ++rnd) {
+      for (int pw = warp; pw < N / 2; pw += nwarps) {
+        int p, q;
+        rr_pair(rnd, pw, N, p, q);
+        const float xp = (lane < LP) ? Xt[p * LP + lane] : 0.f;
+        const float xq = (lane < LP) ? Xt[q * LP + lane] : 0.f;
+        float alpha = xp * xp, beta = xq * xq, gamma = xp * xq;   // three interleaved butterflies
+#pragma unroll
+        for (int o = (LP >= 32 ? 16 : LP / 2); o > 0; o >>= 1) {
+          alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+          beta += __shfl_xor_sync(0xffffffffu, beta, o);
+          gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+        }
+        if (fabsf(gamma) > tol * sqrtf(alpha * beta) && alpha > 1e-30f && beta > 1e-30f) {
+          const float zeta = (beta - alpha) / (2.f * gamma);
+          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = rsqrtf(1.f + t * t);
+          const float s = c * t;
+          if (lane < LP) {
+            Xt[p * LP + lane] = c * xp - s * xq;
+            Xt[q * LP + lane] = s * xp + c * xq;
+          }
+          if (lane == 0) flag[0] = 1;
+        }
+      }
+      __syncthreads();
+    }
+    sweeps = sweep + 1;
+    const int any = flag[0];
+    __syncthreads();
+    if (!any) break;
+  }
+  if (tid < LP) {
+    float s2 = 0.f;
+    for (int a = 0; a < LP; ++a) s2 = fmaf(Xt[tid * LP + a], Xt[tid * LP + a], s2);
+    sig[tid] = sqrtf(s2);
+  }
+  __syncthreads();
+  for (int e = tid; e < LP * LP; e += nt) {
+    const int a = e / LP, b = e % LP;
+    w.U[e] = (sig[b] > 0.f) ? Xt[b * LP + a] / sig[b] : 0.f;
+  }
+  if (tid < LP) {
+    int rank = 0;
+    for (int c = 0; c < LP; ++c) rank += (sig[c] > sig[tid] || (sig[c] == sig[tid] && c < tid)) ? 1 : 0;
+    perm[rank] = tid;
+    coef[tid] = (sig[tid] > tau) ? (sig[tid] - tau) / sig[tid] : 0.f;
+  }
+  __syncthreads();
+  float* M = w.Cm;
+  for (int e = tid; e < LP * LP; e += nt) {
+    const int a = e / LP, c = e % LP;
+    float acc = 0.f;
+    for (int b = 0; b < LP; ++b) acc = fmaf(w.U[a * LP + b] * coef[b], w.U[c * LP + b], acc);
+    M[e] = acc;
+  }
+  int r = 0;
+  for (int c = 0; c < LP; ++c) r += (sig[c] > tau) ? 1 : 0;
+  const int keep = update_rp ? max(0, min(r, l - 2)) : 0;
+  __syncthreads();
+  for (int64_t e = tid; e < ns * LP; e += nt) {
+    const int64_t i = e / LP;
+    const int k = static_cast<int>(e % LP);
+    float acc = 0.f, accq = 0.f;
+    const int pk = (k < keep) ? perm[k] : 0;
+    for (int a = 0; a < LP; ++a) {
+      const float qa = Q[i * LP + a];
+      acc = fmaf(qa, M[a * LP + k], acc);
+      accq = fmaf(qa, w.U[a * LP + pk], accq);
+    }
+    Rf[e] = acc;
+    if (update_rp && k < keep) Qt[e] = accq;
+  }
+  if (tid == 0) {
+    dst->r = r;
+    if (update_rp) dst->keep = keep;
+    if (advance_counter) dst->counter += 1;
+    if (sweeps >= max_sweeps) dst->status |= kDevNotConverged;
+    bool finite = true;
+    for (int c = 0; c < LP; ++c) {
+      dst->sigma[c] = sig[perm[c]];
+      finite = finite && isfinite(sig[c]);
+    }
+    for (int c = LP; c < kMaxL; ++c) dst->sigma[c] = 0.f;
+    if (!finite) dst->status |= kDevNonfinite;
+    dst->sigma1 = static_cast<double>(sig[perm[0]]);
+  }
+  __syncthreads();
+}
+
+}  // namespace frsvt

@@ -34,6 +34,7 @@ struct DevState {
 constexpr uint32_t kDevRankDeficient = 1u << 0;
 constexpr uint32_t kDevNotConverged = 1u << 1;
 constexpr uint32_t kDevNonfinite = 1u << 2;
+constexpr uint32_t kDevTimeout = 1u << 3;
 
 // ------------------------------------------------------------------ launchers
 // All launchers enqueue on `st` (cudaStream_t) and return the launch error.

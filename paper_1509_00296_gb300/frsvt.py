@@ -61,6 +61,7 @@ _SIGS = {
     "frsvt_enable_timing": [_P, ctypes.c_int32],
     "frsvt_get_timings": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
     "frsvt_phase_name": [ctypes.c_int32],
+    "frsvt_debug_rows_tc": [_P, _P, _I64, _I64, _I64, _P, _P],
     "frsvt_debug_omega": [_P, _I64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P],
     "frsvt_debug_philox": [_P, _I64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P],
 }
@@ -196,6 +197,15 @@ class Handle:
         cnt = (ctypes.c_int32 * NPHASE)()
         self._chk(lib().frsvt_get_timings(self._h, ms, cnt))
         return {lib().frsvt_phase_name(p).decode(): (ms[p], cnt[p]) for p in range(NPHASE)}
+
+    def debug_rows_tc(self, A, Q):
+        """Z = A Q by the tensor-core row pass (Q: n x LP float32 CUDA tensor)."""
+        import torch
+        _check_f32_cuda(A, "A")
+        m, n = A.shape
+        Z = torch.empty((m, Q.shape[1]), dtype=torch.float32, device=A.device)
+        self._chk(lib().frsvt_debug_rows_tc(self._h, _ptr(A), m, n, A.stride(0), _ptr(Q), _ptr(Z)))
+        return Z
 
     def sigma(self):
         buf = (ctypes.c_float * 32)()

@@ -44,6 +44,7 @@ CASES = [  # m, n, rank, decay, noise, l, q, ld
     (513, 200, 60, 0.9, 0.01, 16, 2, None),
     (700, 300, 60, 0.93, 0.01, 32, 1, 304),
     (4100, 33, 20, 0.7, 0.0, 5, 1, 36),
+    (3000, 1500, 60, 0.9, 0.01, 16, 1, None),     # short side too wide for the fused single-CTA tails
 ]
 
 
