@@ -224,6 +224,11 @@ frsvt_status frsvt_debug_omega(float* out, int64_t rows, int32_t cols, uint64_t 
  * Enqueued on the handle's stream; device errors go to the handle's status word. */
 frsvt_status frsvt_debug_rows_tc(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda,
                                  const float* Q, float* Z);
+/* Y = A^T B on the tensor cores (tcgen05, 3xTF32): the column pass of Alg. 1 steps 5 / 9 / 14 alone.
+ * B: m x LP row-major, or NULL for B = Omega of the (seed, stream) Philox stream (Alg. 1 step 4).
+ * Y: n x LP row-major (n <= 256).  Enqueued on the handle's stream. */
+frsvt_status frsvt_debug_cols_tc(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda,
+                                 const float* B, uint64_t seed, uint64_t stream, float* Y);
 /* Raw Philox4x64-10 words for counters (i, j, stream, problem), i < rows, j < blocks: rows x blocks x 4 uint64. */
 frsvt_status frsvt_debug_philox(uint64_t* out, int64_t rows, int32_t blocks, uint64_t seed,
                                 uint64_t stream, uint64_t problem, void* cuda_stream);

@@ -59,6 +59,15 @@ cudaError_t launch_tc_lr(int LP, const CUtensorMap& tmA, int64_t m, int64_t n, i
                          DevState* dst, cudaStream_t st);
 int tc_box_cols();
 int tc_box_rows();
+int tc_sc_stages(int LP, int64_t n, bool omega, size_t limit);
+size_t tc_sc_smem(int LP, int64_t n, bool omega, int ns);
+cudaError_t prepare_tc_sc_kernels(int smem_limit);
+int tc_sc_resident_grid(int LP, int64_t n, int ns);
+cudaError_t launch_tc_sc(int LP, const CUtensorMap& tmA, const CUtensorMap* tmZ, int64_t m, int64_t n, int grid,
+                         int ns, uint64_t seed, uint64_t ctr, DevState* dst, float* cpart, float* Y,
+                         unsigned* tickets, bool tail, int l, int use_rp, int passes, const float* Qt, float* Q,
+                         double rank_tol, cudaStream_t st);
+int tc_sc_rows();
 }
 
 using namespace frsvt;
@@ -88,6 +97,8 @@ struct frsvt_handle {
   bool fused = false;
   bool tma = false;          // persistent TMA-pipelined passes (short side <= 256 columns)
   int tma_grid = 8;
+  int tc_sc_ns = 0;          // stages of the tensor-core column pass (0: not available)
+  int tc_sc_grid = 0;
   float* cpart_sc = nullptr;
   double* cpart_lr = nullptr;
   double* cpart_alm = nullptr;
@@ -190,8 +201,11 @@ bool make_row_map(CUtensorMap* map, const float* base, int64_t rows, int64_t col
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Same with 32-column (128-byte) boxes in the 128-byte swizzle read by tcgen05 as a K-major operand.
-bool make_row_map_sw128(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+// Same with 32-column (128-byte) boxes in a 128-byte swizzle: 16-byte chunks (read by tcgen05 as a
+// K-major operand) or, with sw = CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B, 32-byte chunks (the layout a
+// kind::tf32 MMA takes for an MN-major operand).
+bool make_row_map_sw128(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                        CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (enc == nullptr) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
@@ -199,7 +213,7 @@ bool make_row_map_sw128(CUtensorMap* map, const float* base, int64_t rows, int64
   cuuint32_t box[2] = {32u, static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -290,17 +304,35 @@ frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t 
     const int64_t rpc = cdiv(cdiv(m, G), tma_rows_per_tile()) * tma_rows_per_tile();
     const int64_t rpl = cdiv(cdiv(m, G), tma_rows_per_tile_lr()) * tma_rows_per_tile_lr();
     const int nst = tma_lr_stages(LP, n, kSmemLimit - 16384);
-    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_tp_sc(LP, tmA, nullptr, m, n, rpc, G, h->cfg.seed, ctr, h->dst,
-                                                  h->cpart_sc, h->Ys, h->tickets, l, use_rp, q == 0 ? 2 : 1, h->Qt,
-                                                  h->Qs, tol, st));
+    // Column passes (A^T Omega, A^T Z): on the tensor cores when the handle prepared them, with A
+    // read MN-major (32-byte-atom swizzle) and Omega / Z as the K-major operand.
+    const bool tcc = h->tc_sc_ns > 0;
+    CUtensorMap tmAc, tmZc;
+    if (tcc && (!make_row_map_sw128(&tmAc, A, m, n, lda, tc_sc_rows(), CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) ||
+                !make_row_map(&tmZc, h->Zl, m, LP, LP, LP, tc_sc_rows())))
+      return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A / Z (column pass)");
+    if (tcc)
+      FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_tc_sc(LP, tmAc, nullptr, m, n, h->tc_sc_grid, h->tc_sc_ns, h->cfg.seed,
+                                                    ctr, h->dst, h->cpart_sc, h->Ys, h->tickets, true, l, use_rp,
+                                                    q == 0 ? 2 : 1, h->Qt, h->Qs, tol, st));
+    else
+      FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_tp_sc(LP, tmA, nullptr, m, n, rpc, G, h->cfg.seed, ctr, h->dst,
+                                                    h->cpart_sc, h->Ys, h->tickets, l, use_rp, q == 0 ? 2 : 1, h->Qt,
+                                                    h->Qs, tol, st));
     CUtensorMap tmAs;                       // 128-byte swizzled boxes for the tensor-core row pass
     if (!make_row_map_sw128(&tmAs, A, m, n, lda, tc_box_rows()))
       return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A (swizzled)");
     for (int it = 0; it < q; ++it) {
+      const int passes = it == q - 1 ? 2 : 1;
       FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_tc_lr(LP, tmAs, m, n, h->sms, h->Qs, h->Zl, h->dst, st));
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_tp_sc(LP, tmA, &tmZ, m, n, rpc, G, h->cfg.seed, ctr, h->dst,
-                                                       h->cpart_sc, h->Ys, h->tickets, l, 0, it == q - 1 ? 2 : 1,
-                                                       h->Qt, h->Qs, tol, st));
+      if (tcc)
+        FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_tc_sc(LP, tmAc, &tmZc, m, n, h->tc_sc_grid, h->tc_sc_ns,
+                                                         h->cfg.seed, ctr, h->dst, h->cpart_sc, h->Ys, h->tickets,
+                                                         true, l, 0, passes, h->Qt, h->Qs, tol, st));
+      else
+        FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_tp_sc(LP, tmA, &tmZ, m, n, rpc, G, h->cfg.seed, ctr, h->dst,
+                                                         h->cpart_sc, h->Ys, h->tickets, l, 0, passes, h->Qt, h->Qs,
+                                                         tol, st));
     }
     FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_tp_lr(LP, true, tmAl, m, n, rpl, G, nst, h->Qs, h->Zl, h->cpart_lr,
                                                    h->Gfin, h->tickets, l, tau_host, tau_from_mu, update_rp,
@@ -416,7 +448,8 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
       prepare_small_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
       prepare_fused_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
       prepare_tma_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
-      prepare_tc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
+      prepare_tc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
+      prepare_tc_sc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
     delete h;
     return FRSVT_ERR_CUDA;
   }
@@ -453,6 +486,17 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
     // clusters of 8 that can be resident at once (GPCs hold a whole number of clusters)
     h->tma_grid = h->tma ? tma_resident_grid(h->LP, nt) : 0;
     if (h->tma_grid < 8) h->tma = false;
+    if (h->tma) {
+      const int ns_o = tc_sc_stages(h->LP, nt, true, kSmemLimit - 8192);
+      const int ns_z = tc_sc_stages(h->LP, nt, false, kSmemLimit - 8192);
+      h->tc_sc_ns = ns_o < ns_z ? ns_o : ns_z;
+      if (h->tc_sc_ns >= 2 && tc_sc_smem(h->LP, nt, false, h->tc_sc_ns) <= kSmemLimit - 8192) {
+        h->tc_sc_grid = tc_sc_resident_grid(h->LP, nt, h->tc_sc_ns);
+        if (h->tc_sc_grid < 8) h->tc_sc_ns = 0;
+      } else {
+        h->tc_sc_ns = 0;
+      }
+    }
   }
   {
     const int64_t ntl = ntiles_max;
@@ -719,6 +763,25 @@ frsvt_status frsvt_debug_rows_tc(frsvt_handle* h, const float* A, int64_t m, int
   if (!make_row_map_sw128(&tm, A, m, n, lda, tc_box_rows()))
     return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A");
   FRSVT_CK(launch_tc_lr(h->LP, tm, m, n, h->sms, Q, Z, h->dst, h->stream));
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_debug_cols_tc(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, const float* B,
+                                 uint64_t seed, uint64_t stream, float* Y) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = check_shape(h, m, n);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, A, m, n, lda, "A")) != FRSVT_OK) return s;
+  if (Y == nullptr) return fail(h, FRSVT_ERR_INVALID_ARG, "Y is required");
+  if (n > 256) return fail(h, FRSVT_ERR_UNSUPPORTED, "the tensor-core column pass serves n <= 256");
+  if (m == 0 || n == 0) return FRSVT_OK;
+  if (!h->tc_sc_ns) return fail(h, FRSVT_ERR_UNSUPPORTED, "tensor-core column pass unavailable for this handle");
+  CUtensorMap tmA, tmZ;
+  if (!make_row_map_sw128(&tmA, A, m, n, lda, tc_sc_rows(), CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) ||
+      (B != nullptr && !make_row_map(&tmZ, B, m, h->LP, h->LP, h->LP, tc_sc_rows())))
+    return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  FRSVT_CK(launch_tc_sc(h->LP, tmA, B ? &tmZ : nullptr, m, n, h->tc_sc_grid, h->tc_sc_ns, seed, stream, h->dst,
+                        h->cpart_sc, Y, h->tickets, false, 0, 0, 1, h->Qt, h->Qs, h->cfg.rank_tol, h->stream));
   return FRSVT_OK;
 }
 

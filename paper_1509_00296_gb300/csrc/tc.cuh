@@ -40,6 +40,21 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void* tile, uint32_t l
   return d;
 }
 
+// Descriptor of an MN-major 32-bit operand (kind::tf32 reads it only in this layout): K-rows of
+// 128 bytes (32 MN elements) whose 32-byte chunks are XOR-ed with (K-row mod 4), layout type 1
+// (128-byte swizzle, 32-byte atoms); groups of 4 K-rows are 512 bytes apart and consecutive
+// 32-element MN groups lbo_bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128a32_mn(const void* tile, uint32_t lbo_bytes) {
+  const uint32_t a = smem_addr(tile);
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((a & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo_bytes >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>(512u >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(1) << 61;
+  return d;
+}
+
 // Instruction descriptor of kind::tf32 with FP32 accumulation, both operands K-major (or A
 // MN-major when a_mn), shape M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, bool a_mn = false, bool b_mn = false) {

@@ -62,6 +62,7 @@ _SIGS = {
     "frsvt_get_timings": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
     "frsvt_phase_name": [ctypes.c_int32],
     "frsvt_debug_rows_tc": [_P, _P, _I64, _I64, _I64, _P, _P],
+    "frsvt_debug_cols_tc": [_P, _P, _I64, _I64, _I64, _P, ctypes.c_uint64, ctypes.c_uint64, _P],
     "frsvt_debug_omega": [_P, _I64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P],
     "frsvt_debug_philox": [_P, _I64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P],
 }
@@ -206,6 +207,15 @@ class Handle:
         Z = torch.empty((m, Q.shape[1]), dtype=torch.float32, device=A.device)
         self._chk(lib().frsvt_debug_rows_tc(self._h, _ptr(A), m, n, A.stride(0), _ptr(Q), _ptr(Z)))
         return Z
+
+    def debug_cols_tc(self, A, LP: int, B=None, seed: int = 0, stream: int = 0):
+        """Y = A^T B by the tensor-core column pass (B: m x LP tensor, or None for the Omega stream)."""
+        import torch
+        _check_f32_cuda(A, "A")
+        m, n = A.shape
+        Y = torch.empty((n, LP), dtype=torch.float32, device=A.device)
+        self._chk(lib().frsvt_debug_cols_tc(self._h, _ptr(A), m, n, A.stride(0), _ptr(B), seed, stream, _ptr(Y)))
+        return Y
 
     def sigma(self):
         buf = (ctypes.c_float * 32)()
