@@ -15,23 +15,23 @@ constexpr int kCL = 8;   // CTAs per cluster (portable size)
 // part_sm: this CTA's partial (count elements, shared).  cpart: [nclusters][count] global
 // scratch.  out: the final sum (count, global).  Returns true in the CTAs of the cluster that
 // finished last; they have written `out` (fenced) when the call returns.
-template <typename T>
+template <typename T, int CL = kCL>
 __device__ bool cluster_split_reduce(T* part_sm, int count, T* cpart, T* out, unsigned* ticket, int cluster_idx,
                                      int nclusters, int* flag_sm) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = static_cast<int>(cl.block_rank());
   cl.sync();
-  const int per = (count + kCL - 1) / kCL;
+  const int per = (count + CL - 1) / CL;
   const int e0 = rank * per;
   const int e1 = min(count, e0 + per);
   for (int e = e0 + static_cast<int>(threadIdx.x); e < e1; e += blockDim.x) {
-    T v[kCL];
+    T v[CL];
 #pragma unroll
-    for (int r = 0; r < kCL; ++r) v[r] = cl.map_shared_rank(part_sm, r)[e];
+    for (int r = 0; r < CL; ++r) v[r] = cl.map_shared_rank(part_sm, r)[e];
     T s = 0;
 #pragma unroll
-    for (int r = 0; r < kCL; ++r) s += v[r];
+    for (int r = 0; r < CL; ++r) s += v[r];
     cpart[static_cast<int64_t>(cluster_idx) * count + e] = s;
   }
   __threadfence();

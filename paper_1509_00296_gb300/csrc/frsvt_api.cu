@@ -53,9 +53,10 @@ cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS
                           const CUtensorMap& tmZ, int64_t m, int64_t n, int64_t rpc, int grid, const float* Rf,
                           float* S, float* A, int64_t ld, float* L, int64_t ldl, DevState* dst, double* cpart,
                           double* rsum, unsigned* tickets, cudaStream_t st);
-size_t tc_lr_smem(int LP, int64_t n);
+size_t tc_lr_smem(int LP, int64_t n, int ns);
+int tc_lr_stages(int LP, int64_t n, size_t limit);
 cudaError_t prepare_tc_kernels(int smem_limit);
-cudaError_t launch_tc_lr(int LP, const CUtensorMap& tmA, int64_t m, int64_t n, int grid, const float* Q, float* Z,
+cudaError_t launch_tc_lr(int LP, const CUtensorMap& tmA, int64_t m, int64_t n, int grid, int ns, const float* Q, float* Z,
                          DevState* dst, cudaStream_t st);
 int tc_box_cols();
 int tc_box_rows();
@@ -98,6 +99,7 @@ struct frsvt_handle {
   bool tma = false;          // persistent TMA-pipelined passes (short side <= 256 columns)
   int tma_grid = 8;
   int tc_sc_ns = 0;          // stages of the tensor-core column pass (0: not available)
+  int tc_lr_ns = 0;          // stages of the tensor-core row pass
   int tc_sc_grid = 0;
   float* cpart_sc = nullptr;
   double* cpart_lr = nullptr;
@@ -324,7 +326,7 @@ frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t 
       return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A (swizzled)");
     for (int it = 0; it < q; ++it) {
       const int passes = it == q - 1 ? 2 : 1;
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_tc_lr(LP, tmAs, m, n, h->sms, h->Qs, h->Zl, h->dst, st));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_tc_lr(LP, tmAs, m, n, h->sms, h->tc_lr_ns, h->Qs, h->Zl, h->dst, st));
       if (tcc)
         FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_tc_sc(LP, tmAc, &tmZc, m, n, h->tc_sc_grid, h->tc_sc_ns,
                                                          h->cfg.seed, ctr, h->dst, h->cpart_sc, h->Ys, h->tickets,
@@ -480,7 +482,8 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   {
     const int64_t nt = cfg->n_max < 256 ? cfg->n_max : 256;
     const int nst = tma_lr_stages(h->LP, nt, kSmemLimit - 16384);
-    h->tma = tensor_map_encoder() != nullptr && nst >= 2 &&
+    h->tc_lr_ns = tc_lr_stages(h->LP, nt, kSmemLimit - 2048);
+    h->tma = tensor_map_encoder() != nullptr && nst >= 2 && h->tc_lr_ns >= 2 &&
              tma_sc_smem(h->LP, nt) <= kSmemLimit - 8192 &&
              tma_lr_smem(h->LP, nt, nst) <= kSmemLimit - 8192 && tma_alm_smem(h->LP, nt) <= kSmemLimit - 8192;
     // clusters of 8 that can be resident at once (GPCs hold a whole number of clusters)
@@ -762,7 +765,9 @@ frsvt_status frsvt_debug_rows_tc(frsvt_handle* h, const float* A, int64_t m, int
   CUtensorMap tm;
   if (!make_row_map_sw128(&tm, A, m, n, lda, tc_box_rows()))
     return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A");
-  FRSVT_CK(launch_tc_lr(h->LP, tm, m, n, h->sms, Q, Z, h->dst, h->stream));
+  const int ns = tc_lr_stages(h->LP, n, kSmemLimit - 2048);
+  if (ns < 2) return fail(h, FRSVT_ERR_UNSUPPORTED, "tensor-core row pass does not fit");
+  FRSVT_CK(launch_tc_lr(h->LP, tm, m, n, h->sms, ns, Q, Z, h->dst, h->stream));
   return FRSVT_OK;
 }
 

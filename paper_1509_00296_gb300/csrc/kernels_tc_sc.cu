@@ -3,14 +3,22 @@
 //
 // This is the column pass of Alg. 1: the sketch Y = A^T Omega (steps 4-5 / 8-9, Omega drawn
 // in-kernel from the Philox stream) and the second half of a power step, Y = A^T Z (step 14).
-// As an MMA, D (n x LP) += A_blk^T (n x 32 rows) B_blk (32 rows x LP): the A tile is the
-// MN-major operand (each loaded 128-byte row holds 32 consecutive columns of A, the MN
-// index), B_blk^T is written by the split warps as a K-major operand.  M = 128 columns of A
-// per MMA (one or two M tiles cover n <= 256), N = LP, K = 8; the accumulators stay in tensor
-// memory across all row blocks of the CTA (split-K over rows), then go to shared memory, to
-// the cluster reduction (cluster.cuh) and to the orthonormalisation (small_dense.cuh).
-// 3xTF32: the split warps rewrite each tile as A_hi in place and write A_lo to a small ring.
-// Warp roles: 0 TMA producer, 1 tensor-memory owner + MMA issuer, 2-5 split / drain.
+//
+// A kind::tf32 MMA instruction (K = 8) occupies the tensor core for about the same time
+// whatever its N (up to 256), so every instruction covers all n <= 256 columns of A:
+//     D (128 x N) += Bs (128 x 8 rows of A) . A_blk (8 rows x N),  N = n rounded up to 16,
+// i.e. D holds Y^T.  Bs is B_blk^T split into TF32 parts and stacked (row 32 (k / 16) +
+// 16 part + k % 16 holds part hi / lo of column k of B), written K-major by the B warps; the
+// rest of its 128-row window is whatever follows in shared memory and only feeds accumulator
+// rows that are never read.  The A tile is the MN-major operand (each loaded 128-byte row
+// holds 32 consecutive columns of A), which kind::tf32 reads only in the 128-byte swizzle with
+// 32-byte atoms.  3xTF32: Bs . A_hi + Bs . A_lo with the raw tile as A_hi (the MMA reads only
+// the 19 leading bits of each word); once the A_hi MMAs of a block have completed, split warps
+// overwrite the tile in place with A_lo = A - A_hi.  The accumulator stays in tensor memory
+// across all row blocks of the CTA (split-K over rows), then goes to shared memory, to the
+// cluster reduction (cluster.cuh) and to the orthonormalisation (small_dense.cuh).
+// Warp roles: 0 TMA producer, 1 tensor-memory owner + MMA issuer (A_hi MMAs of block b, then
+// the A_lo MMAs of block b - 1), 2-5 B warps, 6-13 split warps; lane-quarter 0 / 1 warps drain.
 #include <cuda.h>
 
 #include "cluster.cuh"
@@ -25,40 +33,51 @@ namespace frsvt {
 namespace {
 
 constexpr int kRows = 32;                 // rows of A per block (the MMA K of one block)
-constexpr int kChunk = kRows * 128;       // one 32-column chunk of a block: 4 KB
-constexpr int kThr = 192;
+constexpr int kChunk = kRows * 128;       // one 32-column group of a block: 4 KB
+constexpr int kBWarps = 4;
+constexpr int kSplitWarps = 8;
+constexpr int kThr = 64 + 32 * (kBWarps + kSplitWarps);
+constexpr int kScCL = 4;                  // CTAs per cluster of the split-K reduction
+constexpr int kMaxNS = 6;                 // most pipeline stages
 constexpr int kGaccT = 1024;
 
 struct ScLayout {
-  int mt, nch, ns;
-  uint32_t a_bytes, z_bytes, stage, lo, b;
-  uint32_t off_lo, off_b, total;
+  int nch, ns, N;
+  uint32_t a_bytes, z_bytes, stage, bslot;
+  uint32_t off_b, total;
 };
 
 __host__ __device__ inline ScLayout sc_layout(int LP, int n, bool omega, int ns) {
   ScLayout L;
-  L.mt = (n + 127) / 128;
-  L.nch = 4 * L.mt;
+  L.nch = (n + 31) / 32;
   L.ns = ns;
+  L.N = (n + 15) / 16 * 16;
   L.a_bytes = static_cast<uint32_t>(L.nch) * kChunk;
   L.z_bytes = omega ? 0u : static_cast<uint32_t>(kRows * LP * 4);
   L.stage = (L.a_bytes + L.z_bytes + 1023u) / 1024u * 1024u;
-  L.lo = L.a_bytes;
-  L.b = static_cast<uint32_t>(LP) * 128u * 2u;      // B_hi | B_lo of one block
-  L.off_lo = static_cast<uint32_t>(ns) * L.stage;
-  L.off_b = L.off_lo + 2u * L.lo;
-  L.total = L.off_b + 2u * L.b;
+  L.bslot = static_cast<uint32_t>(2 * LP) * 128u;
+  L.off_b = static_cast<uint32_t>(ns) * L.stage;
+  L.total = L.off_b + static_cast<uint32_t>(ns) * L.bslot + static_cast<uint32_t>(128 - 2 * LP) * 128u;
   return L;
 }
 
+// Stacked row of part (0 hi, 1 lo) of column k in the M operand.
+__host__ __device__ constexpr int stack_row(int k, int part) { return 32 * (k / 16) + 16 * part + (k % 16); }
+
+// Tensor-memory columns for `need` accumulator columns (a power of two, at least 32).
+__host__ __device__ constexpr uint32_t tmem_cols(int need) {
+  return need <= 32 ? 32u : need <= 64 ? 64u : need <= 128 ? 128u : 256u;
+}
+
 template <int LP, bool OMEGA, bool TAIL>
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kThr, 1)
+__global__ void __cluster_dims__(kScCL, 1, 1) __launch_bounds__(kThr, 1)
 k_tc_sc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ, int64_t m, int n,
         int64_t rpc, int ns, uint64_t seed, uint64_t ctr, DevState* __restrict__ dst, float* __restrict__ cpart,
         float* __restrict__ Y, unsigned* __restrict__ tickets, int l, int use_rp, int passes,
         const float* __restrict__ Qt, float* __restrict__ Qout, double rank_tol) {
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t full[4], ready[4], empty[4], lofree[2], acc_full;
+  __shared__ __align__(8) uint64_t full[kMaxNS], bready[kMaxNS], hidone[kMaxNS], lo_ready[kMaxNS], empty[kMaxNS],
+      acc_full;
   __shared__ uint32_t tmem_base;
   __shared__ int flag;
   const ScLayout Lt = sc_layout(LP, n, OMEGA, ns);
@@ -66,20 +85,24 @@ k_tc_sc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rpc;
   const int64_t r1 = imin64(m, r0 + rpc);
   const int nb = (r1 > r0) ? static_cast<int>((r1 - r0 + kRows - 1) / kRows) : 0;
-  const uint32_t ncols = (Lt.mt * LP >= 32) ? static_cast<uint32_t>(Lt.mt * LP) : 32u;
+  const uint32_t ncols = tmem_cols(Lt.N);
+  constexpr int kDrainQ = LP / 16;
   const uint64_t stream = OMEGA ? ((ctr == kCounterFromState) ? dst->counter : ctr) : 0ull;
+  unsigned char* bring = dsm + Lt.off_b;
+  for (uint32_t e = threadIdx.x; e < (Lt.total - Lt.off_b) / 4; e += kThr) reinterpret_cast<float*>(bring)[e] = 0.f;
+  fence_proxy_async();
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&ready[s], 4);
+      mbar_init(&bready[s], kBWarps);
+      mbar_init(&hidone[s], 1);
+      mbar_init(&lo_ready[s], kSplitWarps);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&lofree[0], 1);
-    mbar_init(&lofree[1], 1);
     mbar_init(&acc_full, 1);
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(&tmem_base, ncols <= 32 ? 32u : 64u);
+  if (warp == 1) tmem_alloc(&tmem_base, ncols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -106,63 +129,54 @@ k_tc_sc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(128, LP, true, false);
-      for (int b = 0; b < nb; ++b) {
+      const uint32_t idesc = idesc_tf32(128, Lt.N, false, true);
+      auto issue = [&](int b, bool lo_part) {
+        const int s = b % ns;
+        const unsigned char* bs = bring + s * Lt.bslot;
+        const unsigned char* at = dsm + s * Lt.stage;
+#pragma unroll
+        for (int ks = 0; ks < kRows / 8; ++ks)
+          tc_mma_tf32(tbase, smem_desc_sw128(bs + 32 * ks, 16, 1024), smem_desc_sw128a32_mn(at + ks * 1024, kChunk),
+                      idesc, lo_part || b > 0 || ks > 0);
+      };
+      auto issue_lo = [&](int b) {
         const int s = b % ns, u = b / ns;
-        if (ok && !mbar_wait(&ready[s], static_cast<uint32_t>(u) & 1u)) {
+        if (ok && !mbar_wait(&lo_ready[s], static_cast<uint32_t>(u) & 1u)) {
           ok = false;
           atomicOr(&dst->status, kDevTimeout);
         }
         tc_fence_after();
-        const unsigned char* ahi = dsm + s * Lt.stage;
-        const unsigned char* alo = dsm + Lt.off_lo + (b & 1) * Lt.lo;
-        const unsigned char* bh = dsm + Lt.off_b + (b & 1) * Lt.b;
-        const unsigned char* bl = bh + LP * 128;
-        for (int mt = 0; mt < Lt.mt; ++mt) {
-          const uint32_t d = tbase + static_cast<uint32_t>(mt * LP);
-#pragma unroll
-          for (int ks = 0; ks < kRows / 8; ++ks) {
-            const uint64_t dah = smem_desc_sw128a32_mn(ahi + (4 * mt) * kChunk + ks * 1024, kChunk);
-            const uint64_t dal = smem_desc_sw128a32_mn(alo + (4 * mt) * kChunk + ks * 1024, kChunk);
-            const uint64_t dbh = smem_desc_sw128(bh + 32 * ks, 16, 1024);
-            const uint64_t dbl = smem_desc_sw128(bl + 32 * ks, 16, 1024);
-            tc_mma_tf32(d, dah, dbh, idesc, b > 0 || ks > 0);
-            tc_mma_tf32(d, dah, dbl, idesc, true);
-            tc_mma_tf32(d, dal, dbh, idesc, true);
-          }
-        }
+        issue(b, true);
         tc_commit(&empty[s]);
-        tc_commit(&lofree[b & 1]);
+      };
+      for (int b = 0; b < nb; ++b) {
+        const int s = b % ns, u = b / ns;
+        if (ok && (!mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u) ||
+                   !mbar_wait(&bready[s], static_cast<uint32_t>(u) & 1u))) {
+          ok = false;
+          atomicOr(&dst->status, kDevTimeout);
+        }
+        tc_fence_after();
+        issue(b, false);
+        tc_commit(&hidone[s]);
+        if (b > 0) issue_lo(b - 1);
       }
+      if (nb > 0) issue_lo(nb - 1);
       tc_commit(&acc_full);
     }
-  } else {
-    const int t = threadIdx.x - 64;                                  // 0..127
+  } else if (warp < 2 + kBWarps) {
+    // B warps: [B_hi; B_lo]^T of each block into its slot (K-major, 128-byte swizzle).
+    const int t = threadIdx.x - 64;
     for (int b = 0; b < nb; ++b) {
       const int s = b % ns, u = b / ns;
       if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) {
         ok = false;
         atomicOr(&dst->status, kDevTimeout);
       }
-      if (b >= 2 && ok && !mbar_wait(&lofree[b & 1], static_cast<uint32_t>(b / 2 - 1) & 1u)) {
-        ok = false;
-        atomicOr(&dst->status, kDevTimeout);
-      }
-      float4* hi = reinterpret_cast<float4*>(dsm + s * Lt.stage);
-      float4* lo = reinterpret_cast<float4*>(dsm + Lt.off_lo + (b & 1) * Lt.lo);
-      const int nv = static_cast<int>(Lt.a_bytes / 16);
-      for (int e = t; e < nv; e += 128) {
-        const float4 v = hi[e];
-        const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-        hi[e] = h;
-        lo[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-      }
-      // B^T of the block: row k (0..LP) of 32 K-elements = B[row r of the block][k]
-      unsigned char* bh = dsm + Lt.off_b + (b & 1) * Lt.b;
-      unsigned char* bl = bh + LP * 128;
+      unsigned char* bs = bring + s * Lt.bslot;
       const int64_t i0 = r0 + static_cast<int64_t>(b) * kRows;
       if (OMEGA) {
-        for (int q = t; q < kRows * (LP / 4); q += 128) {
+        for (int q = t; q < kRows * (LP / 4); q += 32 * kBWarps) {
           const int r = q / (LP / 4), blk = q % (LP / 4);
           float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
           if (i0 + r < r1) gv = gaussian4(seed, static_cast<uint64_t>(i0 + r), static_cast<uint64_t>(blk), stream, 0ull);
@@ -171,53 +185,84 @@ k_tc_sc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           for (int c = 0; c < 4; ++c) {
             const int k = 4 * blk + c;
             const float hv = tf32_hi(vals[c]);
-            *reinterpret_cast<float*>(bh + sw128_offset(k, r)) = hv;
-            *reinterpret_cast<float*>(bl + sw128_offset(k, r)) = vals[c] - hv;
+            *reinterpret_cast<float*>(bs + sw128_offset(stack_row(k, 0), r)) = hv;
+            *reinterpret_cast<float*>(bs + sw128_offset(stack_row(k, 1), r)) = vals[c] - hv;
           }
         }
       } else {
         const float* zt = reinterpret_cast<const float*>(dsm + s * Lt.stage + Lt.a_bytes);   // kRows x LP
-        for (int q = t; q < kRows * LP; q += 128) {
+        for (int q = t; q < kRows * LP; q += 32 * kBWarps) {
           const int r = q / LP, k = q % LP;
           const float v = (i0 + r < r1) ? zt[r * LP + k] : 0.f;
           const float hv = tf32_hi(v);
-          *reinterpret_cast<float*>(bh + sw128_offset(k, r)) = hv;
-          *reinterpret_cast<float*>(bl + sw128_offset(k, r)) = v - hv;
+          *reinterpret_cast<float*>(bs + sw128_offset(stack_row(k, 0), r)) = hv;
+          *reinterpret_cast<float*>(bs + sw128_offset(stack_row(k, 1), r)) = v - hv;
         }
       }
       fence_proxy_async();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&ready[s]);
+      if (lane == 0) mbar_arrive(&bready[s]);
     }
-    // drain the accumulators: warp quarter q reads tensor-memory lanes 32q..32q+31 = columns of A
     if (ok && !mbar_wait(&acc_full, 0u)) {
       ok = false;
       atomicOr(&dst->status, kDevTimeout);
     }
-    tc_fence_after();
+  } else {
+    // split warps: once the A_hi MMAs of a block are done, its tile becomes A_lo in place
+    const int t = threadIdx.x - 32 * (2 + kBWarps);
+    const int nv = static_cast<int>(Lt.a_bytes / 16);
+    for (int b = 0; b < nb; ++b) {
+      const int s = b % ns, u = b / ns;
+      if (ok && !mbar_wait(&hidone[s], static_cast<uint32_t>(u) & 1u)) {
+        ok = false;
+        atomicOr(&dst->status, kDevTimeout);
+      }
+      float4* a = reinterpret_cast<float4*>(dsm + s * Lt.stage);
+#pragma unroll 4
+      for (int e = t; e < nv; e += 32 * kSplitWarps) {
+        const float4 v = a[e];
+        a[e] = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&lo_ready[s]);
+    }
+    if (ok && !mbar_wait(&acc_full, 0u)) {
+      ok = false;
+      atomicOr(&dst->status, kDevTimeout);
+    }
   }
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  // drain: accumulator row 32 q + L (lane quarter q) is part (L / 16) of column 16 q + L % 16
+  // of Y; TMEM column j is column j of A.  The three warps of a quarter take every third group
+  // of 16 columns.
   float* part_sm = reinterpret_cast<float*>(dsm);                   // n x LP (the pipeline is idle)
-  if (warp >= 2) {
-    const int sub = warp & 3;
-    for (int mt = 0; mt < Lt.mt; ++mt) {
-      const int j = 128 * mt + 32 * sub + lane;
+  if (warp >= 4 && (warp & 3) < kDrainQ) {
+    const int q = warp & 3, idx = (warp >> 2) - 1;
+    const int nwq = (kThr / 32 - 1 - q) / 4;                        // warps >= 4 in quarter q
+    for (int grp = idx; grp < Lt.N / 16; grp += nwq) {
+      float v[16];
+      tmem_ld16(tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(16 * grp), v);
 #pragma unroll
-      for (int h16 = 0; h16 < LP / 16; ++h16) {
-        float v[16];
-        tmem_ld16(tbase + (static_cast<uint32_t>(32 * sub) << 16) + static_cast<uint32_t>(mt * LP + 16 * h16), v);
-        if (j < n)
+      for (int i = 0; i < 16; ++i) v[i] += __shfl_down_sync(0xffffffffu, v[i], 16);
+      if (lane < 16) {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) part_sm[j * LP + 16 * h16 + k] = (nb > 0) ? v[k] : 0.f;
+        for (int i = 0; i < 16; ++i) {
+          const int j = 16 * grp + i;
+          if (j < n) part_sm[j * LP + 16 * q + lane] = (nb > 0) ? v[i] : 0.f;
+        }
       }
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tbase, ncols <= 32 ? 32u : 64u);
-  const int nclusters = gridDim.x / kCL;
-  if (!cluster_split_reduce<float>(part_sm, n * LP, cpart, Y, tickets, blockIdx.x / kCL, nclusters, &flag)) return;
+  if (warp == 1) tmem_dealloc(tbase, ncols);
+  const int nclusters = gridDim.x / kScCL;
+  if (!cluster_split_reduce<float, kScCL>(part_sm, n * LP, cpart, Y, tickets, blockIdx.x / kScCL, nclusters, &flag))
+    return;
   if (!TAIL) return;
   if (cooperative_groups::this_cluster().block_rank() != 0) return;
   SmallWs<LP> w = carve_small_ws<LP>(dsm, kGaccT);
@@ -253,7 +298,7 @@ cudaError_t set_limit(K kernel, int smem_limit) {
 
 // Stages of the tensor-core column pass that fit in `limit` bytes (0 if none fits).
 int tc_sc_stages(int LP, int64_t n, bool omega, size_t limit) {
-  for (int ns = 4; ns >= 2; --ns)
+  for (int ns = kMaxNS; ns >= 2; --ns)
     if (sc_layout(LP, static_cast<int>(n), omega, ns).total <= limit) return ns;
   return 0;
 }
@@ -285,12 +330,12 @@ cudaError_t prepare_tc_sc_kernels(int smem_limit) {
 // Largest resident grid of this kernel in whole clusters.
 int tc_sc_resident_grid(int LP, int64_t n, int ns) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kCL, 1, 1);
+  cfg.gridDim = dim3(kScCL, 1, 1);
   cfg.blockDim = dim3(kThr, 1, 1);
   cfg.dynamicSmemBytes = tc_sc_smem(LP, n, false, ns);
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = kCL;
+  attr.val.clusterDim.x = kScCL;
   attr.val.clusterDim.y = 1;
   attr.val.clusterDim.z = 1;
   cfg.attrs = &attr;
@@ -300,7 +345,7 @@ int tc_sc_resident_grid(int LP, int64_t n, int ns) {
                             : reinterpret_cast<const void*>(k_tc_sc<32, false, true>);
   if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) nc = 0;
   (void)cudaGetLastError();
-  return nc * kCL;
+  return nc * kScCL;
 }
 
 // tmA: 32-column x 32-row boxes in the 128-byte swizzle with 32-byte atoms; tmZ (when B = Z): LP x 32-row boxes of Z.
