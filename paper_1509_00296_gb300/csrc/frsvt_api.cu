@@ -55,6 +55,13 @@ cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS
                           double* rsum, unsigned* tickets, cudaStream_t st);
 size_t tc_lr_smem(int LP, int64_t n, int ns);
 int tc_lr_stages(int LP, int64_t n, size_t limit);
+size_t gram_core_smem(int LP, int64_t n);
+int gram_resident_grid(int LP, int64_t n);
+cudaError_t prepare_gram_kernels(int smem_limit);
+cudaError_t launch_gram_core(int LP, const float* Z, int64_t m, int64_t n, int grid, const float* Q, double* cpart,
+                             double* G, unsigned* tickets, int l, float tau_host, int tau_from_mu, int update_rp,
+                             int advance_counter, float* Rf, float* Qt, DevState* dst, double rank_tol,
+                             int max_sweeps, cudaStream_t st);
 cudaError_t prepare_tc_kernels(int smem_limit);
 cudaError_t launch_tc_lr(int LP, const CUtensorMap& tmA, int64_t m, int64_t n, int grid, int ns, const float* Q, float* Z,
                          DevState* dst, cudaStream_t st);
@@ -100,6 +107,7 @@ struct frsvt_handle {
   int tma_grid = 8;
   int tc_sc_ns = 0;          // stages of the tensor-core column pass (0: not available)
   int tc_lr_ns = 0;          // stages of the tensor-core row pass
+  int gram_grid = 8;         // CTAs of the Gram / core kernel (whole clusters)
   int tc_sc_grid = 0;
   float* cpart_sc = nullptr;
   double* cpart_lr = nullptr;
@@ -336,10 +344,14 @@ frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t 
                                                          h->cpart_sc, h->Ys, h->tickets, l, 0, passes, h->Qt, h->Qs,
                                                          tol, st));
     }
-    FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_tp_lr(LP, true, tmAl, m, n, rpl, G, nst, h->Qs, h->Zl, h->cpart_lr,
-                                                   h->Gfin, h->tickets, l, tau_host, tau_from_mu, update_rp,
-                                                   advance_counter, h->Rf, h->Qt, h->dst, tol,
-                                                   h->cfg.max_jacobi_sweeps, st));
+    // Projection B^T = Z = A Q on the tensor cores, then B B^T = Z^T Z and the core (steps 16-19).
+    FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_tc_lr(LP, tmAs, m, n, h->sms, h->tc_lr_ns, h->Qs, h->Zl, h->dst, st));
+    FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_gram_core(LP, h->Zl, m, n, h->gram_grid, h->Qs, h->cpart_lr, h->Gfin,
+                                                    h->tickets, l, tau_host, tau_from_mu, update_rp, advance_counter,
+                                                    h->Rf, h->Qt, h->dst, tol, h->cfg.max_jacobi_sweeps, st));
+    (void)rpl;
+    (void)nst;
+    (void)tmAl;
     return FRSVT_OK;
   }
   if (h->fused) {
@@ -451,7 +463,8 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
       prepare_fused_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
       prepare_tma_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
       prepare_tc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
-      prepare_tc_sc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
+      prepare_tc_sc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
+      prepare_gram_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
     delete h;
     return FRSVT_ERR_CUDA;
   }
@@ -483,6 +496,8 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
     const int64_t nt = cfg->n_max < 256 ? cfg->n_max : 256;
     const int nst = tma_lr_stages(h->LP, nt, kSmemLimit - 16384);
     h->tc_lr_ns = tc_lr_stages(h->LP, nt, kSmemLimit - 2048);
+    h->gram_grid = gram_resident_grid(h->LP, nt);
+    if (h->gram_grid < 8) h->gram_grid = 8;
     h->tma = tensor_map_encoder() != nullptr && nst >= 2 && h->tc_lr_ns >= 2 &&
              tma_sc_smem(h->LP, nt) <= kSmemLimit - 8192 &&
              tma_lr_smem(h->LP, nt, nst) <= kSmemLimit - 8192 && tma_alm_smem(h->LP, nt) <= kSmemLimit - 8192;

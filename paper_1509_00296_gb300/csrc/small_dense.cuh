@@ -283,45 +283,62 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
   int* flag = w.iv + 2 * LP;
   block_cholesky<LP>(w, l, rank_tol);
   const int N = (l + 1) / 2 * 2;   // even number of Jacobi columns covering the live ones
-  if (tid == 0) flag[1] = 0;
-  __syncthreads();
   const float tol = 1e-6f;
   int sweeps = 0;
-  for (int sweep = 0; sweep < max_sweeps && N >= 2; ++sweep) {
-    if (tid == 0) flag[0] = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < N - 1; ++rnd) {
-      for (int pw = warp; pw < N / 2; pw += nwarps) {
-        int p, q;
-        rr_pair(rnd, pw, N, p, q);
-        const float xp = (lane < LP) ? Xt[p * LP + lane] : 0.f;
-        const float xq = (lane < LP) ? Xt[q * LP + lane] : 0.f;
-        float alpha = xp * xp, beta = xq * xq, gamma = xp * xq;   // three interleaved butterflies
+  // One-sided Jacobi on the columns of R^T by one warp: lane c holds column c in registers and,
+  // in round rnd of the round-robin schedule, meets partner (2 rnd - c) mod (N - 1) (lane rnd
+  // meets N - 1).  Both lanes of a pair form alpha, beta, gamma with the same operations in
+  // the same order, so they agree bit for bit on the rotation.
+  if (warp == 0) {
+    float x[LP];
 #pragma unroll
-        for (int o = (LP >= 32 ? 16 : LP / 2); o > 0; o >>= 1) {
-          alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
-          beta += __shfl_xor_sync(0xffffffffu, beta, o);
-          gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+    for (int a = 0; a < LP; ++a) x[a] = (lane < N) ? Xt[lane * LP + a] : 0.f;
+    for (int sweep = 0; sweep < max_sweeps && N >= 2; ++sweep) {
+      bool rotated = false;
+      for (int rnd = 0; rnd < N - 1; ++rnd) {
+        int partner;
+        if (lane == N - 1) partner = rnd;
+        else if (lane == rnd) partner = N - 1;
+        else partner = ((2 * rnd - lane) % (N - 1) + (N - 1)) % (N - 1);
+        if (lane >= N) partner = lane;
+        float y[LP];
+#pragma unroll
+        for (int a = 0; a < LP; ++a) y[a] = __shfl_sync(0xffffffffu, x[a], partner);
+        const bool is_p = lane < partner;
+        // own / partner squared norms and the inner product, two partial chains each
+        float so0 = 0.f, so1 = 0.f, sp0 = 0.f, sp1 = 0.f, g0 = 0.f, g1 = 0.f;
+#pragma unroll
+        for (int a = 0; a < LP; a += 2) {
+          so0 = fmaf(x[a], x[a], so0);
+          so1 = fmaf(x[a + 1], x[a + 1], so1);
+          sp0 = fmaf(y[a], y[a], sp0);
+          sp1 = fmaf(y[a + 1], y[a + 1], sp1);
+          g0 = fmaf(x[a], y[a], g0);
+          g1 = fmaf(x[a + 1], y[a + 1], g1);
         }
-        if (fabsf(gamma) > tol * sqrtf(alpha * beta) && alpha > 1e-30f && beta > 1e-30f) {
+        const float so = so0 + so1, sp = sp0 + sp1, gamma = g0 + g1;
+        const float alpha = is_p ? so : sp, beta = is_p ? sp : so;  // column p, column q
+        if (lane < N && partner != lane && fabsf(gamma) > tol * sqrtf(alpha * beta) && alpha > 1e-30f &&
+            beta > 1e-30f) {
           const float zeta = (beta - alpha) / (2.f * gamma);
           const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
           const float c = rsqrtf(1.f + t * t);
-          const float s = c * t;
-          if (lane < LP) {
-            Xt[p * LP + lane] = c * xp - s * xq;
-            Xt[q * LP + lane] = s * xp + c * xq;
-          }
-          if (lane == 0) flag[0] = 1;
+          const float sy = is_p ? -(c * t) : (c * t);           // x_p' = c x_p - s x_q, x_q' = s x_p + c x_q
+#pragma unroll
+          for (int a = 0; a < LP; ++a) x[a] = fmaf(sy, y[a], c * x[a]);
+          rotated = true;
         }
       }
-      __syncthreads();
+      sweeps = sweep + 1;
+      if (!__any_sync(0xffffffffu, rotated)) break;
     }
-    sweeps = sweep + 1;
-    const int any = flag[0];
-    __syncthreads();
-    if (!any) break;
+    if (lane < N)
+#pragma unroll
+      for (int a = 0; a < LP; ++a) Xt[lane * LP + a] = x[a];
+    if (lane == 0) flag[1] = sweeps;
   }
+  __syncthreads();
+  sweeps = flag[1];
   if (tid < LP) {
     float s2 = 0.f;
     for (int a = 0; a < LP; ++a) s2 = fmaf(Xt[tid * LP + a], Xt[tid * LP + a], s2);
