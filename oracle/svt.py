@@ -16,6 +16,13 @@
                      Pinned by reduction to SVT for constant weights and by
                      brute-force minimization of the weighted problem on 4x3
                      inputs with non-descending weights.
+- ``wnnm_weights``   the WNNM weight rule w_j = c sqrt(n) / (sigma_j + eps) of the
+                     patch-group workload (weights from the input's own sigma_j).
+- ``frsvt`` with ``weights``: Alg. 1 with the soft threshold of step 19 replaced
+                     by the weighted one, max(D - w(D), 0), w evaluated on the
+                     approximate singular values D.  Pinned by equality with
+                     ``wsvt`` when rank(A) <= l and with the unweighted ``frsvt``
+                     for constant weights.
 - ``psvt``           partial SVT of the truncated nuclear norm (Table 6, Type B):
                      the k leading singular values are kept, the rest shrunk.
 
@@ -72,6 +79,11 @@ def wsvt(A: np.ndarray, w: np.ndarray):
     return (U * f) @ Vt
 
 
+def wnnm_weights(n: int, c: float, eps: float):
+    """Weight rule of the WNNM patch groups: w_j = c sqrt(n) / (sigma_j + eps), n = columns."""
+    return lambda sig: c * np.sqrt(float(n)) / (np.asarray(sig, dtype=np.float64) + eps)
+
+
 def psvt(A: np.ndarray, tau: float, k: int):
     """Partial SVT for the truncated nuclear norm sum_{i>k} sigma_i (Table 6, Type B)."""
     U, s, Vt = linalg.jacobi_svd(A)
@@ -95,12 +107,15 @@ class FRSVTResult:
 
 def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
           Q_prev: np.ndarray | None = None, rank_tol: float = 1e-12,
-          problem: int = 0) -> FRSVTResult:
+          problem: int = 0, weights=None) -> FRSVTResult:
     """Fast randomized SVT, Alg. 1, on A (m x n) in FP64.
 
     Omega is the (seed, stream, problem) Philox Gaussian matrix with max(m, n)
     rows; under range propagation (Q_prev given and non-empty) only its first
     p = l - |Q_prev| columns are used.  Q_prev lives on the short side of A.
+    With ``weights`` (a callable on the singular values D of B), step 19
+    shrinks by max(D - weights(D), 0) instead of S_tau(D) and r counts
+    D_j > w_j.
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
@@ -140,10 +155,33 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
     # Step 19 / Eq. 6: S_tau(A) ~= (QV) S_tau(D) (HWV)^T.
     QV = Q @ V
     HWV = H @ (W @ V)
-    fD = soft(D, tau)
+    if weights is None:
+        fD = soft(D, tau)
+        r = int(np.sum(D > tau))
+    else:
+        wD = weights(D)
+        fD = np.maximum(D - wD, 0.0)
+        r = int(np.sum(D > wD))
     Xh = (QV * fD) @ HWV.T
-    r = int(np.sum(D > tau))
     keep = min(r, l - 2)
     Q_tilde = np.ascontiguousarray(QV[:, :max(keep, 0)])          # step 21
     X = Xh.T if transposed else Xh
     return FRSVTResult(np.ascontiguousarray(X), Q_tilde, r, D, s, pit)
+
+
+def wsvt_batch(mats, c: float, eps: float, variant: str = "exact", l: int = 12, q: int = 1,
+               seed: int = 0, stream: int = 0):
+    """Weighted SVT of each patch group with the WNNM weights of its own n_i.
+
+    variant "exact": ``wsvt`` with weights from the exact sigma_j; "frsvt": Alg. 1 on the
+    problem with Philox problem index b (its position in the batch) and the weights on D.
+    """
+    out = []
+    for b, A in enumerate(mats):
+        n = A.shape[1]
+        w = wnnm_weights(n, c, eps)
+        if variant == "exact":
+            out.append(wsvt(A, w))
+        else:
+            out.append(frsvt(A, 0.0, l, q, seed, stream, problem=b, weights=w).X)
+    return out

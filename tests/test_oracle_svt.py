@@ -250,6 +250,44 @@ def test_wsvt_brute_force_nondescending_weights(seed):
     assert f(X.ravel()) <= best.fun + 1e-9
 
 
+def test_wnnm_weights_rule():
+    w = svt.wnnm_weights(100, 2.8, 1e-8)(np.array([4.0, 1.0]))
+    assert np.allclose(w, [28.0 / (4.0 + 1e-8), 28.0 / (1.0 + 1e-8)], rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("shape", [(64, 100), (64, 64), (64, 40)])
+def test_weighted_frsvt_equals_wsvt_when_rank_fits(shape):
+    """rank(A) <= l: D are the exact singular values, so the weighted FRSVT is the exact WSVT."""
+    rng = np.random.default_rng(52)
+    m, n = shape
+    A = rng.standard_normal((m, 4)) @ rng.standard_normal((4, n))
+    w = svt.wnnm_weights(n, 2.8, 1e-8)
+    X = svt.frsvt(A, 0.0, 12, 1, 3, 0, problem=5, weights=w).X
+    Xe = svt.wsvt(A, w)
+    assert np.linalg.norm(X - Xe) <= 1e-10 * np.linalg.norm(Xe)
+    # the weights kill some but not all directions: X is neither A nor 0
+    assert 0 < np.linalg.norm(Xe) < np.linalg.norm(A)
+
+
+def test_weighted_frsvt_constant_weights_is_frsvt():
+    rng = np.random.default_rng(53)
+    A = rng.standard_normal((64, 120))
+    a = svt.frsvt(A, 2.5, 12, 1, 7, 1, problem=3)
+    b = svt.frsvt(A, 0.0, 12, 1, 7, 1, problem=3, weights=lambda d: np.full_like(d, 2.5))
+    assert np.array_equal(a.X, b.X) and a.r == b.r
+
+
+def test_wsvt_batch_matches_per_problem_calls():
+    rng = np.random.default_rng(54)
+    mats = [rng.standard_normal((64, n)) for n in (40, 64, 97)]
+    ex = svt.wsvt_batch(mats, 2.8, 1e-8, "exact")
+    fr = svt.wsvt_batch(mats, 2.8, 1e-8, "frsvt", l=12, q=1, seed=9, stream=2)
+    for b, A in enumerate(mats):
+        w = svt.wnnm_weights(A.shape[1], 2.8, 1e-8)
+        assert np.array_equal(ex[b], svt.wsvt(A, w))
+        assert np.array_equal(fr[b], svt.frsvt(A, 0.0, 12, 1, 9, 2, problem=b, weights=w).X)
+
+
 def test_psvt_keeps_leading_values():
     rng = np.random.default_rng(19)
     A = rng.standard_normal((15, 10))
