@@ -52,6 +52,7 @@ typedef enum frsvt_status {
 #define FRSVT_DEV_NOT_CONVERGED  (1u << 1)
 #define FRSVT_DEV_NONFINITE      (1u << 2)
 #define FRSVT_DEV_TIMEOUT        (1u << 3)   /* a bounded wait on an asynchronous copy gave up */
+#define FRSVT_DEV_BAD_PROBLEM    (1u << 4)   /* a batched problem had an unsupported size and was skipped */
 
 typedef enum frsvt_precision {
   FRSVT_PREC_FP32 = 0            /* float32 data, FP32-accurate passes */
@@ -214,6 +215,39 @@ frsvt_status frsvt_svt_noalloc(const float* A, int64_t m, int64_t n, int64_t lda
 
 const char* frsvt_status_string(frsvt_status s);
 const char* frsvt_last_error(const frsvt_handle* h);
+
+/* ------------------------------------------------------------------ batched weighted SVT
+ * Weighted SVT (the WSVT footnote of Sec. 1) of a batch of small independent matrices, the
+ * patch groups of weighted nuclear norm minimisation:
+ *     X_b = U_b max(Sigma_b - w_b, 0) V_b^T,   w_{b,j} = c sqrt(n_b) / (sigma_{b,j} + eps),
+ * with the weights evaluated on the problem's own singular values (non-descending in j, so the
+ * closed form is the exact minimiser of sum_j w_j sigma_j(X) + 1/2 ||X - A_b||_F^2).
+ *   A, X : device arrays of `batch` device pointers; problem b is m x n_b, row-major and
+ *          contiguous (ld = n_b), FP32.  X_b may not alias A_b.  Caller-owned.
+ *   n_i  : device array of the `batch` column counts, 1 <= n_b <= cfg.n_max of the handle.
+ *   m    : rows of every problem, 1 <= m <= 64.
+ *   variant FRSVT_WSVT_EXACT: Gram matrix on the short side and a two-sided Jacobi eigensolver
+ *          (FP32).  FRSVT_WSVT_FRSVT: Alg. 1 per problem with l sketch columns (l <= 32),
+ *          cfg.q power steps, Omega from the Philox stream (cfg.seed, stream 0, problem b),
+ *          double-float Gram / Cholesky and the l x l SVD, the weights applied to D.
+ * One persistent launch on the handle's stream: no allocation, no host synchronisation, so a
+ * call can be captured in a CUDA graph.  A problem with an unsupported size is skipped and sets
+ * FRSVT_DEV_BAD_PROBLEM in the device status.  The launch shape (threads per CTA, CTAs per
+ * SM) is the one frsvt_wsvt_tune chose for the variant, else 256 threads and as many CTAs as fit.
+ * Errors: FRSVT_ERR_INVALID_ARG (null arrays, m, l, c < 0, eps <= 0), FRSVT_ERR_UNSUPPORTED
+ * (m > 64 or n_max too large for shared memory), FRSVT_ERR_CUDA. */
+#define FRSVT_WSVT_EXACT 0
+#define FRSVT_WSVT_FRSVT 1
+frsvt_status frsvt_wsvt(frsvt_handle* h, int32_t batch, const float* const* A, const int32_t* n_i, int32_t m,
+                        float c, float eps, float* const* X, int32_t variant, int32_t l);
+/* Autotuner of frsvt_wsvt: runs the batch with every candidate launch shape (128 / 256 / 512
+ * threads per CTA x 1 .. resident CTAs per SM), timed with CUDA events on the handle's stream
+ * (synchronises; not capturable), and keeps the fastest for `variant` in the handle.  X holds
+ * the result of the last run.  Same arguments and errors as frsvt_wsvt. */
+frsvt_status frsvt_wsvt_tune(frsvt_handle* h, int32_t batch, const float* const* A, const int32_t* n_i, int32_t m,
+                             float c, float eps, float* const* X, int32_t variant, int32_t l);
+/* The launch shape frsvt_wsvt uses for `variant` (ctas_per_sm 0: as many as fit). */
+frsvt_status frsvt_wsvt_get_tuning(const frsvt_handle* h, int32_t variant, int32_t* threads, int32_t* ctas_per_sm);
 
 /* Debug access to stages of the path, for parity tests of single kernels. */
 /* Omega[:rows, :cols] of (seed, stream, problem) into a device buffer (ld = cols). */

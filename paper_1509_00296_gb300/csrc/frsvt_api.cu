@@ -57,6 +57,12 @@ size_t tc_lr_smem(int LP, int64_t n, int ns);
 int tc_lr_stages(int LP, int64_t n, size_t limit);
 size_t gram_core_smem(int LP, int64_t n);
 int gram_resident_grid(int LP, int64_t n);
+size_t wsvt_smem(int variant, int m, int n_max, int LP);
+int wsvt_ctas_per_sm(int variant, int nt, int m, int n_max, int LP);
+cudaError_t launch_wsvt(int variant, int nt, int grid, int LP, const float* const* A, float* const* X,
+                        const int32_t* n, int batch, int m, int n_max, float c, float eps, uint64_t seed,
+                        uint64_t stream, int l, int q, double rank_tol, int max_sweeps, unsigned* next,
+                        DevState* dst, cudaStream_t st);
 cudaError_t prepare_gram_kernels(int smem_limit);
 cudaError_t launch_gram_core(int LP, const float* Z, int64_t m, int64_t n, int grid, const float* Q, double* cpart,
                              double* G, unsigned* tickets, int l, float tau_host, int tau_from_mu, int update_rp,
@@ -108,6 +114,9 @@ struct frsvt_handle {
   int tc_sc_ns = 0;          // stages of the tensor-core column pass (0: not available)
   int tc_lr_ns = 0;          // stages of the tensor-core row pass
   int gram_grid = 8;         // CTAs of the Gram / core kernel (whole clusters)
+  unsigned* wsvt_next = nullptr;   // work counter of the batched WSVT launch
+  int wsvt_nt[2] = {256, 256};     // threads per CTA per variant (autotuner)
+  int wsvt_cps[2] = {0, 0};        // CTAs per SM per variant (0: as many as fit)
   int tc_sc_grid = 0;
   float* cpart_sc = nullptr;
   double* cpart_lr = nullptr;
@@ -408,7 +417,7 @@ void free_all(frsvt_handle* h) {
   h->ev_pool.clear();
   void* ptrs[] = {h->dst, h->Ys,       h->Qs,       h->Qt,        h->Zl,   h->Rf,   h->part,    h->gpart,
                   h->rpart, h->pmax,   h->psum,     h->cpart_sc,  h->cpart_lr, h->cpart_alm, h->Gfin, h->rsum,
-                  h->tickets};
+                  h->tickets, h->wsvt_next};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -530,6 +539,7 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
     alloc(reinterpret_cast<void**>(&h->tickets), sizeof(unsigned) * (ntl + 1));
   }
   alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
+  alloc(reinterpret_cast<void**>(&h->wsvt_next), sizeof(unsigned));
   if (!ok) {
     free_all(h);
     delete h;
@@ -676,6 +686,101 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
     FRSVT_CK(cudaStreamSynchronize(h->stream));
     *residual = v;
   }
+  return FRSVT_OK;
+}
+
+static frsvt_status wsvt_check(frsvt_handle* h, int32_t batch, const float* const* A, const int32_t* n_i, int32_t m,
+                        float c, float eps, float* const* X, int32_t variant, int32_t l) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (batch < 0) return fail(h, FRSVT_ERR_INVALID_ARG, "negative batch");
+  if (variant != FRSVT_WSVT_EXACT && variant != FRSVT_WSVT_FRSVT) return fail(h, FRSVT_ERR_INVALID_ARG, "unknown variant");
+  if (m < 1 || m > 64) return fail(h, FRSVT_ERR_UNSUPPORTED, "batched WSVT serves m in [1, 64]");
+  if (variant == FRSVT_WSVT_FRSVT && (l < 1 || l > 32)) return fail(h, FRSVT_ERR_INVALID_ARG, "l must be in [1, 32]");
+  if (!(c >= 0.f) || !(eps > 0.f)) return fail(h, FRSVT_ERR_INVALID_ARG, "c must be >= 0 and eps > 0");
+  if (batch > 0 && (A == nullptr || X == nullptr || n_i == nullptr))
+    return fail(h, FRSVT_ERR_INVALID_ARG, "A, X and n_i are required");
+  return FRSVT_OK;
+}
+
+static int wsvt_grid(frsvt_handle* h, int variant, int nt, int cps_req, int m, int LP, int batch) {
+  const int occ = wsvt_ctas_per_sm(variant, nt, m, static_cast<int>(h->cfg.n_max), LP);
+  if (occ <= 0) return 0;
+  const int cps = (cps_req > 0 && cps_req < occ) ? cps_req : occ;
+  const int grid = h->sms * cps;
+  return grid < batch ? grid : batch;
+}
+
+frsvt_status frsvt_wsvt(frsvt_handle* h, int32_t batch, const float* const* A, const int32_t* n_i, int32_t m,
+                        float c, float eps, float* const* X, int32_t variant, int32_t l) {
+  frsvt_status s = wsvt_check(h, batch, A, n_i, m, c, eps, X, variant, l);
+  if (s != FRSVT_OK || batch == 0) return s;
+  const int LP = (variant == FRSVT_WSVT_FRSVT && l > 16) ? 32 : 16;
+  const int nt = h->wsvt_nt[variant];
+  const int grid = wsvt_grid(h, variant, nt, h->wsvt_cps[variant], m, LP, batch);
+  if (grid <= 0) return fail(h, FRSVT_ERR_UNSUPPORTED, "batched WSVT problem does not fit in shared memory");
+  FRSVT_CK(launch_wsvt(variant, nt, grid, LP, A, X, n_i, batch, m, static_cast<int>(h->cfg.n_max), c, eps,
+                       h->cfg.seed, 0ull, l, h->cfg.q, h->cfg.rank_tol, h->cfg.max_jacobi_sweeps, h->wsvt_next,
+                       h->dst, h->stream));
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_wsvt_tune(frsvt_handle* h, int32_t batch, const float* const* A, const int32_t* n_i, int32_t m,
+                             float c, float eps, float* const* X, int32_t variant, int32_t l) {
+  frsvt_status s = wsvt_check(h, batch, A, n_i, m, c, eps, X, variant, l);
+  if (s != FRSVT_OK || batch == 0) return s;
+  const int LP = (variant == FRSVT_WSVT_FRSVT && l > 16) ? 32 : 16;
+  cudaEvent_t e0, e1;
+  FRSVT_CK(cudaEventCreate(&e0));
+  FRSVT_CK(cudaEventCreate(&e1));
+  float best = -1.f;
+  int best_nt = h->wsvt_nt[variant], best_cps = h->wsvt_cps[variant];
+  const int nts[3] = {128, 256, 512};
+  for (int nt : nts) {
+    const int occ = wsvt_ctas_per_sm(variant, nt, m, static_cast<int>(h->cfg.n_max), LP);
+    for (int cps = 1; cps <= occ; ++cps) {
+      const int grid = wsvt_grid(h, variant, nt, cps, m, LP, batch);
+      if (grid <= 0) continue;
+      float tot = 0.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaError_t e = launch_wsvt(variant, nt, grid, LP, A, X, n_i, batch, m, static_cast<int>(h->cfg.n_max), c,
+                                    eps, h->cfg.seed, 0ull, l, h->cfg.q, h->cfg.rank_tol, h->cfg.max_jacobi_sweeps,
+                                    h->wsvt_next, h->dst, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess)
+          e = launch_wsvt(variant, nt, grid, LP, A, X, n_i, batch, m, static_cast<int>(h->cfg.n_max), c, eps,
+                          h->cfg.seed, 0ull, l, h->cfg.q, h->cfg.rank_tol, h->cfg.max_jacobi_sweeps, h->wsvt_next,
+                          h->dst, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return fail(h, FRSVT_ERR_CUDA, cudaGetErrorString(e));
+        }
+        tot += ms;
+      }
+      if (best < 0.f || tot < best) {
+        best = tot;
+        best_nt = nt;
+        best_cps = cps;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0.f) return fail(h, FRSVT_ERR_UNSUPPORTED, "no WSVT launch shape fits");
+  h->wsvt_nt[variant] = best_nt;
+  h->wsvt_cps[variant] = best_cps;
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_wsvt_get_tuning(const frsvt_handle* h, int32_t variant, int32_t* threads, int32_t* ctas_per_sm) {
+  if (h == nullptr || threads == nullptr || ctas_per_sm == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (variant != FRSVT_WSVT_EXACT && variant != FRSVT_WSVT_FRSVT) return FRSVT_ERR_INVALID_ARG;
+  *threads = h->wsvt_nt[variant];
+  *ctas_per_sm = h->wsvt_cps[variant];
   return FRSVT_OK;
 }
 

@@ -267,18 +267,16 @@ __device__ __forceinline__ void rr_pair(int rnd, int w, int N, int& p, int& q) {
   if (p > q) { const int t = p; p = q; q = t; }
 }
 
-// Core of Alg. 1 steps 16-21 from the Gram w.G = Z^T Z (LP x LP, leading l x l live).
-// Q: ns x LP (global).  Writes Rf = Q M (ns x LP), the first keep columns of Qt = Q U[:, perm],
-// and the DevState fields r, keep, sigma, status, counter.  Block-wide.
+// SVD of B (B B^T = w.G = Z^T Z, LP x LP, leading l x l live), Alg. 1 steps 16-18: Cholesky
+// R^T R = G, one-sided Jacobi on the columns of R^T.  On return w.vec[0..LP) holds sigma_b,
+// w.U the left singular vectors (column b), w.iv[LP..2LP) the order by descending sigma (perm[k]
+// = index of the k-th largest).  Returns the number of Jacobi sweeps.  Block-wide.
 template <int LP>
-__device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, float tau, int update_rp,
-                           int advance_counter, float* Rf, float* Qt, DevState* dst, double rank_tol,
-                           int max_sweeps) {
+__device__ int core_svd_block(SmallWs<LP>& w, int l, double rank_tol, int max_sweeps) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const int lane = tid & 31, warp = tid >> 5;
   float* Xt = w.Rf32;          // after the Cholesky: Xt[b * LP + a] = R[b][a] (columns of R^T)
   float* sig = w.vec;
-  float* coef = w.vec + LP;
   int* perm = w.iv + LP;
   int* flag = w.iv + 2 * LP;
   block_cholesky<LP>(w, l, rank_tol);
@@ -353,8 +351,24 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
     int rank = 0;
     for (int c = 0; c < LP; ++c) rank += (sig[c] > sig[tid] || (sig[c] == sig[tid] && c < tid)) ? 1 : 0;
     perm[rank] = tid;
-    coef[tid] = (sig[tid] > tau) ? (sig[tid] - tau) / sig[tid] : 0.f;
   }
+  __syncthreads();
+  return sweeps;
+}
+
+// Core of Alg. 1 steps 16-21 from the Gram w.G = Z^T Z (LP x LP, leading l x l live).
+// Q: ns x LP (global).  Writes Rf = Q M (ns x LP), the first keep columns of Qt = Q U[:, perm],
+// and the DevState fields r, keep, sigma, status, counter.  Block-wide.
+template <int LP>
+__device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, float tau, int update_rp,
+                           int advance_counter, float* Rf, float* Qt, DevState* dst, double rank_tol,
+                           int max_sweeps) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float* sig = w.vec;
+  float* coef = w.vec + LP;
+  int* perm = w.iv + LP;
+  const int sweeps = core_svd_block<LP>(w, l, rank_tol, max_sweeps);
+  if (tid < LP) coef[tid] = (sig[tid] > tau) ? (sig[tid] - tau) / sig[tid] : 0.f;
   __syncthreads();
   float* M = w.Cm;
   for (int e = tid; e < LP * LP; e += nt) {

@@ -35,6 +35,7 @@ constexpr uint32_t kDevRankDeficient = 1u << 0;
 constexpr uint32_t kDevNotConverged = 1u << 1;
 constexpr uint32_t kDevNonfinite = 1u << 2;
 constexpr uint32_t kDevTimeout = 1u << 3;
+constexpr uint32_t kDevBadProblem = 1u << 4;
 
 // ------------------------------------------------------------------ launchers
 // All launchers enqueue on `st` (cudaStream_t) and return the launch error.

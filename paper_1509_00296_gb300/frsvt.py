@@ -18,7 +18,8 @@ FRSVT_OK = 0
 STATUS_NAMES = {0: "FRSVT_OK", 1: "FRSVT_ERR_INVALID_ARG", 2: "FRSVT_ERR_UNSUPPORTED", 3: "FRSVT_ERR_ALLOC",
                 4: "FRSVT_ERR_CUDA", 5: "FRSVT_ERR_RANK_DEFICIENT", 6: "FRSVT_ERR_NOT_CONVERGED",
                 7: "FRSVT_ERR_NONFINITE"}
-DEV_RANK_DEFICIENT, DEV_NOT_CONVERGED, DEV_NONFINITE = 1, 2, 4
+DEV_RANK_DEFICIENT, DEV_NOT_CONVERGED, DEV_NONFINITE, DEV_TIMEOUT, DEV_BAD_PROBLEM = 1, 2, 4, 8, 16
+WSVT_EXACT, WSVT_FRSVT = 0, 1
 NPHASE = 10
 
 
@@ -61,6 +62,11 @@ _SIGS = {
     "frsvt_enable_timing": [_P, ctypes.c_int32],
     "frsvt_get_timings": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
     "frsvt_phase_name": [ctypes.c_int32],
+    "frsvt_wsvt": [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P, ctypes.c_int32,
+                   ctypes.c_int32],
+    "frsvt_wsvt_tune": [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P,
+                        ctypes.c_int32, ctypes.c_int32],
+    "frsvt_wsvt_get_tuning": [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "frsvt_debug_rows_tc": [_P, _P, _I64, _I64, _I64, _P, _P],
     "frsvt_debug_cols_tc": [_P, _P, _I64, _I64, _I64, _P, ctypes.c_uint64, ctypes.c_uint64, _P],
     "frsvt_debug_omega": [_P, _I64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P],
@@ -216,6 +222,43 @@ class Handle:
         Y = torch.empty((n, LP), dtype=torch.float32, device=A.device)
         self._chk(lib().frsvt_debug_cols_tc(self._h, _ptr(A), m, n, A.stride(0), _ptr(B), seed, stream, _ptr(Y)))
         return Y
+
+    def wsvt_raw(self, A_ptrs, n_i, m: int, c: float, eps: float, X_ptrs, variant: int = WSVT_EXACT,
+                 l: int = 12, tune: bool = False):
+        """Batched weighted SVT on device arrays: A_ptrs / X_ptrs int64 CUDA tensors of device
+        pointers (problem b: m x n_b row-major contiguous float32), n_i an int32 CUDA tensor."""
+        import torch
+        if A_ptrs.dtype != torch.int64 or X_ptrs.dtype != torch.int64 or n_i.dtype != torch.int32:
+            raise TypeError("A_ptrs / X_ptrs must be int64 and n_i int32 CUDA tensors")
+        batch = int(n_i.numel())
+        fn = lib().frsvt_wsvt_tune if tune else lib().frsvt_wsvt
+        self._chk(fn(self._h, batch, _ptr(A_ptrs), _ptr(n_i), m, c, eps, _ptr(X_ptrs), variant, l))
+
+    def wsvt(self, mats, c: float, eps: float, variant: int = WSVT_EXACT, l: int = 12, out=None,
+             tune: bool = False):
+        """Batched weighted SVT of a list of m x n_b float32 CUDA tensors; returns the list of X_b."""
+        import torch
+        if not mats:
+            return []
+        m = mats[0].shape[0]
+        for t in mats:
+            _check_f32_cuda(t, "A_b")
+            if t.shape[0] != m or not t.is_contiguous():
+                raise TypeError("every A_b must be a contiguous m x n_b tensor with the same m")
+        if out is None:
+            out = [torch.empty_like(t) for t in mats]
+        dev = mats[0].device
+        a = torch.tensor([t.data_ptr() for t in mats], dtype=torch.int64, device=dev)
+        x = torch.tensor([t.data_ptr() for t in out], dtype=torch.int64, device=dev)
+        n = torch.tensor([t.shape[1] for t in mats], dtype=torch.int32, device=dev)
+        self._keep = (a, x, n)                 # alive until the asynchronous launch has read them
+        self.wsvt_raw(a, n, m, c, eps, x, variant, l, tune)
+        return out
+
+    def wsvt_tuning(self, variant: int = WSVT_EXACT):
+        nt, cps = ctypes.c_int32(), ctypes.c_int32()
+        self._chk(lib().frsvt_wsvt_get_tuning(self._h, variant, ctypes.byref(nt), ctypes.byref(cps)))
+        return nt.value, cps.value
 
     def sigma(self):
         buf = (ctypes.c_float * 32)()
