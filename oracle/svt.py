@@ -23,6 +23,9 @@
                      approximate singular values D.  Pinned by equality with
                      ``wsvt`` when rank(A) <= l and with the unweighted ``frsvt``
                      for constant weights.
+- ``svt_vjp``        adjoint of the exact SVT (divided-difference form of the derivative
+                     of a spectral function, and the tau derivative).  Pinned by central
+                     finite differences of ``exact_svt`` in FP64.
 - ``psvt``           partial SVT of the truncated nuclear norm (Table 6, Type B):
                      the k leading singular values are kept, the rest shrunk.
 
@@ -185,3 +188,55 @@ def wsvt_batch(mats, c: float, eps: float, variant: str = "exact", l: int = 12, 
         else:
             out.append(frsvt(A, 0.0, l, q, seed, stream, problem=b, weights=w).X)
     return out
+
+
+def svt_vjp(A: np.ndarray, tau: float, Xbar: np.ndarray):
+    """Adjoint of the exact SVT X = S_tau(A) (Def. 1): returns (Abar, taubar) for the cotangent Xbar.
+
+    With A = U diag(sigma) V^T (thin, k = min(m, n)), f_i = max(sigma_i - tau, 0) and
+    Ubar = U^T Xbar V, the divided-difference form of the derivative of a spectral function:
+        Abar = U K V^T + (I - U U^T) Xbar V diag(f / sigma) + U diag(f / sigma) U^T Xbar (I - V V^T),
+        K_ij = Gs_ij sym(Ubar)_ij + Gk_ij skew(Ubar)_ij (i != j),  K_ii = f'(sigma_i) Ubar_ii,
+        Gs_ij = (f_i - f_j) / (sigma_i - sigma_j)  (f' where the two coincide),
+        Gk_ij = (f_i + f_j) / (sigma_i + sigma_j),
+    and taubar = -sum_{sigma_i > tau} Ubar_ii (df_i / dtau = -1 above the threshold).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    Xbar = np.asarray(Xbar, dtype=np.float64)
+    U, s, Vt = linalg.jacobi_svd(A)
+    V = Vt.T
+    f = np.maximum(s - tau, 0.0)
+    fp = (s > tau).astype(np.float64)
+    Ub = U.T @ Xbar @ V
+    sym = 0.5 * (Ub + Ub.T)
+    skw = 0.5 * (Ub - Ub.T)
+    k = s.size
+    Gs = np.empty((k, k))
+    Gk = np.zeros((k, k))
+    for i in range(k):
+        for j in range(k):
+            d = s[i] - s[j]
+            Gs[i, j] = (f[i] - f[j]) / d if abs(d) > 1e-12 * max(s[0], 1e-300) else 0.5 * (fp[i] + fp[j])
+            if s[i] + s[j] > 0:
+                Gk[i, j] = (f[i] + f[j]) / (s[i] + s[j])
+    K = Gs * sym + Gk * skw
+    K[np.diag_indices(k)] = fp * np.diag(Ub)
+    D = np.where(s > 0, f / np.where(s > 0, s, 1.0), 0.0)
+    Abar = U @ K @ V.T
+    Abar += (Xbar @ V - U @ (U.T @ Xbar @ V)) * D[None, :] @ V.T
+    Abar += U @ (D[:, None] * (U.T @ Xbar - (U.T @ Xbar @ V) @ V.T))
+    taubar = -float(np.sum(np.diag(Ub)[s > tau]))
+    return Abar, taubar
+
+
+def frsvt_directional_fd(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
+                         Xbar: np.ndarray, E: np.ndarray, h: float = 1e-3, dtau: float = 0.0) -> float:
+    """Central difference of <Xbar, FRSVT(A, tau)> along (E, dtau) with the same Omega.
+
+    The FRSVT map with a fixed Omega is what a backward pass of Alg. 1 differentiates; it is
+    smooth where no singular value of B sits at tau (the shrinkage kink) and the sketch keeps
+    its rank.
+    """
+    fp = frsvt(A + h * E, tau + h * dtau, l, q, seed, stream).X
+    fm = frsvt(A - h * E, tau - h * dtau, l, q, seed, stream).X
+    return float(np.sum(Xbar * (fp - fm)) / (2.0 * h))

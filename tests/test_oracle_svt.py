@@ -296,3 +296,52 @@ def test_psvt_keeps_leading_values():
     sx = np.linalg.svd(X, compute_uv=False)
     assert abs(sx[0] - s[0]) < 1e-12 * s[0]
     assert np.allclose(np.sort(sx[1:])[::-1][: np.sum(s[1:] > 0.8)], (s[1:] - 0.8)[s[1:] > 0.8], atol=1e-12)
+
+
+# ---------------------------------------------------------------- SVT adjoint
+
+@pytest.mark.parametrize("shape", [(7, 5), (5, 7), (6, 6)])
+def test_svt_vjp_matches_central_differences(shape):
+    """<Abar, E> and taubar against central differences of exact_svt (FP64, h = 1e-6)."""
+    rng = np.random.default_rng(61)
+    m, n = shape
+    A = rng.standard_normal((m, n))
+    s = np.linalg.svd(A, compute_uv=False)
+    tau = 0.5 * (s[1] + s[2])                     # away from every sigma_i
+    Xbar = rng.standard_normal((m, n))
+    Abar, taubar = svt.svt_vjp(A, tau, Xbar)
+    h = 1e-6
+    for _ in range(4):
+        E = rng.standard_normal((m, n))
+        fd = np.sum(Xbar * (svt.exact_svt(A + h * E, tau)[0] - svt.exact_svt(A - h * E, tau)[0])) / (2 * h)
+        assert abs(np.sum(Abar * E) - fd) < 1e-6 * max(1.0, abs(fd))
+    fdt = np.sum(Xbar * (svt.exact_svt(A, tau + h)[0] - svt.exact_svt(A, tau - h)[0])) / (2 * h)
+    assert abs(taubar - fdt) < 1e-6 * max(1.0, abs(fdt))
+
+
+def test_svt_vjp_full_gradient_entrywise():
+    """Every entry of Abar against a one-entry central difference on a 4 x 3 input."""
+    rng = np.random.default_rng(62)
+    A = rng.standard_normal((4, 3)) * 2
+    s = np.linalg.svd(A, compute_uv=False)
+    tau = 0.5 * (s[0] + s[1])
+    Xbar = rng.standard_normal((4, 3))
+    Abar, _ = svt.svt_vjp(A, tau, Xbar)
+    h = 1e-6
+    for i in range(4):
+        for j in range(3):
+            E = np.zeros((4, 3))
+            E[i, j] = 1.0
+            fd = np.sum(Xbar * (svt.exact_svt(A + h * E, tau)[0] - svt.exact_svt(A - h * E, tau)[0])) / (2 * h)
+            assert abs(Abar[i, j] - fd) < 1e-6
+
+
+def test_svt_vjp_tau_zero_is_identity_map():
+    """tau = 0 (all sigma > 0): X = A, so Abar = Xbar and taubar = -trace(U^T Xbar V)."""
+    rng = np.random.default_rng(63)
+    A = rng.standard_normal((6, 4))
+    Xbar = rng.standard_normal((6, 4))
+    Abar, taubar = svt.svt_vjp(A, 0.0, Xbar)
+    assert np.allclose(Abar, Xbar, atol=1e-12)
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    assert abs(taubar + np.trace(U.T @ Xbar @ Vt.T)) < 1e-12
