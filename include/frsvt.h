@@ -58,6 +58,8 @@ typedef enum frsvt_precision {
   FRSVT_PREC_FP32 = 0            /* float32 data, FP32-accurate passes */
 } frsvt_precision;
 
+#define FRSVT_CFG_ADJOINT 1      /* allocate the workspace of frsvt_svt_save / frsvt_backward */
+
 typedef struct frsvt_config {
   int64_t m_max;                 /* largest row count served by the handle */
   int64_t n_max;                 /* largest column count served by the handle */
@@ -67,7 +69,7 @@ typedef struct frsvt_config {
   int32_t precision;             /* frsvt_precision */
   uint64_t seed;                 /* Philox4x64-10 key of Omega */
   int32_t max_jacobi_sweeps;     /* cap of the l x l Jacobi SVD (<= 0: 30) */
-  int32_t reserved;
+  int32_t flags;                 /* FRSVT_CFG_* bits */
   double rank_tol;               /* relative pivot cut of the Cholesky QR (<= 0: 1e-12) */
 } frsvt_config;
 
@@ -215,6 +217,36 @@ frsvt_status frsvt_svt_noalloc(const float* A, int64_t m, int64_t n, int64_t lda
 
 const char* frsvt_status_string(frsvt_status s);
 const char* frsvt_last_error(const frsvt_handle* h);
+
+/* ------------------------------------------------------------------ adjoint (backward pass)
+ * Differentiation of the FRSVT map with a fixed Omega, X = FRSVT_tau(A) of Alg. 1 (steps 3-19:
+ * Gaussian sketch, q power steps with re-orthonormalisation, projection, l x l SVD, shrinkage,
+ * reconstruction), for the tall orientation m >= n; the basis Q lives on the column side.
+ * The handle must be created with FRSVT_CFG_ADJOINT in cfg.flags (this allocates the backward
+ * workspace); n <= 2048 (l <= 16) or n <= 1024 (l <= 32).
+ *
+ * frsvt_adjoint_saved_bytes: size of the device buffer `saved` for an m x n problem (it holds
+ *   Q_i and R_i of the q + 1 CholeskyQR2 factorisations, U_B, sigma and V_B).
+ * frsvt_svt_save: X = FRSVT_tau(A) with Omega from the Philox stream (cfg.seed, omega_stream),
+ *   every orthonormalisation by CholeskyQR2, and the factors written to `saved` (caller-owned
+ *   device memory of frsvt_adjoint_saved_bytes).  Range propagation is not used here.
+ * frsvt_backward: given dX (m x n, the cotangent of X), writes dA (m x n, overwritten) and *dtau
+ *   (one float in device memory): the vector-Jacobian product of the same map, with the
+ *   divided-difference adjoint of the shrinkage on B (Gs_ij = (f_i - f_j) / (sigma_i - sigma_j),
+ *   replaced by the mean of f' where sigma_i and sigma_j coincide: the gap regularisation of the
+ *   1 / (sigma_j^2 - sigma_i^2) term), the QR adjoint Ybar = (Qbar - Q copyltu(Qbar^T Q)) R^{-T}
+ *   through each CholeskyQR2, and the recomputed power-step products.  A, tau, l and
+ *   omega_stream must be those of the frsvt_svt_save call that wrote `saved`.
+ * All pointers are device pointers; row-major; lda, ldx >= n.  Asynchronous on the handle's
+ * stream, no allocation.  Errors: FRSVT_ERR_INVALID_ARG, FRSVT_ERR_UNSUPPORTED (no adjoint
+ * workspace, m < n, size limits), FRSVT_ERR_CUDA.  Rank deficiency of a sketch sets
+ * FRSVT_DEV_RANK_DEFICIENT (the QR adjoint then is not defined for the dropped columns). */
+size_t frsvt_adjoint_saved_bytes(const frsvt_handle* h, int64_t m, int64_t n);
+frsvt_status frsvt_svt_save(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, float tau,
+                            int32_t l, uint64_t omega_stream, float* X, int64_t ldx, void* saved);
+frsvt_status frsvt_backward(frsvt_handle* h, const void* saved, const float* A, int64_t m, int64_t n, int64_t lda,
+                            float tau, int32_t l, uint64_t omega_stream, const float* dX, int64_t lddx, float* dA,
+                            int64_t ldda, float* dtau);
 
 /* ------------------------------------------------------------------ batched weighted SVT
  * Weighted SVT (the WSVT footnote of Sec. 1) of a batch of small independent matrices, the

@@ -58,6 +58,24 @@ int tc_lr_stages(int LP, int64_t n, size_t limit);
 size_t gram_core_smem(int LP, int64_t n);
 int gram_resident_grid(int LP, int64_t n);
 size_t wsvt_smem(int variant, int m, int n_max, int LP);
+int ad_col_splits(int64_t m, int n);
+cudaError_t prepare_adjoint_kernels(int smem_limit);
+cudaError_t ad_rows(int LP, const float* M, int64_t ldm, int64_t m, int n, const float* S, float* C, int ldc, int coff,
+                    float beta, cudaStream_t st);
+cudaError_t ad_cols(int LP, const float* M, int64_t ldm, int64_t m, int n, const float* T, int ldt, double* part,
+                    float* out, double* out_d, int ldo, int coff, float beta, cudaStream_t st);
+cudaError_t ad_rank(float* A, int64_t lda, int64_t m, int n, const float* L, int ldl, const float* R, int ldr, int K,
+                    float beta, cudaStream_t st);
+cudaError_t ad_omega(int LP, float* out, int ldo, int coff, int64_t m, int l, uint64_t seed, uint64_t stream,
+                     cudaStream_t st);
+cudaError_t ad_cholqr2(int LP, const float* Y, int n, int l, double rank_tol, float* Q, double* Qd, float* R,
+                       DevState* dst, cudaStream_t st);
+cudaError_t ad_core(int LP, const float* Z, int64_t m, int l, float tau, double rank_tol, int max_sweeps, float* U,
+                    float* sig, float* S1, float* S2, DevState* dst, cudaStream_t st);
+cudaError_t ad_svt_adjoint(int LP, const float* W1, const float* U, const float* sig, int l, float tau, float* C1,
+                           float* C2, float* C3, float* taubar, cudaStream_t st);
+cudaError_t ad_qr_adjoint(int LP, const double* Q, const float* R, const double* Qbar, int n, int l, float* Ybar,
+                          cudaStream_t st);
 int wsvt_ctas_per_sm(int variant, int nt, int m, int n_max, int LP);
 cudaError_t launch_wsvt(int variant, int nt, int grid, int LP, const float* const* A, float* const* X,
                         const int32_t* n, int batch, int m, int n_max, float c, float eps, uint64_t seed,
@@ -115,6 +133,8 @@ struct frsvt_handle {
   int tc_lr_ns = 0;          // stages of the tensor-core row pass
   int gram_grid = 8;         // CTAs of the Gram / core kernel (whole clusters)
   unsigned* wsvt_next = nullptr;   // work counter of the batched WSVT launch
+  float* ad_ws = nullptr;          // adjoint workspace (FRSVT_CFG_ADJOINT)
+  int ad_K = 0;                    // columns of the stacked rank-update factors
   int wsvt_nt[2] = {256, 256};     // threads per CTA per variant (autotuner)
   int wsvt_cps[2] = {0, 0};        // CTAs per SM per variant (0: as many as fit)
   int tc_sc_grid = 0;
@@ -417,9 +437,82 @@ void free_all(frsvt_handle* h) {
   h->ev_pool.clear();
   void* ptrs[] = {h->dst, h->Ys,       h->Qs,       h->Qt,        h->Zl,   h->Rf,   h->part,    h->gpart,
                   h->rpart, h->pmax,   h->psum,     h->cpart_sc,  h->cpart_lr, h->cpart_alm, h->Gfin, h->rsum,
-                  h->tickets, h->wsvt_next};
+                  h->tickets, h->wsvt_next, h->ad_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+}
+
+// Adjoint workspace (floats): L (m x K), R (n x K), P, T, Z (m x LP each), Yb, Y, RQ (n x LP
+// each), small (16 x LP x LP), then doubles: Qbar (n x LP) and column-pass partials (64 x n x LP).
+struct AdWs {
+  float *L, *R, *P, *T, *Z, *Y, *Yb, *RQ, *W1, *C1, *C2, *C3, *S1, *S2;
+  double *Qb, *part;
+};
+
+int64_t ad_ws_floats(const frsvt_handle* h, int64_t m, int64_t n) {
+  const int64_t LP = h->LP, K = h->ad_K;
+  const int64_t f = m * K + n * K + 4 * m * LP + 4 * n * LP + 16 * LP * LP;
+  return (f + 1) / 2 * 2 + 2 * (n * LP + 64 * (n > LP ? n : LP) * LP);
+}
+
+AdWs ad_carve(const frsvt_handle* h, int64_t m, int64_t n) {
+  const int64_t LP = h->LP, K = h->ad_K;
+  float* p = h->ad_ws;
+  AdWs w;
+  w.L = p; p += m * K;
+  w.R = p; p += n * K;
+  w.P = p; p += m * LP;
+  w.T = p; p += m * LP;
+  w.Z = p; p += m * LP;
+  p += m * LP;                        // spare m x LP block
+  w.Y = p; p += n * LP;
+  p += n * LP;                        // spare n x LP block
+  w.Yb = p; p += n * LP;
+  w.RQ = p; p += n * LP;
+  w.W1 = p; p += LP * LP;
+  w.C1 = p; p += LP * LP;
+  w.C2 = p; p += LP * LP;
+  w.C3 = p; p += LP * LP;
+  w.S1 = p; p += LP * LP;
+  w.S2 = p; p += LP * LP;
+  const int64_t used = p - h->ad_ws;
+  double* d = reinterpret_cast<double*>(h->ad_ws + (used + 1) / 2 * 2);
+  w.Qb = d;
+  w.part = d + n * LP;
+  return w;
+}
+
+// Saved buffer: Qd_0..Qd_q (double, n x LP each), then floats Q_0..Q_q, R_0..R_q, U, sigma, V_B.
+struct AdSaved {
+  double* Qd;
+  float *Q, *R, *U, *sig, *VB;
+};
+
+size_t ad_saved_floats(const frsvt_handle* h, int64_t m, int64_t n) {
+  const int64_t LP = h->LP, q1 = h->cfg.q + 1;
+  return static_cast<size_t>(2 * q1 * n * LP + q1 * n * LP + q1 * LP * LP + LP * LP + LP + m * LP);
+}
+
+AdSaved ad_saved(const frsvt_handle* h, float* base, int64_t n) {
+  const int64_t LP = h->LP, q1 = h->cfg.q + 1;
+  AdSaved s;
+  s.Qd = reinterpret_cast<double*>(base);
+  s.Q = base + 2 * q1 * n * LP;
+  s.R = s.Q + q1 * n * LP;
+  s.U = s.R + q1 * LP * LP;
+  s.sig = s.U + LP * LP;
+  s.VB = s.sig + LP;
+  return s;
+}
+
+frsvt_status ad_check(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int32_t l) {
+  if (h->ad_ws == nullptr) return fail(h, FRSVT_ERR_UNSUPPORTED, "handle created without FRSVT_CFG_ADJOINT");
+  frsvt_status s = check_shape(h, m, n);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, A, m, n, lda, "A")) != FRSVT_OK) return s;
+  if (l < 1 || l > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "l must be in [1, l_max]");
+  if (n > (h->LP == 16 ? 2048 : 1024)) return fail(h, FRSVT_ERR_UNSUPPORTED, "the adjoint path serves n <= 2048 / 1024");
+  return FRSVT_OK;
 }
 
 }  // namespace
@@ -473,7 +566,8 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
       prepare_tma_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
       prepare_tc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
       prepare_tc_sc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
-      prepare_gram_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
+      prepare_gram_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
+      prepare_adjoint_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
     delete h;
     return FRSVT_ERR_CUDA;
   }
@@ -540,6 +634,10 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   }
   alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
   alloc(reinterpret_cast<void**>(&h->wsvt_next), sizeof(unsigned));
+  if (cfg->flags & FRSVT_CFG_ADJOINT) {
+    h->ad_K = static_cast<int>(LP) * (2 + 2 * h->cfg.q);
+    alloc(reinterpret_cast<void**>(&h->ad_ws), sizeof(float) * ad_ws_floats(h, cfg->m_max, cfg->n_max));
+  }
   if (!ok) {
     free_all(h);
     delete h;
@@ -781,6 +879,95 @@ frsvt_status frsvt_wsvt_get_tuning(const frsvt_handle* h, int32_t variant, int32
   if (variant != FRSVT_WSVT_EXACT && variant != FRSVT_WSVT_FRSVT) return FRSVT_ERR_INVALID_ARG;
   *threads = h->wsvt_nt[variant];
   *ctas_per_sm = h->wsvt_cps[variant];
+  return FRSVT_OK;
+}
+
+size_t frsvt_adjoint_saved_bytes(const frsvt_handle* h, int64_t m, int64_t n) {
+  if (h == nullptr || m < 0 || n < 0) return 0;
+  return ad_saved_floats(h, m, n) * sizeof(float);
+}
+
+frsvt_status frsvt_svt_save(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, float tau,
+                            int32_t l, uint64_t omega_stream, float* X, int64_t ldx, void* saved) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = ad_check(h, A, m, n, lda, l);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, X, m, n, ldx, "X")) != FRSVT_OK) return s;
+  if (saved == nullptr) return fail(h, FRSVT_ERR_INVALID_ARG, "saved is required");
+  if (!(tau >= 0.f)) return fail(h, FRSVT_ERR_INVALID_ARG, "tau must be >= 0");
+  if (m == 0 || n == 0) return FRSVT_OK;
+  const int LP = h->LP, q = h->cfg.q, nn = static_cast<int>(n);
+  cudaStream_t st = h->stream;
+  AdWs w = ad_carve(h, m, n);
+  AdSaved sv = ad_saved(h, static_cast<float*>(saved), n);
+  const double tol = h->cfg.rank_tol;
+  FRSVT_CK(ad_omega(LP, w.Z, LP, 0, m, l, h->cfg.seed, omega_stream, st));                  // Omega (m x LP)
+  FRSVT_CK(ad_cols(LP, A, lda, m, nn, w.Z, LP, w.part, w.Y, nullptr, LP, 0, 0.f, st));       // Y_0 = A^T Omega
+  FRSVT_CK(ad_cholqr2(LP, w.Y, nn, l, tol, sv.Q, sv.Qd, sv.R, h->dst, st));
+  for (int i = 1; i <= q; ++i) {
+    const float* Qp = sv.Q + static_cast<int64_t>(i - 1) * n * LP;
+    FRSVT_CK(ad_rows(LP, A, lda, m, nn, Qp, w.Z, LP, 0, 0.f, st));                          // Z_i = A Q_{i-1}
+    FRSVT_CK(ad_cols(LP, A, lda, m, nn, w.Z, LP, w.part, w.Y, nullptr, LP, 0, 0.f, st));     // Y_i = A^T Z_i
+    FRSVT_CK(ad_cholqr2(LP, w.Y, nn, l, tol, sv.Q + static_cast<int64_t>(i) * n * LP,
+                        sv.Qd + static_cast<int64_t>(i) * n * LP, sv.R + static_cast<int64_t>(i) * LP * LP, h->dst,
+                        st));
+  }
+  const float* Qf = sv.Q + static_cast<int64_t>(q) * n * LP;
+  FRSVT_CK(ad_rows(LP, A, lda, m, nn, Qf, w.Z, LP, 0, 0.f, st));                              // Z = A Q = B^T
+  FRSVT_CK(ad_core(LP, w.Z, m, l, tau, tol, h->cfg.max_jacobi_sweeps, sv.U, sv.sig, w.S1, w.S2, h->dst, st));
+  FRSVT_CK(ad_rows(LP, w.Z, LP, m, LP, w.S1, sv.VB, LP, 0, 0.f, st));                         // V_B = Z U / sigma
+  FRSVT_CK(ad_rows(LP, Qf, LP, n, LP, w.S2, w.RQ, LP, 0, 0.f, st));                           // Q U diag(f)
+  FRSVT_CK(ad_rank(X, ldx, m, nn, sv.VB, LP, w.RQ, LP, LP, 0.f, st));                          // X = V_B (Q U f)^T
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_backward(frsvt_handle* h, const void* saved, const float* A, int64_t m, int64_t n, int64_t lda,
+                            float tau, int32_t l, uint64_t omega_stream, const float* dX, int64_t lddx, float* dA,
+                            int64_t ldda, float* dtau) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = ad_check(h, A, m, n, lda, l);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, dX, m, n, lddx, "dX")) != FRSVT_OK) return s;
+  if ((s = check_matrix(h, dA, m, n, ldda, "dA")) != FRSVT_OK) return s;
+  if (saved == nullptr || dtau == nullptr) return fail(h, FRSVT_ERR_INVALID_ARG, "saved and dtau are required");
+  if (m == 0 || n == 0) return FRSVT_OK;
+  const int LP = h->LP, q = h->cfg.q, nn = static_cast<int>(n), K = h->ad_K;
+  cudaStream_t st = h->stream;
+  AdWs w = ad_carve(h, m, n);
+  AdSaved sv = ad_saved(h, static_cast<float*>(const_cast<void*>(saved)), n);
+  const float* Qf = sv.Q + static_cast<int64_t>(q) * n * LP;
+  auto copy_cols = [&](float* dst, int ldd, int coff, const float* src, int64_t rows) {
+    return cudaMemcpy2DAsync(dst + coff, sizeof(float) * ldd, src, sizeof(float) * LP, sizeof(float) * LP, rows,
+                             cudaMemcpyDeviceToDevice, st);
+  };
+  // SVT adjoint on B
+  FRSVT_CK(ad_rows(LP, dX, lddx, m, nn, Qf, w.P, LP, 0, 0.f, st));                            // P = dX Q
+  FRSVT_CK(ad_cols(LP, sv.VB, LP, m, LP, w.P, LP, w.part, w.W1, nullptr, LP, 0, 0.f, st));    // W1 = V_B^T P
+  FRSVT_CK(ad_svt_adjoint(LP, w.W1, sv.U, sv.sig, l, tau, w.C1, w.C2, w.C3, dtau, st));
+  FRSVT_CK(ad_rows(LP, sv.VB, LP, m, LP, w.C1, w.L, K, 0, 0.f, st));                          // Bbar^T ...
+  FRSVT_CK(ad_rows(LP, w.P, LP, m, LP, w.C2, w.L, K, 0, 1.f, st));                            // ... + P C2
+  FRSVT_CK(copy_cols(w.R, K, 0, Qf, n));                                                      // dA += Bbar^T Q^T
+  FRSVT_CK(ad_rows(LP, sv.VB, LP, m, LP, w.C3, w.T, LP, 0, 0.f, st));                         // V_B diag(f) U^T
+  FRSVT_CK(ad_cols(LP, dX, lddx, m, nn, w.T, LP, w.part, nullptr, w.Qb, LP, 0, 0.f, st));      // Qbar = dX^T ...
+  FRSVT_CK(ad_cols(LP, A, lda, m, nn, w.L, K, w.part, nullptr, w.Qb, LP, 0, 1.f, st));         // ... + A^T Bbar^T
+  // power steps, last to first
+  for (int i = q; i >= 1; --i) {
+    const float* Ri = sv.R + static_cast<int64_t>(i) * LP * LP;
+    const float* Qp = sv.Q + static_cast<int64_t>(i - 1) * n * LP;
+    const int b1 = 1 + 2 * (q - i), b2 = b1 + 1;
+    FRSVT_CK(ad_qr_adjoint(LP, sv.Qd + static_cast<int64_t>(i) * n * LP, Ri, w.Qb, nn, l, w.Yb, st));  // Ybar_i
+    FRSVT_CK(ad_rows(LP, A, lda, m, nn, Qp, w.L, K, b1 * LP, 0.f, st));                          // Z_i (recomputed)
+    FRSVT_CK(copy_cols(w.R, K, b1 * LP, w.Yb, n));                                              // dA += Z_i Ybar_i^T
+    FRSVT_CK(ad_rows(LP, A, lda, m, nn, w.Yb, w.L, K, b2 * LP, 0.f, st));                        // Zbar_i = A Ybar_i
+    FRSVT_CK(copy_cols(w.R, K, b2 * LP, Qp, n));                                                // dA += Zbar_i Q_{i-1}^T
+    FRSVT_CK(ad_cols(LP, A, lda, m, nn, w.L + b2 * LP, K, w.part, nullptr, w.Qb, LP, 0, 0.f, st));  // Qbar_{i-1}
+  }
+  // sketch
+  const int bl = 1 + 2 * q;
+  FRSVT_CK(ad_qr_adjoint(LP, sv.Qd, sv.R, w.Qb, nn, l, w.Yb, st));                              // Ybar_0
+  FRSVT_CK(ad_omega(LP, w.L, K, bl * LP, m, l, h->cfg.seed, omega_stream, st));                // Omega
+  FRSVT_CK(copy_cols(w.R, K, bl * LP, w.Yb, n));                                                // dA += Omega Ybar_0^T
+  FRSVT_CK(ad_rank(dA, ldda, m, nn, w.L, K, w.R, K, K, 0.f, st));
   return FRSVT_OK;
 }
 

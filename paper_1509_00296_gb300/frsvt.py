@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "FRSVT_OK", 1: "FRSVT_ERR_INVALID_ARG", 2: "FRSVT_ERR_UNSUPPO
                 7: "FRSVT_ERR_NONFINITE"}
 DEV_RANK_DEFICIENT, DEV_NOT_CONVERGED, DEV_NONFINITE, DEV_TIMEOUT, DEV_BAD_PROBLEM = 1, 2, 4, 8, 16
 WSVT_EXACT, WSVT_FRSVT = 0, 1
+CFG_ADJOINT = 1
 NPHASE = 10
 
 
@@ -32,7 +33,7 @@ class FrsvtError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("m_max", ctypes.c_int64), ("n_max", ctypes.c_int64), ("l_max", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("range_prop", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("max_jacobi_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("max_jacobi_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("rank_tol", ctypes.c_double)]
 
 
@@ -62,6 +63,9 @@ _SIGS = {
     "frsvt_enable_timing": [_P, ctypes.c_int32],
     "frsvt_get_timings": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
     "frsvt_phase_name": [ctypes.c_int32],
+    "frsvt_svt_save": [_P, _P, _I64, _I64, _I64, ctypes.c_float, ctypes.c_int32, ctypes.c_uint64, _P, _I64, _P],
+    "frsvt_backward": [_P, _P, _P, _I64, _I64, _I64, ctypes.c_float, ctypes.c_int32, ctypes.c_uint64, _P, _I64, _P,
+                       _I64, _P],
     "frsvt_wsvt": [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P, ctypes.c_int32,
                    ctypes.c_int32],
     "frsvt_wsvt_tune": [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P,
@@ -86,6 +90,8 @@ def lib():
             fn.argtypes = args
             fn.restype = (ctypes.c_char_p if name in ("frsvt_status_string", "frsvt_last_error", "frsvt_phase_name")
                           else ctypes.c_int)
+        L.frsvt_adjoint_saved_bytes.argtypes = [_P, _I64, _I64]
+        L.frsvt_adjoint_saved_bytes.restype = ctypes.c_size_t
         _lib = L
     return _lib
 
@@ -124,8 +130,10 @@ class Handle:
     """An FRSVT handle: workspace, propagated basis and Omega counter (include/frsvt.h)."""
 
     def __init__(self, m_max: int, n_max: int, l_max: int, q: int = 2, range_prop: bool = True,
-                 seed: int = 0, max_jacobi_sweeps: int = 30, rank_tol: float = 1e-12, stream=None):
-        cfg = Config(m_max, n_max, l_max, q, 1 if range_prop else 0, 0, seed, max_jacobi_sweeps, 0, rank_tol)
+                 seed: int = 0, max_jacobi_sweeps: int = 30, rank_tol: float = 1e-12, stream=None,
+                 adjoint: bool = False):
+        cfg = Config(m_max, n_max, l_max, q, 1 if range_prop else 0, 0, seed, max_jacobi_sweeps,
+                     CFG_ADJOINT if adjoint else 0, rank_tol)
         h = _P()
         self._stream = stream
         st = lib().frsvt_create(ctypes.byref(h), ctypes.byref(cfg), _stream_ptr(stream))
@@ -223,6 +231,34 @@ class Handle:
         self._chk(lib().frsvt_debug_cols_tc(self._h, _ptr(A), m, n, A.stride(0), _ptr(B), seed, stream, _ptr(Y)))
         return Y
 
+    def svt_save(self, A, tau: float, l: int, omega_stream: int = 0, X=None, saved=None):
+        """X = FRSVT_tau(A) recording the factors of the backward pass; returns (X, saved)."""
+        import torch
+        _check_f32_cuda(A, "A")
+        m, n = A.shape
+        if X is None:
+            X = torch.empty_like(A)
+        if saved is None:
+            nb = lib().frsvt_adjoint_saved_bytes(self._h, m, n)
+            saved = torch.empty(nb, dtype=torch.uint8, device=A.device)
+        self._chk(lib().frsvt_svt_save(self._h, _ptr(A), m, n, A.stride(0), tau, l, omega_stream, _ptr(X),
+                                       X.stride(0), _ptr(saved)))
+        return X, saved
+
+    def backward(self, saved, A, tau: float, l: int, omega_stream: int, dX, dA=None, dtau=None):
+        """Vector-Jacobian product of the FRSVT map: returns (dA, dtau) for the cotangent dX."""
+        import torch
+        _check_f32_cuda(A, "A")
+        _check_f32_cuda(dX, "dX")
+        m, n = A.shape
+        if dA is None:
+            dA = torch.empty_like(A)
+        if dtau is None:
+            dtau = torch.empty(1, dtype=torch.float32, device=A.device)
+        self._chk(lib().frsvt_backward(self._h, _ptr(saved), _ptr(A), m, n, A.stride(0), tau, l, omega_stream,
+                                       _ptr(dX), dX.stride(0), _ptr(dA), dA.stride(0), _ptr(dtau)))
+        return dA, dtau
+
     def wsvt_raw(self, A_ptrs, n_i, m: int, c: float, eps: float, X_ptrs, variant: int = WSVT_EXACT,
                  l: int = 12, tune: bool = False):
         """Batched weighted SVT on device arrays: A_ptrs / X_ptrs int64 CUDA tensors of device
@@ -310,3 +346,37 @@ def rpca(O, lam=None, l: int = 10, q: int = 2, iters: int = 30, rho: float = 1.5
     info = h.info()
     h.close()
     return L, S, info
+
+
+def _autograd_function():
+    import torch
+
+    class FRSVTFunction(torch.autograd.Function):
+        """X = FRSVT_tau(A) (fixed Omega stream) with the library's adjoint as its backward.
+
+        Inputs: A (m x n float32 CUDA, m >= n), tau (0-d float32 tensor), and non-tensor
+        arguments handle (created with adjoint=True), l, omega_stream.
+        """
+
+        @staticmethod
+        def forward(ctx, A, tau, handle, l, omega_stream):
+            A = A.contiguous()
+            t = float(tau)
+            X, saved = handle.svt_save(A, t, l, omega_stream)
+            ctx.save_for_backward(A, saved)
+            ctx.meta = (handle, t, l, omega_stream)
+            return X
+
+        @staticmethod
+        def backward(ctx, dX):
+            A, saved = ctx.saved_tensors
+            handle, t, l, omega_stream = ctx.meta
+            dA, dtau = handle.backward(saved, A, t, l, omega_stream, dX.contiguous())
+            return dA, dtau.reshape(()), None, None, None
+
+    return FRSVTFunction
+
+
+def frsvt_svt_autograd(A, tau, handle, l: int, omega_stream: int = 0):
+    """Differentiable X = FRSVT_tau(A): gradients with respect to A and tau by the library's adjoint."""
+    return _autograd_function().apply(A, tau, handle, l, omega_stream)
