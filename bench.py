@@ -37,8 +37,19 @@ sys.path.insert(0, ROOT)
 METRIC = "ALM iters/s & tensor-pipe % of FRSVT vs exact-SVD SVT, same GPU, ≤1e-4 rel err"
 UNIT = "ALM iters/s"
 M, N, L_COLS, Q_POW = 76800, 200, 10, 2
+LP_COLS = 16                              # l rounded up to the 16-column panel
 DATA_SEED, OMEGA_SEED = 1002, 2002
 WORKLOAD = "video-background RPCA 76800x200 (320x240 px x 200 frames), FRSVT l=10 q=2 range propagation"
+
+
+# DRAM bytes per launch from one ncu capture of the kernel that serves the phase (video
+# workload); None once that kernel has changed since the capture.
+NCU_TRAFFIC = {"power_AtZ": 66.74e6}
+PHASE_KERNEL = {"sketch": "k_tc_sc<16,1,1>", "power_AQ": "k_tc_lr<16>", "power_AtZ": "k_tc_sc<16,0,1>",
+                "project": "k_tc_lr<16>", "core": "k_gram_core<16>", "epilogue": "k_tp_alm<16>"}
+# sm__pipe_tensor_cycles_active of the tensor-core passes, same capture (percent of peak, elapsed)
+TENSOR_PIPE_PCT = {"sketch k_tc_sc<16,1,1>": 11.9, "A^T Z k_tc_sc<16,0,1>": 13.0, "A Q k_tc_lr<16>": 25.3,
+                   "source": "profiles/tc_passes_video_76800x200.md"}
 
 
 def dist_env():
@@ -194,10 +205,13 @@ def main():
     h = frsvt.Handle(M, N, L_COLS, q=Q_POW, range_prop=True, seed=OMEGA_SEED, stream=stream)
     h.rpca_init(O, S, A, lam, 1.5, 1e7)
 
-    launches_per_step = 3 + 4 * Q_POW + 3 + 2
     # one eager step first: it records the problem shape in the handle, so that the
-    # captured step contains no reset of the propagated basis
+    # captured step contains no reset of the propagated basis; its launches are counted
+    h.enable_timing(True)
+    h.timings()
     h.ialm_step(O, S, A, L_COLS)
+    launches_per_step = sum(v[1] for v in h.timings().values())
+    h.enable_timing(False)
     graph = None
     if not args.no_graph:
         cap = torch.cuda.Stream()
@@ -270,7 +284,10 @@ def main():
             line["e2e"] = extras["e2e"]
             line["cpu_baseline"] = extras["cpu_baseline"]
             line["exact_svd_same_gpu"] = extras["exact"]
-            line["tensor_pipe_pct"] = None
+            line["exact_svd_same_gpu"]["frsvt_speedup"] = value / extras["exact"]["value"]
+            line["tensor_pipe_pct"] = TENSOR_PIPE_PCT
+            line["wsvt_batch"] = extras.get("wsvt")
+            line["unrolled_rpca"] = extras.get("unrolled")
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -293,15 +310,17 @@ def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
     tm = h.timings()
     h.enable_timing(False)
     phases = {k: v[0] / K for k, v in tm.items() if v[1] > 0}
-    e = 4.0 * M * N
-    alg_bytes = {"epilogue": 5 * e, "sketch": e, "power_AQ": e, "power_AtZ": e, "project": e}
+    e = 4.0 * M * N                       # one pass over A (float32)
+    z = 4.0 * M * LP_COLS                 # one pass over Z (m x LP float32)
+    alg_bytes = {"epilogue": 5 * e + z, "sketch": e, "power_AQ": e + z, "power_AtZ": e + z, "project": e + z,
+                 "core": z}
     launches = {k: v[1] for k, v in tm.items()}
-    dom = max(alg_bytes, key=lambda k: tm[k][0])
+    dom = max((k for k in alg_bytes if k in tm), key=lambda k: tm[k][0])
     avg_ms = tm[dom][0] / max(1, launches[dom])
     peak, _ = peaks()
     achieved = alg_bytes[dom] / (avg_ms / 1e3) / 1e9
-    out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                       "frac": achieved / peak, "traffic": None,
+    out["roofline"] = {"bound": "hbm", "kernel": dom, "kernel_name": PHASE_KERNEL.get(dom), "achieved": achieved,
+                       "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom),
                        "algorithmic_bytes_per_launch": alg_bytes[dom], "avg_launch_ms": avg_ms}
     out["phases"] = phases
 
@@ -361,7 +380,71 @@ def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
     out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                            "sample": f"{args.oracle_iters} iALM-FRSVT iterations of the full workload ({dt:.1f} s)"}
     out["exact"]["frsvt_speedup"] = None
+    out["wsvt"] = bench_wsvt(dev)
+    out["unrolled"] = bench_unrolled(dev)
     return out
+
+
+def bench_wsvt(dev):
+    """Batched weighted SVT: 16384 WNNM patch groups 64 x n_i, n_i in [40, 160], one launch per
+    variant after the autotuner; problems per second (device time, CUDA events)."""
+    import torch
+    from paper_1509_00296_gb300 import frsvt, synth
+    mats, _ = synth.wnnm_batch(seed=1004)
+    dm = [torch.from_numpy(a).to(dev) for a in mats]
+    out = [torch.empty_like(t) for t in dm]
+    a = torch.tensor([t.data_ptr() for t in dm], dtype=torch.int64, device=dev)
+    x = torch.tensor([t.data_ptr() for t in out], dtype=torch.int64, device=dev)
+    n = torch.tensor([t.shape[1] for t in dm], dtype=torch.int32, device=dev)
+    h = frsvt.Handle(64, 160, 16, q=1, seed=11, stream=torch.cuda.current_stream())
+    res = {"workload": "16384 patch groups 64 x n_i, n_i uniform in [40, 160], rank 4 + N(0, 0.05^2), "
+                       "w_j = 2.8 sqrt(n_i) / (sigma_j + 1e-8)", "unit": "problems/s"}
+    for v, name in ((frsvt.WSVT_EXACT, "exact"), (frsvt.WSVT_FRSVT, "frsvt_l12_q1")):
+        h.wsvt_raw(a, n, 64, 2.8, 1e-8, x, v, 12, tune=True)
+        for _ in range(2):
+            h.wsvt_raw(a, n, 64, 2.8, 1e-8, x, v, 12)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            h.wsvt_raw(a, n, 64, 2.8, 1e-8, x, v, 12)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        res[name] = {"ms_per_batch": ms, "value": 16384 / ms * 1e3, "launch_shape": h.wsvt_tuning(v)}
+    return res
+
+
+def bench_unrolled(dev):
+    """Unrolled RPCA training step: batch of 8 matrices 2048 x 512, 10 iALM steps with FRSVT
+    (l = 16, q = 1), loss ||L_10 - L_true||^2, forward + backward (device time)."""
+    import numpy as np
+    import torch
+    from paper_1509_00296_gb300 import synth
+    from paper_1509_00296_gb300.unrolled import RPCAUnrolled
+    O, L, _ = synth.unrolled_batch(seed=1005)
+    Ob = torch.from_numpy(O.astype(np.float32)).to(dev)
+    Lb = torch.from_numpy(L.astype(np.float32)).to(dev)
+    net = RPCAUnrolled(2048, 512, steps=10, l=16, q=1, mu0=1.25 / float(np.linalg.norm(O[0], 2)))
+
+    def train_step():
+        net.tau.grad = None
+        net.mu.grad = None
+        loss = net.loss(Ob, Lb)
+        loss.backward()
+        return loss
+
+    train_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 3
+    for _ in range(reps):
+        loss = train_step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": "8 x (2048 x 512), rank 8 + 5 % outliers, 10 unrolled iALM steps, FRSVT l=16 q=1",
+            "ms_per_training_step": ms, "loss": float(loss.detach()), "unit": "training steps/s", "value": 1e3 / ms}
 
 
 if __name__ == "__main__":
