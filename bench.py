@@ -49,7 +49,7 @@ PHASE_KERNEL = {"sketch": "k_tc_sc<16,1,1>", "power_AQ": "k_tc_lr<16>", "power_A
                 "project": "k_tc_lr<16>", "core": "k_gram_core<16>", "epilogue": "k_tp_alm<16>"}
 # sm__pipe_tensor_cycles_active of the tensor-core passes, same capture (percent of peak, elapsed)
 TENSOR_PIPE_PCT = {"sketch k_tc_sc<16,1,1>": 11.9, "A^T Z k_tc_sc<16,0,1>": 13.0, "A Q k_tc_lr<16>": 25.3,
-                   "source": "profiles/tc_passes_video_76800x200.md"}
+                   "source": "ncu --set full capture of the passes on the video workload"}
 
 
 def dist_env():
