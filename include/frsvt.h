@@ -54,8 +54,15 @@ typedef enum frsvt_status {
 #define FRSVT_DEV_TIMEOUT        (1u << 3)   /* a bounded wait on an asynchronous copy gave up */
 #define FRSVT_DEV_BAD_PROBLEM    (1u << 4)   /* a batched problem had an unsupported size and was skipped */
 
+/* Precision of the passes over A (Alg. 1 steps 5, 9, 14, 16).  FRSVT_PREC_BF16: the handle keeps
+ * a BF16 shadow of A (written by rpca_init and by every rpca_ialm_step epilogue, converted by
+ * frsvt_svt); the sketch and the first q - 1 power steps read the shadow (BF16 operands, FP32
+ * accumulation), the last power step and the projection stay FP32-accurate (the "residual"
+ * step that wins the accuracy back).  Served for n <= 256; frsvt_create returns
+ * FRSVT_ERR_UNSUPPORTED for a precision it does not build. */
 typedef enum frsvt_precision {
-  FRSVT_PREC_FP32 = 0            /* float32 data, FP32-accurate passes */
+  FRSVT_PREC_FP32 = 0,           /* float32 data, FP32-accurate passes */
+  FRSVT_PREC_BF16 = 1            /* BF16 shadow for the sketch and the early power steps */
 } frsvt_precision;
 
 #define FRSVT_CFG_ADJOINT 1      /* allocate the workspace of frsvt_svt_save / frsvt_backward */

@@ -52,7 +52,21 @@ cudaError_t launch_tp_lr(int LP, bool gram, const CUtensorMap& tmA, int64_t m, i
 cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS, const CUtensorMap& tmA,
                           const CUtensorMap& tmZ, int64_t m, int64_t n, int64_t rpc, int grid, const float* Rf,
                           float* S, float* A, int64_t ld, float* L, int64_t ldl, DevState* dst, double* cpart,
-                          double* rsum, unsigned* tickets, cudaStream_t st);
+                          double* rsum, unsigned* tickets, void* Ab, int64_t ldb, cudaStream_t st);
+int tb_lr_stages(int LP, int64_t n, size_t limit);
+int tb_sc_stages(int LP, int64_t n, bool omega, size_t limit);
+size_t tb_sc_smem(int LP, int64_t n, bool omega, int ns);
+cudaError_t prepare_tb_kernels(int smem_limit);
+int tb_sc_resident_grid(int LP, int64_t n, int ns);
+cudaError_t launch_tb_lr(int LP, const CUtensorMap& tmA, int64_t m, int64_t n, int grid, int ns, const float* Q,
+                         float* Z, DevState* dst, cudaStream_t st);
+cudaError_t launch_tb_sc(int LP, const CUtensorMap& tmA, const CUtensorMap* tmZ, int64_t m, int64_t n, int grid,
+                         int ns, uint64_t seed, uint64_t ctr, DevState* dst, float* cpart, float* Y,
+                         unsigned* tickets, int l, int use_rp, int passes, const float* Qt, float* Q,
+                         double rank_tol, cudaStream_t st);
+cudaError_t launch_to_bf16(const float* A, int64_t lda, int64_t m, int64_t n, void* Ab, int64_t ldb, cudaStream_t st);
+int tb_box_rows_lr();
+int tb_box_rows_sc();
 size_t tc_lr_smem(int LP, int64_t n, int ns);
 int tc_lr_stages(int LP, int64_t n, size_t limit);
 size_t gram_core_smem(int LP, int64_t n);
@@ -134,6 +148,9 @@ struct frsvt_handle {
   int gram_grid = 8;         // CTAs of the Gram / core kernel (whole clusters)
   unsigned* wsvt_next = nullptr;   // work counter of the batched WSVT launch
   float* ad_ws = nullptr;          // adjoint workspace (FRSVT_CFG_ADJOINT)
+  void* Ab = nullptr;              // BF16 shadow of A (FRSVT_PREC_BF16)
+  int64_t ldb = 0;                 // its row stride in elements
+  int tb_lr_ns = 0, tb_sc_ns = 0, tb_sc_grid = 0;
   int ad_K = 0;                    // columns of the stacked rank-update factors
   int wsvt_nt[2] = {256, 256};     // threads per CTA per variant (autotuner)
   int wsvt_cps[2] = {0, 0};        // CTAs per SM per variant (0: as many as fit)
@@ -256,6 +273,19 @@ bool make_row_map_sw128(CUtensorMap* map, const float* base, int64_t rows, int64
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// BF16 row-major matrix, boxes of 64 columns (128 bytes) x box_rows in the 128-byte swizzle.
+bool make_row_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2u};
+  cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int g_tc_prepared = 0;
 
 int64_t ns_limit(int LP) {
@@ -329,7 +359,7 @@ frsvt_status check_shape(frsvt_handle* h, int64_t m, int64_t n) {
 // so that X = Z Rf^T.
 frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int l, int q,
                             int use_rp, uint64_t ctr, float tau_host, int tau_from_mu, int update_rp,
-                            int advance_counter) {
+                            int advance_counter, const void* Ab = nullptr) {
   const int LP = h->LP;
   cudaStream_t st = h->stream;
   const double tol = h->cfg.rank_tol;
@@ -350,7 +380,19 @@ frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t 
     if (tcc && (!make_row_map_sw128(&tmAc, A, m, n, lda, tc_sc_rows(), CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) ||
                 !make_row_map(&tmZc, h->Zl, m, LP, LP, LP, tc_sc_rows())))
       return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A / Z (column pass)");
-    if (tcc)
+    // Reduced precision (a BF16 shadow Ab of A is current): the sketch and the first q - 1 power
+    // steps read Ab; the last power step and the projection stay FP32-accurate.
+    const bool bf = Ab != nullptr && h->tb_sc_ns > 0;
+    CUtensorMap tmBr, tmBc, tmZb;
+    if (bf && (!make_row_map_bf16(&tmBr, Ab, m, n, h->ldb, tb_box_rows_lr()) ||
+               !make_row_map_bf16(&tmBc, Ab, m, n, h->ldb, tb_box_rows_sc()) ||
+               !make_row_map(&tmZb, h->Zl, m, LP, LP, LP, tb_box_rows_sc())))
+      return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the BF16 shadow");
+    if (bf)
+      FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_tb_sc(LP, tmBc, nullptr, m, n, h->tb_sc_grid, h->tb_sc_ns, h->cfg.seed,
+                                                    ctr, h->dst, h->cpart_sc, h->Ys, h->tickets, l, use_rp,
+                                                    q == 0 ? 2 : 1, h->Qt, h->Qs, tol, st));
+    else if (tcc)
       FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_tc_sc(LP, tmAc, nullptr, m, n, h->tc_sc_grid, h->tc_sc_ns, h->cfg.seed,
                                                     ctr, h->dst, h->cpart_sc, h->Ys, h->tickets, true, l, use_rp,
                                                     q == 0 ? 2 : 1, h->Qt, h->Qs, tol, st));
@@ -363,6 +405,13 @@ frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t 
       return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A (swizzled)");
     for (int it = 0; it < q; ++it) {
       const int passes = it == q - 1 ? 2 : 1;
+      if (bf && it < q - 1) {
+        FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_tb_lr(LP, tmBr, m, n, h->sms, h->tb_lr_ns, h->Qs, h->Zl, h->dst, st));
+        FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_tb_sc(LP, tmBc, &tmZb, m, n, h->tb_sc_grid, h->tb_sc_ns,
+                                                         h->cfg.seed, ctr, h->dst, h->cpart_sc, h->Ys, h->tickets, l,
+                                                         0, passes, h->Qt, h->Qs, tol, st));
+        continue;
+      }
       FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_tc_lr(LP, tmAs, m, n, h->sms, h->tc_lr_ns, h->Qs, h->Zl, h->dst, st));
       if (tcc)
         FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_tc_sc(LP, tmAc, &tmZc, m, n, h->tc_sc_grid, h->tc_sc_ns,
@@ -437,7 +486,7 @@ void free_all(frsvt_handle* h) {
   h->ev_pool.clear();
   void* ptrs[] = {h->dst, h->Ys,       h->Qs,       h->Qt,        h->Zl,   h->Rf,   h->part,    h->gpart,
                   h->rpart, h->pmax,   h->psum,     h->cpart_sc,  h->cpart_lr, h->cpart_alm, h->Gfin, h->rsum,
-                  h->tickets, h->wsvt_next, h->ad_ws};
+                  h->tickets, h->wsvt_next, h->ad_ws, h->Ab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -541,7 +590,7 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   *out = nullptr;
   if (cfg->m_max < 1 || cfg->n_max < 1 || cfg->l_max < 1 || cfg->l_max > kMaxL || cfg->q < 0 || cfg->q > 64)
     return FRSVT_ERR_INVALID_ARG;
-  if (cfg->precision != FRSVT_PREC_FP32) return FRSVT_ERR_UNSUPPORTED;
+  if (cfg->precision != FRSVT_PREC_FP32 && cfg->precision != FRSVT_PREC_BF16) return FRSVT_ERR_UNSUPPORTED;
   h = new (std::nothrow) frsvt_handle();
   if (h == nullptr) return FRSVT_ERR_ALLOC;
   h->cfg = *cfg;
@@ -567,7 +616,8 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
       prepare_tc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
       prepare_tc_sc_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
       prepare_gram_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
-      prepare_adjoint_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
+      prepare_adjoint_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
+      prepare_tb_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
     delete h;
     return FRSVT_ERR_CUDA;
   }
@@ -634,6 +684,17 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   }
   alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
   alloc(reinterpret_cast<void**>(&h->wsvt_next), sizeof(unsigned));
+  if (cfg->precision == FRSVT_PREC_BF16 && h->tma) {
+    const int64_t nt = cfg->n_max < 256 ? cfg->n_max : 256;
+    h->ldb = (cfg->n_max + 7) / 8 * 8;
+    h->tb_lr_ns = tb_lr_stages(h->LP, nt, kSmemLimit - 2048);
+    const int ns_o = tb_sc_stages(h->LP, nt, true, kSmemLimit - 8192);
+    const int ns_z = tb_sc_stages(h->LP, nt, false, kSmemLimit - 8192);
+    h->tb_sc_ns = ns_o < ns_z ? ns_o : ns_z;
+    h->tb_sc_grid = (h->tb_sc_ns >= 2 && h->tb_lr_ns >= 2) ? tb_sc_resident_grid(h->LP, nt, h->tb_sc_ns) : 0;
+    if (h->tb_sc_grid < 4) h->tb_sc_ns = 0;
+    if (h->tb_sc_ns > 0) alloc(&h->Ab, 2 * static_cast<size_t>(cfg->m_max) * h->ldb);
+  }
   if (cfg->flags & FRSVT_CFG_ADJOINT) {
     h->ad_K = static_cast<int>(LP) * (2 + 2 * h->cfg.q);
     alloc(reinterpret_cast<void**>(&h->ad_ws), sizeof(float) * ad_ws_floats(h, cfg->m_max, cfg->n_max));
@@ -691,7 +752,11 @@ frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, in
   if (l > n) l = static_cast<int32_t>(n);
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
   const int rp = h->cfg.range_prop ? 1 : 0;
-  if ((s = range_and_core(h, A, m, n, lda, l, h->cfg.q, rp, kCounterFromState, tau, 0, rp, 1)) != FRSVT_OK) return s;
+  const bool bf = h->Ab != nullptr && h->tma && n <= 256;
+  if (bf) FRSVT_CK(launch_to_bf16(A, lda, m, n, h->Ab, h->ldb, h->stream));
+  if ((s = range_and_core(h, A, m, n, lda, l, h->cfg.q, rp, kCounterFromState, tau, 0, rp, 1,
+                          bf ? h->Ab : nullptr)) != FRSVT_OK)
+    return s;
   const Splits sp = row_splits(h, m, n);
   FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_recon(h->LP, h->Zl, h->Rf, m, n, X, ldx, sp.nsplit, sp.rps, h->stream));
   return FRSVT_OK;
@@ -736,6 +801,7 @@ frsvt_status rpca_init(frsvt_handle* h, const float* O, float* S, float* A, int6
   FRSVT_CK(launch_init_scalars(h->pmax, h->psum, h->absmax_blocks, normO2, lambda, rho, mu_bar_factor, h->dst,
                                h->stream));
   FRSVT_CK(launch_init_state(O, S, A, m, n, ld, h->dst, h->stream));
+  if (h->Ab != nullptr) FRSVT_CK(launch_to_bf16(A, ld, m, n, h->Ab, h->ldb, h->stream));
   h->last_m = m;
   h->last_n = n;
   h->last_l = -1;
@@ -757,7 +823,10 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
   if (l > n) l = static_cast<int32_t>(n);
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
   const int rp = h->cfg.range_prop ? 1 : 0;
-  if ((s = range_and_core(h, A, m, n, ld, l, h->cfg.q, rp, kCounterFromState, 0.f, 1, rp, 1)) != FRSVT_OK) return s;
+  const bool bf = h->Ab != nullptr && h->tma && n <= 256;   // the shadow is kept current by rpca_init / the epilogue
+  if ((s = range_and_core(h, A, m, n, ld, l, h->cfg.q, rp, kCounterFromState, 0.f, 1, rp, 1,
+                          bf ? h->Ab : nullptr)) != FRSVT_OK)
+    return s;
   if (h->tma && n <= 256 && m < (int64_t(1) << 31)) {
     CUtensorMap tO, tS, tA, tZ;
     const int re = tma_rows_per_tile_epilogue();
@@ -767,7 +836,8 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
     const int G = h->tma_grid;
     const int64_t rpc = cdiv(cdiv(m, G), re) * re;
     FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_tp_alm(h->LP, tO, tS, tA, tZ, m, n, rpc, G, h->Rf, S, A, ld, L, ldl,
-                                                     h->dst, h->cpart_alm, h->rsum, h->tickets, h->stream));
+                                                     h->dst, h->cpart_alm, h->rsum, h->tickets, bf ? h->Ab : nullptr,
+                                                     h->ldb, h->stream));
   } else if (h->fused) {
     const Splits fs = fused_splits(h, m, n);
     FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_alm2(h->LP, h->Zl, h->Rf, O, S, A, m, n, ld, L, ldl, h->dst, fs.nsplit,

@@ -18,6 +18,7 @@
 // FRSVT_DEV_TIMEOUT, stops computing, and still walks every barrier so that no
 // thread is left waiting.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include "cluster.cuh"
 #include "common.cuh"
@@ -365,7 +366,7 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
          const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ, int64_t m, int n, int np4,
          int64_t rpc, const float* __restrict__ Rf, float* __restrict__ S, float* __restrict__ A, int64_t ld,
          float* __restrict__ L, int64_t ldl, DevState* __restrict__ dst, double* __restrict__ cpart,
-         double* __restrict__ rsum, unsigned* __restrict__ tickets) {
+         double* __restrict__ rsum, unsigned* __restrict__ tickets, __nv_bfloat16* __restrict__ Ab, int64_t ldb) {
   constexpr int NC = Cfg<LP>::NC, NT = Cfg<LP>::NT;
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kStagesE], empty[kStagesE];
@@ -454,6 +455,11 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
             *reinterpret_cast<float4*>(S + idx) = make_float4(sn[0], sn[1], sn[2], sn[3]);
             *reinterpret_cast<float4*>(A + idx) = make_float4(an[0], an[1], an[2], an[3]);
             if (L != nullptr) *reinterpret_cast<float4*>(L + row * ldl + col) = make_float4(x[0], x[1], x[2], x[3]);
+            if (Ab != nullptr) {                                             // BF16 shadow of A'
+              __nv_bfloat162* ab = reinterpret_cast<__nv_bfloat162*>(Ab + row * ldb + col);
+              ab[0] = __floats2bfloat162_rn(an[0], an[1]);
+              ab[1] = __floats2bfloat162_rn(an[2], an[3]);
+            }
           } else {
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc)
@@ -461,6 +467,7 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
                 S[idx + cc] = sn[cc];
                 A[idx + cc] = an[cc];
                 if (L != nullptr) L[row * ldl + col + cc] = x[cc];
+                if (Ab != nullptr) Ab[row * ldb + col + cc] = __float2bfloat16_rn(an[cc]);
               }
           }
         }
@@ -636,16 +643,17 @@ cudaError_t launch_tp_lr(int LP, bool gram, const CUtensorMap& tmA, int64_t m, i
 cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS, const CUtensorMap& tmA,
                           const CUtensorMap& tmZ, int64_t m, int64_t n, int64_t rpc, int grid, const float* Rf,
                           float* S, float* A, int64_t ld, float* L, int64_t ldl, DevState* dst, double* cpart,
-                          double* rsum, unsigned* tickets, cudaStream_t st) {
+                          double* rsum, unsigned* tickets, void* Ab, int64_t ldb, cudaStream_t st) {
   const int np4 = tma_np4(n);
   const size_t smem = tma_alm_smem(LP, n);
   const int nn = static_cast<int>(n);
+  __nv_bfloat16* ab = static_cast<__nv_bfloat16*>(Ab);
   if (LP == 16)
     k_tp_alm<16><<<grid, Cfg<16>::NT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
-                                                   cpart, rsum, tickets);
+                                                   cpart, rsum, tickets, ab, ldb);
   else
     k_tp_alm<32><<<grid, Cfg<32>::NT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
-                                                   cpart, rsum, tickets);
+                                                   cpart, rsum, tickets, ab, ldb);
   return cudaGetLastError();
 }
 
