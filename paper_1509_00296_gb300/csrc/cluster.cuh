@@ -22,7 +22,7 @@ __device__ bool cluster_split_reduce(T* part_sm, int count, T* cpart, T* out, un
   cg::cluster_group cl = cg::this_cluster();
   const int rank = static_cast<int>(cl.block_rank());
   cl.sync();
-  const int per = (count + CL - 1) / CL;
+  const int per = (count + 4 * CL - 1) / (4 * CL) * 4;   // multiples of 4 (float4 columns)
   const int e0 = rank * per;
   const int e1 = min(count, e0 + per);
   for (int e = e0 + static_cast<int>(threadIdx.x); e < e1; e += blockDim.x) {
@@ -45,17 +45,71 @@ __device__ bool cluster_split_reduce(T* part_sm, int count, T* cpart, T* out, un
   cl.sync();                                   // rank 0's flag is read before anyone leaves
   if (!last) return false;
   __threadfence();
-  for (int e = e0 + static_cast<int>(threadIdx.x); e < e1; e += blockDim.x) {
-    T s = 0;
-    for (int c0 = 0; c0 < nclusters; c0 += 8) {   // 8 loads in flight, summed in cluster order
-      T v[8];
+  if constexpr (sizeof(T) == 4) {
+    if ((count & 3) == 0 && (e0 & 3) == 0) {
+      // float4 columns; the clusters split into H interleaved groups summed by different
+      // threads (all loads of a group in flight), the H group sums then added in group order
+      // through part_sm (no longer read by the cluster): one L2 round trip instead of one per
+      // eight clusters.
+      const int nv = (e1 - e0) / 4;
+      int H = nv > 0 ? static_cast<int>(blockDim.x) / nv : 1;
+      H = H < 1 ? 1 : (H > CL ? CL : H);
+      if (nv > 0 && H * nv > count / 4) H = (count / 4) / nv;   // red[] stays inside part_sm
+      if (H < 1) H = 1;
+      float4* red = reinterpret_cast<float4*>(part_sm);
+      const int t = static_cast<int>(threadIdx.x);
+      for (int w = t; w < nv * H; w += blockDim.x) {
+        const int j = w % nv, h = w / nv;
+        const float4* src = reinterpret_cast<const float4*>(cpart) + (e0 / 4 + j);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c0 = h; c0 < nclusters; c0 += 8 * H) {
+          float4 v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        v[u] = (c0 + u < nclusters) ? __ldcg(cpart + static_cast<int64_t>(c0 + u) * count + e) : T(0);
+          for (int u = 0; u < 8; ++u)
+            v[u] = (c0 + u * H < nclusters) ? __ldcg(src + static_cast<int64_t>(c0 + u * H) * (count / 4))
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s += v[u];
+          for (int u = 0; u < 8; ++u) {
+            acc.x += v[u].x;
+            acc.y += v[u].y;
+            acc.z += v[u].z;
+            acc.w += v[u].w;
+          }
+        }
+        red[h * nv + j] = acc;
+      }
+      __syncthreads();
+      for (int j = t; j < nv; j += blockDim.x) {
+        float4 s4 = red[j];
+        for (int h = 1; h < H; ++h) {
+          const float4 v = red[h * nv + j];
+          s4.x += v.x;
+          s4.y += v.y;
+          s4.z += v.z;
+          s4.w += v.w;
+        }
+        reinterpret_cast<float4*>(out)[e0 / 4 + j] = s4;
+      }
+    } else {
+      for (int e = e0 + static_cast<int>(threadIdx.x); e < e1; e += blockDim.x) {
+        T s = 0;
+        for (int c0 = 0; c0 < nclusters; ++c0) s += __ldcg(cpart + static_cast<int64_t>(c0) * count + e);
+        out[e] = s;
+      }
     }
-    out[e] = s;
+  } else {
+    for (int e = e0 + static_cast<int>(threadIdx.x); e < e1; e += blockDim.x) {
+      T s = 0;
+      for (int c0 = 0; c0 < nclusters; c0 += 8) {   // 8 loads in flight, summed in cluster order
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          v[u] = (c0 + u < nclusters) ? __ldcg(cpart + static_cast<int64_t>(c0 + u) * count + e) : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+      }
+      out[e] = s;
+    }
   }
   __threadfence();
   cl.sync();
