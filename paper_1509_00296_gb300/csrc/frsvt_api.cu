@@ -38,6 +38,7 @@ size_t tma_lr_smem(int LP, int64_t n, int nst);
 int tma_lr_stages(int LP, int64_t n, size_t limit);
 int tma_rows_per_tile_lr();
 int tma_resident_grid(int LP, int64_t n);
+int tma_alm_resident_grid(int LP, int64_t n);
 size_t tma_alm_smem(int LP, int64_t n);
 int tma_rows_per_tile();
 int tma_rows_per_tile_epilogue();
@@ -146,6 +147,7 @@ struct frsvt_handle {
   int tc_sc_ns = 0;          // stages of the tensor-core column pass (0: not available)
   int tc_lr_ns = 0;          // stages of the tensor-core row pass
   int gram_grid = 8;         // CTAs of the Gram / core kernel (whole clusters)
+  int alm_grid = 4;          // CTAs of the fused iALM epilogue (whole clusters)
   unsigned* wsvt_next = nullptr;   // work counter of the batched WSVT launch
   float* ad_ws = nullptr;          // adjoint workspace (FRSVT_CFG_ADJOINT)
   void* Ab = nullptr;              // BF16 shadow of A (FRSVT_PREC_BF16)
@@ -650,8 +652,9 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
     const int nst = tma_lr_stages(h->LP, nt, kSmemLimit - 16384);
     h->tc_lr_ns = tc_lr_stages(h->LP, nt, kSmemLimit - 2048);
     h->gram_grid = gram_resident_grid(h->LP, nt);
+    h->alm_grid = tma_alm_resident_grid(h->LP, nt);
     if (h->gram_grid < 8) h->gram_grid = 8;
-    h->tma = tensor_map_encoder() != nullptr && nst >= 2 && h->tc_lr_ns >= 2 &&
+    h->tma = tensor_map_encoder() != nullptr && nst >= 2 && h->tc_lr_ns >= 2 && h->alm_grid >= 4 &&
              tma_sc_smem(h->LP, nt) <= kSmemLimit - 8192 &&
              tma_lr_smem(h->LP, nt, nst) <= kSmemLimit - 8192 && tma_alm_smem(h->LP, nt) <= kSmemLimit - 8192;
     // clusters of 8 that can be resident at once (GPCs hold a whole number of clusters)
@@ -833,7 +836,7 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
     if (!make_row_map(&tO, O, m, n, ld, tma_np4(n), re) || !make_row_map(&tS, S, m, n, ld, tma_np4(n), re) ||
         !make_row_map(&tA, A, m, n, ld, tma_np4(n), re) || !make_row_map(&tZ, h->Zl, m, h->LP, h->LP, h->LP, re))
       return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for O/S/A/Z");
-    const int G = h->tma_grid;
+    const int G = h->alm_grid;
     const int64_t rpc = cdiv(cdiv(m, G), re) * re;
     FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_tp_alm(h->LP, tO, tS, tA, tZ, m, n, rpc, G, h->Rf, S, A, ld, L, ldl,
                                                      h->dst, h->cpart_alm, h->rsum, h->tickets, bf ? h->Ab : nullptr,

@@ -34,7 +34,7 @@ constexpr int kRB = 32;               // rows per tile of the column pass
 constexpr int kStages = 4;
 constexpr int kRBL = 64;              // rows per tile of the row pass
 constexpr int kRBE = 16;              // rows per tile of the epilogue
-constexpr int kStagesE = 3;
+constexpr int kStagesE = 5;
 constexpr int kGacc = 1024;
 
 template <int LP>
@@ -360,8 +360,12 @@ k_tp_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int np4, int6
 }
 
 // ---------------------------------------------------------------- fused reconstruction + iALM update
+// Clusters of 4 (the cluster only serves the final one-value residual reduction): more of them
+// fit at once than clusters of 8, so the streaming kernel covers (nearly) every SM.
+constexpr int kAlmCL = 4;
+
 template <int LP>
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(Cfg<LP>::NT, 1)
+__global__ void __cluster_dims__(kAlmCL, 1, 1) __launch_bounds__(Cfg<LP>::NT, 1)
 k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmS,
          const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ, int64_t m, int n, int np4,
          int64_t rpc, const float* __restrict__ Rf, float* __restrict__ S, float* __restrict__ A, int64_t ld,
@@ -391,8 +395,44 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
       prefetch_tensormap(&tmS);
       prefetch_tensormap(&tmA);
       prefetch_tensormap(&tmZ);
-      const Box boxes[4] = {{&tmO, box, 0u}, {&tmS, box, box}, {&tmA, box, 2 * box}, {&tmZ, zbox, 3 * box}};
-      produce<4>(boxes, kStagesE, ring, sb, full, empty, rw, kRBE, NC / 32, dst);
+      // Tiles of O, S, A, Z in; once the consumers have overwritten the S and A slots of a tile
+      // with S' and A', TMA stores them before the stage is refilled.
+      const uint32_t total = 3 * box + zbox;
+      bool pok = true;
+      for (int c = 0; c < rw.nchunks && pok; ++c) {
+        const int s = c % kStagesE;
+        if (c >= kStagesE) {
+          if (!mbar_wait(&empty[s], static_cast<uint32_t>(c / kStagesE - 1) & 1u)) {
+            atomicOr(&dst->status, kDevTimeout);
+            pok = false;
+            break;
+          }
+          const int yp = static_cast<int>(rw.r0 + static_cast<int64_t>(c - kStagesE) * kRBE);
+          tma_store_2d(&tmS, 0, yp, ring + s * sb + box);
+          tma_store_2d(&tmA, 0, yp, ring + s * sb + 2 * box);
+          bulk_commit();
+          bulk_wait_read_all();
+        }
+        mbar_arrive_expect_tx(&full[s], total);
+        const int y = static_cast<int>(rw.r0 + static_cast<int64_t>(c) * kRBE);
+        tma_load_2d(ring + s * sb, &tmO, 0, y, &full[s]);
+        tma_load_2d(ring + s * sb + box, &tmS, 0, y, &full[s]);
+        tma_load_2d(ring + s * sb + 2 * box, &tmA, 0, y, &full[s]);
+        tma_load_2d(ring + s * sb + 3 * box, &tmZ, 0, y, &full[s]);
+      }
+      const int c0 = rw.nchunks > kStagesE ? rw.nchunks - kStagesE : 0;
+      for (int c = c0; c < rw.nchunks && pok; ++c) {
+        const int s = c % kStagesE;
+        if (!mbar_wait(&empty[s], static_cast<uint32_t>(c / kStagesE) & 1u)) {
+          atomicOr(&dst->status, kDevTimeout);
+          break;
+        }
+        const int yp = static_cast<int>(rw.r0 + static_cast<int64_t>(c) * kRBE);
+        tma_store_2d(&tmS, 0, yp, ring + s * sb + box);
+        tma_store_2d(&tmA, 0, yp, ring + s * sb + 2 * box);
+        bulk_commit();
+      }
+      bulk_wait_all();
     }
   } else {
     const int nq = np4 / 4;
@@ -416,8 +456,8 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
       const int s = c % kStagesE;
       if (ok && active) {
         const float* tO = reinterpret_cast<const float*>(ring + s * sb);
-        const float* tS = tO + kRBE * np4;
-        const float* tA = tS + kRBE * np4;
+        float* tS = reinterpret_cast<float*>(ring + s * sb) + kRBE * np4;
+        float* tA = tS + kRBE * np4;
         const float* tZ = tA + kRBE * np4;
         for (int rr = rg; rr < nr; rr += rgc) {
           float x[4];
@@ -450,10 +490,10 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
             if (col + cc < n) res2 = fmaf(rz, rz, res2);
           }
           const int64_t row = i0 + rr;
-          const int64_t idx = row * ld + col;
+          // S' and A' replace S and A in the tile; the producer stores the tile by TMA
+          reinterpret_cast<float4*>(tS + rr * np4)[qd] = make_float4(sn[0], sn[1], sn[2], sn[3]);
+          reinterpret_cast<float4*>(tA + rr * np4)[qd] = make_float4(an[0], an[1], an[2], an[3]);
           if (fullq) {
-            *reinterpret_cast<float4*>(S + idx) = make_float4(sn[0], sn[1], sn[2], sn[3]);
-            *reinterpret_cast<float4*>(A + idx) = make_float4(an[0], an[1], an[2], an[3]);
             if (L != nullptr) *reinterpret_cast<float4*>(L + row * ldl + col) = make_float4(x[0], x[1], x[2], x[3]);
             if (Ab != nullptr) {                                             // BF16 shadow of A'
               __nv_bfloat162* ab = reinterpret_cast<__nv_bfloat162*>(Ab + row * ldb + col);
@@ -464,14 +504,13 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc)
               if (col + cc < n) {
-                S[idx + cc] = sn[cc];
-                A[idx + cc] = an[cc];
                 if (L != nullptr) L[row * ldl + col + cc] = x[cc];
                 if (Ab != nullptr) Ab[row * ldb + col + cc] = __float2bfloat16_rn(an[cc]);
               }
           }
         }
       }
+      fence_proxy_async();                          // S', A' in the tile -> visible to the TMA store
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
@@ -484,8 +523,9 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
     for (int w2 = 0; w2 < NT / 32; ++w2) t += red[w2];
     mine = t;
   }
-  const int nclusters = gridDim.x / kCL;
-  if (!cluster_split_reduce<double>(&mine, 1, cpart, rsum, tickets, blockIdx.x / kCL, nclusters, &flag)) return;
+  const int nclusters = gridDim.x / kAlmCL;
+  if (!cluster_split_reduce<double, kAlmCL>(&mine, 1, cpart, rsum, tickets, blockIdx.x / kAlmCL, nclusters, &flag))
+    return;
   if (cooperative_groups::this_cluster().block_rank() != 0) return;
   if (threadIdx.x == 0) {
     const double s2 = __ldcg(rsum);
@@ -573,14 +613,32 @@ int tma_resident_grid(int LP, int64_t n) {
   if (LP == 16) {
     probe(reinterpret_cast<const void*>(k_tp_sc<16, false>), tma_sc_smem(16, n));
     probe(reinterpret_cast<const void*>(k_tp_lr<16, true>), tma_lr_smem(16, n, nst));
-    probe(reinterpret_cast<const void*>(k_tp_alm<16>), tma_alm_smem(16, n));
   } else {
     probe(reinterpret_cast<const void*>(k_tp_sc<32, false>), tma_sc_smem(32, n));
     probe(reinterpret_cast<const void*>(k_tp_lr<32, true>), tma_lr_smem(32, n, nst));
-    probe(reinterpret_cast<const void*>(k_tp_alm<32>), tma_alm_smem(32, n));
   }
   (void)cudaGetLastError();
   return best * kCL;
+}
+
+// Resident grid of the epilogue kernel (clusters of kAlmCL).
+int tma_alm_resident_grid(int LP, int64_t n) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kAlmCL, 1, 1);
+  cfg.blockDim = dim3(threads_of(LP), 1, 1);
+  cfg.dynamicSmemBytes = tma_alm_smem(LP, n);
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = kAlmCL;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  const void* fn = LP == 16 ? reinterpret_cast<const void*>(k_tp_alm<16>) : reinterpret_cast<const void*>(k_tp_alm<32>);
+  if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) nc = 0;
+  (void)cudaGetLastError();
+  return nc * kAlmCL;
 }
 
 cudaError_t prepare_tma_kernels(int smem_limit) {
