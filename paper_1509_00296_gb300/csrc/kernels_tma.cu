@@ -34,7 +34,8 @@ constexpr int kRB = 32;               // rows per tile of the column pass
 constexpr int kStages = 4;
 constexpr int kRBL = 64;              // rows per tile of the row pass
 constexpr int kRBE = 16;              // rows per tile of the epilogue
-constexpr int kStagesE = 5;
+constexpr int kStagesE = 5;              // deepest epilogue ring (fewer stages where n is wide)
+constexpr size_t kAlmSmemCap = 219 * 1024; // dynamic shared memory the epilogue may take
 constexpr int kGacc = 1024;
 
 template <int LP>
@@ -370,7 +371,8 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
          const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ, int64_t m, int n, int np4,
          int64_t rpc, const float* __restrict__ Rf, float* __restrict__ S, float* __restrict__ A, int64_t ld,
          float* __restrict__ L, int64_t ldl, DevState* __restrict__ dst, double* __restrict__ cpart,
-         double* __restrict__ rsum, unsigned* __restrict__ tickets, __nv_bfloat16* __restrict__ Ab, int64_t ldb) {
+         double* __restrict__ rsum, unsigned* __restrict__ tickets, __nv_bfloat16* __restrict__ Ab, int64_t ldb,
+         int nse) {
   constexpr int NC = Cfg<LP>::NC, NT = Cfg<LP>::NT;
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kStagesE], empty[kStagesE];
@@ -387,7 +389,7 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
   const double mu_next = fmin(dst->rho * mu, dst->mu_bar);
   const float thr = static_cast<float>(dst->lambda / mu);
   const float ratio = static_cast<float>(mu / mu_next);
-  init_ring(full, empty, kStagesE, NC / 32);
+  init_ring(full, empty, nse, NC / 32);
   float res2 = 0.f;
   if (warp == NC / 32) {
     if (lane == 0) {
@@ -400,14 +402,14 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
       const uint32_t total = 3 * box + zbox;
       bool pok = true;
       for (int c = 0; c < rw.nchunks && pok; ++c) {
-        const int s = c % kStagesE;
-        if (c >= kStagesE) {
-          if (!mbar_wait(&empty[s], static_cast<uint32_t>(c / kStagesE - 1) & 1u)) {
+        const int s = c % nse;
+        if (c >= nse) {
+          if (!mbar_wait(&empty[s], static_cast<uint32_t>(c / nse - 1) & 1u)) {
             atomicOr(&dst->status, kDevTimeout);
             pok = false;
             break;
           }
-          const int yp = static_cast<int>(rw.r0 + static_cast<int64_t>(c - kStagesE) * kRBE);
+          const int yp = static_cast<int>(rw.r0 + static_cast<int64_t>(c - nse) * kRBE);
           tma_store_2d(&tmS, 0, yp, ring + s * sb + box);
           tma_store_2d(&tmA, 0, yp, ring + s * sb + 2 * box);
           bulk_commit();
@@ -420,10 +422,10 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
         tma_load_2d(ring + s * sb + 2 * box, &tmA, 0, y, &full[s]);
         tma_load_2d(ring + s * sb + 3 * box, &tmZ, 0, y, &full[s]);
       }
-      const int c0 = rw.nchunks > kStagesE ? rw.nchunks - kStagesE : 0;
+      const int c0 = rw.nchunks > nse ? rw.nchunks - nse : 0;
       for (int c = c0; c < rw.nchunks && pok; ++c) {
-        const int s = c % kStagesE;
-        if (!mbar_wait(&empty[s], static_cast<uint32_t>(c / kStagesE) & 1u)) {
+        const int s = c % nse;
+        if (!mbar_wait(&empty[s], static_cast<uint32_t>(c / nse) & 1u)) {
           atomicOr(&dst->status, kDevTimeout);
           break;
         }
@@ -452,8 +454,8 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
     for (int c = 0; c < rw.nchunks; ++c) {
       const int64_t i0 = rw.r0 + static_cast<int64_t>(c) * kRBE;
       const int nr = static_cast<int>(imin64(kRBE, rw.r1 - i0));
-      wait_tile(full, c, kStagesE, ok, dst);
-      const int s = c % kStagesE;
+      wait_tile(full, c, nse, ok, dst);
+      const int s = c % nse;
       if (ok && active) {
         const float* tO = reinterpret_cast<const float*>(ring + s * sb);
         float* tS = reinterpret_cast<float*>(ring + s * sb) + kRBE * np4;
@@ -580,8 +582,18 @@ size_t tma_lr_smem(int LP, int64_t n, int nst) {
   return ws > a ? ws : a;
 }
 
+// Ring depth of the epilogue: as many stages (<= kStagesE) as fit in kAlmSmemCap; 0 if fewer than 2 fit.
+int tma_alm_stages(int LP, int64_t n) {
+  const size_t sb = align1k(static_cast<uint32_t>(3 * kRBE * tma_np4(n) * 4 + kRBE * LP * 4));
+  int ns = static_cast<int>(kAlmSmemCap / sb);
+  if (ns > kStagesE) ns = kStagesE;
+  return ns >= 2 ? ns : 0;
+}
+
 size_t tma_alm_smem(int LP, int64_t n) {
-  return static_cast<size_t>(kStagesE) * align1k(static_cast<uint32_t>(3 * kRBE * tma_np4(n) * 4 + kRBE * LP * 4));
+  const int ns = tma_alm_stages(LP, n);
+  const size_t sb = align1k(static_cast<uint32_t>(3 * kRBE * tma_np4(n) * 4 + kRBE * LP * 4));
+  return static_cast<size_t>(ns > 0 ? ns : kStagesE) * sb;
 }
 
 int tma_rows_per_tile() { return kRB; }
@@ -704,14 +716,16 @@ cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS
                           double* rsum, unsigned* tickets, void* Ab, int64_t ldb, cudaStream_t st) {
   const int np4 = tma_np4(n);
   const size_t smem = tma_alm_smem(LP, n);
+  const int nse = tma_alm_stages(LP, n);
+  if (nse < 2) return cudaErrorInvalidValue;
   const int nn = static_cast<int>(n);
   __nv_bfloat16* ab = static_cast<__nv_bfloat16*>(Ab);
   if (LP == 16)
     k_tp_alm<16><<<grid, Cfg<16>::NT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
-                                                   cpart, rsum, tickets, ab, ldb);
+                                                   cpart, rsum, tickets, ab, ldb, nse);
   else
     k_tp_alm<32><<<grid, Cfg<32>::NT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
-                                                   cpart, rsum, tickets, ab, ldb);
+                                                   cpart, rsum, tickets, ab, ldb, nse);
   return cudaGetLastError();
 }
 
