@@ -115,6 +115,27 @@ cudaError_t launch_tc_sc(int LP, const CUtensorMap& tmA, const CUtensorMap* tmZ,
                          unsigned* tickets, bool tail, int l, int use_rp, int passes, const float* Qt, float* Q,
                          double rank_tol, cudaStream_t st);
 int tc_sc_rows();
+int wide_lp();
+int wide_tile();
+cudaError_t prepare_wide_kernels();
+int wide_gram_grid();
+int wide_gram_count();
+int wide_splits(int64_t nlong, int64_t nk, int sms);
+cudaError_t launch_wd_omega(float* OT, float* OTl, int64_t ldo, int64_t m, int l, int use_rp, uint64_t seed,
+                            uint64_t ctr, const DevState* dst, cudaStream_t st);
+cudaError_t launch_wd_pass(bool col, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
+                           int64_t nlong, int64_t nk, int S, float* part, int64_t ldp, unsigned* tickets, float* outT,
+                           float* outTl, int64_t ldo, float* outR, float* outRl, DevState* dst, cudaStream_t st);
+cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len, int grid, double* cpart, double* Gpk,
+                           unsigned* ticket, int p, double rank_tol, int l, float tau_host, int tau_from_mu,
+                           int update_rp, int advance_counter, int max_sweeps, float* T1, float* T2, DevState* dst,
+                           cudaStream_t st);
+cudaError_t launch_wd_apply(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
+                            int64_t ldo, float* outR, float* outRl, cudaStream_t st);
+cudaError_t launch_wd_alm(bool alm, const CUtensorMap& tmZ, const CUtensorMap& tmZl, const CUtensorMap& tmR,
+                          const CUtensorMap& tmRl, int64_t m, int64_t n, const float* O, float* S, float* A, int64_t ld,
+                          float* L, int64_t ldl, DevState* dst, double* cpart, unsigned* ticket, int grid,
+                          cudaStream_t st);
 }
 
 using namespace frsvt;
@@ -167,6 +188,17 @@ struct frsvt_handle {
   int lr_blocks = 8;
   int64_t last_m = -1, last_n = -1;
   int last_l = -1;
+  // wide basis (cfg.l_max > 32, LP = 128, any short side): basis-side matrices transposed
+  // (128 x ld_m / ld_n), Z and Rf row-major (len x 128), K-split partials, Gram partials
+  bool wide = false;
+  int64_t w_ldm = 0, w_ldn = 0, w_ldp = 0;
+  float *wOT = nullptr, *wOTl = nullptr, *wZT = nullptr, *wZTl = nullptr, *wZ = nullptr, *wZl = nullptr;
+  float *wYT = nullptr, *wQT = nullptr, *wQTl = nullptr, *wQp = nullptr, *wRf = nullptr, *wRfl = nullptr;
+  float *wT1 = nullptr, *wT2 = nullptr, *wpart = nullptr;
+  double *wgc = nullptr, *wGpk = nullptr, *wac = nullptr;
+  unsigned* wtick = nullptr;       // pass tiles, then the Gram ticket, then the epilogue ticket
+  int64_t w_ntiles = 0;
+  int w_gram_grid = 8;
   std::string err;
   // tracing: CUDA events around every launch when enabled
   int timing = 0;
@@ -180,6 +212,7 @@ struct frsvt_handle {
 namespace {
 
 constexpr size_t kSmemLimit = 227 * 1024;
+constexpr int kCLw = 8;            // cluster size of the wide-basis Gram reduction
 
 frsvt_status fail(frsvt_handle* h, frsvt_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -488,9 +521,130 @@ void free_all(frsvt_handle* h) {
   h->ev_pool.clear();
   void* ptrs[] = {h->dst, h->Ys,       h->Qs,       h->Qt,        h->Zl,   h->Rf,   h->part,    h->gpart,
                   h->rpart, h->pmax,   h->psum,     h->cpart_sc,  h->cpart_lr, h->cpart_alm, h->Gfin, h->rsum,
-                  h->tickets, h->wsvt_next, h->ad_ws, h->Ab};
+                  h->tickets, h->wsvt_next, h->ad_ws, h->Ab,
+                  h->wOT, h->wOTl, h->wZT, h->wZTl, h->wZ, h->wZl, h->wYT, h->wQT, h->wQTl, h->wQp, h->wRf,
+                  h->wRfl, h->wT1, h->wT2, h->wpart, h->wgc, h->wGpk, h->wac, h->wtick};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+}
+
+// ---------------------------------------------------------------- wide basis (32 < l <= 128)
+// Orthonormal basis of the columns of Y (given transposed, 128 x n at h->wYT) into QT / QTl:
+// Cholesky QR, `passes` times (Alg. 1 steps 6 / 14; only span(Q) matters, Prop. 1).
+frsvt_status wide_orth(frsvt_handle* h, int64_t n, int l, int passes) {
+  cudaStream_t st = h->stream;
+  const int64_t ld = h->w_ldn;
+  unsigned* gt = h->wtick + h->w_ntiles;
+  for (int pass = 0; pass < passes; ++pass) {
+    const float* src = pass == 0 ? h->wYT : h->wQT;
+    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_gram(false, src, ld, n, h->w_gram_grid, h->wgc, h->wGpk, gt, l,
+                                                  h->cfg.rank_tol, l, 0.f, 0, 0, 0, h->cfg.max_jacobi_sweeps, h->wT1,
+                                                  h->wT2, h->dst, st));
+    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_apply(src, ld, n, h->wT1, h->wQT, h->wQTl, ld, nullptr, nullptr, st));
+  }
+  return FRSVT_OK;
+}
+
+// Alg. 1 up to the core on the wide basis: leaves Z / Z_lo (m x 128) and Rf / Rf_lo (n x 128)
+// so that X = Z Rf^T, and sets r, s, sigma (and the counter) in the device state.
+frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int l, int q,
+                                 uint64_t ctr, float tau_host, int tau_from_mu, int advance_counter) {
+  cudaStream_t st = h->stream;
+  const int64_t LW = wide_lp();
+  CUtensorMap tmAr, tmAc, tmOT, tmOTl, tmZT, tmZTl, tmQT, tmQTl;
+  if (!make_row_map_sw128(&tmAr, A, m, n, lda, wide_tile()) ||
+      !make_row_map_sw128(&tmAc, A, m, n, lda, 32, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) ||
+      !make_row_map_sw128(&tmOT, h->wOT, LW, m, h->w_ldm, 128) ||
+      !make_row_map_sw128(&tmOTl, h->wOTl, LW, m, h->w_ldm, 128) ||
+      !make_row_map_sw128(&tmZT, h->wZT, LW, m, h->w_ldm, 128) ||
+      !make_row_map_sw128(&tmZTl, h->wZTl, LW, m, h->w_ldm, 128) ||
+      !make_row_map_sw128(&tmQT, h->wQT, LW, n, h->w_ldn, 128) ||
+      !make_row_map_sw128(&tmQTl, h->wQTl, LW, n, h->w_ldn, 128))
+    return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis)");
+  const int Sr = wide_splits(m, n, h->sms), Sc = wide_splits(n, m, h->sms);
+  FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_omega(h->wOT, h->wOTl, h->w_ldm, m, l, 0, h->cfg.seed, ctr, h->dst, st));
+  FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(true, tmAc, tmOT, tmOTl, n, m, Sc, h->wpart, h->w_ldp, h->wtick,
+                                                  h->wYT, nullptr, h->w_ldn, nullptr, nullptr, h->dst, st));
+  frsvt_status s = wide_orth(h, n, l, q == 0 ? 2 : 1);
+  if (s != FRSVT_OK) return s;
+  for (int it = 0; it < q; ++it) {
+    FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(false, tmAr, tmQT, tmQTl, m, n, Sr, h->wpart, h->w_ldp,
+                                                      h->wtick, h->wZT, h->wZTl, h->w_ldm, nullptr, nullptr, h->dst,
+                                                      st));
+    FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(true, tmAc, tmZT, tmZTl, n, m, Sc, h->wpart, h->w_ldp,
+                                                       h->wtick, h->wYT, nullptr, h->w_ldn, nullptr, nullptr, h->dst,
+                                                       st));
+    if ((s = wide_orth(h, n, l, it == q - 1 ? 2 : 1)) != FRSVT_OK) return s;
+  }
+  // projection B^T = Z = A Q (step 16), then B B^T = Z^T Z and the core (steps 16-19)
+  FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_wd_pass(false, tmAr, tmQT, tmQTl, m, n, Sr, h->wpart, h->w_ldp, h->wtick,
+                                                   h->wZT, nullptr, h->w_ldm, h->wZ, h->wZl, h->dst, st));
+  FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_wd_gram(true, h->wZT, h->w_ldm, m, h->w_gram_grid, h->wgc, h->wGpk,
+                                                h->wtick + h->w_ntiles, l, h->cfg.rank_tol, l, tau_host, tau_from_mu, 0,
+                                                advance_counter, h->cfg.max_jacobi_sweeps, h->wT1, h->wT2, h->dst,
+                                                st));
+  FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_wd_apply(h->wQT, h->w_ldn, n, h->wT1, nullptr, nullptr, 0, h->wRf, h->wRfl,
+                                                 st));
+  return FRSVT_OK;
+}
+
+// X = Z Rf^T (alm = false: written to L) or the fused iALM update (alm = true).
+frsvt_status wide_epilogue(frsvt_handle* h, bool alm, int64_t m, int64_t n, const float* O, float* S, float* A,
+                           int64_t ld, float* L, int64_t ldl) {
+  CUtensorMap tmZ, tmZl, tmR, tmRl;
+  if (!make_row_map_sw128(&tmZ, h->wZ, m, wide_lp(), wide_lp(), 128) ||
+      !make_row_map_sw128(&tmZl, h->wZl, m, wide_lp(), wide_lp(), 128) ||
+      !make_row_map_sw128(&tmR, h->wRf, n, wide_lp(), wide_lp(), wide_tile()) ||
+      !make_row_map_sw128(&tmRl, h->wRfl, n, wide_lp(), wide_lp(), wide_tile()))
+    return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide epilogue)");
+  const int64_t ntiles = cdiv(m, 128) * cdiv(n, wide_tile());
+  const int grid = static_cast<int>(ntiles < h->sms ? ntiles : h->sms);
+  FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_wd_alm(alm, tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, h->dst,
+                                                   h->wac, h->wtick + h->w_ntiles + 1, grid, h->stream));
+  return FRSVT_OK;
+}
+
+// Workspace of a wide handle (sizes from the configuration); false on an allocation failure.
+bool wide_alloc(frsvt_handle* h) {
+  const frsvt_config* cfg = &h->cfg;
+  const int64_t T = wide_tile(), LW = wide_lp();
+  h->w_ldm = cdiv(cfg->m_max, T) * T;
+  h->w_ldn = cdiv(cfg->n_max, T) * T;
+  h->w_ldp = h->w_ldm > h->w_ldn ? h->w_ldm : h->w_ldn;
+  h->w_ntiles = h->w_ldp / T;
+  h->w_gram_grid = wide_gram_grid();
+  if (h->w_gram_grid < kCLw) h->w_gram_grid = kCLw;
+  bool ok = true;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (ok && cudaMalloc(p, bytes < 16 ? 16 : bytes) != cudaSuccess) ok = false;
+  };
+  const size_t fm = sizeof(float) * LW * h->w_ldm, fn = sizeof(float) * LW * h->w_ldn;
+  alloc(reinterpret_cast<void**>(&h->wOT), fm);
+  alloc(reinterpret_cast<void**>(&h->wOTl), fm);
+  alloc(reinterpret_cast<void**>(&h->wZT), fm);
+  alloc(reinterpret_cast<void**>(&h->wZTl), fm);
+  alloc(reinterpret_cast<void**>(&h->wZ), fm);
+  alloc(reinterpret_cast<void**>(&h->wZl), fm);
+  alloc(reinterpret_cast<void**>(&h->wYT), fn);
+  alloc(reinterpret_cast<void**>(&h->wQT), fn);
+  alloc(reinterpret_cast<void**>(&h->wQTl), fn);
+  alloc(reinterpret_cast<void**>(&h->wQp), fn);
+  alloc(reinterpret_cast<void**>(&h->wRf), fn);
+  alloc(reinterpret_cast<void**>(&h->wRfl), fn);
+  alloc(reinterpret_cast<void**>(&h->wT1), sizeof(float) * LW * LW);
+  alloc(reinterpret_cast<void**>(&h->wT2), sizeof(float) * LW * LW);
+  alloc(reinterpret_cast<void**>(&h->wpart), sizeof(float) * 8 * LW * h->w_ldp);
+  alloc(reinterpret_cast<void**>(&h->wgc), sizeof(double) * (h->w_gram_grid / kCLw) * wide_gram_count());
+  alloc(reinterpret_cast<void**>(&h->wGpk), sizeof(double) * wide_gram_count());
+  alloc(reinterpret_cast<void**>(&h->wac), sizeof(double) * (h->sms > 0 ? h->sms : 1));
+  alloc(reinterpret_cast<void**>(&h->wtick), sizeof(unsigned) * (h->w_ntiles + 2));
+  alloc(reinterpret_cast<void**>(&h->dst), sizeof(DevState));
+  alloc(reinterpret_cast<void**>(&h->pmax), sizeof(float) * h->absmax_blocks);
+  alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
+  alloc(reinterpret_cast<void**>(&h->wsvt_next), sizeof(unsigned));
+  if (!ok) return false;
+  return cudaMemsetAsync(h->wtick, 0, sizeof(unsigned) * (h->w_ntiles + 2), h->stream) == cudaSuccess &&
+         cudaMemsetAsync(h->wT2, 0, sizeof(float) * LW * LW, h->stream) == cudaSuccess;
 }
 
 // Adjoint workspace (floats): L (m x K), R (n x K), P, T, Z (m x LP each), Yb, Y, RQ (n x LP
@@ -599,9 +753,12 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   if (h->cfg.max_jacobi_sweeps <= 0) h->cfg.max_jacobi_sweeps = 30;
   if (!(h->cfg.rank_tol > 0.0)) h->cfg.rank_tol = 1e-12;
   h->stream = static_cast<cudaStream_t>(stream);
-  h->LP = cfg->l_max <= 16 ? 16 : 32;
+  h->wide = cfg->l_max > 32;
+  h->LP = cfg->l_max <= 16 ? 16 : (cfg->l_max <= 32 ? 32 : wide_lp());
   const int64_t nsmax = cfg->n_max < cfg->m_max ? cfg->n_max : cfg->m_max;
-  if (nsmax > ns_limit(h->LP)) {
+  if (h->wide ? (cfg->range_prop || cfg->precision != FRSVT_PREC_FP32 || (cfg->flags & FRSVT_CFG_ADJOINT) ||
+                 cfg->m_max >= (int64_t(1) << 31))
+              : nsmax > ns_limit(h->LP)) {
     delete h;
     return FRSVT_ERR_UNSUPPORTED;
   }
@@ -610,6 +767,28 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
       cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     delete h;
     return FRSVT_ERR_CUDA;
+  }
+  if (h->wide) {
+    h->absmax_blocks = 2 * h->sms;
+    if (tensor_map_encoder() == nullptr || prepare_wide_kernels() != cudaSuccess ||
+        prepare_pass_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
+        prepare_small_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess) {
+      delete h;
+      return FRSVT_ERR_CUDA;
+    }
+    if (!wide_alloc(h)) {
+      free_all(h);
+      delete h;
+      return FRSVT_ERR_ALLOC;
+    }
+    if (cudaMemsetAsync(h->dst, 0, sizeof(DevState), h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+      free_all(h);
+      delete h;
+      return FRSVT_ERR_CUDA;
+    }
+    *out = h;
+    return FRSVT_OK;
   }
   if (prepare_pass_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
       prepare_small_kernels(static_cast<int>(kSmemLimit)) != cudaSuccess ||
@@ -754,6 +933,10 @@ frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, in
   if (static_cast<const void*>(A) == static_cast<const void*>(X)) return fail(h, FRSVT_ERR_INVALID_ARG, "X aliases A");
   if (l > n) l = static_cast<int32_t>(n);
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
+  if (h->wide) {
+    if ((s = wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1)) != FRSVT_OK) return s;
+    return wide_epilogue(h, false, m, n, nullptr, nullptr, nullptr, 0, X, ldx);
+  }
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;
   if (bf) FRSVT_CK(launch_to_bf16(A, lda, m, n, h->Ab, h->ldb, h->stream));
@@ -776,7 +959,9 @@ frsvt_status frsvt_spectral_norm(frsvt_handle* h, const float* A, int64_t m, int
   if (m == 0 || n == 0) return FRSVT_OK;
   const int l = static_cast<int>(n < h->cfg.l_max ? n : h->cfg.l_max);
   const uint64_t ctr = 0x5350454354524131ull;   // a fixed stream index reserved for this estimate
-  if ((s = range_and_core(h, A, m, n, lda, l, iters, 0, ctr, FLT_MAX, 0, 0, 0)) != FRSVT_OK) return s;
+  if ((s = h->wide ? wide_range_and_core(h, A, m, n, lda, l, iters, ctr, FLT_MAX, 0, 0)
+                   : range_and_core(h, A, m, n, lda, l, iters, 0, ctr, FLT_MAX, 0, 0, 0)) != FRSVT_OK)
+    return s;
   double v = 0.0;
   FRSVT_CK(cudaMemcpyAsync(&v, &h->dst->sigma1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   FRSVT_CK(cudaStreamSynchronize(h->stream));
@@ -797,7 +982,9 @@ frsvt_status rpca_init(frsvt_handle* h, const float* O, float* S, float* A, int6
   if (m == 0 || n == 0) return FRSVT_OK;
   if (!(normO2 > 0.0)) {
     const int l = static_cast<int>(n < h->cfg.l_max ? n : h->cfg.l_max);
-    if ((s = range_and_core(h, O, m, n, ld, l, power_iters, 0, 0x5350454354524131ull, FLT_MAX, 0, 0, 0)) != FRSVT_OK)
+    if ((s = h->wide ? wide_range_and_core(h, O, m, n, ld, l, power_iters, 0x5350454354524131ull, FLT_MAX, 0, 0)
+                     : range_and_core(h, O, m, n, ld, l, power_iters, 0, 0x5350454354524131ull, FLT_MAX, 0, 0, 0)) !=
+        FRSVT_OK)
       return s;
   }
   FRSVT_CK(launch_absmax_sumsq(O, m, n, ld, h->pmax, h->psum, h->absmax_blocks, h->stream));
@@ -827,6 +1014,10 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;   // the shadow is kept current by rpca_init / the epilogue
+  if (h->wide) {
+    if ((s = wide_range_and_core(h, A, m, n, ld, l, h->cfg.q, kCounterFromState, 0.f, 1, 1)) != FRSVT_OK) return s;
+    if ((s = wide_epilogue(h, true, m, n, O, S, A, ld, L, ldl)) != FRSVT_OK) return s;
+  } else {
   if ((s = range_and_core(h, A, m, n, ld, l, h->cfg.q, rp, kCounterFromState, 0.f, 1, rp, 1,
                           bf ? h->Ab : nullptr)) != FRSVT_OK)
     return s;
@@ -851,6 +1042,7 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
                                                  sp.nsplit, sp.rps, h->stream));
   FRSVT_LAUNCH(FRSVT_PHASE_FINISH, launch_alm_finish(h->rpart, sp.nsplit * sp.ntiles, h->dst, h->stream));
   }
+  }
   if (residual != nullptr) {
     double v = 0.0;
     FRSVT_CK(cudaMemcpyAsync(&v, &h->dst->resid_ratio, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -863,6 +1055,7 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
 static frsvt_status wsvt_check(frsvt_handle* h, int32_t batch, const float* const* A, const int32_t* n_i, int32_t m,
                         float c, float eps, float* const* X, int32_t variant, int32_t l) {
   if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (h->wide) return fail(h, FRSVT_ERR_UNSUPPORTED, "batched WSVT needs a handle with l_max <= 32");
   if (batch < 0) return fail(h, FRSVT_ERR_INVALID_ARG, "negative batch");
   if (variant != FRSVT_WSVT_EXACT && variant != FRSVT_WSVT_FRSVT) return fail(h, FRSVT_ERR_INVALID_ARG, "unknown variant");
   if (m < 1 || m > 64) return fail(h, FRSVT_ERR_UNSUPPORTED, "batched WSVT serves m in [1, 64]");
@@ -1131,6 +1324,7 @@ frsvt_status frsvt_debug_philox(uint64_t* out, int64_t rows, int32_t blocks, uin
 
 frsvt_status frsvt_debug_rows_tc(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, const float* Q,
                                  float* Z) {
+  if (h != nullptr && h->wide) return fail(h, FRSVT_ERR_UNSUPPORTED, "needs a handle with l_max <= 32");
   if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
   frsvt_status s = check_shape(h, m, n);
   if (s != FRSVT_OK) return s;
@@ -1153,6 +1347,7 @@ frsvt_status frsvt_debug_rows_tc(frsvt_handle* h, const float* A, int64_t m, int
 
 frsvt_status frsvt_debug_cols_tc(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, const float* B,
                                  uint64_t seed, uint64_t stream, float* Y) {
+  if (h != nullptr && h->wide) return fail(h, FRSVT_ERR_UNSUPPORTED, "needs a handle with l_max <= 32");
   if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
   frsvt_status s = check_shape(h, m, n);
   if (s != FRSVT_OK) return s;

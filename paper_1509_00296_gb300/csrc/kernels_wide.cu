@@ -1,0 +1,1022 @@
+// FRSVT (Alg. 1) for a wide oversampled basis (32 < l <= 128) and any short side n: the
+// large low-rank recovery shape (8192 x 8192, l = 120).
+//
+// At this size the basis (n x 128 floats) no longer fits in one CTA, so every step that the
+// l <= 32 path runs as a single-CTA tail becomes a grid-wide kernel, and the narrow factor of
+// each pass streams from L2 next to the tiles of A:
+//
+//   k_wd_omega  Omega^T (128 x m) from the Philox stream (steps 4 / 8), split into TF32 hi / lo.
+//   k_wd_pass   the passes over A on tcgen05, FP32-accurate (3xTF32):
+//                 row pass    Z^T = Q^T A^T   (steps 14 and 16: Z = A Q = B^T)
+//                 column pass Y^T = M^T A     (steps 5 / 9 with M = Omega, step 14 with M = Z)
+//               D (128 x 256) accumulates in tensor memory, the M = 128 operand being the
+//               basis side (k = 0..127) and N = 256 the long side of the tile; K is split over
+//               S CTAs per tile whose partials the last CTA of the tile sums in a fixed order.
+//   k_wd_gram   X^T X (128 x 128) of a basis-side matrix in double-float arithmetic, cluster
+//               split-K reduction, then in one CTA either the orthonormalisation tail
+//               (Cholesky with the rank cut, R^{-1}: Cholesky QR, steps 6 / 11 / 14) or the core
+//               tail (Cholesky of B B^T, one-sided Jacobi SVD, shrinkage: steps 16-19, Eq. 6).
+//   k_wd_apply  Out = T^T In for a 128 x 128 T: Q = Y R^{-1}, Rf = Q M, Q~ = Q U.
+//   k_wd_alm    X = Z Rf^T on tcgen05 (3xTF32) fused with the iALM sparse shrinkage, dual update
+//               and residual (or X written out for a plain SVT).
+//
+// Layouts: basis-side matrices are kept transposed (128 x len, row stride ld*) so that they are
+// K-major MMA operands and coalesced along the long side; Z and Rf are also kept row-major
+// (len x 128) for the reconstruction.  Every wait is bounded (FRSVT_DEV_TIMEOUT on expiry).
+#include <cooperative_groups.h>
+#include <cuda.h>
+
+#include "cluster.cuh"
+#include "common.cuh"
+#include "state.cuh"
+#include "tc.cuh"
+#include "tma.cuh"
+
+namespace frsvt {
+
+namespace {
+
+constexpr int kWL = 128;                       // basis width of this path
+constexpr int kWN = 256;                       // long-side extent of a pass tile (MMA N)
+constexpr int kWK = 32;                        // floats per K-chunk (128 bytes)
+constexpr int kWStages = 3;
+constexpr int kWSplit = 8;                     // split warps of the pass
+constexpr int kWThr = 64 + 32 * (4 + kWSplit); // 448
+constexpr uint32_t kWABytes = kWN * kWK * 4;   // 32 KB
+constexpr uint32_t kWMBytes = kWL * kWK * 4;   // 16 KB
+constexpr uint32_t kWStage = kWABytes + 2 * kWMBytes;
+
+__device__ __forceinline__ void flag_timeout(bool& ok, DevState* dst) {
+  ok = false;
+  atomicOr(&dst->status, kDevTimeout);
+}
+
+__device__ __forceinline__ float4 f4_lo(float4 v) {
+  return make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+}
+
+__device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// ---------------------------------------------------------------- Omega^T
+// OT[k][i] = Omega[i][k] for k < p (p = l, or l - keep under range propagation), 0 for k >= p;
+// OTl = OT - tf32(OT).  One Philox call gives Omega[i][4 blk .. 4 blk + 3].
+__global__ void k_wd_omega(float* __restrict__ OT, float* __restrict__ OTl, int64_t ldo, int64_t m, int l,
+                           int use_rp, uint64_t seed, uint64_t ctr, const DevState* __restrict__ dst) {
+  const uint64_t stream = (ctr == kCounterFromState) ? dst->counter : ctr;
+  int p = l;
+  if (use_rp) {
+    const int keep = max(0, min(dst->keep, l));
+    if (keep > 0) p = l - keep;
+  }
+  const int64_t total = m * (kWL / 4);
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e % m;
+    const int blk = static_cast<int>(e / m);
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (4 * blk < p) g = gaussian4(seed, static_cast<uint64_t>(i), static_cast<uint64_t>(blk), stream, 0ull);
+    const float v[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = 4 * blk + c;
+      const float x = (k < p) ? v[c] : 0.f;
+      OT[k * ldo + i] = x;
+      OTl[k * ldo + i] = x - tf32_hi(x);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- passes over A
+// COL = false (row pass): D[k][i] = sum_j M[k][j] A[i][j] for the 256 rows i of the tile, K = n,
+//   A tiles 256 rows x 32 columns (K-major, 128-byte swizzle).
+// COL = true (column pass): D[k][j] = sum_i M[k][i] A[i][j] for the 256 columns j of the tile,
+//   K = m, A tiles 32 rows x 256 columns read MN-major (8 boxes of 32 x 32, 32-byte atoms).
+// M and M_lo (128 x K, K-major boxes of 32 x 128) arrive by TMA with each chunk of A; the MMAs
+// are M_hi A_hi + M_lo A_hi, then (after the split warps rewrote the A tile as A_lo in place)
+// M_hi A_lo.  Warps: 0 TMA, 1 tensor memory + MMA, 2-5 drain, 6-13 split.
+template <bool COL>
+__global__ void __launch_bounds__(kWThr, 1)
+k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmM,
+          const __grid_constant__ CUtensorMap tmMl, int64_t nlong, int64_t nk, int S, float* __restrict__ part,
+          int64_t ldp, unsigned* __restrict__ tickets, float* __restrict__ outT, float* __restrict__ outTl,
+          int64_t ldo, float* __restrict__ outR, float* __restrict__ outRl, DevState* __restrict__ dst) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t full[kWStages], hidone[kWStages], lo_ready[kWStages], empty[kWStages], acc_full;
+  __shared__ uint32_t tmem_base;
+  __shared__ int flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x / S, split = blockIdx.x % S;
+  const int nkc = static_cast<int>((nk + kWK - 1) / kWK);
+  const int c0 = static_cast<int>(static_cast<int64_t>(split) * nkc / S);
+  const int c1 = static_cast<int>(static_cast<int64_t>(split + 1) * nkc / S);
+  const int nc = c1 - c0;
+  const int x0 = tile * kWN;
+  // every block-scope declaration of dsm in this file asks for 1024-byte alignment (one entity);
+  // the swizzled TMA destinations need it, so a misplaced base is reported and nothing is issued
+  if ((smem_addr(dsm) & 1023u) != 0u) {
+    if (threadIdx.x == 0) atomicOr(&dst->status, kDevBadProblem);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&hidone[s], 1);
+      mbar_init(&lo_ready[s], kWSplit);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&acc_full, 1);
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tensormap(&tmA);
+      prefetch_tensormap(&tmM);
+      prefetch_tensormap(&tmMl);
+      for (int g = 0; g < nc && ok; ++g) {
+        const int s = g % kWStages, u = g / kWStages;
+        if (u > 0 && !mbar_wait(&empty[s], static_cast<uint32_t>(u - 1) & 1u)) {
+          flag_timeout(ok, dst);
+          break;
+        }
+        unsigned char* st = dsm + s * kWStage;
+        const int c = c0 + g;
+        mbar_arrive_expect_tx(&full[s], kWStage);
+        if (COL) {
+#pragma unroll
+          for (int v = 0; v < kWN / 32; ++v) tma_load_2d(st + v * 4096, &tmA, x0 + 32 * v, kWK * c, &full[s]);
+        } else {
+          tma_load_2d(st, &tmA, kWK * c, x0, &full[s]);
+        }
+        tma_load_2d(st + kWABytes, &tmM, kWK * c, 0, &full[s]);
+        tma_load_2d(st + kWABytes + kWMBytes, &tmMl, kWK * c, 0, &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(128, kWN, false, COL);
+      auto bdesc = [&](const unsigned char* a, int ks) -> uint64_t {
+        return COL ? smem_desc_sw128a32_mn(a + ks * 1024, 4096) : smem_desc_sw128(a + 32 * ks, 16, 1024);
+      };
+      auto issue_lo = [&](int g) {
+        const int s = g % kWStages, u = g / kWStages;
+        if (ok && !mbar_wait(&lo_ready[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
+        tc_fence_after();
+        const unsigned char* st = dsm + s * kWStage;
+#pragma unroll
+        for (int ks = 0; ks < kWK / 8; ++ks)
+          tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc, true);
+        tc_commit(&empty[s]);
+      };
+      for (int g = 0; g < nc; ++g) {
+        const int s = g % kWStages, u = g / kWStages;
+        if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
+        tc_fence_after();
+        const unsigned char* st = dsm + s * kWStage;
+#pragma unroll
+        for (int ks = 0; ks < kWK / 8; ++ks) {
+          tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
+                      g > 0 || ks > 0);
+          tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + kWMBytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
+                      true);
+        }
+        tc_commit(&hidone[s]);
+        if (g > 0) issue_lo(g - 1);
+      }
+      if (nc > 0) issue_lo(nc - 1);
+      tc_commit(&acc_full);
+    }
+  } else if (warp < 6) {
+    // drain: TMEM lane 32 q + L is row k of D, column x its long-side index; partial of split s
+    // goes to part[s][k][x0 + x].
+    const int q = warp & 3;
+    if (!mbar_wait(&acc_full, 0u)) flag_timeout(ok, dst);
+    tc_fence_after();
+    const int k = 32 * q + lane;
+    float* dstp = part + (static_cast<int64_t>(split) * kWL + k) * ldp + x0;
+    for (int grp = 0; grp < kWN / 16; ++grp) {
+      float v[16];
+      tmem_ld16(tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(16 * grp), v);
+      float4* d4 = reinterpret_cast<float4*>(dstp + 16 * grp);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        d4[u] = (nc > 0 && ok) ? make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3])
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  } else {
+    const int t = threadIdx.x - 32 * 6;
+    for (int g = 0; g < nc; ++g) {
+      const int s = g % kWStages, u = g / kWStages;
+      if (ok && !mbar_wait(&hidone[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
+      float4* a = reinterpret_cast<float4*>(dsm + s * kWStage);
+#pragma unroll 4
+      for (int e = t; e < static_cast<int>(kWABytes / 16); e += 32 * kWSplit) a[e] = f4_lo(a[e]);
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&lo_ready[s]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tbase, 256);
+
+  // last CTA of the tile: sum the S partials in split order, write the outputs
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned old = atomicAdd(&tickets[tile], 1u);
+    flag = (old == static_cast<unsigned>(S - 1)) ? 1 : 0;
+    if (flag) tickets[tile] = 0;
+  }
+  __syncthreads();
+  if (!flag) return;
+  __threadfence();
+  constexpr int kSt = kWL + 1;
+  float* sm = reinterpret_cast<float*>(dsm);               // kWN x kSt staging for the row-major outputs
+  for (int e = threadIdx.x; e < kWL * (kWN / 4); e += kWThr) {
+    const int k = e / (kWN / 4), x4 = e % (kWN / 4);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < S; ++s)
+      v = f4_add(v, __ldcg(reinterpret_cast<const float4*>(part + (static_cast<int64_t>(s) * kWL + k) * ldp + x0) + x4));
+    if (outT != nullptr) reinterpret_cast<float4*>(outT + k * ldo + x0)[x4] = v;
+    if (outTl != nullptr) reinterpret_cast<float4*>(outTl + k * ldo + x0)[x4] = f4_lo(v);
+    if (outR != nullptr) {
+      sm[(4 * x4 + 0) * kSt + k] = v.x;
+      sm[(4 * x4 + 1) * kSt + k] = v.y;
+      sm[(4 * x4 + 2) * kSt + k] = v.z;
+      sm[(4 * x4 + 3) * kSt + k] = v.w;
+    }
+  }
+  if (outR == nullptr) return;
+  __syncthreads();
+  const int nx = static_cast<int>(imin64(kWN, nlong - x0));
+  for (int e = threadIdx.x; e < nx * (kWL / 4); e += kWThr) {
+    const int x = e / (kWL / 4), k4 = e % (kWL / 4);
+    const float* r = sm + x * kSt + 4 * k4;
+    const float4 v = make_float4(r[0], r[1], r[2], r[3]);
+    reinterpret_cast<float4*>(outR + (x0 + x) * static_cast<int64_t>(kWL))[k4] = v;
+    if (outRl != nullptr) reinterpret_cast<float4*>(outRl + (x0 + x) * static_cast<int64_t>(kWL))[k4] = f4_lo(v);
+  }
+}
+
+// ---------------------------------------------------------------- Gram + small dense tails
+constexpr int kGW = 544;                 // 17 warps; threads < 528 own a 4 x 4 block of the upper triangle
+constexpr int kGB = 528;                 // 4 x 4 blocks (bi <= bj) of a 128 x 128 symmetric matrix
+constexpr int kGCount = kGB * 16;        // packed partial (doubles)
+constexpr int kGCols = 64;               // long-side columns staged per step
+constexpr int kGSt = kWL + 4;            // staging row stride (floats)
+constexpr int kWCL = 8;                  // cluster size of the Gram reduction
+
+enum { kTailOrth = 0, kTailCore = 1 };
+
+// Shared-memory regions of the tails (the Gram staging and partial are dead by then).
+constexpr size_t kTG = 0;                                      // df64 G, 128 x 128 (128 KB)
+constexpr size_t kTR = kTG + sizeof(df64) * kWL * kWL;         // float 128 x 128 (64 KB)
+constexpr size_t kTV = kTR + sizeof(float) * kWL * kWL;        // small vectors
+constexpr size_t kTEnd = kTV + 8 * 1024;
+constexpr size_t kGMain = sizeof(float) * kGCols * kGSt + sizeof(double) * kGCount;
+constexpr size_t kGSmem = kTEnd > kGMain ? kTEnd : kGMain;
+
+__device__ __forceinline__ void block_of(int t, int& bi, int& bj) {
+  bi = 0;
+  int rem = t;
+  while (rem >= 32 - bi) {
+    rem -= 32 - bi;
+    ++bi;
+  }
+  bj = bi + rem;
+}
+
+struct TailVec {
+  df64* rdiag;     // 128: R_jj
+  int* drop;       // 128
+  float* thr;      // 128: drop thresholds on the pivots
+  float* g0;       // 128: original diagonal
+  float* sig;      // 128
+  float* coef;     // 128
+  int* perm;       // 128
+  int* misc;       // 16
+};
+
+__device__ TailVec carve_vec(unsigned char* base) {
+  TailVec v;
+  unsigned char* p = base + kTV;
+  v.rdiag = reinterpret_cast<df64*>(p);
+  p += sizeof(df64) * kWL;
+  v.drop = reinterpret_cast<int*>(p);
+  p += sizeof(int) * kWL;
+  v.thr = reinterpret_cast<float*>(p);
+  p += sizeof(float) * kWL;
+  v.g0 = reinterpret_cast<float*>(p);
+  p += sizeof(float) * kWL;
+  v.sig = reinterpret_cast<float*>(p);
+  p += sizeof(float) * kWL;
+  v.coef = reinterpret_cast<float*>(p);
+  p += sizeof(float) * kWL;
+  v.perm = reinterpret_cast<int*>(p);
+  p += sizeof(int) * kWL;
+  v.misc = reinterpret_cast<int*>(p);
+  return v;
+}
+
+// Unpack the block-packed Gram (global, doubles) into the full symmetric df64 matrix G.
+__device__ void unpack_gram(const double* __restrict__ Gpk, df64* G) {
+  for (int e = threadIdx.x; e < kGCount; e += blockDim.x) {
+    const int blk = e / 16, ij = e % 16;
+    int bi, bj;
+    block_of(blk, bi, bj);
+    const int a = 4 * bi + ij / 4, b = 4 * bj + ij % 4;
+    const df64 v = df_from_double(__ldcg(Gpk + e));
+    G[a * kWL + b] = v;
+    G[b * kWL + a] = v;
+  }
+  __syncthreads();
+}
+
+// Right-looking Cholesky G = R^T R of the leading p x p block in double-float arithmetic, with
+// the column drops of the l <= 32 path: column j is dropped (row j of R zero) when its pivot is
+// not above rank_tol * G_jj (original), when G_jj is below 1e-15 of the largest diagonal, or when
+// it is not a finite positive number.  R_jj goes to v.rdiag[j]; R[j][a] (a > j) to G[a][j] (the
+// lower triangle, never read by the updates of the upper one).  One barrier per column: every
+// thread forms the pivot itself, warps own rows a of the trailing upper triangle.
+__device__ void wide_cholesky(df64* G, const TailVec& v, int p, double rank_tol) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  if (tid < kWL) {
+    const float g0 = (tid < p) ? G[tid * kWL + tid].hi : 0.f;
+    v.g0[tid] = g0;
+    v.thr[tid] = static_cast<float>(rank_tol * static_cast<double>(g0));
+  }
+  __syncthreads();
+  float maxdiag = 0.f;
+  for (int a = 0; a < p; ++a) maxdiag = fmaxf(maxdiag, v.g0[a]);
+  for (int j = 0; j < p; ++j) {
+    const df64 d = G[j * kWL + j];
+    const bool drop = !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
+    df64 inv{0.f, 0.f};
+    if (!drop) inv = df_rsqrt(d);
+    if (tid == 0) {
+      v.rdiag[j] = drop ? df64{0.f, 0.f} : df_mul(d, inv);
+      v.drop[j] = drop ? 1 : 0;
+    }
+    for (int a = j + 1 + warp; a < p; a += nw) {
+      const df64 ra = drop ? df64{0.f, 0.f} : df_mul(G[j * kWL + a], inv);
+      if (lane == 0) G[a * kWL + j] = ra;
+      if (!drop)
+        for (int b = a + lane; b < p; b += 32) {
+          const df64 rb = df_mul(G[j * kWL + b], inv);
+          G[a * kWL + b] = df_add(G[a * kWL + b], df_neg(df_mul(ra, rb)));
+        }
+    }
+    __syncthreads();
+  }
+  for (int j = p + tid; j < kWL; j += nt) {
+    v.rdiag[j] = df64{0.f, 0.f};
+    v.drop[j] = 1;
+  }
+  __syncthreads();
+}
+
+// R (FP32, row-major, upper) from the factorization: R[j][j] = rdiag, R[j][a] = G[a][j].
+__device__ void extract_r(const df64* G, const TailVec& v, float* R, int p) {
+  for (int e = threadIdx.x; e < kWL * kWL; e += blockDim.x) {
+    const int j = e / kWL, a = e % kWL;
+    float x = 0.f;
+    if (j < p && a < p && !v.drop[j]) {
+      if (a == j) x = v.rdiag[j].hi;
+      else if (a > j) x = G[a * kWL + j].hi;
+    }
+    R[e] = x;
+  }
+  __syncthreads();
+}
+
+// X = R^{-1} (upper triangular, FP32) with the rows and columns of dropped indices zero;
+// back substitution row by row from the bottom, warps own columns, lanes split the dot.
+__device__ void wide_rinv(const float* R, const TailVec& v, float* X, int p) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  for (int e = tid; e < kWL * kWL; e += nt) X[e] = 0.f;
+  __syncthreads();
+  for (int r = p - 1; r >= 0; --r) {
+    if (!v.drop[r]) {
+      const float inv = 1.f / R[r * kWL + r];
+      for (int c = r + warp; c < p; c += nw) {
+        float acc = 0.f;
+        if (c > r && !v.drop[c])
+          for (int k = r + 1 + lane; k <= c; k += 32) acc = fmaf(R[r * kWL + k], X[k * kWL + c], acc);
+        acc = warp_sum(acc);
+        if (lane == 0 && !v.drop[c]) X[r * kWL + c] = (c == r) ? inv : -acc * inv;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Round-robin schedule: pair w of round rnd among N (even) indices.
+__device__ __forceinline__ void wd_rr_pair(int rnd, int w, int N, int& p, int& q) {
+  if (w == 0) {
+    p = N - 1;
+    q = rnd;
+  } else {
+    p = (rnd + w) % (N - 1);
+    q = (rnd - w + (N - 1)) % (N - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// One-sided Jacobi on the columns of R^T (Xt[c][a] = R[c][a], c < N even): a pair of columns
+// per 8 threads, each thread holding 16 elements (float4 at 4 sub + 32 jj).  The 8 threads of a
+// pair reduce alpha, beta, gamma with xor butterflies (every lane forms the same sums, so they
+// agree on the rotation).  Returns the sweeps taken.
+__device__ int wide_jacobi(float* Xt, int N, int max_sweeps, float tol) {
+  const int tid = threadIdx.x;
+  const int slot = tid >> 3, sub = tid & 7;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < max_sweeps && N >= 2; ++sweep) {
+    int rotated = 0;
+    for (int rnd = 0; rnd < N - 1; ++rnd) {
+      if (tid < 512) {                       // whole warps: every lane takes part in the shuffles
+        const bool act = slot < N / 2;
+        int p = 0, q = 0;
+        if (act) wd_rr_pair(rnd, slot, N, p, q);
+        float4* xp = reinterpret_cast<float4*>(Xt + p * kWL);
+        float4* xq = reinterpret_cast<float4*>(Xt + q * kWL);
+        float4 a[4], b[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          a[jj] = act ? xp[sub + 8 * jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+          b[jj] = act ? xq[sub + 8 * jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          al = fmaf(a[jj].x, a[jj].x, al); al = fmaf(a[jj].y, a[jj].y, al);
+          al = fmaf(a[jj].z, a[jj].z, al); al = fmaf(a[jj].w, a[jj].w, al);
+          be = fmaf(b[jj].x, b[jj].x, be); be = fmaf(b[jj].y, b[jj].y, be);
+          be = fmaf(b[jj].z, b[jj].z, be); be = fmaf(b[jj].w, b[jj].w, be);
+          ga = fmaf(a[jj].x, b[jj].x, ga); ga = fmaf(a[jj].y, b[jj].y, ga);
+          ga = fmaf(a[jj].z, b[jj].z, ga); ga = fmaf(a[jj].w, b[jj].w, ga);
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (act && fabsf(ga) > tol * sqrtf(al * be) && al > 1e-30f && be > 1e-30f) {
+          const float zeta = (be - al) / (2.f * ga);
+          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = rsqrtf(1.f + t * t);
+          const float s = c * t;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const float4 x = a[jj], y = b[jj];
+            xp[sub + 8 * jj] = make_float4(c * x.x - s * y.x, c * x.y - s * y.y, c * x.z - s * y.z, c * x.w - s * y.w);
+            xq[sub + 8 * jj] = make_float4(s * x.x + c * y.x, s * x.y + c * y.y, s * x.z + c * y.z, s * x.w + c * y.w);
+          }
+          rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    sweeps = sweep + 1;
+    if (!__syncthreads_or(rotated)) break;
+  }
+  return sweeps;
+}
+
+struct CoreArgs {
+  int l;
+  float tau_host;
+  int tau_from_mu;
+  int update_rp;
+  int advance_counter;
+  int max_sweeps;
+};
+
+template <int TAIL>
+__global__ void __cluster_dims__(kWCL, 1, 1) __launch_bounds__(kGW, 1)
+k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_cta, double* __restrict__ cpart,
+          double* __restrict__ Gpk, unsigned* __restrict__ ticket, int p, double rank_tol, CoreArgs ca,
+          float* __restrict__ T1, float* __restrict__ T2, DevState* __restrict__ dst) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ int flag;
+  float* stg = reinterpret_cast<float*>(dsm);                                         // kGCols x kGSt
+  double* part_sm = reinterpret_cast<double*>(dsm + sizeof(float) * kGCols * kGSt);  // kGCount
+  const int tid = threadIdx.x;
+  int bi = 0, bj = 0;
+  if (tid < kGB) block_of(tid, bi, bj);
+  df64 acc[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = df64{0.f, 0.f};
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * per_cta;
+  const int64_t x1 = imin64(len, x0 + per_cta);
+  for (int64_t xs = x0; xs < x1; xs += kGCols) {
+    const int nxc = static_cast<int>(imin64(kGCols, x1 - xs));
+    for (int e = tid; e < kWL * kGCols; e += kGW) {
+      const int a = e / kGCols, x = e % kGCols;
+      stg[x * kGSt + a] = (x < nxc && a < p) ? __ldcg(XT + a * ldx + xs + x) : 0.f;
+    }
+    __syncthreads();
+    if (tid < kGB) {
+      for (int x = 0; x < nxc; ++x) {
+        const float4 ua = *reinterpret_cast<const float4*>(stg + x * kGSt + 4 * bi);
+        const float4 ub = *reinterpret_cast<const float4*>(stg + x * kGSt + 4 * bj);
+        const float va[4] = {ua.x, ua.y, ua.z, ua.w};
+        const float vb[4] = {ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df64_add_prod(acc[4 * i + j], va[i], vb[j]);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < kGB)
+#pragma unroll
+    for (int u = 0; u < 16; ++u) part_sm[tid * 16 + u] = df64_value(acc[u]);
+  __syncthreads();
+  const int nclusters = gridDim.x / kWCL;
+  if (!cluster_split_reduce<double, kWCL>(part_sm, kGCount, cpart, Gpk, ticket, blockIdx.x / kWCL, nclusters, &flag))
+    return;
+  if (cooperative_groups::this_cluster().block_rank() != 0) return;
+  __syncthreads();
+  df64* G = reinterpret_cast<df64*>(dsm + kTG);
+  float* R = reinterpret_cast<float*>(dsm + kTR);
+  const TailVec v = carve_vec(dsm);
+  unpack_gram(Gpk, G);
+  wide_cholesky(G, v, p, rank_tol);
+  if (TAIL == kTailOrth) {
+    extract_r(G, v, R, p);
+    float* X = reinterpret_cast<float*>(dsm + kTG);            // G is dead
+    wide_rinv(R, v, X, p);
+    for (int e = tid; e < kWL * kWL; e += kGW) T1[e] = X[e];
+    if (tid == 0) {
+      int s = 0;
+      for (int j = 0; j < p; ++j) s += v.drop[j] ? 0 : 1;
+      dst->s = s;
+      if (s < p) dst->status |= kDevRankDeficient;
+    }
+    return;
+  }
+  // core (steps 16-19): columns of R^T are the rows of R
+  extract_r(G, v, R, p);
+  const int N = (p + 1) / 2 * 2;
+  const int sweeps = wide_jacobi(R, N, ca.max_sweeps, 8e-6f);
+  float* U = reinterpret_cast<float*>(dsm + kTG);              // U[a][c], 64 KB
+  float* M = U + kWL * kWL;                                     // 64 KB
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int c = warp; c < kWL; c += kGW / 32) {
+    float s2 = 0.f;
+    for (int a = lane; a < kWL; a += 32) s2 = fmaf(R[c * kWL + a], R[c * kWL + a], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) v.sig[c] = (c < N) ? sqrtf(s2) : 0.f;
+  }
+  __syncthreads();
+  const float tau = ca.tau_from_mu ? static_cast<float>(1.0 / dst->mu) : ca.tau_host;
+  for (int e = tid; e < kWL * kWL; e += kGW) {
+    const int a = e / kWL, c = e % kWL;
+    U[e] = (v.sig[c] > 0.f) ? R[c * kWL + a] / v.sig[c] : 0.f;
+  }
+  if (tid < kWL) {
+    const float sc = v.sig[tid];
+    int rank = 0;
+    for (int c = 0; c < kWL; ++c) rank += (v.sig[c] > sc || (v.sig[c] == sc && c < tid)) ? 1 : 0;
+    v.perm[rank] = tid;
+    v.coef[tid] = (sc > tau) ? (sc - tau) / sc : 0.f;
+  }
+  __syncthreads();
+  int r = 0;
+  for (int c = 0; c < kWL; ++c) r += (v.sig[c] > tau) ? 1 : 0;
+  const int keep = ca.update_rp ? max(0, min(r, ca.l - 2)) : 0;
+  // M = U diag(coef) U^T (only columns with coef > 0 contribute)
+  for (int e = tid; e < kWL * kWL; e += kGW) {
+    const int a = e / kWL, b = e % kWL;
+    float s = 0.f;
+    for (int c = 0; c < kWL; ++c) {
+      const float w = v.coef[c];
+      if (w != 0.f) s = fmaf(U[a * kWL + c] * w, U[b * kWL + c], s);
+    }
+    M[e] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < kWL * kWL; e += kGW) {
+    T1[e] = M[e];
+    const int a = e / kWL, j = e % kWL;
+    T2[e] = (j < keep) ? U[a * kWL + v.perm[j]] : 0.f;
+  }
+  if (tid == 0) {
+    dst->r = r;
+    if (ca.update_rp) dst->keep = keep;
+    if (ca.advance_counter) dst->counter += 1;
+    if (sweeps >= ca.max_sweeps) dst->status |= kDevNotConverged;
+    bool finite = true;
+    for (int c = 0; c < kWL; ++c) {
+      dst->sigma[c] = v.sig[v.perm[c]];
+      finite = finite && isfinite(v.sig[c]);
+    }
+    for (int c = kWL; c < kMaxL; ++c) dst->sigma[c] = 0.f;
+    if (!finite) dst->status |= kDevNonfinite;
+    dst->sigma1 = static_cast<double>(v.sig[v.perm[0]]);
+  }
+}
+
+// ---------------------------------------------------------------- Out = T^T In
+// out[b][x] = sum_a T[a][b] in[a][x] for the 64 long-side columns x of the CTA (staged first, so
+// the output may alias the input).  Thread: x4 = t % 16 (4 columns), b4 = t / 16 (4 rows).
+constexpr int kAThr = 512;
+constexpr int kACols = 64;
+
+__global__ void __launch_bounds__(kAThr, 1)
+k_wd_apply(const float* in, int64_t ldi, int64_t len, const float* __restrict__ T, float* outT, float* outTl,
+           int64_t ldo, float* __restrict__ outR, float* __restrict__ outRl) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  float* Ts = reinterpret_cast<float*>(dsm);              // 128 x 128
+  float* Is = Ts + kWL * kWL;                             // 128 x 64
+  const int64_t xs = static_cast<int64_t>(blockIdx.x) * kACols;
+  const int nx = static_cast<int>(imin64(kACols, len - xs));
+  for (int e = threadIdx.x; e < kWL * kWL / 4; e += kAThr)
+    reinterpret_cast<float4*>(Ts)[e] = __ldcg(reinterpret_cast<const float4*>(T) + e);
+  for (int e = threadIdx.x; e < kWL * kACols; e += kAThr) {
+    const int a = e / kACols, x = e % kACols;
+    Is[e] = (x < nx) ? __ldcg(in + a * ldi + xs + x) : 0.f;
+  }
+  __syncthreads();
+  const int x4 = threadIdx.x % 16, b4 = threadIdx.x / 16;
+  float acc[4][4] = {};
+  for (int a = 0; a < kWL; ++a) {
+    const float4 t = reinterpret_cast<const float4*>(Ts + a * kWL)[b4];
+    const float4 u = reinterpret_cast<const float4*>(Is + a * kACols)[x4];
+    const float tb[4] = {t.x, t.y, t.z, t.w};
+    const float ux[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(tb[i], ux[j], acc[i][j]);
+  }
+  __syncthreads();                                         // all reads of `in` done (in-place outputs)
+  for (int i = 0; i < 4; ++i) {
+    const int b = 4 * b4 + i;
+    const float4 v = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    if (4 * x4 < nx) {
+      if (outT != nullptr) reinterpret_cast<float4*>(outT + b * ldo + xs)[x4] = v;
+      if (outTl != nullptr) reinterpret_cast<float4*>(outTl + b * ldo + xs)[x4] = f4_lo(v);
+    }
+  }
+  if (outR != nullptr) {
+    for (int j = 0; j < 4; ++j) {
+      const int x = 4 * x4 + j;
+      if (x >= nx) continue;
+      const float4 v = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+      reinterpret_cast<float4*>(outR + (xs + x) * kWL)[b4] = v;
+      if (outRl != nullptr) reinterpret_cast<float4*>(outRl + (xs + x) * kWL)[b4] = f4_lo(v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- reconstruction (+ iALM)
+// X tile (128 rows x 256 columns) = Z_blk Rf_blk^T on tcgen05: M = 128 rows of Z, N = 256 rows
+// of Rf (columns of X), K = 128 in 4 chunks of 32; 3xTF32 as Z_hi Rf_hi + Z_lo Rf_hi + Z_hi Rf_lo
+// (Z_lo, Rf_lo precomputed).  Persistent CTAs walk the tiles; the accumulator is double
+// buffered in tensor memory so the epilogue of one tile overlaps the MMAs of the next.
+// Epilogue: 8 warps, two per lane quarter (columns 0-127 / 128-255 of the tile); a thread owns
+// row 32 q + L and reads O, S, A directly (16 consecutive columns per tcgen05.ld).
+constexpr int kEStages = 2;
+constexpr int kEW = 8;                                   // epilogue warps
+constexpr int kEThr = 64 + 32 * kEW;
+constexpr uint32_t kEZ = 128 * kWK * 4;                  // 16 KB
+constexpr uint32_t kER = kWN * kWK * 4;                  // 32 KB
+constexpr uint32_t kEStage = 2 * kEZ + 2 * kER;          // 96 KB
+
+template <bool ALM>
+__global__ void __launch_bounds__(kEThr, 1)
+k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtensorMap tmZl,
+         const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmRl, int64_t m, int64_t n,
+         const float* __restrict__ O, float* __restrict__ S, float* __restrict__ A, int64_t ld, float* __restrict__ L,
+         int64_t ldl, DevState* __restrict__ dst, double* __restrict__ cpart, unsigned* __restrict__ ticket) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t full[kEStages], empty[kEStages], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ double red[kEThr / 32];
+  __shared__ int flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntr = static_cast<int>((m + 127) / 128), ntc = static_cast<int>((n + kWN - 1) / kWN);
+  const int ntiles = ntr * ntc;
+  const int mine = (blockIdx.x < ntiles) ? (ntiles - 1 - static_cast<int>(blockIdx.x)) / gridDim.x + 1 : 0;
+  if ((smem_addr(dsm) & 1023u) != 0u) {               // swizzled TMA destinations need 1024-byte alignment
+    if (threadIdx.x == 0) atomicOr(&dst->status, kDevBadProblem);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kEStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kEW);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  bool ok = true;
+  float res2 = 0.f;
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tensormap(&tmZ);
+      prefetch_tensormap(&tmZl);
+      prefetch_tensormap(&tmR);
+      prefetch_tensormap(&tmRl);
+      for (int g = 0; g < 4 * mine && ok; ++g) {
+        const int s = g % kEStages, u = g / kEStages;
+        const int tl = static_cast<int>(blockIdx.x) + (g / 4) * static_cast<int>(gridDim.x);
+        const int tr = tl / ntc, tc = tl % ntc, c = g % 4;
+        if (u > 0 && !mbar_wait(&empty[s], static_cast<uint32_t>(u - 1) & 1u)) {
+          flag_timeout(ok, dst);
+          break;
+        }
+        unsigned char* st = dsm + s * kEStage;
+        mbar_arrive_expect_tx(&full[s], kEStage);
+        tma_load_2d(st, &tmZ, kWK * c, 128 * tr, &full[s]);
+        tma_load_2d(st + kEZ, &tmZl, kWK * c, 128 * tr, &full[s]);
+        tma_load_2d(st + 2 * kEZ, &tmR, kWK * c, kWN * tc, &full[s]);
+        tma_load_2d(st + 2 * kEZ + kER, &tmRl, kWK * c, kWN * tc, &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(128, kWN);
+      for (int k = 0; k < mine; ++k) {
+        const int buf = k & 1;
+        if (k >= 2 && ok && !mbar_wait(&acc_empty[buf], static_cast<uint32_t>(k / 2 - 1) & 1u)) flag_timeout(ok, dst);
+        tc_fence_after();
+        const uint32_t d = tbase + static_cast<uint32_t>(buf * kWN);
+        for (int c = 0; c < 4; ++c) {
+          const int g = 4 * k + c;
+          const int s = g % kEStages, u = g / kEStages;
+          if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
+          tc_fence_after();
+          const unsigned char* st = dsm + s * kEStage;
+#pragma unroll
+          for (int ks = 0; ks < kWK / 8; ++ks) {
+            const uint64_t zh = smem_desc_sw128(st + 32 * ks, 16, 1024);
+            const uint64_t zl = smem_desc_sw128(st + kEZ + 32 * ks, 16, 1024);
+            const uint64_t rh = smem_desc_sw128(st + 2 * kEZ + 32 * ks, 16, 1024);
+            const uint64_t rl = smem_desc_sw128(st + 2 * kEZ + kER + 32 * ks, 16, 1024);
+            tc_mma_tf32(d, zh, rh, idesc, c > 0 || ks > 0);
+            tc_mma_tf32(d, zl, rh, idesc, true);
+            tc_mma_tf32(d, zh, rl, idesc, true);
+          }
+          tc_commit(&empty[s]);
+        }
+        tc_commit(&acc_full[buf]);
+      }
+    }
+  } else {
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    double mu = 0.0, mu_next = 0.0;
+    float thr = 0.f, ratio = 0.f;
+    if (ALM) {
+      mu = dst->mu;
+      mu_next = fmin(dst->rho * mu, dst->mu_bar);
+      thr = static_cast<float>(dst->lambda / mu);
+      ratio = static_cast<float>(mu / mu_next);
+    }
+    for (int k = 0; k < mine; ++k) {
+      const int buf = k & 1;
+      const int tl = static_cast<int>(blockIdx.x) + k * static_cast<int>(gridDim.x);
+      const int tr = tl / ntc, tc = tl % ntc;
+      if (ok && !mbar_wait(&acc_full[buf], static_cast<uint32_t>(k / 2) & 1u)) flag_timeout(ok, dst);
+      tc_fence_after();
+      const int64_t row = 128 * static_cast<int64_t>(tr) + 32 * q + lane;
+      for (int cg = 0; cg < 8; ++cg) {
+        float x[16];
+        const int colt = 128 * half + 16 * cg;
+        tmem_ld16(tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(buf * kWN + colt), x);
+        const int64_t col0 = static_cast<int64_t>(kWN) * tc + colt;
+        if (row >= m || col0 >= n || !ok) continue;
+        const bool full16 = col0 + 16 <= n;
+        if (!ALM) {
+          if (full16) {
+            float4* o4 = reinterpret_cast<float4*>(L + row * ldl + col0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) o4[u] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
+          } else {
+            for (int u = 0; u < 16; ++u)
+              if (col0 + u < n) L[row * ldl + col0 + u] = x[u];
+          }
+          continue;
+        }
+        float ov[16], sv[16], av[16];
+        if (full16) {
+          const float4* O4 = reinterpret_cast<const float4*>(O + row * ld + col0);
+          const float4* S4 = reinterpret_cast<const float4*>(S + row * ld + col0);
+          const float4* A4 = reinterpret_cast<const float4*>(A + row * ld + col0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 o = __ldcs(O4 + u), s = __ldcs(S4 + u), a = __ldcs(A4 + u);
+            ov[4 * u] = o.x; ov[4 * u + 1] = o.y; ov[4 * u + 2] = o.z; ov[4 * u + 3] = o.w;
+            sv[4 * u] = s.x; sv[4 * u + 1] = s.y; sv[4 * u + 2] = s.z; sv[4 * u + 3] = s.w;
+            av[4 * u] = a.x; av[4 * u + 1] = a.y; av[4 * u + 2] = a.z; av[4 * u + 3] = a.w;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const bool in = col0 + u < n;
+            ov[u] = in ? O[row * ld + col0 + u] : 0.f;
+            sv[u] = in ? S[row * ld + col0 + u] : 0.f;
+            av[u] = in ? A[row * ld + col0 + u] : 0.f;
+          }
+        }
+        float sn[16], an[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const float t = av[u] + sv[u] - x[u];                        // O - L + Y / mu
+          sn[u] = (t > thr) ? (t - thr) : ((t < -thr) ? (t + thr) : 0.f);
+          an[u] = ov[u] - sn[u] + ratio * (t - sn[u]);                  // O - S' + Y' / mu'
+          const float rz = ov[u] - x[u] - sn[u];                        // O - L - S'
+          if (col0 + u < n) res2 = fmaf(rz, rz, res2);
+        }
+        if (full16) {
+          float4* S4 = reinterpret_cast<float4*>(S + row * ld + col0);
+          float4* A4 = reinterpret_cast<float4*>(A + row * ld + col0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            __stcs(S4 + u, make_float4(sn[4 * u], sn[4 * u + 1], sn[4 * u + 2], sn[4 * u + 3]));
+            __stcs(A4 + u, make_float4(an[4 * u], an[4 * u + 1], an[4 * u + 2], an[4 * u + 3]));
+          }
+          if (L != nullptr) {
+            float4* L4 = reinterpret_cast<float4*>(L + row * ldl + col0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) L4[u] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
+          }
+        } else {
+          for (int u = 0; u < 16; ++u)
+            if (col0 + u < n) {
+              S[row * ld + col0 + u] = sn[u];
+              A[row * ld + col0 + u] = an[u];
+              if (L != nullptr) L[row * ldl + col0 + u] = x[u];
+            }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tbase, 512);
+  if (!ALM) return;
+  const double v = warp_sum(static_cast<double>(res2));
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kEThr / 32; ++w) t += red[w];
+    cpart[blockIdx.x] = t;
+  }
+  if (!last_of(ticket, gridDim.x, &flag)) return;
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) s2 += __ldcg(cpart + b);
+    const double rr = (dst->normO_F > 0.0) ? sqrt(s2) / dst->normO_F : 0.0;
+    const double mu = dst->mu;
+    dst->resid_ratio = rr;
+    if (!isfinite(rr)) dst->status |= kDevNonfinite;
+    dst->mu = fmin(dst->rho * mu, dst->mu_bar);
+    dst->iter += 1;
+  }
+}
+
+template <typename K>
+cudaError_t set_dyn(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+int wide_lp() { return kWL; }
+int wide_tile() { return kWN; }
+
+cudaError_t prepare_wide_kernels() {
+  cudaError_t e = set_dyn(k_wd_pass<false>, kWStages * kWStage);
+  if (e == cudaSuccess) e = set_dyn(k_wd_pass<true>, kWStages * kWStage);
+  if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailOrth>, kGSmem);
+  if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailCore>, kGSmem);
+  if (e == cudaSuccess) e = set_dyn(k_wd_apply, sizeof(float) * kWL * (kWL + kACols));
+  if (e == cudaSuccess) e = set_dyn(k_wd_alm<true>, kEStages * kEStage);
+  if (e == cudaSuccess) e = set_dyn(k_wd_alm<false>, kEStages * kEStage);
+  return e;
+}
+
+// Resident clusters of the Gram kernel, in CTAs (a multiple of its cluster size).
+int wide_gram_grid() {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kWCL, 1, 1);
+  cfg.blockDim = dim3(kGW, 1, 1);
+  cfg.dynamicSmemBytes = kGSmem;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = kWCL;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, reinterpret_cast<const void*>(k_wd_gram<kTailCore>), &cfg) != cudaSuccess)
+    nc = 0;
+  (void)cudaGetLastError();
+  return nc * kWCL;
+}
+
+int wide_gram_count() { return kGCount; }
+
+cudaError_t launch_wd_omega(float* OT, float* OTl, int64_t ldo, int64_t m, int l, int use_rp, uint64_t seed,
+                            uint64_t ctr, const DevState* dst, cudaStream_t st) {
+  const int64_t total = m * (kWL / 4);
+  int64_t grid = (total + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  k_wd_omega<<<static_cast<int>(grid), 256, 0, st>>>(OT, OTl, ldo, m, l, use_rp, seed, ctr, dst);
+  return cudaGetLastError();
+}
+
+// Splits of K per tile so that ntiles * S covers the SMs once (S <= 8, at least 2 chunks each).
+int wide_splits(int64_t nlong, int64_t nk, int sms) {
+  const int64_t ntiles = (nlong + kWN - 1) / kWN;
+  const int64_t nkc = (nk + kWK - 1) / kWK;
+  int64_t S = sms / (ntiles > 0 ? ntiles : 1);
+  if (S > 8) S = 8;
+  if (S > nkc / 2) S = nkc / 2;
+  if (S < 1) S = 1;
+  return static_cast<int>(S);
+}
+
+cudaError_t launch_wd_pass(bool col, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
+                           int64_t nlong, int64_t nk, int S, float* part, int64_t ldp, unsigned* tickets, float* outT,
+                           float* outTl, int64_t ldo, float* outR, float* outRl, DevState* dst, cudaStream_t st) {
+  const int ntiles = static_cast<int>((nlong + kWN - 1) / kWN);
+  const size_t smem = kWStages * kWStage;
+  if (col)
+    k_wd_pass<true><<<ntiles * S, kWThr, smem, st>>>(tmA, tmM, tmMl, nlong, nk, S, part, ldp, tickets, outT, outTl,
+                                                     ldo, outR, outRl, dst);
+  else
+    k_wd_pass<false><<<ntiles * S, kWThr, smem, st>>>(tmA, tmM, tmMl, nlong, nk, S, part, ldp, tickets, outT, outTl,
+                                                      ldo, outR, outRl, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len, int grid, double* cpart, double* Gpk,
+                           unsigned* ticket, int p, double rank_tol, int l, float tau_host, int tau_from_mu,
+                           int update_rp, int advance_counter, int max_sweeps, float* T1, float* T2, DevState* dst,
+                           cudaStream_t st) {
+  const int64_t per = (len + grid - 1) / grid;
+  CoreArgs ca{l, tau_host, tau_from_mu, update_rp, advance_counter, max_sweeps};
+  if (core)
+    k_wd_gram<kTailCore><<<grid, kGW, kGSmem, st>>>(XT, ldx, len, per, cpart, Gpk, ticket, p, rank_tol, ca, T1, T2, dst);
+  else
+    k_wd_gram<kTailOrth><<<grid, kGW, kGSmem, st>>>(XT, ldx, len, per, cpart, Gpk, ticket, p, rank_tol, ca, T1, T2, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wd_apply(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
+                            int64_t ldo, float* outR, float* outRl, cudaStream_t st) {
+  const int grid = static_cast<int>((len + kACols - 1) / kACols);
+  if (grid == 0) return cudaSuccess;
+  k_wd_apply<<<grid, kAThr, sizeof(float) * kWL * (kWL + kACols), st>>>(in, ldi, len, T, outT, outTl, ldo, outR, outRl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wd_alm(bool alm, const CUtensorMap& tmZ, const CUtensorMap& tmZl, const CUtensorMap& tmR,
+                          const CUtensorMap& tmRl, int64_t m, int64_t n, const float* O, float* S, float* A, int64_t ld,
+                          float* L, int64_t ldl, DevState* dst, double* cpart, unsigned* ticket, int grid,
+                          cudaStream_t st) {
+  const size_t smem = kEStages * kEStage;
+  if (alm)
+    k_wd_alm<true><<<grid, kEThr, smem, st>>>(tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, dst, cpart, ticket);
+  else
+    k_wd_alm<false><<<grid, kEThr, smem, st>>>(tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, dst, cpart, ticket);
+  return cudaGetLastError();
+}
+
+}  // namespace frsvt

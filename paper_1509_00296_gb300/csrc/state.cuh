@@ -8,7 +8,7 @@
 
 namespace frsvt {
 
-constexpr int kMaxL = 32;                // largest padded basis width (l_max <= 32)
+constexpr int kMaxL = 128;               // largest padded basis width (l_max <= 128)
 constexpr uint64_t kCounterFromState = ~0ull;
 
 struct DevState {

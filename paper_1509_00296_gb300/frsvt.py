@@ -298,9 +298,9 @@ class Handle:
         return nt.value, cps.value
 
     def sigma(self):
-        buf = (ctypes.c_float * 32)()
+        buf = (ctypes.c_float * 128)()
         cnt = ctypes.c_int32()
-        self._chk(lib().frsvt_get_sigma(self._h, buf, 32, ctypes.byref(cnt)))
+        self._chk(lib().frsvt_get_sigma(self._h, buf, 128, ctypes.byref(cnt)))
         return [buf[i] for i in range(cnt.value)]
 
 

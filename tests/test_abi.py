@@ -50,8 +50,10 @@ def test_invalid_arguments_rejected_on_host(libpath):
     h = ctypes.c_void_p()
     bad = frsvt.Config(0, 10, 8, 1, 1, 0, 0, 30, 0, 1e-10)           # m_max = 0
     assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
-    bad = frsvt.Config(10, 10, 33, 1, 1, 0, 0, 30, 0, 1e-10)         # l_max > 32
+    bad = frsvt.Config(10, 10, 129, 1, 1, 0, 0, 30, 0, 1e-10)        # l_max > 128
     assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
+    bad = frsvt.Config(10, 10, 33, 1, 1, 0, 0, 30, 0, 1e-10)         # wide basis with range propagation
+    assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 2
     bad = frsvt.Config(10, 10, 8, 1, 1, 7, 0, 30, 0, 1e-10)          # unknown precision
     assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 2
     assert L.frsvt_create(None, None, None) == 1

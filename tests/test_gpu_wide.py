@@ -1,0 +1,138 @@
+"""Parity of the wide-basis path (32 < l <= 128, any short side) with the FP64 oracle.
+
+The large low-rank recovery configuration runs FRSVT with l = 120 on an 8192 x 8192 matrix;
+the basis then spans several 256-column tiles of the tensor-core passes and the small dense
+steps (Cholesky QR, the l x l core) run as grid-wide kernels.  Parity is checked on shapes that
+span several tiles with ragged tails, on a rank-deficient input, on iALM iterations, and on the
+full-size configuration.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import rel_fro, spectrum_matrix, to_gpu
+from oracle import rpca as orpca
+from oracle import svt as osvt
+from paper_1509_00296_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def fr():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1509_00296_gb300 import build, frsvt
+    build.build()
+    return frsvt
+
+
+def power_norm2(O, iters=40, seed=0):
+    """||O||_2 estimate (FP64 power method); both sides receive the same value."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(O.shape[1])
+    s = 0.0
+    for _ in range(iters):
+        u = O @ v
+        v = O.T @ u
+        s = np.linalg.norm(v)
+        v /= s
+    return float(np.sqrt(s))
+
+
+@pytest.mark.parametrize("m,n,l,q,rank,decay", [
+    (1000, 700, 120, 2, 160, 0.985),
+    (2048, 2048, 120, 1, 200, 0.99),
+    (777, 333, 50, 1, 80, 0.97),
+    (600, 90, 48, 2, 60, 0.95),
+    (1500, 1000, 96, 0, 110, 0.98),
+])
+def test_wide_frsvt_parity(fr, m, n, l, q, rank, decay):
+    """FRSVT with a wide basis: X, r and the leading sigma against the oracle's Alg. 1."""
+    A, s = spectrum_matrix(m, n, rank, decay, 0.01, seed=31 * m + n)
+    A = A.astype(np.float32).astype(np.float64)
+    tau = float(0.5 * (s[l // 2] + s[l // 2 + 1]))
+    ref = osvt.frsvt(A, tau, l, q, seed=11, stream=0)
+    h = fr.Handle(m, n, l, q=q, range_prop=False, seed=11)
+    X = h.svt(to_gpu(A), tau, l, X=to_gpu(np.zeros_like(A))).cpu().numpy()
+    info = h.info()
+    assert info.device_status & ~1 == 0, info
+    assert rel_fro(X, ref.X) <= TOL
+    assert info.r == ref.r
+    sig = h.sigma()
+    k = ref.r
+    assert np.allclose(sig[:k], ref.sigma[:k], rtol=1e-4)
+    h.close()
+
+
+def test_wide_rank_deficient(fr):
+    """rank(A) = 20 < l = 64: X equals the exact SVT; the rank cut keeps the basis usable."""
+    m, n = 1200, 900
+    A, s = spectrum_matrix(m, n, 20, 0.9, 0.0, seed=5)
+    A = A.astype(np.float32).astype(np.float64)
+    tau = float(0.5 * (s[9] + s[10]))
+    ref, _ = osvt.exact_svt(A, tau)
+    h = fr.Handle(m, n, 64, q=1, range_prop=False, seed=3)
+    X = h.svt(to_gpu(A), tau, 64, X=to_gpu(np.zeros_like(A))).cpu().numpy()
+    info = h.info()
+    assert info.device_status & ~1 == 0, info
+    assert rel_fro(X, ref) <= TOL
+    assert info.r == 10
+    h.close()
+
+
+def test_wide_ragged_leading_dimension(fr):
+    """Padded rows (ld > n) and sizes that are not multiples of any tile."""
+    m, n, l = 1031, 517, 72
+    A, s = spectrum_matrix(m, n, 90, 0.97, 0.01, seed=9)
+    A = A.astype(np.float32).astype(np.float64)
+    tau = float(0.5 * (s[30] + s[31]))
+    ref = osvt.frsvt(A, tau, l, 1, seed=4, stream=0)
+    h = fr.Handle(m, n, l, q=1, range_prop=False, seed=4)
+    ld = n + 7 + 4 - (n + 7) % 4
+    X = h.svt(to_gpu(A, ld=ld), tau, l, X=to_gpu(np.zeros_like(A), ld=ld)).cpu().numpy()
+    assert rel_fro(X, ref.X) <= TOL
+    h.close()
+
+
+def run_ialm(fr, O, l, q, iters, seed, normO2):
+    import torch
+    m, n = O.shape
+    Og = torch.from_numpy(np.ascontiguousarray(O, dtype=np.float32)).cuda()
+    S, A, L = torch.empty_like(Og), torch.empty_like(Og), torch.empty_like(Og)
+    h = fr.Handle(m, n, l, q=q, range_prop=False, seed=seed)
+    h.rpca_init(Og, S, A, 1.0 / np.sqrt(max(m, n)), 1.5, 1e7, normO2=normO2)
+    hist = []
+    for k in range(iters):
+        hist.append(h.ialm_step(Og, S, A, l, L=L if k == iters - 1 else None, sync_residual=True))
+    info = h.info()
+    out = L.cpu().numpy(), S.cpu().numpy(), hist, info
+    h.close()
+    return out
+
+
+def test_wide_ialm_parity(fr):
+    """iALM with FRSVT (l = 60, q = 2) on 1024 x 1024 rank 20 + 10 % corruption: 4 iterations."""
+    O, _, _ = synth.lowrank_sparse(1024, 1024, 20, 0.10, 10.0, seed=77, scale=1.0 / np.sqrt(20.0))
+    O = O.astype(np.float32).astype(np.float64)
+    nrm = power_norm2(O)
+    ref = orpca.ialm_rpca(O, method="frsvt", l=60, q=2, seed=2003, range_prop=False, fixed_iters=4, normO2=nrm)
+    L, S, hist, info = run_ialm(fr, O, 60, 2, 4, 2003, nrm)
+    assert info.alm_iter == 4
+    assert rel_fro(L, ref.L) <= TOL
+    assert rel_fro(S, ref.S) <= TOL
+    assert np.allclose(hist, ref.history, rtol=1e-3)
+
+
+def test_wide_recovery_8192_full_size(fr):
+    """Large low-rank recovery, 8192 x 8192 rank 100 + 10 % corruption, FRSVT l = 120, q = 2:
+    three iALM iterations at full size against the oracle."""
+    O, _, _ = synth.recovery_8192()
+    O = O.astype(np.float64)
+    nrm = power_norm2(O, iters=30)
+    ref = orpca.ialm_rpca(O, method="frsvt", l=120, q=2, seed=2004, range_prop=False, fixed_iters=3, normO2=nrm)
+    L, S, hist, info = run_ialm(fr, O, 120, 2, 3, 2004, nrm)
+    assert info.device_status & ~1 == 0, info
+    assert rel_fro(L, ref.L) <= TOL
+    assert rel_fro(S, ref.S) <= TOL
+    assert np.allclose(hist, ref.history, rtol=1e-3)
