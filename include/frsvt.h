@@ -87,7 +87,7 @@ typedef struct frsvt_info {
   uint32_t device_status;        /* sticky FRSVT_DEV_* bits, cleared by the read */
   uint64_t counter;              /* Omega stream index the next SVT will use */
   int32_t alm_iter;              /* iALM iterations done since rpca_init */
-  int32_t reserved;
+  int32_t sweeps;                /* Jacobi sweeps of the last l x l core SVD (Alg. 1 step 18) */
   double mu;                     /* iALM penalty mu for the next iteration */
   double residual;               /* ||O - L - S||_F / ||O||_F of the last iALM step */
 } frsvt_info;

@@ -132,6 +132,8 @@ cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len,
                            cudaStream_t st);
 cudaError_t launch_wd_apply(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
                             int64_t ldo, float* outR, float* outRl, cudaStream_t st);
+cudaError_t launch_wd_trsm(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
+                           int64_t ldo, cudaStream_t st);
 cudaError_t launch_wd_alm(bool alm, const CUtensorMap& tmZ, const CUtensorMap& tmZl, const CUtensorMap& tmR,
                           const CUtensorMap& tmRl, int64_t m, int64_t n, const float* O, float* S, float* A, int64_t ld,
                           float* L, int64_t ldl, DevState* dst, double* cpart, unsigned* ticket, int grid,
@@ -540,7 +542,7 @@ frsvt_status wide_orth(frsvt_handle* h, int64_t n, int l, int passes) {
     FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_gram(false, src, ld, n, h->w_gram_grid, h->wgc, h->wGpk, gt, l,
                                                   h->cfg.rank_tol, l, 0.f, 0, 0, 0, h->cfg.max_jacobi_sweeps, h->wT1,
                                                   h->wT2, h->dst, st));
-    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_apply(src, ld, n, h->wT1, h->wQT, h->wQTl, ld, nullptr, nullptr, st));
+    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_trsm(src, ld, n, h->wT1, h->wQT, h->wQTl, ld, st));
   }
   return FRSVT_OK;
 }
@@ -1251,6 +1253,7 @@ frsvt_status frsvt_get_info(frsvt_handle* h, frsvt_info* info) {
   info->device_status = d.status;
   info->counter = d.counter;
   info->alm_iter = d.iter;
+  info->sweeps = d.sweeps;
   info->mu = d.mu;
   info->residual = d.resid_ratio;
   return FRSVT_OK;

@@ -328,98 +328,109 @@ __device__ TailVec carve_vec(unsigned char* base) {
   return v;
 }
 
-// Unpack the block-packed Gram (global, doubles) into the full symmetric df64 matrix G.
-__device__ void unpack_gram(const double* __restrict__ Gpk, df64* G) {
-  for (int e = threadIdx.x; e < kGCount; e += blockDim.x) {
-    const int blk = e / 16, ij = e % 16;
-    int bi, bj;
-    block_of(blk, bi, bj);
-    const int a = 4 * bi + ij / 4, b = 4 * bj + ij % 4;
-    const df64 v = df_from_double(__ldcg(Gpk + e));
-    G[a * kWL + b] = v;
-    G[b * kWL + a] = v;
-  }
-  __syncthreads();
+// Entry k (runtime, 0..3) of four registers, by selects (no local-memory indexing).
+__device__ __forceinline__ df64 sel4(df64 a, df64 b, df64 c, df64 d, int k) {
+  return k == 0 ? a : (k == 1 ? b : (k == 2 ? c : d));
+}
+
+// Pivot of column j from its (updated) diagonal entry d: the drop rule of the l <= 32 path
+// (pivot not above rank_tol * original G_jj, G_jj below 1e-15 of the largest diagonal, or not a
+// finite positive number) and 1 / sqrt(d).
+__device__ __forceinline__ void wide_pivot(df64 d, int j, const TailVec& v, float maxdiag, df64* s_inv, int* s_drop,
+                                           float* Rout) {
+  const bool drop = !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
+  df64 inv{0.f, 0.f};
+  if (!drop) inv = df_rsqrt(d);
+  *s_inv = inv;
+  *s_drop = drop ? 1 : 0;
+  v.rdiag[j] = drop ? df64{0.f, 0.f} : df_mul(d, inv);
+  v.drop[j] = drop ? 1 : 0;
+  Rout[j * kWL + j] = drop ? 0.f : v.rdiag[j].hi;
 }
 
 // Right-looking Cholesky G = R^T R of the leading p x p block in double-float arithmetic, with
-// the column drops of the l <= 32 path: column j is dropped (row j of R zero) when its pivot is
-// not above rank_tol * G_jj (original), when G_jj is below 1e-15 of the largest diagonal, or when
-// it is not a finite positive number.  R_jj goes to v.rdiag[j]; R[j][a] (a > j) to G[a][j] (the
-// lower triangle, never read by the updates of the upper one).  One barrier per column: every
-// thread forms the pivot itself, warps own rows a of the trailing upper triangle.
-__device__ void wide_cholesky(df64* G, const TailVec& v, int p, double rank_tol) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  if (tid < kWL) {
-    const float g0 = (tid < p) ? G[tid * kWL + tid].hi : 0.f;
-    v.g0[tid] = g0;
-    v.thr[tid] = static_cast<float>(rank_tol * static_cast<double>(g0));
-  }
+// the column drops of the l <= 32 path.  Thread t < 528 keeps its 4 x 4 block (bi, bj), bi <= bj,
+// of the upper triangle in registers for the whole factorization.  Per column j: the owners of
+// row j publish R[j][:] = G[j][:] / R_jj (shared), then every block takes its rank-1 update; the
+// owner of the next pivot updates that entry first and forms the next 1 / R_jj during the same
+// phase (double-buffered), so each column costs two barriers.  R (FP32, row-major, upper,
+// dropped rows zero) goes to Rout; v.rdiag / v.drop receive the diagonal and the drop flags.
+__device__ void wide_cholesky(const double* __restrict__ Gpk, const TailVec& v, df64* Rrow, float* Rout, int p,
+                              double rank_tol) {
+  const int tid = threadIdx.x;
+  const bool own = tid < kGB;
+  int bi = 0, bj = 0;
+  if (own) block_of(tid, bi, bj);
+  df64 g[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) g[u] = own ? df_from_double(__ldcg(Gpk + tid * 16 + u)) : df64{0.f, 0.f};
+  for (int e = tid; e < kWL * kWL; e += blockDim.x) Rout[e] = 0.f;
+  if (own && bi == bj)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int a = 4 * bi + i;
+      v.g0[a] = (a < p) ? g[5 * i].hi : 0.f;
+    }
+  __syncthreads();
+  if (tid < kWL) v.thr[tid] = static_cast<float>(rank_tol * static_cast<double>(v.g0[tid]));
   __syncthreads();
   float maxdiag = 0.f;
   for (int a = 0; a < p; ++a) maxdiag = fmaxf(maxdiag, v.g0[a]);
+  __shared__ df64 s_inv[2];
+  __shared__ int s_drop[2];
+  if (p > 0 && own && bi == 0 && bj == 0) wide_pivot(g[0], 0, v, maxdiag, &s_inv[0], &s_drop[0], Rout);
+  __syncthreads();
   for (int j = 0; j < p; ++j) {
-    const df64 d = G[j * kWL + j];
-    const bool drop = !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
-    df64 inv{0.f, 0.f};
-    if (!drop) inv = df_rsqrt(d);
-    if (tid == 0) {
-      v.rdiag[j] = drop ? df64{0.f, 0.f} : df_mul(d, inv);
-      v.drop[j] = drop ? 1 : 0;
-    }
-    for (int a = j + 1 + warp; a < p; a += nw) {
-      const df64 ra = drop ? df64{0.f, 0.f} : df_mul(G[j * kWL + a], inv);
-      if (lane == 0) G[a * kWL + j] = ra;
-      if (!drop)
-        for (int b = a + lane; b < p; b += 32) {
-          const df64 rb = df_mul(G[j * kWL + b], inv);
-          G[a * kWL + b] = df_add(G[a * kWL + b], df_neg(df_mul(ra, rb)));
+    const int jb = j >> 2, jr = j & 3, buf = j & 1;
+    const int drop = s_drop[buf];
+    if (own && bi == jb) {                             // row j of R, columns b > j
+      const df64 inv = s_inv[buf];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int b = 4 * bj + c;
+        const df64 gv = sel4(g[c], g[4 + c], g[8 + c], g[12 + c], jr);
+        if (b > j && b < p) {
+          const df64 r = drop ? df64{0.f, 0.f} : df_mul(gv, inv);
+          Rrow[b] = r;
+          Rout[j * kWL + b] = r.hi;
         }
+      }
     }
     __syncthreads();
-  }
-  for (int j = p + tid; j < kWL; j += nt) {
-    v.rdiag[j] = df64{0.f, 0.f};
-    v.drop[j] = 1;
-  }
-  __syncthreads();
-}
-
-// R (FP32, row-major, upper) from the factorization: R[j][j] = rdiag, R[j][a] = G[a][j].
-__device__ void extract_r(const df64* G, const TailVec& v, float* R, int p) {
-  for (int e = threadIdx.x; e < kWL * kWL; e += blockDim.x) {
-    const int j = e / kWL, a = e % kWL;
-    float x = 0.f;
-    if (j < p && a < p && !v.drop[j]) {
-      if (a == j) x = v.rdiag[j].hi;
-      else if (a > j) x = G[a * kWL + j].hi;
-    }
-    R[e] = x;
-  }
-  __syncthreads();
-}
-
-// X = R^{-1} (upper triangular, FP32) with the rows and columns of dropped indices zero;
-// back substitution row by row from the bottom, warps own columns, lanes split the dot.
-__device__ void wide_rinv(const float* R, const TailVec& v, float* X, int p) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  for (int e = tid; e < kWL * kWL; e += nt) X[e] = 0.f;
-  __syncthreads();
-  for (int r = p - 1; r >= 0; --r) {
-    if (!v.drop[r]) {
-      const float inv = 1.f / R[r * kWL + r];
-      for (int c = r + warp; c < p; c += nw) {
-        float acc = 0.f;
-        if (c > r && !v.drop[c])
-          for (int k = r + 1 + lane; k <= c; k += 32) acc = fmaf(R[r * kWL + k], X[k * kWL + c], acc);
-        acc = warp_sum(acc);
-        if (lane == 0 && !v.drop[c]) X[r * kWL + c] = (c == r) ? inv : -acc * inv;
+    const int jn = j + 1;
+    const bool piv = own && jn < p && bi == (jn >> 2) && bj == (jn >> 2);
+    if (own && 4 * bi + 3 > j) {                      // the block still has trailing entries
+      df64 ra[4], rb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ra[i] = Rrow[4 * bi + i];
+        rb[i] = Rrow[4 * bj + i];
+      }
+      if (piv) {                                       // next pivot first: its update, then 1 / R_jj
+        const int kn = jn & 3;
+        df64 d = sel4(g[0], g[5], g[10], g[15], kn);
+        if (!drop) d = df_add(d, df_neg(df_mul(sel4(ra[0], ra[1], ra[2], ra[3], kn), sel4(rb[0], rb[1], rb[2], rb[3], kn))));
+        wide_pivot(d, jn, v, maxdiag, &s_inv[buf ^ 1], &s_drop[buf ^ 1], Rout);
+      }
+      if (!drop) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int a = 4 * bi + i;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int b = 4 * bj + c;
+            if (a > j && b >= a && b < p) g[4 * i + c] = df_add(g[4 * i + c], df_neg(df_mul(ra[i], rb[c])));
+          }
+        }
       }
     }
     __syncthreads();
   }
+  for (int j = p + tid; j < kWL; j += blockDim.x) {
+    v.rdiag[j] = df64{0.f, 0.f};
+    v.drop[j] = 1;
+  }
+  __syncthreads();
 }
 
 // Round-robin schedule: pair w of round rnd among N (even) indices.
@@ -555,16 +566,19 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
     return;
   if (cooperative_groups::this_cluster().block_rank() != 0) return;
   __syncthreads();
-  df64* G = reinterpret_cast<df64*>(dsm + kTG);
-  float* R = reinterpret_cast<float*>(dsm + kTR);
+  float* R = reinterpret_cast<float*>(dsm + kTR);               // R (FP32, upper); the core rotates its rows
+  df64* Rrow = reinterpret_cast<df64*>(dsm + kTG);              // pivot row of the factorization
   const TailVec v = carve_vec(dsm);
-  unpack_gram(Gpk, G);
-  wide_cholesky(G, v, p, rank_tol);
+  wide_cholesky(Gpk, v, Rrow, R, p, rank_tol);
   if (TAIL == kTailOrth) {
-    extract_r(G, v, R, p);
-    float* X = reinterpret_cast<float*>(dsm + kTG);            // G is dead
-    wide_rinv(R, v, X, p);
-    for (int e = tid; e < kWL * kWL; e += kGW) T1[e] = X[e];
+    // T1 = R with 1 / R_cc on the diagonal (0 for dropped columns): the operand of the forward
+    // substitution Q^T = R^{-T} Y^T (k_wd_trsm)
+    for (int e = tid; e < kWL * kWL; e += kGW) {
+      const int a = e / kWL, c = e % kWL;
+      float x = R[e];
+      if (a == c) x = (c < p && !v.drop[c] && x != 0.f) ? 1.f / x : 0.f;
+      T1[e] = x;
+    }
     if (tid == 0) {
       int s = 0;
       for (int j = 0; j < p; ++j) s += v.drop[j] ? 0 : 1;
@@ -573,12 +587,11 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
     }
     return;
   }
-  // core (steps 16-19): columns of R^T are the rows of R
-  extract_r(G, v, R, p);
+  // core (steps 16-19): one-sided Jacobi on the columns of R^T (the rows of R); then
+  // sigma_c = ||row c||, U[:, c] = row c / sigma_c, and M = U diag(coef) U^T = X^T diag(w) X with
+  // w_c = coef_c / sigma_c^2 (X: the rotated rows)
   const int N = (p + 1) / 2 * 2;
   const int sweeps = wide_jacobi(R, N, ca.max_sweeps, 8e-6f);
-  float* U = reinterpret_cast<float*>(dsm + kTG);              // U[a][c], 64 KB
-  float* M = U + kWL * kWL;                                     // 64 KB
   const int warp = tid >> 5, lane = tid & 31;
   for (int c = warp; c < kWL; c += kGW / 32) {
     float s2 = 0.f;
@@ -588,39 +601,55 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
   }
   __syncthreads();
   const float tau = ca.tau_from_mu ? static_cast<float>(1.0 / dst->mu) : ca.tau_host;
-  for (int e = tid; e < kWL * kWL; e += kGW) {
-    const int a = e / kWL, c = e % kWL;
-    U[e] = (v.sig[c] > 0.f) ? R[c * kWL + a] / v.sig[c] : 0.f;
-  }
+  float* wv = v.thr;                                            // w_c (the thresholds are no longer needed)
   if (tid < kWL) {
     const float sc = v.sig[tid];
     int rank = 0;
     for (int c = 0; c < kWL; ++c) rank += (v.sig[c] > sc || (v.sig[c] == sc && c < tid)) ? 1 : 0;
     v.perm[rank] = tid;
-    v.coef[tid] = (sc > tau) ? (sc - tau) / sc : 0.f;
+    const float cf = (sc > tau) ? (sc - tau) / sc : 0.f;
+    v.coef[tid] = cf;
+    wv[tid] = (cf > 0.f) ? cf / (sc * sc) : 0.f;
   }
   __syncthreads();
   int r = 0;
   for (int c = 0; c < kWL; ++c) r += (v.sig[c] > tau) ? 1 : 0;
   const int keep = ca.update_rp ? max(0, min(r, ca.l - 2)) : 0;
-  // M = U diag(coef) U^T (only columns with coef > 0 contribute)
-  for (int e = tid; e < kWL * kWL; e += kGW) {
-    const int a = e / kWL, b = e % kWL;
-    float s = 0.f;
-    for (int c = 0; c < kWL; ++c) {
-      const float w = v.coef[c];
-      if (w != 0.f) s = fmaf(U[a * kWL + c] * w, U[b * kWL + c], s);
+  if (tid < kGB) {
+    int bi2, bj2;
+    block_of(tid, bi2, bj2);
+    float m4[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) m4[u] = 0.f;
+    for (int c = 0; c < N; ++c) {
+      const float w = wv[c];
+      if (w == 0.f) continue;
+      const float4 xa = *reinterpret_cast<const float4*>(R + c * kWL + 4 * bi2);
+      const float4 xb = *reinterpret_cast<const float4*>(R + c * kWL + 4 * bj2);
+      const float va[4] = {xa.x * w, xa.y * w, xa.z * w, xa.w * w};
+      const float vb[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m4[4 * i + j] = fmaf(va[i], vb[j], m4[4 * i + j]);
     }
-    M[e] = s;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        T1[(4 * bi2 + i) * kWL + 4 * bj2 + j] = m4[4 * i + j];
+        T1[(4 * bj2 + j) * kWL + 4 * bi2 + i] = m4[4 * i + j];
+      }
   }
-  __syncthreads();
-  for (int e = tid; e < kWL * kWL; e += kGW) {
-    T1[e] = M[e];
-    const int a = e / kWL, j = e % kWL;
-    T2[e] = (j < keep) ? U[a * kWL + v.perm[j]] : 0.f;
-  }
+  if (ca.update_rp)
+    for (int e = tid; e < kWL * kWL; e += kGW) {
+      const int j = e / kWL, a = e % kWL;
+      const int c = v.perm[j];
+      T2[a * kWL + j] = (j < keep && v.sig[c] > 0.f) ? R[c * kWL + a] / v.sig[c] : 0.f;
+    }
   if (tid == 0) {
     dst->r = r;
+    dst->sweeps = sweeps;
     if (ca.update_rp) dst->keep = keep;
     if (ca.advance_counter) dst->counter += 1;
     if (sweeps >= ca.max_sweeps) dst->status |= kDevNotConverged;
@@ -632,6 +661,77 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
     for (int c = kWL; c < kMaxL; ++c) dst->sigma[c] = 0.f;
     if (!finite) dst->status |= kDevNonfinite;
     dst->sigma1 = static_cast<double>(v.sig[v.perm[0]]);
+  }
+}
+
+// ---------------------------------------------------------------- Q^T = R^{-T} Y^T
+// One thread per long-side column x: q_c = (y_c - sum_{a<c} R[a][c] q_a) / R_cc (forward
+// substitution, T = R with 1 / R_cc on the diagonal).  R^T (row c = column c of R, stride kTS)
+// and the CTA's 128 input columns are staged in shared memory with coalesced loads; the column
+// is solved in four blocks of 32: the block first takes the contributions of the solved blocks
+// (read back from shared memory), then its own 32 x 32 triangle in registers.  The results go
+// back through shared memory to coalesced stores; the output may alias the input.
+constexpr int kTThr = 128;
+constexpr int kTS = kWL + 4;
+constexpr int kTX = kTThr + 4;                     // staged column block stride (floats)
+constexpr int kTB = 32;                            // rows per block of the substitution
+
+__global__ void __launch_bounds__(kTThr, 1)
+k_wd_trsm(const float* in, int64_t ldi, int64_t len, const float* __restrict__ T, float* outT, float* outTl,
+          int64_t ldo) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  float* RT = reinterpret_cast<float*>(dsm);                 // kWL x kTS
+  float* Ys = RT + kWL * kTS;                                 // kWL x kTX: Ys[c][x]
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTThr;
+  const int nx = static_cast<int>(imin64(kTThr, len - x0));
+  for (int e = threadIdx.x; e < kWL * kWL; e += kTThr) {
+    const int a = e / kWL, c = e % kWL;
+    RT[c * kTS + a] = __ldcg(T + e);
+  }
+  for (int e = threadIdx.x; e < kWL * (kTThr / 4); e += kTThr) {
+    const int c = e / (kTThr / 4), x4 = e % (kTThr / 4);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (4 * x4 < nx) v = __ldcg(reinterpret_cast<const float4*>(in + c * ldi + x0) + x4);
+    *reinterpret_cast<float4*>(Ys + c * kTX + 4 * x4) = v;
+  }
+  __syncthreads();
+  const int x = threadIdx.x;
+  for (int cb = 0; cb < kWL; cb += kTB) {
+    float q[kTB];
+#pragma unroll
+    for (int i = 0; i < kTB; ++i) q[i] = Ys[(cb + i) * kTX + x];
+    // contributions of the solved rows a < cb: q_i -= sum_a R[a][cb + i] q_a
+    for (int a = 0; a < cb; a += 4) {
+      const float y0 = Ys[a * kTX + x], y1 = Ys[(a + 1) * kTX + x];
+      const float y2 = Ys[(a + 2) * kTX + x], y3 = Ys[(a + 3) * kTX + x];
+#pragma unroll
+      for (int i = 0; i < kTB; ++i) {
+        const float4 rv = *reinterpret_cast<const float4*>(RT + (cb + i) * kTS + a);
+        q[i] = fmaf(-rv.x, y0, q[i]);
+        q[i] = fmaf(-rv.y, y1, q[i]);
+        q[i] = fmaf(-rv.z, y2, q[i]);
+        q[i] = fmaf(-rv.w, y3, q[i]);
+      }
+    }
+    // the block's own triangle
+#pragma unroll
+    for (int i = 0; i < kTB; ++i) {
+      const float* rt = RT + (cb + i) * kTS + cb;
+      float acc = q[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) acc = fmaf(-rt[k], q[k], acc);
+      q[i] = acc * rt[i];
+    }
+#pragma unroll
+    for (int i = 0; i < kTB; ++i) Ys[(cb + i) * kTX + x] = q[i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kWL * (kTThr / 4); e += kTThr) {
+    const int c = e / (kTThr / 4), x4 = e % (kTThr / 4);
+    if (4 * x4 >= nx) continue;
+    const float4 v = *reinterpret_cast<const float4*>(Ys + c * kTX + 4 * x4);
+    reinterpret_cast<float4*>(outT + c * ldo + x0)[x4] = v;
+    reinterpret_cast<float4*>(outTl + c * ldo + x0)[x4] = f4_lo(v);
   }
 }
 
@@ -925,6 +1025,7 @@ cudaError_t prepare_wide_kernels() {
   if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailOrth>, kGSmem);
   if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailCore>, kGSmem);
   if (e == cudaSuccess) e = set_dyn(k_wd_apply, sizeof(float) * kWL * (kWL + kACols));
+  if (e == cudaSuccess) e = set_dyn(k_wd_trsm, sizeof(float) * kWL * (kTS + kTX));
   if (e == cudaSuccess) e = set_dyn(k_wd_alm<true>, kEStages * kEStage);
   if (e == cudaSuccess) e = set_dyn(k_wd_alm<false>, kEStages * kEStage);
   return e;
@@ -1004,6 +1105,14 @@ cudaError_t launch_wd_apply(const float* in, int64_t ldi, int64_t len, const flo
   const int grid = static_cast<int>((len + kACols - 1) / kACols);
   if (grid == 0) return cudaSuccess;
   k_wd_apply<<<grid, kAThr, sizeof(float) * kWL * (kWL + kACols), st>>>(in, ldi, len, T, outT, outTl, ldo, outR, outRl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wd_trsm(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
+                           int64_t ldo, cudaStream_t st) {
+  const int grid = static_cast<int>((len + kTThr - 1) / kTThr);
+  if (grid == 0) return cudaSuccess;
+  k_wd_trsm<<<grid, kTThr, sizeof(float) * kWL * (kTS + kTX), st>>>(in, ldi, len, T, outT, outTl, ldo);
   return cudaGetLastError();
 }
 

@@ -396,6 +396,7 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
   }
   if (tid == 0) {
     dst->r = r;
+    dst->sweeps = sweeps;
     if (update_rp) dst->keep = keep;
     if (advance_counter) dst->counter += 1;
     if (sweeps >= max_sweeps) dst->status |= kDevNotConverged;

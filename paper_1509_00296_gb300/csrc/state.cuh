@@ -26,7 +26,7 @@ struct DevState {
   int32_t keep;         // propagated basis columns for the next SVT
   int32_t iter;         // iALM iterations since rpca_init
   uint32_t status;      // sticky FRSVT_DEV_* bits
-  int32_t pad;
+  int32_t sweeps;       // Jacobi sweeps of the last core SVD
   float sigma[kMaxL];   // singular values of B of the last SVT, descending
 };
 

@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int32), ("s", ctypes.c_int32), ("keep", ctypes.c_int32),
                 ("device_status", ctypes.c_uint32), ("counter", ctypes.c_uint64), ("alm_iter", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("mu", ctypes.c_double), ("residual", ctypes.c_double)]
+                ("sweeps", ctypes.c_int32), ("mu", ctypes.c_double), ("residual", ctypes.c_double)]
 
 
 _lib = None
@@ -125,6 +125,7 @@ class SVTInfo:
     alm_iter: int
     mu: float
     residual: float
+    sweeps: int = 0
 
 
 class Handle:
@@ -202,7 +203,8 @@ class Handle:
     def info(self) -> SVTInfo:
         inf = Info()
         self._chk(lib().frsvt_get_info(self._h, ctypes.byref(inf)))
-        return SVTInfo(inf.r, inf.s, inf.keep, inf.device_status, inf.counter, inf.alm_iter, inf.mu, inf.residual)
+        return SVTInfo(inf.r, inf.s, inf.keep, inf.device_status, inf.counter, inf.alm_iter, inf.mu, inf.residual,
+                       inf.sweeps)
 
     def enable_timing(self, on: bool = True):
         self._chk(lib().frsvt_enable_timing(self._h, 1 if on else 0))

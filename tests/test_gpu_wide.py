@@ -46,6 +46,7 @@ def power_norm2(O, iters=40, seed=0):
     (777, 333, 50, 1, 80, 0.97),
     (600, 90, 48, 2, 60, 0.95),
     (1500, 1000, 96, 0, 110, 0.98),
+    (900, 400, 37, 1, 50, 0.96),
 ])
 def test_wide_frsvt_parity(fr, m, n, l, q, rank, decay):
     """FRSVT with a wide basis: X, r and the leading sigma against the oracle's Alg. 1."""
