@@ -121,11 +121,12 @@ cudaError_t prepare_wide_kernels();
 int wide_gram_grid();
 int wide_gram_count();
 int wide_splits(int64_t nlong, int64_t nk, int sms);
-cudaError_t launch_wd_omega(float* OT, float* OTl, int64_t ldo, int64_t m, int l, int use_rp, uint64_t seed,
-                            uint64_t ctr, const DevState* dst, cudaStream_t st);
-cudaError_t launch_wd_pass(bool col, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
+cudaError_t launch_wd_omega(float* OT, float* OTl, void* OTb, void* OTbl, int64_t ldo, int64_t m, int l, int use_rp,
+                            uint64_t seed, uint64_t ctr, const DevState* dst, cudaStream_t st);
+cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
                            int64_t nlong, int64_t nk, int S, float* part, int64_t ldp, unsigned* tickets, float* outT,
-                           float* outTl, int64_t ldo, float* outR, float* outRl, DevState* dst, cudaStream_t st);
+                           float* outTl, void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl,
+                           DevState* dst, cudaStream_t st);
 cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len, int grid, double* cpart, double* Gpk,
                            unsigned* ticket, int p, double rank_tol, int l, float tau_host, int tau_from_mu,
                            int update_rp, int advance_counter, int max_sweeps, float* T1, float* T2, DevState* dst,
@@ -133,11 +134,11 @@ cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len,
 cudaError_t launch_wd_apply(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
                             int64_t ldo, float* outR, float* outRl, cudaStream_t st);
 cudaError_t launch_wd_trsm(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
-                           int64_t ldo, cudaStream_t st);
+                           void* outTb, void* outTbl, int64_t ldo, cudaStream_t st);
 cudaError_t launch_wd_alm(bool alm, const CUtensorMap& tmZ, const CUtensorMap& tmZl, const CUtensorMap& tmR,
                           const CUtensorMap& tmRl, int64_t m, int64_t n, const float* O, float* S, float* A, int64_t ld,
                           float* L, int64_t ldl, DevState* dst, double* cpart, unsigned* ticket, int grid,
-                          cudaStream_t st);
+                          void* Ab, int64_t ldb, cudaStream_t st);
 }
 
 using namespace frsvt;
@@ -197,6 +198,7 @@ struct frsvt_handle {
   float *wOT = nullptr, *wOTl = nullptr, *wZT = nullptr, *wZTl = nullptr, *wZ = nullptr, *wZl = nullptr;
   float *wYT = nullptr, *wQT = nullptr, *wQTl = nullptr, *wQp = nullptr, *wRf = nullptr, *wRfl = nullptr;
   float *wT1 = nullptr, *wT2 = nullptr, *wpart = nullptr;
+  void *wOTb = nullptr, *wOTbl = nullptr, *wZTb = nullptr, *wZTbl = nullptr, *wQTb = nullptr, *wQTbl = nullptr;
   double *wgc = nullptr, *wGpk = nullptr, *wac = nullptr;
   unsigned* wtick = nullptr;       // pass tiles, then the Gram ticket, then the epilogue ticket
   int64_t w_ntiles = 0;
@@ -525,7 +527,8 @@ void free_all(frsvt_handle* h) {
                   h->rpart, h->pmax,   h->psum,     h->cpart_sc,  h->cpart_lr, h->cpart_alm, h->Gfin, h->rsum,
                   h->tickets, h->wsvt_next, h->ad_ws, h->Ab,
                   h->wOT, h->wOTl, h->wZT, h->wZTl, h->wZ, h->wZl, h->wYT, h->wQT, h->wQTl, h->wQp, h->wRf,
-                  h->wRfl, h->wT1, h->wT2, h->wpart, h->wgc, h->wGpk, h->wac, h->wtick};
+                  h->wRfl, h->wT1, h->wT2, h->wpart, h->wgc, h->wGpk, h->wac, h->wtick,
+                  h->wOTb, h->wOTbl, h->wZTb, h->wZTbl, h->wQTb, h->wQTbl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -533,24 +536,32 @@ void free_all(frsvt_handle* h) {
 // ---------------------------------------------------------------- wide basis (32 < l <= 128)
 // Orthonormal basis of the columns of Y (given transposed, 128 x n at h->wYT) into QT / QTl:
 // Cholesky QR, `passes` times (Alg. 1 steps 6 / 14; only span(Q) matters, Prop. 1).
-frsvt_status wide_orth(frsvt_handle* h, int64_t n, int l, int passes) {
+// With bf_next the basis is also written as BF16 hi / lo parts (the next row pass reads the shadow).
+frsvt_status wide_orth(frsvt_handle* h, int64_t n, int l, int passes, bool bf_next) {
   cudaStream_t st = h->stream;
   const int64_t ld = h->w_ldn;
   unsigned* gt = h->wtick + h->w_ntiles;
   for (int pass = 0; pass < passes; ++pass) {
     const float* src = pass == 0 ? h->wYT : h->wQT;
+    const bool last = pass == passes - 1;
     FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_gram(false, src, ld, n, h->w_gram_grid, h->wgc, h->wGpk, gt, l,
                                                   h->cfg.rank_tol, l, 0.f, 0, 0, 0, h->cfg.max_jacobi_sweeps, h->wT1,
                                                   h->wT2, h->dst, st));
-    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_trsm(src, ld, n, h->wT1, h->wQT, h->wQTl, ld, st));
+    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_trsm(src, ld, n, h->wT1, h->wQT, h->wQTl,
+                                                  (bf_next && last) ? h->wQTb : nullptr,
+                                                  (bf_next && last) ? h->wQTbl : nullptr, ld, st));
   }
   return FRSVT_OK;
 }
 
 // Alg. 1 up to the core on the wide basis: leaves Z / Z_lo (m x 128) and Rf / Rf_lo (n x 128)
 // so that X = Z Rf^T, and sets r, s, sigma (and the counter) in the device state.
+// Reduced precision (Ab: the BF16 shadow of A, current): the sketch and the first q - 1 power steps
+// read the shadow with BF16 copies of the narrow factors; the last power step and the projection
+// stay FP32-accurate.
 frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int l, int q,
-                                 uint64_t ctr, float tau_host, int tau_from_mu, int advance_counter) {
+                                 uint64_t ctr, float tau_host, int tau_from_mu, int advance_counter,
+                                 const void* Ab = nullptr) {
   cudaStream_t st = h->stream;
   const int64_t LW = wide_lp();
   CUtensorMap tmAr, tmAc, tmOT, tmOTl, tmZT, tmZTl, tmQT, tmQTl;
@@ -563,24 +574,52 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
       !make_row_map_sw128(&tmQT, h->wQT, LW, n, h->w_ldn, 128) ||
       !make_row_map_sw128(&tmQTl, h->wQTl, LW, n, h->w_ldn, 128))
     return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis)");
+  const bool bf = Ab != nullptr;
+  CUtensorMap tmBr, tmBc, tmOTb, tmOTbl, tmZTb, tmZTbl, tmQTb, tmQTbl;
+  if (bf && (!make_row_map_bf16(&tmBr, Ab, m, n, h->ldb, wide_tile()) ||
+             !make_row_map_bf16(&tmBc, Ab, m, n, h->ldb, 64) ||
+             !make_row_map_bf16(&tmOTb, h->wOTb, LW, m, h->w_ldm, 128) ||
+             !make_row_map_bf16(&tmOTbl, h->wOTbl, LW, m, h->w_ldm, 128) ||
+             !make_row_map_bf16(&tmZTb, h->wZTb, LW, m, h->w_ldm, 128) ||
+             !make_row_map_bf16(&tmZTbl, h->wZTbl, LW, m, h->w_ldm, 128) ||
+             !make_row_map_bf16(&tmQTb, h->wQTb, LW, n, h->w_ldn, 128) ||
+             !make_row_map_bf16(&tmQTbl, h->wQTbl, LW, n, h->w_ldn, 128)))
+    return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis, BF16 shadow)");
   const int Sr = wide_splits(m, n, h->sms), Sc = wide_splits(n, m, h->sms);
-  FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_omega(h->wOT, h->wOTl, h->w_ldm, m, l, 0, h->cfg.seed, ctr, h->dst, st));
-  FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(true, tmAc, tmOT, tmOTl, n, m, Sc, h->wpart, h->w_ldp, h->wtick,
-                                                  h->wYT, nullptr, h->w_ldn, nullptr, nullptr, h->dst, st));
-  frsvt_status s = wide_orth(h, n, l, q == 0 ? 2 : 1);
+  FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_omega(h->wOT, h->wOTl, bf ? h->wOTb : nullptr, bf ? h->wOTbl : nullptr,
+                                                   h->w_ldm, m, l, 0, h->cfg.seed, ctr, h->dst, st));
+  if (bf)
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(true, 1, tmBc, tmOTb, tmOTbl, n, m, Sc, h->wpart, h->w_ldp,
+                                                    h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn, nullptr,
+                                                    nullptr, h->dst, st));
+  else
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(true, 0, tmAc, tmOT, tmOTl, n, m, Sc, h->wpart, h->w_ldp,
+                                                    h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn, nullptr,
+                                                    nullptr, h->dst, st));
+  frsvt_status s = wide_orth(h, n, l, q == 0 ? 2 : 1, bf && q > 1);
   if (s != FRSVT_OK) return s;
   for (int it = 0; it < q; ++it) {
-    FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(false, tmAr, tmQT, tmQTl, m, n, Sr, h->wpart, h->w_ldp,
-                                                      h->wtick, h->wZT, h->wZTl, h->w_ldm, nullptr, nullptr, h->dst,
-                                                      st));
-    FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(true, tmAc, tmZT, tmZTl, n, m, Sc, h->wpart, h->w_ldp,
-                                                       h->wtick, h->wYT, nullptr, h->w_ldn, nullptr, nullptr, h->dst,
-                                                       st));
-    if ((s = wide_orth(h, n, l, it == q - 1 ? 2 : 1)) != FRSVT_OK) return s;
+    if (bf && it < q - 1) {
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(false, 1, tmBr, tmQTb, tmQTbl, m, n, Sr, h->wpart, h->w_ldp,
+                                                        h->wtick, nullptr, nullptr, h->wZTb, h->wZTbl, h->w_ldm,
+                                                        nullptr, nullptr, h->dst, st));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(true, 1, tmBc, tmZTb, tmZTbl, n, m, Sc, h->wpart, h->w_ldp,
+                                                         h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn,
+                                                         nullptr, nullptr, h->dst, st));
+    } else {
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(false, 0, tmAr, tmQT, tmQTl, m, n, Sr, h->wpart, h->w_ldp,
+                                                        h->wtick, h->wZT, h->wZTl, nullptr, nullptr, h->w_ldm,
+                                                        nullptr, nullptr, h->dst, st));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(true, 0, tmAc, tmZT, tmZTl, n, m, Sc, h->wpart, h->w_ldp,
+                                                         h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn,
+                                                         nullptr, nullptr, h->dst, st));
+    }
+    if ((s = wide_orth(h, n, l, it == q - 1 ? 2 : 1, bf && it + 1 < q - 1)) != FRSVT_OK) return s;
   }
   // projection B^T = Z = A Q (step 16), then B B^T = Z^T Z and the core (steps 16-19)
-  FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_wd_pass(false, tmAr, tmQT, tmQTl, m, n, Sr, h->wpart, h->w_ldp, h->wtick,
-                                                   h->wZT, nullptr, h->w_ldm, h->wZ, h->wZl, h->dst, st));
+  FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_wd_pass(false, 0, tmAr, tmQT, tmQTl, m, n, Sr, h->wpart, h->w_ldp,
+                                                   h->wtick, h->wZT, nullptr, nullptr, nullptr, h->w_ldm, h->wZ,
+                                                   h->wZl, h->dst, st));
   FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_wd_gram(true, h->wZT, h->w_ldm, m, h->w_gram_grid, h->wgc, h->wGpk,
                                                 h->wtick + h->w_ntiles, l, h->cfg.rank_tol, l, tau_host, tau_from_mu, 0,
                                                 advance_counter, h->cfg.max_jacobi_sweeps, h->wT1, h->wT2, h->dst,
@@ -602,7 +641,8 @@ frsvt_status wide_epilogue(frsvt_handle* h, bool alm, int64_t m, int64_t n, cons
   const int64_t ntiles = cdiv(m, 128) * cdiv(n, wide_tile());
   const int grid = static_cast<int>(ntiles < h->sms ? ntiles : h->sms);
   FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_wd_alm(alm, tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, h->dst,
-                                                   h->wac, h->wtick + h->w_ntiles + 1, grid, h->stream));
+                                                   h->wac, h->wtick + h->w_ntiles + 1, grid, alm ? h->Ab : nullptr,
+                                                   h->ldb, h->stream));
   return FRSVT_OK;
 }
 
@@ -644,6 +684,17 @@ bool wide_alloc(frsvt_handle* h) {
   alloc(reinterpret_cast<void**>(&h->pmax), sizeof(float) * h->absmax_blocks);
   alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
   alloc(reinterpret_cast<void**>(&h->wsvt_next), sizeof(unsigned));
+  if (cfg->precision == FRSVT_PREC_BF16) {
+    const size_t bm = sizeof(uint16_t) * LW * h->w_ldm, bn = sizeof(uint16_t) * LW * h->w_ldn;
+    h->ldb = (cfg->n_max + 7) / 8 * 8;
+    alloc(&h->Ab, sizeof(uint16_t) * static_cast<size_t>(cfg->m_max) * h->ldb);
+    alloc(&h->wOTb, bm);
+    alloc(&h->wOTbl, bm);
+    alloc(&h->wZTb, bm);
+    alloc(&h->wZTbl, bm);
+    alloc(&h->wQTb, bn);
+    alloc(&h->wQTbl, bn);
+  }
   if (!ok) return false;
   return cudaMemsetAsync(h->wtick, 0, sizeof(unsigned) * (h->w_ntiles + 2), h->stream) == cudaSuccess &&
          cudaMemsetAsync(h->wT2, 0, sizeof(float) * LW * LW, h->stream) == cudaSuccess;
@@ -758,7 +809,7 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   h->wide = cfg->l_max > 32;
   h->LP = cfg->l_max <= 16 ? 16 : (cfg->l_max <= 32 ? 32 : wide_lp());
   const int64_t nsmax = cfg->n_max < cfg->m_max ? cfg->n_max : cfg->m_max;
-  if (h->wide ? (cfg->range_prop || cfg->precision != FRSVT_PREC_FP32 || (cfg->flags & FRSVT_CFG_ADJOINT) ||
+  if (h->wide ? (cfg->range_prop || (cfg->flags & FRSVT_CFG_ADJOINT) ||
                  cfg->m_max >= (int64_t(1) << 31))
               : nsmax > ns_limit(h->LP)) {
     delete h;
@@ -936,7 +987,9 @@ frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, in
   if (l > n) l = static_cast<int32_t>(n);
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
   if (h->wide) {
-    if ((s = wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1)) != FRSVT_OK) return s;
+    if (h->Ab != nullptr) FRSVT_CK(launch_to_bf16(A, lda, m, n, h->Ab, h->ldb, h->stream));
+    if ((s = wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1, h->Ab)) != FRSVT_OK)
+      return s;
     return wide_epilogue(h, false, m, n, nullptr, nullptr, nullptr, 0, X, ldx);
   }
   const int rp = h->cfg.range_prop ? 1 : 0;
@@ -1017,7 +1070,8 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;   // the shadow is kept current by rpca_init / the epilogue
   if (h->wide) {
-    if ((s = wide_range_and_core(h, A, m, n, ld, l, h->cfg.q, kCounterFromState, 0.f, 1, 1)) != FRSVT_OK) return s;
+    if ((s = wide_range_and_core(h, A, m, n, ld, l, h->cfg.q, kCounterFromState, 0.f, 1, 1, h->Ab)) != FRSVT_OK)
+      return s;
     if ((s = wide_epilogue(h, true, m, n, O, S, A, ld, L, ldl)) != FRSVT_OK) return s;
   } else {
   if ((s = range_and_core(h, A, m, n, ld, l, h->cfg.q, rp, kCounterFromState, 0.f, 1, rp, 1,

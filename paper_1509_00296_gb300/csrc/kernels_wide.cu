@@ -25,6 +25,7 @@
 // (len x 128) for the reconstruction.  Every wait is bounded (FRSVT_DEV_TIMEOUT on expiry).
 #include <cooperative_groups.h>
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include "cluster.cuh"
 #include "common.cuh"
@@ -55,6 +56,30 @@ __device__ __forceinline__ float4 f4_lo(float4 v) {
   return make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
 }
 
+// kind::f16 MMA with BF16 A and B (FP32 accumulation); instruction descriptor for M x N with
+// A K-major and B K-major (b_mn = false) or MN-major (b_mn = true).
+__host__ __device__ constexpr uint32_t idesc_bf16w(int M, int N, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn ? 1u : 0u) << 16) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma_bf16w(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, bool acc) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.u32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc ? 1u : 0u)
+      : "memory");
+}
+
+// BF16 hi / lo parts of a float (hi = bf16(v), lo = bf16(v - hi)).
+__device__ __forceinline__ void bf16_split(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
 __device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
@@ -62,8 +87,9 @@ __device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
 // ---------------------------------------------------------------- Omega^T
 // OT[k][i] = Omega[i][k] for k < p (p = l, or l - keep under range propagation), 0 for k >= p;
 // OTl = OT - tf32(OT).  One Philox call gives Omega[i][4 blk .. 4 blk + 3].
-__global__ void k_wd_omega(float* __restrict__ OT, float* __restrict__ OTl, int64_t ldo, int64_t m, int l,
-                           int use_rp, uint64_t seed, uint64_t ctr, const DevState* __restrict__ dst) {
+__global__ void k_wd_omega(float* __restrict__ OT, float* __restrict__ OTl, __nv_bfloat16* __restrict__ OTb,
+                           __nv_bfloat16* __restrict__ OTbl, int64_t ldo, int64_t m, int l, int use_rp, uint64_t seed,
+                           uint64_t ctr, const DevState* __restrict__ dst) {
   const uint64_t stream = (ctr == kCounterFromState) ? dst->counter : ctr;
   int p = l;
   if (use_rp) {
@@ -84,31 +110,41 @@ __global__ void k_wd_omega(float* __restrict__ OT, float* __restrict__ OTl, int6
       const float x = (k < p) ? v[c] : 0.f;
       OT[k * ldo + i] = x;
       OTl[k * ldo + i] = x - tf32_hi(x);
+      if (OTb != nullptr) bf16_split(x, OTb[k * ldo + i], OTbl[k * ldo + i]);
     }
   }
 }
 
 // ---------------------------------------------------------------- passes over A
 // COL = false (row pass): D[k][i] = sum_j M[k][j] A[i][j] for the 256 rows i of the tile, K = n,
-//   A tiles 256 rows x 32 columns (K-major, 128-byte swizzle).
+//   A tiles 256 rows x one K-chunk (K-major, 128-byte swizzle).
 // COL = true (column pass): D[k][j] = sum_i M[k][i] A[i][j] for the 256 columns j of the tile,
-//   K = m, A tiles 32 rows x 256 columns read MN-major (8 boxes of 32 x 32, 32-byte atoms).
-// M and M_lo (128 x K, K-major boxes of 32 x 128) arrive by TMA with each chunk of A; the MMAs
-// are M_hi A_hi + M_lo A_hi, then (after the split warps rewrote the A tile as A_lo in place)
-// M_hi A_lo.  Warps: 0 TMA, 1 tensor memory + MMA, 2-5 drain, 6-13 split.
-template <bool COL>
+//   K = m, A tiles one K-chunk of rows x 256 columns read MN-major.
+// PR = 0 (FP32-accurate): K-chunks of 32 floats; M and M_lo (128 x K, TF32 hi / lo parts of the
+//   narrow factor) arrive by TMA with each chunk of A; the MMAs are M_hi A_hi + M_lo A_hi, then
+//   (after the split warps rewrote the A tile as A_lo in place) M_hi A_lo: 3xTF32.  The column
+//   pass reads A in the 32-byte-atom swizzle (8 boxes of 32 x 32) that kind::tf32 takes MN-major.
+// PR = 1 (BF16 shadow of A): K-chunks of 64 BF16; M arrives as BF16 hi / lo parts, so only A's
+//   BF16 rounding remains: kind::f16 MMAs M_hi A + M_lo A (the column pass reads A MN-major in
+//   the plain 128-byte swizzle, 4 boxes of 64 x 64); no split.
+// Warps: 0 TMA, 1 tensor memory + MMA, 2-5 drain, 6-13 split (PR = 0).  The last CTA of a tile
+// sums the S partials in split order and writes the outputs: outT / outTl (128 x ldo, TF32 hi /
+// lo parts), outTb / outTbl (the same as BF16 hi / lo parts), outR / outRl (row-major).
+template <bool COL, int PR>
 __global__ void __launch_bounds__(kWThr, 1)
 k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmM,
           const __grid_constant__ CUtensorMap tmMl, int64_t nlong, int64_t nk, int S, float* __restrict__ part,
           int64_t ldp, unsigned* __restrict__ tickets, float* __restrict__ outT, float* __restrict__ outTl,
-          int64_t ldo, float* __restrict__ outR, float* __restrict__ outRl, DevState* __restrict__ dst) {
+          __nv_bfloat16* __restrict__ outTb, __nv_bfloat16* __restrict__ outTbl, int64_t ldo,
+          float* __restrict__ outR, float* __restrict__ outRl, DevState* __restrict__ dst) {
+  constexpr int KC = PR ? 64 : kWK;                         // elements of K per chunk (128-byte rows)
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kWStages], hidone[kWStages], lo_ready[kWStages], empty[kWStages], acc_full;
   __shared__ uint32_t tmem_base;
   __shared__ int flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x / S, split = blockIdx.x % S;
-  const int nkc = static_cast<int>((nk + kWK - 1) / kWK);
+  const int nkc = static_cast<int>((nk + KC - 1) / KC);
   const int c0 = static_cast<int>(static_cast<int64_t>(split) * nkc / S);
   const int c1 = static_cast<int>(static_cast<int64_t>(split + 1) * nkc / S);
   const int nc = c1 - c0;
@@ -151,48 +187,71 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         const int c = c0 + g;
         mbar_arrive_expect_tx(&full[s], kWStage);
         if (COL) {
+          if (PR) {
 #pragma unroll
-          for (int v = 0; v < kWN / 32; ++v) tma_load_2d(st + v * 4096, &tmA, x0 + 32 * v, kWK * c, &full[s]);
+            for (int v = 0; v < kWN / 64; ++v) tma_load_2d(st + v * 8192, &tmA, x0 + 64 * v, KC * c, &full[s]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < kWN / 32; ++v) tma_load_2d(st + v * 4096, &tmA, x0 + 32 * v, KC * c, &full[s]);
+          }
         } else {
-          tma_load_2d(st, &tmA, kWK * c, x0, &full[s]);
+          tma_load_2d(st, &tmA, KC * c, x0, &full[s]);
         }
-        tma_load_2d(st + kWABytes, &tmM, kWK * c, 0, &full[s]);
-        tma_load_2d(st + kWABytes + kWMBytes, &tmMl, kWK * c, 0, &full[s]);
+        tma_load_2d(st + kWABytes, &tmM, KC * c, 0, &full[s]);
+        tma_load_2d(st + kWABytes + kWMBytes, &tmMl, KC * c, 0, &full[s]);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(128, kWN, false, COL);
-      auto bdesc = [&](const unsigned char* a, int ks) -> uint64_t {
-        return COL ? smem_desc_sw128a32_mn(a + ks * 1024, 4096) : smem_desc_sw128(a + 32 * ks, 16, 1024);
-      };
-      auto issue_lo = [&](int g) {
-        const int s = g % kWStages, u = g / kWStages;
-        if (ok && !mbar_wait(&lo_ready[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
-        tc_fence_after();
-        const unsigned char* st = dsm + s * kWStage;
+      if (PR) {
+        constexpr uint32_t idesc = idesc_bf16w(128, kWN, COL);
+        for (int g = 0; g < nc; ++g) {
+          const int s = g % kWStages, u = g / kWStages;
+          if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
+          tc_fence_after();
+          const unsigned char* st = dsm + s * kWStage;
 #pragma unroll
-        for (int ks = 0; ks < kWK / 8; ++ks)
-          tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc, true);
-        tc_commit(&empty[s]);
-      };
-      for (int g = 0; g < nc; ++g) {
-        const int s = g % kWStages, u = g / kWStages;
-        if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
-        tc_fence_after();
-        const unsigned char* st = dsm + s * kWStage;
-#pragma unroll
-        for (int ks = 0; ks < kWK / 8; ++ks) {
-          tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
-                      g > 0 || ks > 0);
-          tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + kWMBytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
-                      true);
+          for (int ks = 0; ks < KC / 16; ++ks) {
+            const uint64_t bd = COL ? smem_desc_sw128(st + ks * 2048, 8192, 1024) : smem_desc_sw128(st + 32 * ks, 16, 1024);
+            tc_mma_bf16w(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bd, idesc, g > 0 || ks > 0);
+            tc_mma_bf16w(tbase, smem_desc_sw128(st + kWABytes + kWMBytes + 32 * ks, 16, 1024), bd, idesc, true);
+          }
+          tc_commit(&empty[s]);
         }
-        tc_commit(&hidone[s]);
-        if (g > 0) issue_lo(g - 1);
+        tc_commit(&acc_full);
+      } else {
+        constexpr uint32_t idesc = idesc_tf32(128, kWN, false, COL);
+        auto bdesc = [&](const unsigned char* a, int ks) -> uint64_t {
+          return COL ? smem_desc_sw128a32_mn(a + ks * 1024, 4096) : smem_desc_sw128(a + 32 * ks, 16, 1024);
+        };
+        auto issue_lo = [&](int g) {
+          const int s = g % kWStages, u = g / kWStages;
+          if (ok && !mbar_wait(&lo_ready[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
+          tc_fence_after();
+          const unsigned char* st = dsm + s * kWStage;
+#pragma unroll
+          for (int ks = 0; ks < kWK / 8; ++ks)
+            tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc, true);
+          tc_commit(&empty[s]);
+        };
+        for (int g = 0; g < nc; ++g) {
+          const int s = g % kWStages, u = g / kWStages;
+          if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
+          tc_fence_after();
+          const unsigned char* st = dsm + s * kWStage;
+#pragma unroll
+          for (int ks = 0; ks < kWK / 8; ++ks) {
+            tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
+                        g > 0 || ks > 0);
+            tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + kWMBytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
+                        true);
+          }
+          tc_commit(&hidone[s]);
+          if (g > 0) issue_lo(g - 1);
+        }
+        if (nc > 0) issue_lo(nc - 1);
+        tc_commit(&acc_full);
       }
-      if (nc > 0) issue_lo(nc - 1);
-      tc_commit(&acc_full);
     }
   } else if (warp < 6) {
     // drain: TMEM lane 32 q + L is row k of D, column x its long-side index; partial of split s
@@ -211,7 +270,7 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         d4[u] = (nc > 0 && ok) ? make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3])
                                : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-  } else {
+  } else if (!PR) {
     const int t = threadIdx.x - 32 * 6;
     for (int g = 0; g < nc; ++g) {
       const int s = g % kWStages, u = g / kWStages;
@@ -249,6 +308,19 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       v = f4_add(v, __ldcg(reinterpret_cast<const float4*>(part + (static_cast<int64_t>(s) * kWL + k) * ldp + x0) + x4));
     if (outT != nullptr) reinterpret_cast<float4*>(outT + k * ldo + x0)[x4] = v;
     if (outTl != nullptr) reinterpret_cast<float4*>(outTl + k * ldo + x0)[x4] = f4_lo(v);
+    if (outTb != nullptr) {
+      __nv_bfloat16 h[4], l[4];
+      bf16_split(v.x, h[0], l[0]);
+      bf16_split(v.y, h[1], l[1]);
+      bf16_split(v.z, h[2], l[2]);
+      bf16_split(v.w, h[3], l[3]);
+      __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(outTb + k * ldo + x0 + 4 * x4);
+      __nv_bfloat162* lb = reinterpret_cast<__nv_bfloat162*>(outTbl + k * ldo + x0 + 4 * x4);
+      hb[0] = __halves2bfloat162(h[0], h[1]);
+      hb[1] = __halves2bfloat162(h[2], h[3]);
+      lb[0] = __halves2bfloat162(l[0], l[1]);
+      lb[1] = __halves2bfloat162(l[2], l[3]);
+    }
     if (outR != nullptr) {
       sm[(4 * x4 + 0) * kSt + k] = v.x;
       sm[(4 * x4 + 1) * kSt + k] = v.y;
@@ -328,34 +400,16 @@ __device__ TailVec carve_vec(unsigned char* base) {
   return v;
 }
 
-// Entry k (runtime, 0..3) of four registers, by selects (no local-memory indexing).
-__device__ __forceinline__ df64 sel4(df64 a, df64 b, df64 c, df64 d, int k) {
-  return k == 0 ? a : (k == 1 ? b : (k == 2 ? c : d));
-}
-
-// Pivot of column j from its (updated) diagonal entry d: the drop rule of the l <= 32 path
-// (pivot not above rank_tol * original G_jj, G_jj below 1e-15 of the largest diagonal, or not a
-// finite positive number) and 1 / sqrt(d).
-__device__ __forceinline__ void wide_pivot(df64 d, int j, const TailVec& v, float maxdiag, df64* s_inv, int* s_drop,
-                                           float* Rout) {
-  const bool drop = !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
-  df64 inv{0.f, 0.f};
-  if (!drop) inv = df_rsqrt(d);
-  *s_inv = inv;
-  *s_drop = drop ? 1 : 0;
-  v.rdiag[j] = drop ? df64{0.f, 0.f} : df_mul(d, inv);
-  v.drop[j] = drop ? 1 : 0;
-  Rout[j * kWL + j] = drop ? 0.f : v.rdiag[j].hi;
-}
-
 // Right-looking Cholesky G = R^T R of the leading p x p block in double-float arithmetic, with
-// the column drops of the l <= 32 path.  Thread t < 528 keeps its 4 x 4 block (bi, bj), bi <= bj,
-// of the upper triangle in registers for the whole factorization.  Per column j: the owners of
-// row j publish R[j][:] = G[j][:] / R_jj (shared), then every block takes its rank-1 update; the
-// owner of the next pivot updates that entry first and forms the next 1 / R_jj during the same
-// phase (double-buffered), so each column costs two barriers.  R (FP32, row-major, upper,
-// dropped rows zero) goes to Rout; v.rdiag / v.drop receive the diagonal and the drop flags.
-__device__ void wide_cholesky(const double* __restrict__ Gpk, const TailVec& v, df64* Rrow, float* Rout, int p,
+// the column drops of the l <= 32 path: column j is dropped (row j of R zero) when its pivot is
+// not above rank_tol * G_jj (original), when G_jj is below 1e-15 of the largest diagonal, or when
+// it is not a finite positive number.  Blocked by 4: thread t < 528 keeps its 4 x 4 block (bi, bj),
+// bi <= bj, of the upper triangle in registers for the whole factorization.  Per block column jb:
+// (1) the owner of the diagonal block factors it, R11 (four pivots), and forms W = R11^{-1};
+// (2) the owners of block row jb form R12 = W^T G12 and publish the four rows of R (shared);
+// (3) every trailing block takes its rank-4 update.  Two barriers per four columns.  R (FP32,
+// row-major, upper, dropped rows zero) goes to Rout; v.rdiag / v.drop get the diagonal and flags.
+__device__ void wide_cholesky(const double* __restrict__ Gpk, const TailVec& v, df64* Rpanel, float* Rout, int p,
                               double rank_tol) {
   const int tid = threadIdx.x;
   const bool own = tid < kGB;
@@ -376,60 +430,101 @@ __device__ void wide_cholesky(const double* __restrict__ Gpk, const TailVec& v, 
   __syncthreads();
   float maxdiag = 0.f;
   for (int a = 0; a < p; ++a) maxdiag = fmaxf(maxdiag, v.g0[a]);
-  __shared__ df64 s_inv[2];
-  __shared__ int s_drop[2];
-  if (p > 0 && own && bi == 0 && bj == 0) wide_pivot(g[0], 0, v, maxdiag, &s_inv[0], &s_drop[0], Rout);
-  __syncthreads();
-  for (int j = 0; j < p; ++j) {
-    const int jb = j >> 2, jr = j & 3, buf = j & 1;
-    const int drop = s_drop[buf];
-    if (own && bi == jb) {                             // row j of R, columns b > j
-      const df64 inv = s_inv[buf];
+  __shared__ df64 sW[16];                      // W = R11^{-1} of the current block column (upper)
+  const int nb = (p + 3) / 4;
+  for (int jb = 0; jb < nb; ++jb) {
+    if (own && bi == jb && bj == jb) {         // (1) diagonal block
+      df64 r[16], w[16], inv[4];
+      int dr[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int b = 4 * bj + c;
-        const df64 gv = sel4(g[c], g[4 + c], g[8 + c], g[12 + c], jr);
-        if (b > j && b < p) {
-          const df64 r = drop ? df64{0.f, 0.f} : df_mul(gv, inv);
-          Rrow[b] = r;
-          Rout[j * kWL + b] = r.hi;
-        }
+      for (int u = 0; u < 16; ++u) {
+        r[u] = df64{0.f, 0.f};
+        w[u] = df64{0.f, 0.f};
       }
-    }
-    __syncthreads();
-    const int jn = j + 1;
-    const bool piv = own && jn < p && bi == (jn >> 2) && bj == (jn >> 2);
-    if (own && 4 * bi + 3 > j) {                      // the block still has trailing entries
-      df64 ra[4], rb[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        ra[i] = Rrow[4 * bi + i];
-        rb[i] = Rrow[4 * bj + i];
-      }
-      if (piv) {                                       // next pivot first: its update, then 1 / R_jj
-        const int kn = jn & 3;
-        df64 d = sel4(g[0], g[5], g[10], g[15], kn);
-        if (!drop) d = df_add(d, df_neg(df_mul(sel4(ra[0], ra[1], ra[2], ra[3], kn), sel4(rb[0], rb[1], rb[2], rb[3], kn))));
-        wide_pivot(d, jn, v, maxdiag, &s_inv[buf ^ 1], &s_drop[buf ^ 1], Rout);
-      }
-      if (!drop) {
+        const int j = 4 * jb + i;
+        const df64 d = g[5 * i];
+        const bool drop = j >= p || !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) ||
+                          !(d.hi < 1e30f);
+        dr[i] = drop ? 1 : 0;
+        inv[i] = drop ? df64{0.f, 0.f} : df_rsqrt(d);
+        if (!drop) {
+          r[5 * i] = df_mul(d, inv[i]);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int a = 4 * bi + i;
+          for (int c = i + 1; c < 4; ++c) r[4 * i + c] = df_mul(g[4 * i + c], inv[i]);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int b = 4 * bj + c;
-            if (a > j && b >= a && b < p) g[4 * i + c] = df_add(g[4 * i + c], df_neg(df_mul(ra[i], rb[c])));
-          }
+          for (int a = i + 1; a < 4; ++a)
+#pragma unroll
+            for (int c = a; c < 4; ++c) g[4 * a + c] = df_add(g[4 * a + c], df_neg(df_mul(r[4 * i + a], r[4 * i + c])));
+        }
+      }
+      // W = R11^{-1}: W_cc = 1 / R_cc = inv_c, W_rc = -(sum_{r<k<=c} R_rk W_kc) / R_rr
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        w[5 * c] = inv[c];
+#pragma unroll
+        for (int rr = c - 1; rr >= 0; --rr) {
+          df64 acc{0.f, 0.f};
+#pragma unroll
+          for (int k = rr + 1; k <= c; ++k) acc = df_add(acc, df_mul(r[4 * rr + k], w[4 * k + c]));
+          w[4 * rr + c] = dr[rr] ? df64{0.f, 0.f} : df_neg(df_mul(acc, inv[rr]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) sW[u] = w[u];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = 4 * jb + i;
+        if (j < kWL) {
+          v.rdiag[j] = r[5 * i];
+          v.drop[j] = dr[i];
+#pragma unroll
+          for (int c = i; c < 4; ++c) Rout[j * kWL + 4 * jb + c] = r[4 * i + c].hi;
         }
       }
     }
     __syncthreads();
+    if (own && bi == jb && bj > jb) {          // (2) R12 = W^T G12 for this block of row block jb
+      df64 w[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) w[u] = sW[u];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          df64 acc{0.f, 0.f};
+#pragma unroll
+          for (int k = 0; k <= i; ++k) acc = df_add(acc, df_mul(w[4 * k + i], g[4 * k + c]));
+          const int b = 4 * bj + c;
+          if (b >= p) acc = df64{0.f, 0.f};
+          Rpanel[i * kWL + b] = acc;
+          Rout[(4 * jb + i) * kWL + b] = acc.hi;
+        }
+    }
+    __syncthreads();
+    if (own && bi > jb) {                      // (3) rank-4 update of a trailing block
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        df64 ra[4], rb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          ra[i] = Rpanel[k * kWL + 4 * bi + i];
+          rb[i] = Rpanel[k * kWL + 4 * bj + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (bi < bj || c >= i) g[4 * i + c] = df_add(g[4 * i + c], df_neg(df_mul(ra[i], rb[c])));
+      }
+    }
   }
-  for (int j = p + tid; j < kWL; j += blockDim.x) {
+  for (int j = nb * 4 + tid; j < kWL; j += blockDim.x) {
     v.rdiag[j] = df64{0.f, 0.f};
     v.drop[j] = 1;
   }
+  for (int j = p + tid; j < nb * 4; j += blockDim.x) Rout[j * kWL + j] = 0.f;
   __syncthreads();
 }
 
@@ -678,7 +773,7 @@ constexpr int kTB = 32;                            // rows per block of the subs
 
 __global__ void __launch_bounds__(kTThr, 1)
 k_wd_trsm(const float* in, int64_t ldi, int64_t len, const float* __restrict__ T, float* outT, float* outTl,
-          int64_t ldo) {
+          __nv_bfloat16* __restrict__ outTb, __nv_bfloat16* __restrict__ outTbl, int64_t ldo) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   float* RT = reinterpret_cast<float*>(dsm);                 // kWL x kTS
   float* Ys = RT + kWL * kTS;                                 // kWL x kTX: Ys[c][x]
@@ -732,6 +827,19 @@ k_wd_trsm(const float* in, int64_t ldi, int64_t len, const float* __restrict__ T
     const float4 v = *reinterpret_cast<const float4*>(Ys + c * kTX + 4 * x4);
     reinterpret_cast<float4*>(outT + c * ldo + x0)[x4] = v;
     reinterpret_cast<float4*>(outTl + c * ldo + x0)[x4] = f4_lo(v);
+    if (outTb != nullptr) {
+      __nv_bfloat16 h[4], l[4];
+      bf16_split(v.x, h[0], l[0]);
+      bf16_split(v.y, h[1], l[1]);
+      bf16_split(v.z, h[2], l[2]);
+      bf16_split(v.w, h[3], l[3]);
+      __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(outTb + c * ldo + x0 + 4 * x4);
+      __nv_bfloat162* lb = reinterpret_cast<__nv_bfloat162*>(outTbl + c * ldo + x0 + 4 * x4);
+      hb[0] = __halves2bfloat162(h[0], h[1]);
+      hb[1] = __halves2bfloat162(h[2], h[3]);
+      lb[0] = __halves2bfloat162(l[0], l[1]);
+      lb[1] = __halves2bfloat162(l[2], l[3]);
+    }
   }
 }
 
@@ -807,7 +915,8 @@ __global__ void __launch_bounds__(kEThr, 1)
 k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtensorMap tmZl,
          const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmRl, int64_t m, int64_t n,
          const float* __restrict__ O, float* __restrict__ S, float* __restrict__ A, int64_t ld, float* __restrict__ L,
-         int64_t ldl, DevState* __restrict__ dst, double* __restrict__ cpart, unsigned* __restrict__ ticket) {
+         int64_t ldl, DevState* __restrict__ dst, double* __restrict__ cpart, unsigned* __restrict__ ticket,
+         __nv_bfloat16* __restrict__ Ab, int64_t ldb) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kEStages], empty[kEStages], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
@@ -968,12 +1077,18 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
 #pragma unroll
             for (int u = 0; u < 4; ++u) L4[u] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
           }
+          if (Ab != nullptr) {                                          // BF16 shadow of A'
+            __nv_bfloat162* ab = reinterpret_cast<__nv_bfloat162*>(Ab + row * ldb + col0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) ab[u] = __floats2bfloat162_rn(an[2 * u], an[2 * u + 1]);
+          }
         } else {
           for (int u = 0; u < 16; ++u)
             if (col0 + u < n) {
               S[row * ld + col0 + u] = sn[u];
               A[row * ld + col0 + u] = an[u];
               if (L != nullptr) L[row * ldl + col0 + u] = x[u];
+              if (Ab != nullptr) Ab[row * ldb + col0 + u] = __float2bfloat16_rn(an[u]);
             }
         }
       }
@@ -1020,8 +1135,10 @@ int wide_lp() { return kWL; }
 int wide_tile() { return kWN; }
 
 cudaError_t prepare_wide_kernels() {
-  cudaError_t e = set_dyn(k_wd_pass<false>, kWStages * kWStage);
-  if (e == cudaSuccess) e = set_dyn(k_wd_pass<true>, kWStages * kWStage);
+  cudaError_t e = set_dyn(k_wd_pass<false, 0>, kWStages * kWStage);
+  if (e == cudaSuccess) e = set_dyn(k_wd_pass<true, 0>, kWStages * kWStage);
+  if (e == cudaSuccess) e = set_dyn(k_wd_pass<false, 1>, kWStages * kWStage);
+  if (e == cudaSuccess) e = set_dyn(k_wd_pass<true, 1>, kWStages * kWStage);
   if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailOrth>, kGSmem);
   if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailCore>, kGSmem);
   if (e == cudaSuccess) e = set_dyn(k_wd_apply, sizeof(float) * kWL * (kWL + kACols));
@@ -1053,19 +1170,21 @@ int wide_gram_grid() {
 
 int wide_gram_count() { return kGCount; }
 
-cudaError_t launch_wd_omega(float* OT, float* OTl, int64_t ldo, int64_t m, int l, int use_rp, uint64_t seed,
-                            uint64_t ctr, const DevState* dst, cudaStream_t st) {
+cudaError_t launch_wd_omega(float* OT, float* OTl, void* OTb, void* OTbl, int64_t ldo, int64_t m, int l, int use_rp,
+                            uint64_t seed, uint64_t ctr, const DevState* dst, cudaStream_t st) {
   const int64_t total = m * (kWL / 4);
   int64_t grid = (total + 255) / 256;
   if (grid > 4096) grid = 4096;
-  k_wd_omega<<<static_cast<int>(grid), 256, 0, st>>>(OT, OTl, ldo, m, l, use_rp, seed, ctr, dst);
+  k_wd_omega<<<static_cast<int>(grid), 256, 0, st>>>(OT, OTl, static_cast<__nv_bfloat16*>(OTb),
+                                                     static_cast<__nv_bfloat16*>(OTbl), ldo, m, l, use_rp, seed, ctr,
+                                                     dst);
   return cudaGetLastError();
 }
 
 // Splits of K per tile so that ntiles * S covers the SMs once (S <= 8, at least 2 chunks each).
 int wide_splits(int64_t nlong, int64_t nk, int sms) {
   const int64_t ntiles = (nlong + kWN - 1) / kWN;
-  const int64_t nkc = (nk + kWK - 1) / kWK;
+  const int64_t nkc = (nk + 64 - 1) / 64;
   int64_t S = sms / (ntiles > 0 ? ntiles : 1);
   if (S > 8) S = 8;
   if (S > nkc / 2) S = nkc / 2;
@@ -1073,17 +1192,23 @@ int wide_splits(int64_t nlong, int64_t nk, int sms) {
   return static_cast<int>(S);
 }
 
-cudaError_t launch_wd_pass(bool col, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
+cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
                            int64_t nlong, int64_t nk, int S, float* part, int64_t ldp, unsigned* tickets, float* outT,
-                           float* outTl, int64_t ldo, float* outR, float* outRl, DevState* dst, cudaStream_t st) {
+                           float* outTl, void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl,
+                           DevState* dst, cudaStream_t st) {
   const int ntiles = static_cast<int>((nlong + kWN - 1) / kWN);
   const size_t smem = kWStages * kWStage;
-  if (col)
-    k_wd_pass<true><<<ntiles * S, kWThr, smem, st>>>(tmA, tmM, tmMl, nlong, nk, S, part, ldp, tickets, outT, outTl,
-                                                     ldo, outR, outRl, dst);
-  else
-    k_wd_pass<false><<<ntiles * S, kWThr, smem, st>>>(tmA, tmM, tmMl, nlong, nk, S, part, ldp, tickets, outT, outTl,
-                                                      ldo, outR, outRl, dst);
+  __nv_bfloat16* tb = static_cast<__nv_bfloat16*>(outTb);
+  __nv_bfloat16* tbl = static_cast<__nv_bfloat16*>(outTbl);
+#define ARGS tmA, tmM, tmMl, nlong, nk, S, part, ldp, tickets, outT, outTl, tb, tbl, ldo, outR, outRl, dst
+  if (prec == 0) {
+    if (col) k_wd_pass<true, 0><<<ntiles * S, kWThr, smem, st>>>(ARGS);
+    else k_wd_pass<false, 0><<<ntiles * S, kWThr, smem, st>>>(ARGS);
+  } else {
+    if (col) k_wd_pass<true, 1><<<ntiles * S, kWThr, smem, st>>>(ARGS);
+    else k_wd_pass<false, 1><<<ntiles * S, kWThr, smem, st>>>(ARGS);
+  }
+#undef ARGS
   return cudaGetLastError();
 }
 
@@ -1109,22 +1234,27 @@ cudaError_t launch_wd_apply(const float* in, int64_t ldi, int64_t len, const flo
 }
 
 cudaError_t launch_wd_trsm(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
-                           int64_t ldo, cudaStream_t st) {
+                           void* outTb, void* outTbl, int64_t ldo, cudaStream_t st) {
   const int grid = static_cast<int>((len + kTThr - 1) / kTThr);
   if (grid == 0) return cudaSuccess;
-  k_wd_trsm<<<grid, kTThr, sizeof(float) * kWL * (kTS + kTX), st>>>(in, ldi, len, T, outT, outTl, ldo);
+  k_wd_trsm<<<grid, kTThr, sizeof(float) * kWL * (kTS + kTX), st>>>(in, ldi, len, T, outT, outTl,
+                                                                       static_cast<__nv_bfloat16*>(outTb),
+                                                                       static_cast<__nv_bfloat16*>(outTbl), ldo);
   return cudaGetLastError();
 }
 
 cudaError_t launch_wd_alm(bool alm, const CUtensorMap& tmZ, const CUtensorMap& tmZl, const CUtensorMap& tmR,
                           const CUtensorMap& tmRl, int64_t m, int64_t n, const float* O, float* S, float* A, int64_t ld,
                           float* L, int64_t ldl, DevState* dst, double* cpart, unsigned* ticket, int grid,
-                          cudaStream_t st) {
+                          void* Ab, int64_t ldb, cudaStream_t st) {
   const size_t smem = kEStages * kEStage;
+  __nv_bfloat16* ab = static_cast<__nv_bfloat16*>(Ab);
   if (alm)
-    k_wd_alm<true><<<grid, kEThr, smem, st>>>(tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, dst, cpart, ticket);
+    k_wd_alm<true><<<grid, kEThr, smem, st>>>(tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, dst, cpart, ticket, ab,
+                                              ldb);
   else
-    k_wd_alm<false><<<grid, kEThr, smem, st>>>(tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, dst, cpart, ticket);
+    k_wd_alm<false><<<grid, kEThr, smem, st>>>(tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, dst, cpart, ticket,
+                                               nullptr, 0);
   return cudaGetLastError();
 }
 

@@ -125,15 +125,51 @@ def test_wide_ialm_parity(fr):
     assert np.allclose(hist, ref.history, rtol=1e-3)
 
 
-def test_wide_recovery_8192_full_size(fr):
-    """Large low-rank recovery, 8192 x 8192 rank 100 + 10 % corruption, FRSVT l = 120, q = 2:
-    three iALM iterations at full size against the oracle."""
+@pytest.fixture(scope="module")
+def recovery_ref():
+    """Oracle iALM-FRSVT on the large low-rank recovery input (three iterations, FP64)."""
     O, _, _ = synth.recovery_8192()
     O = O.astype(np.float64)
     nrm = power_norm2(O, iters=30)
     ref = orpca.ialm_rpca(O, method="frsvt", l=120, q=2, seed=2004, range_prop=False, fixed_iters=3, normO2=nrm)
-    L, S, hist, info = run_ialm(fr, O, 120, 2, 3, 2004, nrm)
+    return O, nrm, ref
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_wide_recovery_8192_full_size(fr, recovery_ref, prec):
+    """Large low-rank recovery, 8192 x 8192 rank 100 + 10 % corruption, FRSVT l = 120, q = 2:
+    three iALM iterations at full size against the oracle, FP32-accurate passes and the BF16
+    shadow (sketch and first power step in BF16, FP32-accurate last power step and projection)."""
+    import torch
+    O, nrm, ref = recovery_ref
+    m, n = O.shape
+    Og = torch.from_numpy(np.ascontiguousarray(O, dtype=np.float32)).cuda()
+    S, A, L = torch.empty_like(Og), torch.empty_like(Og), torch.empty_like(Og)
+    h = fr.Handle(m, n, 120, q=2, range_prop=False, seed=2004,
+                  precision=fr.PREC_BF16 if prec == "bf16" else fr.PREC_FP32)
+    h.rpca_init(Og, S, A, 1.0 / np.sqrt(max(m, n)), 1.5, 1e7, normO2=nrm)
+    hist = [h.ialm_step(Og, S, A, 120, L=L if k == 2 else None, sync_residual=True) for k in range(3)]
+    info = h.info()
+    h.close()
+    eL = rel_fro(L.cpu().numpy(), ref.L)
+    eS = rel_fro(S.cpu().numpy(), ref.S)
+    print(f"recovery 8192 {prec}: rel err L {eL:.3e} S {eS:.3e}")
     assert info.device_status & ~1 == 0, info
-    assert rel_fro(L, ref.L) <= TOL
-    assert rel_fro(S, ref.S) <= TOL
+    assert eL <= TOL
+    assert eS <= TOL
     assert np.allclose(hist, ref.history, rtol=1e-3)
+
+
+@pytest.mark.parametrize("m,n,l,q", [(2048, 1024, 64, 2), (1500, 700, 120, 2), (1200, 600, 40, 3)])
+def test_wide_bf16_svt_matches_oracle(fr, m, n, l, q):
+    """BF16 shadow on the wide basis: X against the oracle's FP32-free Alg. 1 at the 1e-4 bar."""
+    A, _ = spectrum_matrix(m, n, rank=l + 8, decay=0.93, noise=0.01, seed=m + 3 * n)
+    d = osvt.frsvt(A.astype(np.float64), 0.0, l, q, 5, 0).sigma
+    tau = float(0.5 * (d[l // 3] + d[l // 3 + 1]))
+    h = fr.Handle(m, n, l, q=q, range_prop=False, seed=5, precision=fr.PREC_BF16)
+    X = h.svt(to_gpu(A), tau, l, X=to_gpu(np.zeros_like(A))).cpu().numpy()
+    info = h.info()
+    assert info.device_status & (fr.DEV_TIMEOUT | fr.DEV_NONFINITE) == 0
+    ref = osvt.frsvt(A.astype(np.float64), tau, l, q, 5, 0).X
+    assert rel_fro(X, ref) <= TOL
+    h.close()
