@@ -62,7 +62,9 @@ typedef enum frsvt_status {
  * FRSVT_ERR_UNSUPPORTED for a precision it does not build. */
 typedef enum frsvt_precision {
   FRSVT_PREC_FP32 = 0,           /* float32 data, FP32-accurate passes */
-  FRSVT_PREC_BF16 = 1            /* BF16 shadow for the sketch and the early power steps */
+  FRSVT_PREC_BF16 = 1,           /* BF16 shadow for the sketch and the early power steps */
+  FRSVT_PREC_FP8 = 2             /* E4M3 shadow, one power-of-two scale per 128 x 128 tile of A, for the
+                                    sketch and the early power steps (cfg.l_max > 32 only) */
 } frsvt_precision;
 
 #define FRSVT_CFG_ADJOINT 1      /* allocate the workspace of frsvt_svt_save / frsvt_backward */

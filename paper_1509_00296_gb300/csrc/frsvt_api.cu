@@ -126,7 +126,9 @@ cudaError_t launch_wd_omega(float* OT, float* OTl, void* OTb, void* OTbl, int64_
 cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
                            int64_t nlong, int64_t nk, int S, float* part, int64_t ldp, unsigned* tickets, float* outT,
                            float* outTl, void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl,
-                           DevState* dst, cudaStream_t st);
+                           DevState* dst, cudaStream_t st, const float* scales = nullptr, int ntr8 = 0, int ntc8 = 0);
+cudaError_t launch_wd_quant8(const float* A, int64_t lda, int64_t m, int64_t n, void* A8, int64_t ld8, float* scales,
+                             cudaStream_t st);
 cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len, int grid, double* cpart, double* Gpk,
                            unsigned* ticket, int p, double rank_tol, int l, float tau_host, int tau_from_mu,
                            int update_rp, int advance_counter, int max_sweeps, float* T1, float* T2, DevState* dst,
@@ -199,6 +201,9 @@ struct frsvt_handle {
   float *wYT = nullptr, *wQT = nullptr, *wQTl = nullptr, *wQp = nullptr, *wRf = nullptr, *wRfl = nullptr;
   float *wT1 = nullptr, *wT2 = nullptr, *wpart = nullptr;
   void *wOTb = nullptr, *wOTbl = nullptr, *wZTb = nullptr, *wZTbl = nullptr, *wQTb = nullptr, *wQTbl = nullptr;
+  void* A8 = nullptr;              // E4M3 shadow of A (FRSVT_PREC_FP8), row stride ld8 bytes
+  float* w8s = nullptr;            // its per-128 x 128-tile scales
+  int64_t ld8 = 0;
   double *wgc = nullptr, *wGpk = nullptr, *wac = nullptr;
   unsigned* wtick = nullptr;       // pass tiles, then the Gram ticket, then the epilogue ticket
   int64_t w_ntiles = 0;
@@ -322,6 +327,20 @@ bool make_row_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t
   cuuint32_t estr[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 8-bit row-major matrix (the E4M3 shadow), box_cols x box_rows boxes, no swizzle.
+bool make_row_map_u8(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                     int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -528,7 +547,7 @@ void free_all(frsvt_handle* h) {
                   h->tickets, h->wsvt_next, h->ad_ws, h->Ab,
                   h->wOT, h->wOTl, h->wZT, h->wZTl, h->wZ, h->wZl, h->wYT, h->wQT, h->wQTl, h->wQp, h->wRf,
                   h->wRfl, h->wT1, h->wT2, h->wpart, h->wgc, h->wGpk, h->wac, h->wtick,
-                  h->wOTb, h->wOTbl, h->wZTb, h->wZTbl, h->wQTb, h->wQTbl};
+                  h->wOTb, h->wOTbl, h->wZTb, h->wZTbl, h->wQTb, h->wQTbl, h->A8, h->w8s};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -556,12 +575,15 @@ frsvt_status wide_orth(frsvt_handle* h, int64_t n, int l, int passes, bool bf_ne
 
 // Alg. 1 up to the core on the wide basis: leaves Z / Z_lo (m x 128) and Rf / Rf_lo (n x 128)
 // so that X = Z Rf^T, and sets r, s, sigma (and the counter) in the device state.
-// Reduced precision (Ab: the BF16 shadow of A, current): the sketch and the first q - 1 power steps
+// Shadow the reduced-precision passes read: 0 none, 1 the BF16 shadow (kept current by rpca_init,
+// frsvt_svt and the epilogue), 2 the E4M3 shadow (quantized at the start of each SVT).
+int wide_lowp(const frsvt_handle* h) { return h->A8 != nullptr ? 2 : (h->Ab != nullptr ? 1 : 0); }
+
+// Reduced precision (lowp, see wide_lowp): the sketch and the first q - 1 power steps
 // read the shadow with BF16 copies of the narrow factors; the last power step and the projection
 // stay FP32-accurate.
 frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int l, int q,
-                                 uint64_t ctr, float tau_host, int tau_from_mu, int advance_counter,
-                                 const void* Ab = nullptr) {
+                                 uint64_t ctr, float tau_host, int tau_from_mu, int advance_counter, int lowp = 0) {
   cudaStream_t st = h->stream;
   const int64_t LW = wide_lp();
   CUtensorMap tmAr, tmAc, tmOT, tmOTl, tmZT, tmZTl, tmQT, tmQTl;
@@ -574,24 +596,32 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
       !make_row_map_sw128(&tmQT, h->wQT, LW, n, h->w_ldn, 128) ||
       !make_row_map_sw128(&tmQTl, h->wQTl, LW, n, h->w_ldn, 128))
     return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis)");
-  const bool bf = Ab != nullptr;
+  const bool bf = lowp != 0;
   CUtensorMap tmBr, tmBc, tmOTb, tmOTbl, tmZTb, tmZTbl, tmQTb, tmQTbl;
-  if (bf && (!make_row_map_bf16(&tmBr, Ab, m, n, h->ldb, wide_tile()) ||
-             !make_row_map_bf16(&tmBc, Ab, m, n, h->ldb, 64) ||
-             !make_row_map_bf16(&tmOTb, h->wOTb, LW, m, h->w_ldm, 128) ||
+  if (lowp == 2) {
+    if (!make_row_map_u8(&tmBr, h->A8, m, n, h->ld8, 64, wide_tile()) ||
+        !make_row_map_u8(&tmBc, h->A8, m, n, h->ld8, wide_tile(), 64))
+      return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis, FP8 shadow)");
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_quant8(A, lda, m, n, h->A8, h->ld8, h->w8s, st));
+  } else if (lowp == 1 && (!make_row_map_bf16(&tmBr, h->Ab, m, n, h->ldb, wide_tile()) ||
+                           !make_row_map_bf16(&tmBc, h->Ab, m, n, h->ldb, 64)))
+    return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis, BF16 shadow)");
+  const float* sc8 = lowp == 2 ? h->w8s : nullptr;
+  const int ntr8 = static_cast<int>(cdiv(m, 128)), ntc8 = static_cast<int>(cdiv(n, 128));
+  if (bf && (!make_row_map_bf16(&tmOTb, h->wOTb, LW, m, h->w_ldm, 128) ||
              !make_row_map_bf16(&tmOTbl, h->wOTbl, LW, m, h->w_ldm, 128) ||
              !make_row_map_bf16(&tmZTb, h->wZTb, LW, m, h->w_ldm, 128) ||
              !make_row_map_bf16(&tmZTbl, h->wZTbl, LW, m, h->w_ldm, 128) ||
              !make_row_map_bf16(&tmQTb, h->wQTb, LW, n, h->w_ldn, 128) ||
              !make_row_map_bf16(&tmQTbl, h->wQTbl, LW, n, h->w_ldn, 128)))
-    return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis, BF16 shadow)");
+    return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis, BF16 factors)");
   const int Sr = wide_splits(m, n, h->sms), Sc = wide_splits(n, m, h->sms);
   FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_omega(h->wOT, h->wOTl, bf ? h->wOTb : nullptr, bf ? h->wOTbl : nullptr,
                                                    h->w_ldm, m, l, 0, h->cfg.seed, ctr, h->dst, st));
   if (bf)
-    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(true, 1, tmBc, tmOTb, tmOTbl, n, m, Sc, h->wpart, h->w_ldp,
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(true, lowp, tmBc, tmOTb, tmOTbl, n, m, Sc, h->wpart, h->w_ldp,
                                                     h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn, nullptr,
-                                                    nullptr, h->dst, st));
+                                                    nullptr, h->dst, st, sc8, ntr8, ntc8));
   else
     FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(true, 0, tmAc, tmOT, tmOTl, n, m, Sc, h->wpart, h->w_ldp,
                                                     h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn, nullptr,
@@ -600,12 +630,12 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
   if (s != FRSVT_OK) return s;
   for (int it = 0; it < q; ++it) {
     if (bf && it < q - 1) {
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(false, 1, tmBr, tmQTb, tmQTbl, m, n, Sr, h->wpart, h->w_ldp,
-                                                        h->wtick, nullptr, nullptr, h->wZTb, h->wZTbl, h->w_ldm,
-                                                        nullptr, nullptr, h->dst, st));
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(true, 1, tmBc, tmZTb, tmZTbl, n, m, Sc, h->wpart, h->w_ldp,
-                                                         h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn,
-                                                         nullptr, nullptr, h->dst, st));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(false, lowp, tmBr, tmQTb, tmQTbl, m, n, Sr, h->wpart,
+                                                        h->w_ldp, h->wtick, nullptr, nullptr, h->wZTb, h->wZTbl,
+                                                        h->w_ldm, nullptr, nullptr, h->dst, st, sc8, ntr8, ntc8));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(true, lowp, tmBc, tmZTb, tmZTbl, n, m, Sc, h->wpart,
+                                                         h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr,
+                                                         h->w_ldn, nullptr, nullptr, h->dst, st, sc8, ntr8, ntc8));
     } else {
       FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(false, 0, tmAr, tmQT, tmQTl, m, n, Sr, h->wpart, h->w_ldp,
                                                         h->wtick, h->wZT, h->wZTl, nullptr, nullptr, h->w_ldm,
@@ -684,10 +714,16 @@ bool wide_alloc(frsvt_handle* h) {
   alloc(reinterpret_cast<void**>(&h->pmax), sizeof(float) * h->absmax_blocks);
   alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
   alloc(reinterpret_cast<void**>(&h->wsvt_next), sizeof(unsigned));
-  if (cfg->precision == FRSVT_PREC_BF16) {
+  if (cfg->precision == FRSVT_PREC_BF16 || cfg->precision == FRSVT_PREC_FP8) {
     const size_t bm = sizeof(uint16_t) * LW * h->w_ldm, bn = sizeof(uint16_t) * LW * h->w_ldn;
-    h->ldb = (cfg->n_max + 7) / 8 * 8;
-    alloc(&h->Ab, sizeof(uint16_t) * static_cast<size_t>(cfg->m_max) * h->ldb);
+    if (cfg->precision == FRSVT_PREC_BF16) {
+      h->ldb = (cfg->n_max + 7) / 8 * 8;
+      alloc(&h->Ab, sizeof(uint16_t) * static_cast<size_t>(cfg->m_max) * h->ldb);
+    } else {
+      h->ld8 = (cfg->n_max + 15) / 16 * 16;
+      alloc(&h->A8, static_cast<size_t>(cfg->m_max) * h->ld8);
+      alloc(reinterpret_cast<void**>(&h->w8s), sizeof(float) * cdiv(cfg->m_max, 128) * cdiv(cfg->n_max, 128));
+    }
     alloc(&h->wOTb, bm);
     alloc(&h->wOTbl, bm);
     alloc(&h->wZTb, bm);
@@ -799,7 +835,9 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   *out = nullptr;
   if (cfg->m_max < 1 || cfg->n_max < 1 || cfg->l_max < 1 || cfg->l_max > kMaxL || cfg->q < 0 || cfg->q > 64)
     return FRSVT_ERR_INVALID_ARG;
-  if (cfg->precision != FRSVT_PREC_FP32 && cfg->precision != FRSVT_PREC_BF16) return FRSVT_ERR_UNSUPPORTED;
+  if (cfg->precision != FRSVT_PREC_FP32 && cfg->precision != FRSVT_PREC_BF16 &&
+      !(cfg->precision == FRSVT_PREC_FP8 && cfg->l_max > 32))
+    return FRSVT_ERR_UNSUPPORTED;
   h = new (std::nothrow) frsvt_handle();
   if (h == nullptr) return FRSVT_ERR_ALLOC;
   h->cfg = *cfg;
@@ -988,7 +1026,8 @@ frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, in
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
   if (h->wide) {
     if (h->Ab != nullptr) FRSVT_CK(launch_to_bf16(A, lda, m, n, h->Ab, h->ldb, h->stream));
-    if ((s = wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1, h->Ab)) != FRSVT_OK)
+    if ((s = wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1, wide_lowp(h))) !=
+        FRSVT_OK)
       return s;
     return wide_epilogue(h, false, m, n, nullptr, nullptr, nullptr, 0, X, ldx);
   }
@@ -1070,7 +1109,8 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;   // the shadow is kept current by rpca_init / the epilogue
   if (h->wide) {
-    if ((s = wide_range_and_core(h, A, m, n, ld, l, h->cfg.q, kCounterFromState, 0.f, 1, 1, h->Ab)) != FRSVT_OK)
+    if ((s = wide_range_and_core(h, A, m, n, ld, l, h->cfg.q, kCounterFromState, 0.f, 1, 1, wide_lowp(h))) !=
+        FRSVT_OK)
       return s;
     if ((s = wide_epilogue(h, true, m, n, O, S, A, ld, L, ldl)) != FRSVT_OK) return s;
   } else {

@@ -26,6 +26,7 @@
 #include <cooperative_groups.h>
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "cluster.cuh"
 #include "common.cuh"
@@ -115,6 +116,95 @@ __global__ void k_wd_omega(float* __restrict__ OT, float* __restrict__ OTl, __nv
   }
 }
 
+// ---------------------------------------------------------------- FP8 shadow of A
+// One CTA per 128 x 128 tile of A: s = the smallest power of two with max|A_tile| / s <= 448 (the
+// E4M3 range), A8 = e4m3(A / s) (round to nearest, saturating), scales[tile] = s.  The tile is
+// read once (coalesced float4) and held in registers.
+constexpr int kQT = 128;                       // tile side
+constexpr int kQThr = 256;
+
+__global__ void __launch_bounds__(kQThr)
+k_wd_quant8(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, uint8_t* __restrict__ A8, int64_t ld8,
+            float* __restrict__ scales, int ntc) {
+  __shared__ float red[kQThr / 32];
+  const int tr = blockIdx.x / ntc, tc = blockIdx.x % ntc;
+  const int64_t r0 = static_cast<int64_t>(tr) * kQT;
+  const int64_t c0 = static_cast<int64_t>(tc) * kQT;
+  const int t = threadIdx.x, c4 = t & 31;
+  float4 v[16];
+  float amax = 0.f;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int64_t row = r0 + 8 * i + (t >> 5);
+    const int64_t col = c0 + 4 * c4;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row < m) {
+      if (col + 3 < n) {
+        x = __ldcs(reinterpret_cast<const float4*>(A + row * lda + col));
+      } else {
+        if (col < n) x.x = A[row * lda + col];
+        if (col + 1 < n) x.y = A[row * lda + col + 1];
+        if (col + 2 < n) x.z = A[row * lda + col + 2];
+      }
+    }
+    v[i] = x;
+    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((t & 31) == 0) red[t >> 5] = amax;
+  __syncthreads();
+  amax = 0.f;
+#pragma unroll
+  for (int w = 0; w < kQThr / 32; ++w) amax = fmaxf(amax, red[w]);
+  float sc = 1.f;
+  if (amax > 0.f && isfinite(amax)) {
+    int ex;
+    const float f = frexpf(amax / 448.f, &ex);                 // amax / 448 = f 2^ex, f in [0.5, 1)
+    sc = ldexpf(1.f, f == 0.5f ? ex - 1 : ex);
+  }
+  if (t == 0) scales[blockIdx.x] = sc;
+  const float inv = 1.f / sc;                                   // exact: sc is a power of two
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int64_t row = r0 + 8 * i + (t >> 5);
+    const int64_t col = c0 + 4 * c4;
+    if (row >= m || col >= n) continue;
+    const float xs[4] = {v[i].x * inv, v[i].y * inv, v[i].z * inv, v[i].w * inv};
+    uint8_t b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b[u] = static_cast<uint8_t>(__nv_cvt_float_to_fp8(xs[u], __NV_SATFINITE, __NV_E4M3));
+    if (col + 3 < n) {
+      *reinterpret_cast<uint32_t*>(A8 + row * ld8 + col) =
+          static_cast<uint32_t>(b[0]) | (static_cast<uint32_t>(b[1]) << 8) | (static_cast<uint32_t>(b[2]) << 16) |
+          (static_cast<uint32_t>(b[3]) << 24);
+    } else {
+      for (int u = 0; u < 4; ++u)
+        if (col + u < n) A8[row * ld8 + col + u] = b[u];
+    }
+  }
+}
+
+// Sixteen E4M3 values times a power-of-two scale, as eight packed BF16 pairs (exact: an E4M3
+// value times a power of two has at most four significant bits).
+__device__ __forceinline__ void fp8x16_to_bf16(const uint4 q, float sc, uint4& lo8, uint4& hi8) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  uint32_t o[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const __nv_fp8x2_storage_t pr = static_cast<__nv_fp8x2_storage_t>((w[i] >> (16 * h)) & 0xFFFFu);
+      const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pr, __NV_E4M3);
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+      const __nv_bfloat162 bb = __floats2bfloat162_rn(f.x * sc, f.y * sc);
+      o[2 * i + h] = *reinterpret_cast<const uint32_t*>(&bb);
+    }
+  }
+  lo8 = make_uint4(o[0], o[1], o[2], o[3]);
+  hi8 = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
 // ---------------------------------------------------------------- passes over A
 // COL = false (row pass): D[k][i] = sum_j M[k][j] A[i][j] for the 256 rows i of the tile, K = n,
 //   A tiles 256 rows x one K-chunk (K-major, 128-byte swizzle).
@@ -136,8 +226,12 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           const __grid_constant__ CUtensorMap tmMl, int64_t nlong, int64_t nk, int S, float* __restrict__ part,
           int64_t ldp, unsigned* __restrict__ tickets, float* __restrict__ outT, float* __restrict__ outTl,
           __nv_bfloat16* __restrict__ outTb, __nv_bfloat16* __restrict__ outTbl, int64_t ldo,
-          float* __restrict__ outR, float* __restrict__ outRl, DevState* __restrict__ dst) {
+          float* __restrict__ outR, float* __restrict__ outRl, DevState* __restrict__ dst,
+          const float* __restrict__ scales, int ntr8, int ntc8) {
   constexpr int KC = PR ? 64 : kWK;                         // elements of K per chunk (128-byte rows)
+  constexpr int NS = (PR == 2) ? 2 : kWStages;              // pipeline stages
+  constexpr uint32_t SB = (PR == 2) ? kWStage + 16384u : kWStage;   // stage bytes (+ the FP8 tile)
+  constexpr uint32_t TX = (PR == 2) ? 16384u + 2 * kWMBytes : kWStage;   // bytes the TMA brings per stage
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kWStages], hidone[kWStages], lo_ready[kWStages], empty[kWStages], acc_full;
   __shared__ uint32_t tmem_base;
@@ -156,7 +250,7 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     return;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&hidone[s], 1);
       mbar_init(&lo_ready[s], kWSplit);
@@ -178,15 +272,18 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       prefetch_tensormap(&tmM);
       prefetch_tensormap(&tmMl);
       for (int g = 0; g < nc && ok; ++g) {
-        const int s = g % kWStages, u = g / kWStages;
+        const int s = g % NS, u = g / NS;
         if (u > 0 && !mbar_wait(&empty[s], static_cast<uint32_t>(u - 1) & 1u)) {
           flag_timeout(ok, dst);
           break;
         }
-        unsigned char* st = dsm + s * kWStage;
+        unsigned char* st = dsm + s * SB;
         const int c = c0 + g;
-        mbar_arrive_expect_tx(&full[s], kWStage);
-        if (COL) {
+        mbar_arrive_expect_tx(&full[s], TX);
+        if (PR == 2) {
+          if (COL) tma_load_2d(st + kWABytes + 2 * kWMBytes, &tmA, x0, KC * c, &full[s]);
+          else tma_load_2d(st + kWABytes + 2 * kWMBytes, &tmA, KC * c, x0, &full[s]);
+        } else if (COL) {
           if (PR) {
 #pragma unroll
             for (int v = 0; v < kWN / 64; ++v) tma_load_2d(st + v * 8192, &tmA, x0 + 64 * v, KC * c, &full[s]);
@@ -206,10 +303,10 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       if (PR) {
         constexpr uint32_t idesc = idesc_bf16w(128, kWN, COL);
         for (int g = 0; g < nc; ++g) {
-          const int s = g % kWStages, u = g / kWStages;
-          if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
+          const int s = g % NS, u = g / NS;
+          if (ok && !mbar_wait(PR == 2 ? &lo_ready[s] : &full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
           tc_fence_after();
-          const unsigned char* st = dsm + s * kWStage;
+          const unsigned char* st = dsm + s * SB;
 #pragma unroll
           for (int ks = 0; ks < KC / 16; ++ks) {
             const uint64_t bd = COL ? smem_desc_sw128(st + ks * 2048, 8192, 1024) : smem_desc_sw128(st + 32 * ks, 16, 1024);
@@ -225,20 +322,20 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           return COL ? smem_desc_sw128a32_mn(a + ks * 1024, 4096) : smem_desc_sw128(a + 32 * ks, 16, 1024);
         };
         auto issue_lo = [&](int g) {
-          const int s = g % kWStages, u = g / kWStages;
+          const int s = g % NS, u = g / NS;
           if (ok && !mbar_wait(&lo_ready[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
           tc_fence_after();
-          const unsigned char* st = dsm + s * kWStage;
+          const unsigned char* st = dsm + s * SB;
 #pragma unroll
           for (int ks = 0; ks < kWK / 8; ++ks)
             tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc, true);
           tc_commit(&empty[s]);
         };
         for (int g = 0; g < nc; ++g) {
-          const int s = g % kWStages, u = g / kWStages;
+          const int s = g % NS, u = g / NS;
           if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
           tc_fence_after();
-          const unsigned char* st = dsm + s * kWStage;
+          const unsigned char* st = dsm + s * SB;
 #pragma unroll
           for (int ks = 0; ks < kWK / 8; ++ks) {
             tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
@@ -270,12 +367,47 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         d4[u] = (nc > 0 && ok) ? make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3])
                                : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+  } else if (PR == 2) {
+    // FP8 tile (plain rows) -> BF16 tile in the layout the MMA reads, times the tile scales
+    const int t = threadIdx.x - 32 * 6;
+    for (int g = 0; g < nc; ++g) {
+      const int s = g % NS, u = g / NS, c = c0 + g;
+      if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
+      unsigned char* ab = dsm + s * SB;
+      const uint4* a8 = reinterpret_cast<const uint4*>(ab + kWABytes + 2 * kWMBytes);
+#pragma unroll 2
+      for (int e = t; e < 1024; e += 32 * kWSplit) {
+        int rt, ct;
+        uint32_t off0, off1;
+        if (COL) {                                     // 64 rows x 256 columns; MN-major boxes of 64 columns
+          const int r = e >> 4, j0 = (e & 15) * 16, gb = j0 >> 6, jj = j0 & 63;
+          rt = (KC * c + r) / kQT;
+          ct = (x0 + j0) / kQT;
+          off0 = gb * 8192u + r * 128u + ((((jj >> 3)) ^ (r & 7)) << 4);
+          off1 = gb * 8192u + r * 128u + ((((jj >> 3) + 1) ^ (r & 7)) << 4);
+        } else {                                       // 256 rows x 64 columns, K-major
+          const int r = e >> 2, k0 = (e & 3) * 16;
+          rt = (x0 + r) / kQT;
+          ct = (KC * c) / kQT;
+          off0 = r * 128u + ((((k0 >> 3)) ^ (r & 7)) << 4);
+          off1 = r * 128u + ((((k0 >> 3) + 1) ^ (r & 7)) << 4);
+        }
+        const float sc = (rt < ntr8 && ct < ntc8) ? __ldg(scales + rt * ntc8 + ct) : 1.f;
+        uint4 lo8, hi8;
+        fp8x16_to_bf16(a8[e], sc, lo8, hi8);
+        *reinterpret_cast<uint4*>(ab + off0) = lo8;
+        *reinterpret_cast<uint4*>(ab + off1) = hi8;
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&lo_ready[s]);
+    }
   } else if (!PR) {
     const int t = threadIdx.x - 32 * 6;
     for (int g = 0; g < nc; ++g) {
-      const int s = g % kWStages, u = g / kWStages;
+      const int s = g % NS, u = g / NS;
       if (ok && !mbar_wait(&hidone[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
-      float4* a = reinterpret_cast<float4*>(dsm + s * kWStage);
+      float4* a = reinterpret_cast<float4*>(dsm + s * SB);
 #pragma unroll 4
       for (int e = t; e < static_cast<int>(kWABytes / 16); e += 32 * kWSplit) a[e] = f4_lo(a[e]);
       fence_proxy_async();
@@ -1139,6 +1271,8 @@ cudaError_t prepare_wide_kernels() {
   if (e == cudaSuccess) e = set_dyn(k_wd_pass<true, 0>, kWStages * kWStage);
   if (e == cudaSuccess) e = set_dyn(k_wd_pass<false, 1>, kWStages * kWStage);
   if (e == cudaSuccess) e = set_dyn(k_wd_pass<true, 1>, kWStages * kWStage);
+  if (e == cudaSuccess) e = set_dyn(k_wd_pass<false, 2>, 2 * (kWStage + 16384));
+  if (e == cudaSuccess) e = set_dyn(k_wd_pass<true, 2>, 2 * (kWStage + 16384));
   if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailOrth>, kGSmem);
   if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailCore>, kGSmem);
   if (e == cudaSuccess) e = set_dyn(k_wd_apply, sizeof(float) * kWL * (kWL + kACols));
@@ -1195,18 +1329,22 @@ int wide_splits(int64_t nlong, int64_t nk, int sms) {
 cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
                            int64_t nlong, int64_t nk, int S, float* part, int64_t ldp, unsigned* tickets, float* outT,
                            float* outTl, void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl,
-                           DevState* dst, cudaStream_t st) {
+                           DevState* dst, cudaStream_t st, const float* scales, int ntr8, int ntc8) {
   const int ntiles = static_cast<int>((nlong + kWN - 1) / kWN);
-  const size_t smem = kWStages * kWStage;
+  const size_t smem = prec == 2 ? 2 * (kWStage + 16384) : kWStages * kWStage;
   __nv_bfloat16* tb = static_cast<__nv_bfloat16*>(outTb);
   __nv_bfloat16* tbl = static_cast<__nv_bfloat16*>(outTbl);
-#define ARGS tmA, tmM, tmMl, nlong, nk, S, part, ldp, tickets, outT, outTl, tb, tbl, ldo, outR, outRl, dst
+#define ARGS tmA, tmM, tmMl, nlong, nk, S, part, ldp, tickets, outT, outTl, tb, tbl, ldo, outR, outRl, dst, scales, \
+             ntr8, ntc8
   if (prec == 0) {
     if (col) k_wd_pass<true, 0><<<ntiles * S, kWThr, smem, st>>>(ARGS);
     else k_wd_pass<false, 0><<<ntiles * S, kWThr, smem, st>>>(ARGS);
-  } else {
+  } else if (prec == 1) {
     if (col) k_wd_pass<true, 1><<<ntiles * S, kWThr, smem, st>>>(ARGS);
     else k_wd_pass<false, 1><<<ntiles * S, kWThr, smem, st>>>(ARGS);
+  } else {
+    if (col) k_wd_pass<true, 2><<<ntiles * S, kWThr, smem, st>>>(ARGS);
+    else k_wd_pass<false, 2><<<ntiles * S, kWThr, smem, st>>>(ARGS);
   }
 #undef ARGS
   return cudaGetLastError();
@@ -1230,6 +1368,14 @@ cudaError_t launch_wd_apply(const float* in, int64_t ldi, int64_t len, const flo
   const int grid = static_cast<int>((len + kACols - 1) / kACols);
   if (grid == 0) return cudaSuccess;
   k_wd_apply<<<grid, kAThr, sizeof(float) * kWL * (kWL + kACols), st>>>(in, ldi, len, T, outT, outTl, ldo, outR, outRl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wd_quant8(const float* A, int64_t lda, int64_t m, int64_t n, void* A8, int64_t ld8, float* scales,
+                             cudaStream_t st) {
+  const int ntr = static_cast<int>((m + kQT - 1) / kQT), ntc = static_cast<int>((n + kQT - 1) / kQT);
+  if (ntr == 0 || ntc == 0) return cudaSuccess;
+  k_wd_quant8<<<ntr * ntc, kQThr, 0, st>>>(A, lda, m, n, static_cast<uint8_t*>(A8), ld8, scales, ntc);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "FRSVT_OK", 1: "FRSVT_ERR_INVALID_ARG", 2: "FRSVT_ERR_UNSUPPO
 DEV_RANK_DEFICIENT, DEV_NOT_CONVERGED, DEV_NONFINITE, DEV_TIMEOUT, DEV_BAD_PROBLEM = 1, 2, 4, 8, 16
 WSVT_EXACT, WSVT_FRSVT = 0, 1
 CFG_ADJOINT = 1
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 NPHASE = 10
 
 

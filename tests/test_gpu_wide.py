@@ -16,6 +16,7 @@ from paper_1509_00296_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
+FP8_TOL = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -135,7 +136,7 @@ def recovery_ref():
     return O, nrm, ref
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 def test_wide_recovery_8192_full_size(fr, recovery_ref, prec):
     """Large low-rank recovery, 8192 x 8192 rank 100 + 10 % corruption, FRSVT l = 120, q = 2:
     three iALM iterations at full size against the oracle, FP32-accurate passes and the BF16
@@ -146,7 +147,7 @@ def test_wide_recovery_8192_full_size(fr, recovery_ref, prec):
     Og = torch.from_numpy(np.ascontiguousarray(O, dtype=np.float32)).cuda()
     S, A, L = torch.empty_like(Og), torch.empty_like(Og), torch.empty_like(Og)
     h = fr.Handle(m, n, 120, q=2, range_prop=False, seed=2004,
-                  precision=fr.PREC_BF16 if prec == "bf16" else fr.PREC_FP32)
+                  precision={"fp32": fr.PREC_FP32, "bf16": fr.PREC_BF16, "fp8": fr.PREC_FP8}[prec])
     h.rpca_init(Og, S, A, 1.0 / np.sqrt(max(m, n)), 1.5, 1e7, normO2=nrm)
     hist = [h.ialm_step(Og, S, A, 120, L=L if k == 2 else None, sync_residual=True) for k in range(3)]
     info = h.info()
@@ -155,9 +156,10 @@ def test_wide_recovery_8192_full_size(fr, recovery_ref, prec):
     eS = rel_fro(S.cpu().numpy(), ref.S)
     print(f"recovery 8192 {prec}: rel err L {eL:.3e} S {eS:.3e}")
     assert info.device_status & ~1 == 0, info
-    assert eL <= TOL
-    assert eS <= TOL
-    assert np.allclose(hist, ref.history, rtol=1e-3)
+    tol = FP8_TOL if prec == "fp8" else TOL
+    assert eL <= tol
+    assert eS <= tol
+    assert np.allclose(hist, ref.history, rtol=1e-3 if prec != "fp8" else 1e-2)
 
 
 @pytest.mark.parametrize("m,n,l,q", [(2048, 1024, 64, 2), (1500, 700, 120, 2), (1200, 600, 40, 3)])
@@ -173,3 +175,26 @@ def test_wide_bf16_svt_matches_oracle(fr, m, n, l, q):
     ref = osvt.frsvt(A.astype(np.float64), tau, l, q, 5, 0).X
     assert rel_fro(X, ref) <= TOL
     h.close()
+
+
+@pytest.mark.parametrize("m,n,l,q", [(2048, 1024, 64, 2), (1500, 700, 120, 2), (1200, 600, 40, 3)])
+def test_wide_fp8_svt_against_oracle(fr, m, n, l, q):
+    """E4M3 shadow with per-128 x 128-tile power-of-two scales for the sketch and the early power
+    steps: X against the oracle (error reported; FP32-accurate last power step and projection)."""
+    A, _ = spectrum_matrix(m, n, rank=l + 8, decay=0.93, noise=0.01, seed=m + 3 * n)
+    d = osvt.frsvt(A.astype(np.float64), 0.0, l, q, 5, 0).sigma
+    tau = float(0.5 * (d[l // 3] + d[l // 3 + 1]))
+    h = fr.Handle(m, n, l, q=q, range_prop=False, seed=5, precision=fr.PREC_FP8)
+    X = h.svt(to_gpu(A), tau, l, X=to_gpu(np.zeros_like(A))).cpu().numpy()
+    info = h.info()
+    assert info.device_status & (fr.DEV_TIMEOUT | fr.DEV_NONFINITE | fr.DEV_BAD_PROBLEM) == 0
+    ref = osvt.frsvt(A.astype(np.float64), tau, l, q, 5, 0).X
+    err = rel_fro(X, ref)
+    print(f"fp8 svt {m}x{n} l={l} q={q}: rel err {err:.3e}")
+    assert err <= FP8_TOL
+    h.close()
+
+
+def test_fp8_needs_wide_basis(fr):
+    with pytest.raises(fr.FrsvtError):
+        fr.Handle(100, 40, 16, q=1, precision=fr.PREC_FP8)
