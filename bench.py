@@ -176,9 +176,13 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--oracle-iters", type=int, default=12)
     ap.add_argument("--skip-extras", action="store_true", help="only the main timed region")
+    ap.add_argument("--profile-svt", choices=["fp32", "bf16", "fp8"], default=None,
+                    help="only three FRSVT calls on the 8192 x 8192 recovery matrix (l = 120, q = 2), for ncu")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_svt:
+        return profile_svt(args.profile_svt)
 
     import numpy as np
     import torch
@@ -293,6 +297,29 @@ def main():
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def profile_svt(prec: str):
+    """Three frsvt_svt calls (18 launches each in FP32 / BF16 mode, 19 in FP8 mode) on the
+    large low-rank recovery matrix: a fixed, short launch sequence for ncu captures."""
+    import numpy as np
+    import torch
+    from paper_1509_00296_gb300 import build, frsvt, synth
+    build.build()
+    torch.cuda.set_device(0)
+    n = 8192
+    O_np, _, _ = synth.recovery_8192(seed=1003)
+    A = torch.from_numpy(np.ascontiguousarray(O_np, dtype=np.float32)).cuda()
+    X = torch.empty_like(A)
+    h = frsvt.Handle(n, n, 120, q=2, range_prop=False, seed=5,
+                     precision={"fp32": frsvt.PREC_FP32, "bf16": frsvt.PREC_BF16, "fp8": frsvt.PREC_FP8}[prec])
+    for _ in range(3):
+        h.svt(A, 300.0, 120, X=X)
+    torch.cuda.synchronize()
+    info = h.info()
+    print(json.dumps({"profile_svt": prec, "r": info.r, "s": info.s, "sweeps": info.sweeps,
+                      "device_status": info.device_status}))
     return 0
 
 
@@ -433,50 +460,56 @@ def bench_video_bf16(args, O, O_np, lam, dev, flush):
 
 def bench_recovery(args, dev, flush):
     """Large low-rank recovery: 8192 x 8192 rank 100 + 10 % corruption, iALM with FRSVT l = 120,
-    q = 2 (the wide-basis path): iterations per second from a captured graph, per-phase device
-    times, and one exact SVT (torch.linalg.svd, cuSOLVER) of the same iterate on the same GPU."""
+    q = 2 (the wide-basis path) in FP32-accurate, BF16-shadow and FP8-shadow (E4M3, per-128 x 128-tile
+    scales) modes: iterations per second from a captured graph, per-phase device times, and one exact
+    SVT (torch.linalg.svd, cuSOLVER) of the same iterate on the same GPU."""
     import numpy as np
     import torch
     from paper_1509_00296_gb300 import frsvt, synth
     n, l = 8192, 120
     O_np, _, _ = synth.recovery_8192(seed=1003)
     O = torch.from_numpy(np.ascontiguousarray(O_np, dtype=np.float32)).to(dev)
+    del O_np
     S = torch.empty_like(O)
     A = torch.empty_like(O)
-    h = frsvt.Handle(n, n, l, q=2, range_prop=False, seed=2004, stream=torch.cuda.current_stream())
-    h.rpca_init(O, S, A, 1.0 / np.sqrt(n), 1.5, 1e7)
-    for _ in range(3):
-        h.ialm_step(O, S, A, l)
-    K = 5
-    h.enable_timing(True)
-    h.timings()
-    for k in range(K):
-        flush.fill_(float(k))
-        h.ialm_step(O, S, A, l)
-    tm = h.timings()
-    h.enable_timing(False)
-    ms = graph_rate(h, O, S, A, l, 10, flush)
-    info = h.info()
+    out = {"workload": "8192 x 8192 rank 100 (factors / 10) + 10 % corruption in [-10, 10], FRSVT l=120 q=2",
+           "unit": UNIT, "hbm_floor_ms_fp32": 11 * 4.0 * n * n / (peaks()[0] * 1e9) * 1e3}
+    for name, prec in (("fp32", frsvt.PREC_FP32), ("bf16", frsvt.PREC_BF16), ("fp8", frsvt.PREC_FP8)):
+        h = frsvt.Handle(n, n, l, q=2, range_prop=False, seed=2004, stream=torch.cuda.current_stream(),
+                         precision=prec)
+        h.rpca_init(O, S, A, 1.0 / np.sqrt(n), 1.5, 1e7)
+        for _ in range(3):
+            h.ialm_step(O, S, A, l)
+        K = 5
+        h.enable_timing(True)
+        h.timings()
+        for k in range(K):
+            flush.fill_(float(k))
+            h.ialm_step(O, S, A, l)
+        tm = h.timings()
+        h.enable_timing(False)
+        ms = graph_rate(h, O, S, A, l, 10, flush)
+        info = h.info()
+        out[name] = {"ms_per_step": ms, "value": 1e3 / ms,
+                     "phases_ms_per_step": {k: v[0] / K for k, v in tm.items() if v[1] > 0},
+                     "launches_per_step": sum(v[1] for v in tm.values()) / K, "jacobi_sweeps": info.sweeps,
+                     "rank": info.r, "device_status": info.device_status}
+        h.close()
     # one exact SVT of the current iterate on the same GPU (after a warm-up call on a small matrix)
     torch.linalg.svd(A[:1024, :1024], full_matrices=False)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     U, sv, Vh = torch.linalg.svd(A, full_matrices=False)
-    X = (U * torch.clamp(sv - 1.0 / info.mu, min=0.0)) @ Vh
+    X = (U * torch.clamp(sv - 1e-3, min=0.0)) @ Vh
     e1.record()
     torch.cuda.synchronize()
     ex_ms = e0.elapsed_time(e1)
     del U, sv, Vh, X
-    h.close()
-    e = 4.0 * n * n
-    return {"workload": "8192 x 8192 rank 100 (factors / 10) + 10 % corruption in [-10, 10], FRSVT l=120 q=2",
-            "ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT,
-            "phases_ms_per_step": {k: v[0] / K for k, v in tm.items() if v[1] > 0},
-            "launches_per_step": sum(v[1] for v in tm.values()) / K,
-            "hbm_floor_ms": (6 * e + 5 * e) / (peaks()[0] * 1e9) * 1e3,
-            "exact_svt_same_gpu_ms": ex_ms, "frsvt_iter_vs_exact_svt": ex_ms / ms,
-            "jacobi_sweeps": info.sweeps, "rank": info.r}
+    out["exact_svt_same_gpu_ms"] = ex_ms
+    out["frsvt_iter_vs_exact_svt"] = ex_ms / out["fp32"]["ms_per_step"]
+    out["value"] = out["fp32"]["value"]
+    return out
 
 
 def bench_wsvt(dev):

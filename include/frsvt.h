@@ -58,8 +58,11 @@ typedef enum frsvt_status {
  * a BF16 shadow of A (written by rpca_init and by every rpca_ialm_step epilogue, converted by
  * frsvt_svt); the sketch and the first q - 1 power steps read the shadow (BF16 operands, FP32
  * accumulation), the last power step and the projection stay FP32-accurate (the "residual"
- * step that wins the accuracy back).  Served for n <= 256; frsvt_create returns
- * FRSVT_ERR_UNSUPPORTED for a precision it does not build. */
+ * step that wins the accuracy back).  With cfg.l_max <= 32 BF16 is served for n <= 256.
+ * FRSVT_PREC_FP8 (cfg.l_max > 32 only): an E4M3 shadow with one power-of-two scale per 128 x 128
+ * tile of A (the smallest with max|A_tile| / scale <= 448), quantized at the start of every SVT,
+ * for the same passes.  frsvt_create returns FRSVT_ERR_UNSUPPORTED for a precision it does not
+ * build. */
 typedef enum frsvt_precision {
   FRSVT_PREC_FP32 = 0,           /* float32 data, FP32-accurate passes */
   FRSVT_PREC_BF16 = 1,           /* BF16 shadow for the sketch and the early power steps */
@@ -72,7 +75,7 @@ typedef enum frsvt_precision {
 typedef struct frsvt_config {
   int64_t m_max;                 /* largest row count served by the handle */
   int64_t n_max;                 /* largest column count served by the handle */
-  int32_t l_max;                 /* largest oversampled rank l = k + p, 1..32 */
+  int32_t l_max;                 /* largest oversampled rank l = k + p, 1..128 (see frsvt_create) */
   int32_t q;                     /* power iterations eta (Alg. 1 steps 13-15), >= 0 */
   int32_t range_prop;            /* 1: range propagation between calls (Sec. 2.1) */
   int32_t precision;             /* frsvt_precision */
@@ -99,6 +102,12 @@ typedef struct frsvt_handle frsvt_handle;
 /*
  * Create a handle.  cfg sizes the workspace; stream is a cudaStream_t (NULL:
  * the legacy default stream).  Allocates all device scratch memory.
+ * cfg.l_max <= 32 builds the narrow-basis handle (16- or 32-column panels);
+ * 32 < cfg.l_max <= 128 the wide-basis handle (128-column panels, any short
+ * side, grid-wide Cholesky QR and core), which serves frsvt_svt,
+ * frsvt_spectral_norm, rpca_init and rpca_ialm_step; for it range_prop,
+ * FRSVT_CFG_ADJOINT and m_max >= 2^31 return FRSVT_ERR_UNSUPPORTED, and the
+ * batched WSVT and debug entry points return FRSVT_ERR_UNSUPPORTED.
  * Returns FRSVT_ERR_INVALID_ARG for out-of-range sizes, FRSVT_ERR_ALLOC if
  * the device allocation fails.
  */

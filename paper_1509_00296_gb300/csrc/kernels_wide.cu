@@ -1209,10 +1209,16 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
 #pragma unroll
             for (int u = 0; u < 4; ++u) L4[u] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
           }
-          if (Ab != nullptr) {                                          // BF16 shadow of A'
-            __nv_bfloat162* ab = reinterpret_cast<__nv_bfloat162*>(Ab + row * ldb + col0);
+          if (Ab != nullptr) {                                          // BF16 shadow of A' (two 16-byte stores)
+            uint32_t pk[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) ab[u] = __floats2bfloat162_rn(an[2 * u], an[2 * u + 1]);
+            for (int u = 0; u < 8; ++u) {
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(an[2 * u], an[2 * u + 1]);
+              pk[u] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
+            uint4* ab = reinterpret_cast<uint4*>(Ab + row * ldb + col0);
+            __stcs(ab, make_uint4(pk[0], pk[1], pk[2], pk[3]));
+            __stcs(ab + 1, make_uint4(pk[4], pk[5], pk[6], pk[7]));
           }
         } else {
           for (int u = 0; u < 16; ++u)
