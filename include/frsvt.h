@@ -179,6 +179,24 @@ frsvt_status frsvt_get_info(frsvt_handle* h, frsvt_info* info);
 frsvt_status frsvt_get_sigma(frsvt_handle* h, float* sigma_host, int32_t capacity, int32_t* count);
 
 /*
+ * Adaptive rank prediction (Sec. 2.3, Eq. 7).  From the next frsvt_svt / rpca_init on, the
+ * sampling rate of each SVT is chosen on the device from the previous one: with r the number of
+ * singular values above the threshold and l the last sampling rate,
+ *     l' = min(r + p, b),  p = a if r < l, else ceil(rho n),  b = ceil(gamma n),
+ * n the short side of the problem; the first SVT uses l_0 = ceil(0.1 b), and the propagated basis
+ * keeps min(r, l' - a) columns (so that at least a new Gaussian columns are drawn).  The `l`
+ * argument of later frsvt_svt / rpca_ialm_step calls is then ignored.  Requires range
+ * propagation, FP32 precision, cfg.l_max <= 32 and the tensor-core path (short side <= 256):
+ * b is clamped to the handle's panel width (16 or 32).  a >= 1, 0 < rho <= 1, 0 < gamma <= 1;
+ * a = 0 switches the prediction off.  Returns FRSVT_ERR_UNSUPPORTED for other handles.
+ * Synchronizes the handle's stream.
+ */
+frsvt_status frsvt_set_rank_prediction(frsvt_handle* h, int32_t a, double rho, double gamma);
+
+/* The sampling rate the next SVT will use under adaptive rank prediction (synchronizes). */
+frsvt_status frsvt_get_rank_prediction(frsvt_handle* h, int32_t* l_next);
+
+/*
  * Tracing.  Phases of the path, in launch order within one SVT / iALM step.
  * When timing is enabled every kernel launch is bracketed by CUDA events on
  * the handle's stream (recording events does not synchronize; it adds a few

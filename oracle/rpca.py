@@ -43,6 +43,7 @@ class RPCAResult:
     iters: int
     history: list = field(default_factory=list)     # ||Z||_F / ||O||_F per iteration
     ranks: list = field(default_factory=list)       # #{sigma > 1/mu} per iteration
+    ls: list = field(default_factory=list)          # sampling rates l_i (adaptive rank prediction)
 
 
 def spectral_norm(O: np.ndarray) -> float:
@@ -61,11 +62,26 @@ def ialm_init(O: np.ndarray, lam: float, normO2: float | None = None):
     return Y0, mu0
 
 
+def predict_rank(r: int, l: int, n: int, a: int, rho_ap: float, b: int) -> int:
+    """Adaptive rank prediction, Eq. 7 (Sec. 2.3): the next sampling rate from the current rank
+    estimate r = #{sigma_i > tau} and sampling rate l, for the short side n.  Over-sample by a
+    when r < l, by ceil(rho_ap n) otherwise (the rank may still be growing); at most b."""
+    p = a if r < l else int(np.ceil(rho_ap * n))
+    return int(min(r + p, b))
+
+
 def ialm_rpca(O: np.ndarray, lam: float | None = None, mu0: float | None = None,
               rho: float = 1.5, mu_bar: float | None = None, tol: float = 1e-7,
               max_iter: int = 500, method: str = "exact", l: int = 0, q: int = 0,
               seed: int = 0, range_prop: bool = True, fixed_iters: int | None = None,
-              normO2: float | None = None, rank_tol: float = 1e-12) -> RPCAResult:
+              normO2: float | None = None, rank_tol: float = 1e-12,
+              ap: dict | None = None) -> RPCAResult:
+    """Inexact ALM RPCA.  With ``ap`` (keys a, rho, gamma; FRSVT with range propagation) the
+    sampling rate follows the adaptive rank prediction of Eq. 7: l_0 = ceil(0.1 b), b =
+    ceil(gamma n) for the short side n, l_{i+1} = predict_rank(r_i, l_i, ...); the propagated
+    basis keeps min(r_i, l_{i+1} - a) columns (r_i in the paper, capped so that at least a new
+    Gaussian columns are drawn) and the call draws l_{i+1} - keep new ones.  The sampling rates
+    used are recorded in ``res.ls``."""
     O = np.asarray(O, dtype=np.float64)
     m, n = O.shape
     if lam is None:
@@ -80,15 +96,27 @@ def ialm_rpca(O: np.ndarray, lam: float | None = None, mu0: float | None = None,
     Qt = None
     res = RPCAResult(L, S, Y, mu, 0)
     n_iter = fixed_iters if fixed_iters is not None else max_iter
+    ns = min(m, n)
+    if ap is not None:
+        b = int(np.ceil(ap["gamma"] * ns))
+        l_cur = max(1, int(np.ceil(0.1 * b)))
+        res.ls = []
     for k in range(n_iter):
         Ain = O - S + Y / mu
         if method == "exact":
             L, r = svt_mod.exact_svt(Ain, 1.0 / mu)
         elif method == "frsvt":
-            out = svt_mod.frsvt(Ain, 1.0 / mu, l, q, seed, k,
+            l_k = l if ap is None else l_cur
+            out = svt_mod.frsvt(Ain, 1.0 / mu, l_k, q, seed, k,
                                 Q_prev=Qt if range_prop else None, rank_tol=rank_tol)
             L, r = out.X, out.r
-            Qt = out.Q_tilde
+            if ap is None:
+                Qt = out.Q_tilde
+            else:
+                res.ls.append(l_k)
+                l_cur = predict_rank(r, l_k, ns, ap["a"], ap["rho"], b)
+                keep = max(0, min(r, l_cur - ap["a"]))
+                Qt = np.ascontiguousarray(out.extra["QV"][:, :keep])
         else:
             raise ValueError(method)
         S = svt_mod.soft(O - L + Y / mu, lam / mu)

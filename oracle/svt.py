@@ -169,7 +169,7 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
     keep = min(r, l - 2)
     Q_tilde = np.ascontiguousarray(QV[:, :max(keep, 0)])          # step 21
     X = Xh.T if transposed else Xh
-    return FRSVTResult(np.ascontiguousarray(X), Q_tilde, r, D, s, pit)
+    return FRSVTResult(np.ascontiguousarray(X), Q_tilde, r, D, s, pit, extra={"QV": QV})
 
 
 def wsvt_batch(mats, c: float, eps: float, variant: str = "exact", l: int = 12, q: int = 1,

@@ -208,6 +208,10 @@ struct frsvt_handle {
   unsigned* wtick = nullptr;       // pass tiles, then the Gram ticket, then the epilogue ticket
   int64_t w_ntiles = 0;
   int w_gram_grid = 8;
+  // adaptive rank prediction (Eq. 7): parameters; the state lives in DevState
+  int ap_a = 0;
+  double ap_rho = 0.0, ap_gamma = 0.0;
+  int64_t ap_n = -1;               // short side the device state was set up for
   std::string err;
   // tracing: CUDA events around every launch when enabled
   int timing = 0;
@@ -829,6 +833,8 @@ const char* frsvt_status_string(frsvt_status s) {
 
 const char* frsvt_last_error(const frsvt_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
+frsvt_status ap_setup(frsvt_handle* h, int64_t n);
+
 frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* stream) {
   frsvt_handle* h = nullptr;
   if (out == nullptr || cfg == nullptr) return FRSVT_ERR_INVALID_ARG;
@@ -1023,6 +1029,18 @@ frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, in
   if (m == 0 || n == 0) return FRSVT_OK;
   if (static_cast<const void*>(A) == static_cast<const void*>(X)) return fail(h, FRSVT_ERR_INVALID_ARG, "X aliases A");
   if (l > n) l = static_cast<int32_t>(n);
+  if (h->ap_a > 0) {                                   // adaptive rank prediction: l on the device
+    if (!(h->tma && n <= 256)) return fail(h, FRSVT_ERR_UNSUPPORTED, "rank prediction needs n <= 256");
+    if (h->ap_n != n && (s = ap_setup(h, n)) != FRSVT_OK) return s;
+    h->last_m = m;
+    h->last_n = n;
+    h->last_l = -1;
+    if ((s = range_and_core(h, A, m, n, lda, -1, h->cfg.q, 1, kCounterFromState, tau, 0, 1, 1)) != FRSVT_OK)
+      return s;
+    const Splits sp = row_splits(h, m, n);
+    FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_recon(h->LP, h->Zl, h->Rf, m, n, X, ldx, sp.nsplit, sp.rps, h->stream));
+    return FRSVT_OK;
+  }
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
   if (h->wide) {
     if (h->Ab != nullptr) FRSVT_CK(launch_to_bf16(A, lda, m, n, h->Ab, h->ldb, h->stream));
@@ -1089,6 +1107,10 @@ frsvt_status rpca_init(frsvt_handle* h, const float* O, float* S, float* A, int6
   h->last_m = m;
   h->last_n = n;
   h->last_l = -1;
+  if (h->ap_a > 0) {
+    frsvt_status sa = ap_setup(h, n);                   // l_0, empty propagated basis
+    if (sa != FRSVT_OK) return sa;
+  }
   FRSVT_CK(cudaStreamSynchronize(h->stream));
   return FRSVT_OK;
 }
@@ -1105,7 +1127,15 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
   if (l < 1 || l > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "l must be in [1, l_max]");
   if (m == 0 || n == 0) return FRSVT_OK;
   if (l > n) l = static_cast<int32_t>(n);
-  if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
+  if (h->ap_a > 0) {                                   // adaptive rank prediction: l on the device
+    if (!(h->tma && n <= 256)) return fail(h, FRSVT_ERR_UNSUPPORTED, "rank prediction needs n <= 256");
+    if (h->ap_n != n && (s = ap_setup(h, n)) != FRSVT_OK) return s;
+    h->last_m = m;
+    h->last_n = n;
+    l = -1;
+  } else if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) {
+    return s;
+  }
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;   // the shadow is kept current by rpca_init / the epilogue
   if (h->wide) {
@@ -1330,6 +1360,53 @@ frsvt_status frsvt_backward(frsvt_handle* h, const void* saved, const float* A, 
   FRSVT_CK(ad_omega(LP, w.L, K, bl * LP, m, l, h->cfg.seed, omega_stream, st));                // Omega
   FRSVT_CK(copy_cols(w.R, K, bl * LP, w.Yb, n));                                                // dA += Omega Ybar_0^T
   FRSVT_CK(ad_rank(dA, ldda, m, nn, w.L, K, w.R, K, K, 0.f, st));
+  return FRSVT_OK;
+}
+
+// Device state of the adaptive rank prediction for a problem with short side n: the parameters
+// of Eq. 7, l_0 = ceil(0.1 b) and an empty propagated basis.  Enqueued on the stream.
+frsvt_status ap_setup(frsvt_handle* h, int64_t n) {
+  int32_t v[4] = {0, 0, 0, 0};                          // l_cur, a, ceil(rho n), b
+  if (h->ap_a > 0) {
+    int64_t b = static_cast<int64_t>(std::ceil(h->ap_gamma * static_cast<double>(n)));
+    if (b > h->LP) b = h->LP;
+    if (b > n) b = n;
+    if (b < 1) b = 1;
+    int64_t l0 = static_cast<int64_t>(std::ceil(0.1 * static_cast<double>(b)));
+    v[0] = static_cast<int32_t>(l0 < 1 ? 1 : l0);
+    v[1] = h->ap_a;
+    v[2] = static_cast<int32_t>(std::ceil(h->ap_rho * static_cast<double>(n)));
+    v[3] = static_cast<int32_t>(b);
+  }
+  FRSVT_CK(cudaMemcpyAsync(&h->dst->l_cur, v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+  FRSVT_CK(cudaMemsetAsync(&h->dst->keep, 0, sizeof(int32_t), h->stream));
+  FRSVT_CK(cudaStreamSynchronize(h->stream));          // v lives on this stack frame
+  h->ap_n = n;
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_set_rank_prediction(frsvt_handle* h, int32_t a, double rho, double gamma) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (a < 0 || (a > 0 && (!(rho > 0.0) || rho > 1.0 || !(gamma > 0.0) || gamma > 1.0)))
+    return fail(h, FRSVT_ERR_INVALID_ARG, "need a >= 0, 0 < rho <= 1, 0 < gamma <= 1");
+  if (a > 0 && (h->wide || !h->cfg.range_prop || h->cfg.precision != FRSVT_PREC_FP32 || !h->tma ||
+                h->tc_sc_ns == 0))
+    return fail(h, FRSVT_ERR_UNSUPPORTED,
+                "adaptive rank prediction needs range propagation, FP32 and the tensor-core path (l_max <= 32)");
+  h->ap_a = a;
+  h->ap_rho = rho;
+  h->ap_gamma = gamma;
+  h->ap_n = -1;
+  if (a == 0) return ap_setup(h, 0);
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_get_rank_prediction(frsvt_handle* h, int32_t* l_next) {
+  if (h == nullptr || l_next == nullptr) return FRSVT_ERR_INVALID_ARG;
+  int32_t v = 0;
+  FRSVT_CK(cudaMemcpyAsync(&v, &h->dst->l_cur, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  FRSVT_CK(cudaStreamSynchronize(h->stream));
+  *l_next = v;
   return FRSVT_OK;
 }
 

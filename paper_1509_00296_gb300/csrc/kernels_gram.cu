@@ -26,6 +26,7 @@ k_gram_core(const float* __restrict__ Z, int64_t m, int n, int64_t rpc, const fl
             double* __restrict__ cpart, double* __restrict__ Gout, unsigned* __restrict__ tickets, int l,
             float tau_host, int tau_from_mu, int update_rp, int advance_counter, float* __restrict__ Rf,
             float* __restrict__ Qt, DevState* __restrict__ dst, double rank_tol, int max_sweeps) {
+  if (l <= 0) l = min(max(dst->l_cur, 1), LP);            // adaptive rank prediction: l lives on the device
   constexpr int NP = LP * (LP + 1) / 2;
   constexpr int PPT = (NP + kGThr - 1) / kGThr;                   // pairs per thread
   constexpr int RG = (kGThr / NP) > 0 ? (kGThr / NP) : 1;         // row classes

@@ -266,6 +266,7 @@ k_tc_sc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   if (!TAIL) return;
   if (cooperative_groups::this_cluster().block_rank() != 0) return;
   SmallWs<LP> w = carve_small_ws<LP>(dsm, kGaccT);
+  if (l <= 0) l = min(max(dst->l_cur, 1), LP);            // adaptive rank prediction: l lives on the device
   int keep = use_rp ? dst->keep : 0;
   keep = max(0, min(keep, l));
   for (int e = threadIdx.x; e < n * LP; e += kThr) {

@@ -379,7 +379,11 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
   }
   int r = 0;
   for (int c = 0; c < LP; ++c) r += (sig[c] > tau) ? 1 : 0;
-  const int keep = update_rp ? max(0, min(r, l - 2)) : 0;
+  // propagated columns: min(r, l - 2) for a fixed l; under the adaptive rank prediction of Eq. 7
+  // the next sampling rate l' = min(r + (r < l ? a : ceil(rho n)), b) and min(r, l' - a) columns
+  const int ap_a = dst->ap_a;
+  const int l_next = ap_a > 0 ? min(r + (r < l ? ap_a : dst->ap_pn), dst->ap_b) : l;
+  const int keep = update_rp ? max(0, min(r, l_next - (ap_a > 0 ? ap_a : 2))) : 0;
   __syncthreads();
   for (int64_t e = tid; e < ns * LP; e += nt) {
     const int64_t i = e / LP;
@@ -398,6 +402,7 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
     dst->r = r;
     dst->sweeps = sweeps;
     if (update_rp) dst->keep = keep;
+    if (update_rp && ap_a > 0) dst->l_cur = max(1, l_next);
     if (advance_counter) dst->counter += 1;
     if (sweeps >= max_sweeps) dst->status |= kDevNotConverged;
     bool finite = true;

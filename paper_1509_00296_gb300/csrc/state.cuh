@@ -27,6 +27,10 @@ struct DevState {
   int32_t iter;         // iALM iterations since rpca_init
   uint32_t status;      // sticky FRSVT_DEV_* bits
   int32_t sweeps;       // Jacobi sweeps of the last core SVD
+  int32_t l_cur;        // sampling rate of the next SVT under adaptive rank prediction (Eq. 7)
+  int32_t ap_a;         // Eq. 7: over-sampling a when r < l (0: prediction off)
+  int32_t ap_pn;        // Eq. 7: ceil(rho n), the over-sampling when r >= l
+  int32_t ap_b;         // Eq. 7: the bound b = ceil(gamma n) (<= the panel width)
   float sigma[kMaxL];   // singular values of B of the last SVT, descending
 };
 

@@ -59,6 +59,8 @@ _SIGS = {
     "rpca_ialm_step": [_P, _P, _P, _P, _I64, _I64, _I64, ctypes.c_int32, _P, _I64, ctypes.POINTER(ctypes.c_double)],
     "frsvt_get_info": [_P, ctypes.POINTER(Info)],
     "frsvt_get_sigma": [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+    "frsvt_set_rank_prediction": [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_double],
+    "frsvt_get_rank_prediction": [_P, ctypes.POINTER(ctypes.c_int32)],
     "frsvt_status_string": [ctypes.c_int],
     "frsvt_last_error": [_P],
     "frsvt_enable_timing": [_P, ctypes.c_int32],
@@ -199,6 +201,16 @@ class Handle:
                                        _ptr(L), L.stride(0) if L is not None else 0,
                                        ctypes.byref(res) if sync_residual else None))
         return res.value if sync_residual else None
+
+    def set_rank_prediction(self, a: int = 2, rho: float = 0.05, gamma: float = 0.1):
+        """Adaptive rank prediction of Eq. 7 (a = 0 switches it off)."""
+        self._chk(lib().frsvt_set_rank_prediction(self._h, int(a), float(rho), float(gamma)))
+
+    def rank_prediction(self) -> int:
+        """Sampling rate the next SVT will use under adaptive rank prediction."""
+        v = ctypes.c_int32()
+        self._chk(lib().frsvt_get_rank_prediction(self._h, ctypes.byref(v)))
+        return v.value
 
     def info(self) -> SVTInfo:
         inf = Info()

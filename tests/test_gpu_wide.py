@@ -198,3 +198,30 @@ def test_wide_fp8_svt_against_oracle(fr, m, n, l, q):
 def test_fp8_needs_wide_basis(fr):
     with pytest.raises(fr.FrsvtError):
         fr.Handle(100, 40, 16, q=1, precision=fr.PREC_FP8)
+
+
+def test_wide_edges(fr):
+    """Edge cases of the wide basis: empty input, the largest basis (l = 128), l clamped to a
+    short side below l, and the m < n rejection."""
+    import torch
+    h = fr.Handle(1024, 512, 128, q=1, range_prop=False, seed=9)
+    empty = torch.zeros((8, 0), dtype=torch.float32, device="cuda")
+    h.svt(empty, 1.0, 64, X=torch.zeros_like(empty))                 # nothing to do, no error
+    A, s = spectrum_matrix(1024, 512, 160, 0.985, 0.01, seed=13)
+    A = A.astype(np.float32).astype(np.float64)
+    tau = float(0.5 * (s[60] + s[61]))
+    X = h.svt(to_gpu(A), tau, 128).cpu().numpy()
+    ref = osvt.frsvt(A, tau, 128, 1, seed=9, stream=0)
+    assert rel_fro(X, ref.X) <= TOL
+    with pytest.raises(fr.FrsvtError):
+        h.svt(to_gpu(A[:100, :200]), tau, 64)                        # m < n: transpose first
+    h.close()
+    # l (100) above the short side (60): clamped to 60 on both sides
+    B, sb = spectrum_matrix(600, 60, 40, 0.9, 0.01, seed=17)
+    B = B.astype(np.float32).astype(np.float64)
+    tau = float(0.5 * (sb[10] + sb[11]))
+    h = fr.Handle(600, 60, 100, q=2, range_prop=False, seed=2)
+    X = h.svt(to_gpu(B), tau, 100).cpu().numpy()
+    ref = osvt.frsvt(B, tau, 100, 2, seed=2, stream=0)
+    assert rel_fro(X, ref.X) <= TOL
+    h.close()
