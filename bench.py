@@ -293,6 +293,7 @@ def main():
             line["wsvt_batch"] = extras.get("wsvt")
             line["unrolled_rpca"] = extras.get("unrolled")
             line["video_bf16"] = extras.get("video_bf16")
+            line["video_rank_prediction"] = extras.get("video_rank_prediction")
             line["recovery_8192"] = extras.get("recovery")
         print(json.dumps(line))
     if ws > 1:
@@ -413,6 +414,7 @@ def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
     out["wsvt"] = bench_wsvt(dev)
     out["unrolled"] = bench_unrolled(dev)
     out["video_bf16"] = bench_video_bf16(args, O, O_np, lam, dev, flush)
+    out["video_rank_prediction"] = bench_video_ap(args, O, lam, flush)
     out["recovery"] = bench_recovery(args, dev, flush)
     return out
 
@@ -456,6 +458,29 @@ def bench_video_bf16(args, O, O_np, lam, dev, flush):
     h.close()
     return {"precision": "bf16 sketch + first q-1 power steps, FP32-accurate last power step and projection",
             "ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT}
+
+
+def bench_video_ap(args, O, lam, flush):
+    """The video workload with the adaptive rank prediction of Eq. 7 (a = 2, rho = 0.05,
+    gamma = 0.08: b = 16): the sampling rate is chosen on the device each iteration, so the
+    captured iteration replays without host involvement."""
+    import torch
+    from paper_1509_00296_gb300 import frsvt
+    S = torch.empty_like(O)
+    A = torch.empty_like(O)
+    h = frsvt.Handle(M, N, 16, q=Q_POW, range_prop=True, seed=OMEGA_SEED, stream=torch.cuda.current_stream())
+    h.set_rank_prediction(2, 0.05, 0.08)
+    h.rpca_init(O, S, A, lam, 1.5, 1e7)
+    ls = [h.rank_prediction()]
+    for _ in range(8):
+        h.ialm_step(O, S, A, L_COLS)
+        ls.append(h.rank_prediction())
+    ms = graph_rate(h, O, S, A, L_COLS, max(10, min(args.steps, 50)), flush)
+    info = h.info()
+    h.close()
+    return {"rule": "l' = min(r + (r < l ? 2 : ceil(0.05 n)), b), b = ceil(0.08 n) = 16, l_0 = 2",
+            "sampling_rates_first_iterations": ls, "rank": info.r, "ms_per_step": ms, "value": 1e3 / ms,
+            "unit": UNIT}
 
 
 def bench_recovery(args, dev, flush):
