@@ -294,6 +294,7 @@ def main():
             line["unrolled_rpca"] = extras.get("unrolled")
             line["video_bf16"] = extras.get("video_bf16")
             line["video_rank_prediction"] = extras.get("video_rank_prediction")
+            line["weather_type_b"] = extras.get("weather_type_b")
             line["recovery_8192"] = extras.get("recovery")
         print(json.dumps(line))
     if ws > 1:
@@ -354,32 +355,38 @@ def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
                        "algorithmic_bytes_per_launch": alg_bytes[dom], "avg_launch_ms": avg_ms}
     out["phases"] = phases
 
-    # ---- exact-SVD iALM on the same GPU (cuSOLVER via torch.linalg.svd), a few iterations
-    Oe = O.clone()
-    Se = torch.zeros_like(Oe)
-    normO2 = torch.linalg.matrix_norm(Oe, 2).item()
-    Ye = Oe / max(normO2, Oe.abs().max().item() / lam)
-    mu = 1.25 / normO2
-    torch.linalg.svd(Oe - Se + Ye / mu, full_matrices=False)      # cuSOLVER set-up outside the timing
-    torch.cuda.synchronize()
-    ex_it = 3
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(ex_it):
-        U, s, Vh = torch.linalg.svd(Oe - Se + Ye / mu, full_matrices=False)
-        s = torch.clamp(s - 1.0 / mu, min=0.0)
-        Le = (U * s) @ Vh
-        T = Oe - Le + Ye / mu
-        Se = torch.sign(T) * torch.clamp(T.abs() - lam / mu, min=0.0)
-        Ye = Ye + mu * (Oe - Le - Se)
-        mu = min(1.5 * mu, 1e7 * 1.25 / normO2)
-    t1.record()
-    torch.cuda.synchronize()
-    ex_ms = t0.elapsed_time(t1) / ex_it
+    # ---- exact-SVD iALM on the same GPU (cuSOLVER through torch.linalg.svd), a few iterations per
+    # cuSOLVER driver (gesvd: QR + bidiagonalisation; gesvdj: Jacobi); the faster one is the baseline
+    normO2 = torch.linalg.matrix_norm(O, 2).item()
+    per_driver = {}
+    for drv in ("gesvd", "gesvdj"):
+        Oe = O.clone()
+        Se = torch.zeros_like(Oe)
+        Ye = Oe / max(normO2, Oe.abs().max().item() / lam)
+        mu = 1.25 / normO2
+        torch.linalg.svd(Oe - Se + Ye / mu, full_matrices=False, driver=drv)   # set-up outside the timing
+        torch.cuda.synchronize()
+        ex_it = 3
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(ex_it):
+            U, s, Vh = torch.linalg.svd(Oe - Se + Ye / mu, full_matrices=False, driver=drv)
+            s = torch.clamp(s - 1.0 / mu, min=0.0)
+            Le = (U * s) @ Vh
+            T = Oe - Le + Ye / mu
+            Se = torch.sign(T) * torch.clamp(T.abs() - lam / mu, min=0.0)
+            Ye = Ye + mu * (Oe - Le - Se)
+            mu = min(1.5 * mu, 1e7 * 1.25 / normO2)
+        t1.record()
+        torch.cuda.synchronize()
+        per_driver[drv] = t0.elapsed_time(t1) / ex_it
+    best = min(per_driver, key=per_driver.get)
+    ex_ms = per_driver[best]
     out["exact"] = {"value": 1e3 / ex_ms, "unit": UNIT, "ms_per_step": ex_ms,
-                    "method": "iALM with torch.linalg.svd (cuSOLVER) exact SVT, float32, same GPU",
-                    "frsvt_speedup": None}
+                    "method": f"iALM with exact SVT by torch.linalg.svd (cuSOLVER {best}, the faster of "
+                              f"gesvd / gesvdj), float32, same GPU",
+                    "ms_per_step_by_driver": per_driver, "frsvt_speedup": None}
 
     # ---- end to end through the public API with host buffers
     O_host = torch.from_numpy(O_np).pin_memory()
@@ -415,6 +422,7 @@ def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
     out["unrolled"] = bench_unrolled(dev)
     out["video_bf16"] = bench_video_bf16(args, O, O_np, lam, dev, flush)
     out["video_rank_prediction"] = bench_video_ap(args, O, lam, flush)
+    out["weather_type_b"] = bench_weather()
     out["recovery"] = bench_recovery(args, dev, flush)
     return out
 
@@ -481,6 +489,53 @@ def bench_video_ap(args, O, lam, flush):
     return {"rule": "l' = min(r + (r < l ? 2 : ceil(0.05 n)), b), b = ceil(0.08 n) = 16, l_0 = 2",
             "sampling_rates_first_iterations": ls, "rank": info.r, "ms_per_step": ms, "value": 1e3 / ms,
             "unit": UNIT}
+
+
+def bench_weather():
+    """Type B RPCA (truncated nuclear norm, k = 1) on windows of 5 frames of the synthetic snow
+    video (384 x 288 pixels): per window rpca_init + 30 iALM iterations with partial FRSVT (l = 3,
+    q = 2, range propagation), O copied in and L, S copied out; device time per window."""
+    import numpy as np
+    import torch
+    from paper_1509_00296_gb300 import frsvt, synth
+    O_np, _, _ = synth.snow_video(frames=20)
+    m, F = O_np.shape
+    nwin, win, iters = F // 5, 5, 30
+    def padded():                                   # leading dimension 8 (TMA rows: multiples of 16 bytes)
+        return torch.zeros((m, 8), dtype=torch.float32, device="cuda")[:, :win]
+
+    Od, S, A, L = padded(), padded(), padded(), padded()
+    h = frsvt.Handle(m, win, 3, q=2, range_prop=True, seed=8, stream=torch.cuda.current_stream())
+    h.set_partial(1)
+    host = [torch.from_numpy(np.ascontiguousarray(O_np[:, w * win:(w + 1) * win])).pin_memory() for w in range(nwin)]
+    Lh = torch.empty((m, win), dtype=torch.float32).pin_memory()
+    Sh = torch.empty((m, win), dtype=torch.float32).pin_memory()
+
+    def window(w):
+        Od.copy_(host[w], non_blocking=True)
+        h.rpca_init(Od, S, A, 1.0 / np.sqrt(m), 1.5, 1e7)
+        for k in range(iters):
+            h.ialm_step(Od, S, A, 3, L=L if k == iters - 1 else None)
+        Lh.copy_(L, non_blocking=True)
+        Sh.copy_(S, non_blocking=True)
+
+    window(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for w in range(nwin):
+        window(w)
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    info = h.info()
+    h.close()
+    ms = e0.elapsed_time(e1) / nwin
+    return {"workload": "snow video 384 x 288, windows of 5 frames (110592 x 5), Type B iALM k = 1, l = 3, q = 2, "
+                        "30 iterations per window", "ms_per_window": ms, "ms_per_frame": ms / win,
+            "wall_ms_per_window": 1e3 * wall / nwin, "rank": info.r, "residual": info.residual,
+            "paper_context": "65.5 ms per frame (n = 5 window, Matlab 2014a, one CPU thread, Sec. 4.2)"}
 
 
 def bench_recovery(args, dev, flush):

@@ -197,6 +197,15 @@ frsvt_status frsvt_set_rank_prediction(frsvt_handle* h, int32_t a, double rho, d
 frsvt_status frsvt_get_rank_prediction(frsvt_handle* h, int32_t* l_next);
 
 /*
+ * Partial thresholding (Table 6, Type B: the proximal step of the truncated nuclear norm
+ * sum_{i>k} sigma_i): from the next SVT on, the k leading singular values of B are kept and the
+ * others soft-thresholded, in frsvt_svt and in the L-step of rpca_ialm_step (the Type B RPCA
+ * of the weather-removal application).  r then counts the non-zero values.  0 <= k <= cfg.l_max;
+ * k = 0 restores the plain SVT.  Synchronizes the handle's stream.
+ */
+frsvt_status frsvt_set_partial(frsvt_handle* h, int32_t k);
+
+/*
  * Tracing.  Phases of the path, in launch order within one SVT / iALM step.
  * When timing is enabled every kernel launch is bracketed by CUDA events on
  * the handle's stream (recording events does not synchronize; it adds a few

@@ -75,7 +75,7 @@ def ialm_rpca(O: np.ndarray, lam: float | None = None, mu0: float | None = None,
               max_iter: int = 500, method: str = "exact", l: int = 0, q: int = 0,
               seed: int = 0, range_prop: bool = True, fixed_iters: int | None = None,
               normO2: float | None = None, rank_tol: float = 1e-12,
-              ap: dict | None = None) -> RPCAResult:
+              ap: dict | None = None, partial_k: int = 0) -> RPCAResult:
     """Inexact ALM RPCA.  With ``ap`` (keys a, rho, gamma; FRSVT with range propagation) the
     sampling rate follows the adaptive rank prediction of Eq. 7: l_0 = ceil(0.1 b), b =
     ceil(gamma n) for the short side n, l_{i+1} = predict_rank(r_i, l_i, ...); the propagated
@@ -104,11 +104,15 @@ def ialm_rpca(O: np.ndarray, lam: float | None = None, mu0: float | None = None,
     for k in range(n_iter):
         Ain = O - S + Y / mu
         if method == "exact":
-            L, r = svt_mod.exact_svt(Ain, 1.0 / mu)
+            if partial_k > 0:
+                L = svt_mod.psvt(Ain, 1.0 / mu, partial_k)
+                r = int(np.linalg.matrix_rank(L))
+            else:
+                L, r = svt_mod.exact_svt(Ain, 1.0 / mu)
         elif method == "frsvt":
             l_k = l if ap is None else l_cur
             out = svt_mod.frsvt(Ain, 1.0 / mu, l_k, q, seed, k,
-                                Q_prev=Qt if range_prop else None, rank_tol=rank_tol)
+                                Q_prev=Qt if range_prop else None, rank_tol=rank_tol, partial_k=partial_k)
             L, r = out.X, out.r
             if ap is None:
                 Qt = out.Q_tilde

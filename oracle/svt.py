@@ -110,7 +110,7 @@ class FRSVTResult:
 
 def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
           Q_prev: np.ndarray | None = None, rank_tol: float = 1e-12,
-          problem: int = 0, weights=None) -> FRSVTResult:
+          problem: int = 0, weights=None, partial_k: int = 0) -> FRSVTResult:
     """Fast randomized SVT, Alg. 1, on A (m x n) in FP64.
 
     Omega is the (seed, stream, problem) Philox Gaussian matrix with max(m, n)
@@ -118,7 +118,9 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
     p = l - |Q_prev| columns are used.  Q_prev lives on the short side of A.
     With ``weights`` (a callable on the singular values D of B), step 19
     shrinks by max(D - weights(D), 0) instead of S_tau(D) and r counts
-    D_j > w_j.
+    D_j > w_j.  With ``partial_k`` > 0 step 19 is the partial thresholding of
+    the truncated nuclear norm (Table 6, Type B): the partial_k leading values
+    of D are kept, the others soft-thresholded; r counts the non-zero ones.
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
@@ -160,7 +162,9 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
     HWV = H @ (W @ V)
     if weights is None:
         fD = soft(D, tau)
-        r = int(np.sum(D > tau))
+        if partial_k > 0:                          # partial thresholding (Table 6, Type B)
+            fD[:partial_k] = D[:partial_k]
+        r = int(np.sum(fD > 0.0)) if partial_k > 0 else int(np.sum(D > tau))
     else:
         wD = weights(D)
         fD = np.maximum(D - wD, 0.0)

@@ -1401,6 +1401,14 @@ frsvt_status frsvt_set_rank_prediction(frsvt_handle* h, int32_t a, double rho, d
   return FRSVT_OK;
 }
 
+frsvt_status frsvt_set_partial(frsvt_handle* h, int32_t k) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (k < 0 || k > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "k must be in [0, l_max]");
+  FRSVT_CK(cudaMemcpyAsync(&h->dst->partial_k, &k, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  FRSVT_CK(cudaStreamSynchronize(h->stream));          // k lives on this stack frame
+  return FRSVT_OK;
+}
+
 frsvt_status frsvt_get_rank_prediction(frsvt_handle* h, int32_t* l_next) {
   if (h == nullptr || l_next == nullptr) return FRSVT_ERR_INVALID_ARG;
   int32_t v = 0;

@@ -834,13 +834,13 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
     int rank = 0;
     for (int c = 0; c < kWL; ++c) rank += (v.sig[c] > sc || (v.sig[c] == sc && c < tid)) ? 1 : 0;
     v.perm[rank] = tid;
-    const float cf = (sc > tau) ? (sc - tau) / sc : 0.f;
+    const float cf = (rank < dst->partial_k && sc > 0.f) ? 1.f : ((sc > tau) ? (sc - tau) / sc : 0.f);
     v.coef[tid] = cf;
     wv[tid] = (cf > 0.f) ? cf / (sc * sc) : 0.f;
   }
   __syncthreads();
   int r = 0;
-  for (int c = 0; c < kWL; ++c) r += (v.sig[c] > tau) ? 1 : 0;
+  for (int c = 0; c < kWL; ++c) r += (v.coef[c] > 0.f) ? 1 : 0;
   const int keep = ca.update_rp ? max(0, min(r, ca.l - 2)) : 0;
   if (tid < kGB) {
     int bi2, bj2;

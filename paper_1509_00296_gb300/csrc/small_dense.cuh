@@ -368,7 +368,12 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
   float* coef = w.vec + LP;
   int* perm = w.iv + LP;
   const int sweeps = core_svd_block<LP>(w, l, rank_tol, max_sweeps);
-  if (tid < LP) coef[tid] = (sig[tid] > tau) ? (sig[tid] - tau) / sig[tid] : 0.f;
+  const int pk = dst->partial_k;                   // partial SVT: the pk leading values stay
+  if (tid < LP) {
+    int rk = 0;
+    for (int c = 0; c < LP; ++c) rk += (sig[c] > sig[tid] || (sig[c] == sig[tid] && c < tid)) ? 1 : 0;
+    coef[tid] = (rk < pk && sig[tid] > 0.f) ? 1.f : ((sig[tid] > tau) ? (sig[tid] - tau) / sig[tid] : 0.f);
+  }
   __syncthreads();
   float* M = w.Cm;
   for (int e = tid; e < LP * LP; e += nt) {
@@ -378,7 +383,7 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
     M[e] = acc;
   }
   int r = 0;
-  for (int c = 0; c < LP; ++c) r += (sig[c] > tau) ? 1 : 0;
+  for (int c = 0; c < LP; ++c) r += (coef[c] > 0.f) ? 1 : 0;
   // propagated columns: min(r, l - 2) for a fixed l; under the adaptive rank prediction of Eq. 7
   // the next sampling rate l' = min(r + (r < l ? a : ceil(rho n)), b) and min(r, l' - a) columns
   const int ap_a = dst->ap_a;

@@ -31,6 +31,8 @@ struct DevState {
   int32_t ap_a;         // Eq. 7: over-sampling a when r < l (0: prediction off)
   int32_t ap_pn;        // Eq. 7: ceil(rho n), the over-sampling when r >= l
   int32_t ap_b;         // Eq. 7: the bound b = ceil(gamma n) (<= the panel width)
+  int32_t partial_k;    // leading singular values kept unshrunk (partial SVT, Table 6 Type B)
+  int32_t pad2;
   float sigma[kMaxL];   // singular values of B of the last SVT, descending
 };
 

@@ -61,6 +61,7 @@ _SIGS = {
     "frsvt_get_sigma": [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
     "frsvt_set_rank_prediction": [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_double],
     "frsvt_get_rank_prediction": [_P, ctypes.POINTER(ctypes.c_int32)],
+    "frsvt_set_partial": [_P, ctypes.c_int32],
     "frsvt_status_string": [ctypes.c_int],
     "frsvt_last_error": [_P],
     "frsvt_enable_timing": [_P, ctypes.c_int32],
@@ -205,6 +206,10 @@ class Handle:
     def set_rank_prediction(self, a: int = 2, rho: float = 0.05, gamma: float = 0.1):
         """Adaptive rank prediction of Eq. 7 (a = 0 switches it off)."""
         self._chk(lib().frsvt_set_rank_prediction(self._h, int(a), float(rho), float(gamma)))
+
+    def set_partial(self, k: int):
+        """Partial thresholding (Table 6, Type B): keep the k leading singular values (0: plain SVT)."""
+        self._chk(lib().frsvt_set_partial(self._h, int(k)))
 
     def rank_prediction(self) -> int:
         """Sampling rate the next SVT will use under adaptive rank prediction."""

@@ -125,3 +125,28 @@ def wnnm_batch(seed: int = 1004, batch: int = 16384, m: int = 64, nmin: int = 40
         A += noise * rng.standard_normal(A.shape)
         mats.append(A.astype(np.float32))
     return mats, ns.astype(np.int32)
+
+
+def snow_video(seed: int = 1006, h: int = 288, w: int = 384, frames: int = 20, density: float = 0.03):
+    """Weather-artifact workload (Type B, semi-online removal): frames of a static scene (a smooth
+    image under a per-frame illumination gain in [0.95, 1.05]: rank 1) with a 24 x 24 square moving
+    4 px per frame, and snow: a `density` fraction of each frame's pixels replaced by U[0.85, 1].
+    Returns (O (h*w x frames) float32, the clean frames, the snow mask)."""
+    rng = np.random.default_rng(seed)
+    bg = _smooth_image(rng, h, w)
+    gain = rng.uniform(0.95, 1.05, size=frames)
+    clean = np.empty((h * w, frames), dtype=np.float64)
+    mask = np.zeros((h * w, frames), dtype=bool)
+    O = np.empty((h * w, frames), dtype=np.float64)
+    y0, x0 = h // 2 - 12, 16
+    for t in range(frames):
+        img = bg * gain[t]
+        xs = x0 + 4 * t
+        img[y0:y0 + 24, xs:xs + 24] = 0.9
+        clean[:, t] = img.reshape(-1)
+        flakes = rng.random(h * w) < density
+        mask[:, t] = flakes
+        o = clean[:, t].copy()
+        o[flakes] = rng.uniform(0.85, 1.0, size=int(flakes.sum()))
+        O[:, t] = o
+    return O.astype(np.float32), clean, mask

@@ -298,6 +298,39 @@ def test_psvt_keeps_leading_values():
     assert np.allclose(np.sort(sx[1:])[::-1][: np.sum(s[1:] > 0.8)], (s[1:] - 0.8)[s[1:] > 0.8], atol=1e-12)
 
 
+def test_partial_frsvt_equals_psvt_when_rank_fits():
+    """FRSVT with partial thresholding (Table 6, Type B) is exact when rank(A) <= l, like the plain
+    operator: it equals the partial SVT computed from the full SVD."""
+    rng = np.random.default_rng(23)
+    U, _ = np.linalg.qr(rng.standard_normal((60, 4)))
+    V, _ = np.linalg.qr(rng.standard_normal((9, 4)))
+    A = (U * np.array([9.0, 5.0, 2.0, 0.6])) @ V.T
+    for k in (1, 2):
+        out = svt.frsvt(A, 1.0, 6, 1, 4, 0, partial_k=k)
+        assert np.allclose(out.X, svt.psvt(A, 1.0, k), atol=1e-12)
+        assert out.r == 3                        # kept + the values above tau
+
+
+def test_ialm_partial_svt_separates_rank_one_background():
+    """Type B iALM (truncated nuclear norm, k = 1) on a short window: a rank-1 scene plus sparse
+    bright outliers is separated, by the exact partial SVT and by FRSVT with partial thresholding."""
+    from oracle import rpca
+    rng = np.random.default_rng(5)
+    m, n = 400, 5
+    bg = rng.uniform(0.2, 0.8, size=m)
+    L = np.outer(bg, rng.uniform(0.9, 1.1, size=n))
+    S = np.zeros((m, n))
+    pos = rng.choice(m * n, size=int(0.05 * m * n), replace=False)
+    S.flat[pos] = rng.uniform(0.5, 1.0, size=pos.size)
+    O = L + S
+    ex = rpca.ialm_rpca(O, method="exact", partial_k=1, fixed_iters=60)
+    fr = rpca.ialm_rpca(O, method="frsvt", l=3, q=2, seed=1, partial_k=1, fixed_iters=60)
+    assert ex.history[-1] < 1e-12 and ex.ranks[-1] == 1
+    assert np.linalg.norm(ex.L - L) / np.linalg.norm(L) < 0.1     # the rank-1 scene, up to the model's bias
+    assert np.linalg.norm(fr.L - ex.L) / np.linalg.norm(ex.L) < 1e-5
+    assert fr.ranks[-1] == 1
+
+
 # ---------------------------------------------------------------- SVT adjoint
 
 @pytest.mark.parametrize("shape", [(7, 5), (5, 7), (6, 6)])
