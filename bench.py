@@ -59,6 +59,22 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max_ms(dev_ms: float, device) -> float:
+    """Largest timed-region duration (ms) over the ranks of the process group (the local value on
+    one rank): replicas are timed together, the slowest one counts."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(steps: int, ws: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank runs `steps` iterations of its own replica within max_ms."""
+    return ws * steps / (max_ms / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -251,13 +267,9 @@ def main():
         t_wall = time.perf_counter() - t_wall0
     if ws > 1:
         torch.distributed.barrier()
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    dev_ms_t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(dev_ms_t, op=torch.distributed.ReduceOp.MAX)
-    dev_ms = float(dev_ms_t.item())
+    dev_ms = reduce_max_ms(sum(a.elapsed_time(b) for a, b in evs), dev)
     ms_per_step = dev_ms / args.steps
-    value = ws * args.steps / (dev_ms / 1e3)
+    value = aggregate_rate(args.steps, ws, dev_ms)
     clocks = clk.summary()
     info = h.info()
 
