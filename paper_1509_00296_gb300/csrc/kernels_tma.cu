@@ -364,16 +364,20 @@ k_tp_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int np4, int6
 // Clusters of 4 (the cluster only serves the final one-value residual reduction): more of them
 // fit at once than clusters of 8, so the streaming kernel covers (nearly) every SM.
 constexpr int kAlmCL = 4;
+// 256 consumer threads for either basis width: each holds four rows of Rf (4 LP registers), which
+// 512 threads (at most 96 registers each) would spill.
+constexpr int kAlmNC = 256;
+constexpr int kAlmNT = kAlmNC + 32;
 
 template <int LP>
-__global__ void __cluster_dims__(kAlmCL, 1, 1) __launch_bounds__(Cfg<LP>::NT, 1)
+__global__ void __cluster_dims__(kAlmCL, 1, 1) __launch_bounds__(kAlmNT, 1)
 k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmS,
          const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ, int64_t m, int n, int np4,
          int64_t rpc, const float* __restrict__ Rf, float* __restrict__ S, float* __restrict__ A, int64_t ld,
          float* __restrict__ L, int64_t ldl, DevState* __restrict__ dst, double* __restrict__ cpart,
          double* __restrict__ rsum, unsigned* __restrict__ tickets, __nv_bfloat16* __restrict__ Ab, int64_t ldb,
          int nse) {
-  constexpr int NC = Cfg<LP>::NC, NT = Cfg<LP>::NT;
+  constexpr int NC = kAlmNC, NT = kAlmNT;
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kStagesE], empty[kStagesE];
   __shared__ double red[NT / 32];
@@ -444,11 +448,20 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
     const int rg = threadIdx.x / nq;
     const bool active = rg < rgc;
     const int col = 4 * qd;
-    float rf[4][LP];
+    float rf[4][LP];                                  // rows col .. col + 3 of Rf, 16-byte loads
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc)
+    for (int cc = 0; cc < 4; ++cc) {
+      const bool in = active && col + cc < n;
+      const float4* r4 = reinterpret_cast<const float4*>(Rf + (col + cc) * LP);
 #pragma unroll
-      for (int k = 0; k < LP; ++k) rf[cc][k] = (active && col + cc < n) ? Rf[(col + cc) * LP + k] : 0.f;
+      for (int k4 = 0; k4 < LP / 4; ++k4) {
+        const float4 v = in ? __ldg(r4 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        rf[cc][4 * k4] = v.x;
+        rf[cc][4 * k4 + 1] = v.y;
+        rf[cc][4 * k4 + 2] = v.z;
+        rf[cc][4 * k4 + 3] = v.w;
+      }
+    }
     const bool fullq = col + 3 < n;
     bool ok = true;
     for (int c = 0; c < rw.nchunks; ++c) {
@@ -637,7 +650,7 @@ int tma_resident_grid(int LP, int64_t n) {
 int tma_alm_resident_grid(int LP, int64_t n) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kAlmCL, 1, 1);
-  cfg.blockDim = dim3(threads_of(LP), 1, 1);
+  cfg.blockDim = dim3(kAlmNT, 1, 1);
   cfg.dynamicSmemBytes = tma_alm_smem(LP, n);
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeClusterDimension;
@@ -721,10 +734,10 @@ cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS
   const int nn = static_cast<int>(n);
   __nv_bfloat16* ab = static_cast<__nv_bfloat16*>(Ab);
   if (LP == 16)
-    k_tp_alm<16><<<grid, Cfg<16>::NT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
+    k_tp_alm<16><<<grid, kAlmNT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
                                                    cpart, rsum, tickets, ab, ldb, nse);
   else
-    k_tp_alm<32><<<grid, Cfg<32>::NT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
+    k_tp_alm<32><<<grid, kAlmNT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
                                                    cpart, rsum, tickets, ab, ldb, nse);
   return cudaGetLastError();
 }
