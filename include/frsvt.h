@@ -95,6 +95,13 @@ typedef struct frsvt_info {
   int32_t sweeps;                /* Jacobi sweeps of the last l x l core SVD (Alg. 1 step 18) */
   double mu;                     /* iALM penalty mu for the next iteration */
   double residual;               /* ||O - L - S||_F / ||O||_F of the last iALM step */
+  float rp_residual;             /* Prop. 4 / Eq. 14: ||(I - Q~ Q~^T) y|| for the first new sample
+                                    column y = A^T omega of the last range-propagated sketch, a
+                                    by-product of its Gram-Schmidt step; alpha sqrt(2/pi) times it
+                                    bounds ||(I - Q~ Q~^T) A||_2 >= sigma_{k+1}(A) with probability
+                                    >= 1 - 1/alpha.  -1 when that sketch had no propagated basis
+                                    (and before any sketch with range propagation). */
+  int32_t reserved;
 } frsvt_info;
 
 typedef struct frsvt_handle frsvt_handle;

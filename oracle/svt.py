@@ -11,7 +11,14 @@
                      Pinned by: equality with exact_svt when rank(A) <= l
                      (Sec. 3.1, remark after Cor. 2), invariance to the choice
                      of orthonormalization (Prop. 1), the Theorem 3 average
-                     bound over Omega draws, and the Prop. 4 residual estimate.
+                     bound over Omega draws.  Under range propagation it reports
+                     the residual norm ||(I - Q~ Q~^T) A^T omega|| of the first new
+                     sample column (``extra["rp_residual"]``).
+- ``residual_estimate`` Prop. 4 / Eq. 14: alpha sqrt(2/pi) ||(I - Q Q^T) y||.  Pinned
+                     by the exact failure rate of the bound for a rank-one residual
+                     (|g| < 1 / (alpha sqrt(2/pi)), g ~ N(0, 1)), the mean of the
+                     residual norm (sqrt(2/pi) sigma), the 1 - 1/alpha guarantee and
+                     the zero residual when Q spans the range.
 - ``wsvt``           weighted SVT (the WSVT footnote of Sec. 1): U max(Sigma - w, 0) V^T.
                      Pinned by reduction to SVT for constant weights and by
                      brute-force minimization of the weighted problem on 4x3
@@ -55,6 +62,22 @@ def soft(x, tau):
     """Soft shrinkage S_tau(x) = sgn(x) max(|x| - tau, 0) (Def. 1)."""
     x = np.asarray(x, dtype=np.float64)
     return np.sign(x) * np.maximum(np.abs(x) - tau, 0.0)
+
+
+def residual_norm(Q: np.ndarray, y: np.ndarray) -> float:
+    """||(I - Q Q^T) y||_2 for an orthonormal Q (the Gram-Schmidt residual of Prop. 4)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    return float(np.linalg.norm(y - Q @ (Q.T @ y)))
+
+
+def residual_estimate(Q: np.ndarray, y: np.ndarray, alpha: float = 20.0) -> float:
+    """Prop. 4 / Eq. 14: varsigma = alpha sqrt(2 / pi) ||(I - Q Q^T) A omega||_2 with y = A omega.
+
+    With probability at least 1 - 1 / alpha over the Gaussian omega it bounds
+    ||(I - Q Q^T) A||_2, hence sigma_{k+1}(A) for a rank-k Q (Lemma 3 with one draw).
+    """
+    return float(alpha * np.sqrt(2.0 / np.pi) * residual_norm(Q, y))
 
 
 def exact_svt(A: np.ndarray, tau: float):
@@ -132,6 +155,7 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
     l = min(l, ns)
 
     # Alg. 1 steps 3-12: sketch, with or without range propagation.
+    rp_residual = -1.0                     # no propagated basis: Prop. 4 estimate unavailable
     if Q_prev is None or Q_prev.shape[1] == 0:
         Omega = gaussian_matrix(nl, l, seed, stream, problem)       # step 4
         Y = Ah @ Omega                                              # step 5
@@ -142,6 +166,8 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
         Y = Ah @ Omega                                              # step 9
         QY = linalg.mgs(Q_prev, Y, rank_tol)                        # step 10
         Q = np.hstack([Q_prev, QY])                                 # step 11
+        # Prop. 4: the residual of the first new sample column against the propagated basis
+        rp_residual = residual_norm(Q_prev, Y[:, 0]) if p > 0 else -1.0
 
     # Steps 13-15: power iteration Q = QR(A A^T Q), eta = q times.  The rank is
     # re-checked with a pivoted QR (Sec. 2.1, range propagation paragraph).
@@ -173,7 +199,8 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
     keep = min(r, l - 2)
     Q_tilde = np.ascontiguousarray(QV[:, :max(keep, 0)])          # step 21
     X = Xh.T if transposed else Xh
-    return FRSVTResult(np.ascontiguousarray(X), Q_tilde, r, D, s, pit, extra={"QV": QV})
+    return FRSVTResult(np.ascontiguousarray(X), Q_tilde, r, D, s, pit,
+                       extra={"QV": QV, "rp_residual": rp_residual})
 
 
 def wsvt_batch(mats, c: float, eps: float, variant: str = "exact", l: int = 12, q: int = 1,

@@ -226,6 +226,7 @@ namespace {
 
 constexpr size_t kSmemLimit = 227 * 1024;
 constexpr int kCLw = 8;            // cluster size of the wide-basis Gram reduction
+const float kNoResidual = -1.f;    // DevState::rp_res before any range-propagated sketch (static storage: async copy)
 
 frsvt_status fail(frsvt_handle* h, frsvt_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -879,6 +880,7 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
       return FRSVT_ERR_ALLOC;
     }
     if (cudaMemsetAsync(h->dst, 0, sizeof(DevState), h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&h->dst->rp_res, &kNoResidual, sizeof(float), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
       free_all(h);
       delete h;
@@ -984,6 +986,7 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
     return FRSVT_ERR_ALLOC;
   }
   if (cudaMemsetAsync(h->dst, 0, sizeof(DevState), h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&h->dst->rp_res, &kNoResidual, sizeof(float), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->Qt, 0, sizeof(float) * cfg->n_max * LP, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * (ntiles_max + 1), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1435,6 +1438,7 @@ frsvt_status frsvt_get_info(frsvt_handle* h, frsvt_info* info) {
   info->sweeps = d.sweeps;
   info->mu = d.mu;
   info->residual = d.resid_ratio;
+  info->rp_residual = d.rp_res;
   return FRSVT_OK;
 }
 

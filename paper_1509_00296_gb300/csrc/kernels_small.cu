@@ -140,6 +140,7 @@ k_orth(const float* __restrict__ Y, int64_t ns, int l, int use_rp, const float* 
   }
 
   // Cholesky QR of the new block, twice.
+  if (tid == 0 && use_rp && (keep == 0 || p == 0)) dst->rp_res = -1.f;
   int kept = 0;
   for (int pass = 0; pass < 2 && p > 0; ++pass) {
     const int np = p * (p + 1) / 2;
@@ -162,6 +163,7 @@ k_orth(const float* __restrict__ Y, int64_t ns, int l, int use_rp, const float* 
       G[b * LP + a] = s;
     }
     __syncthreads();
+    if (pass == 0 && tid == 0 && use_rp && keep > 0) dst->rp_res = sqrtf(static_cast<float>(G[0]));   // Prop. 4
     if (tid < 32) {
       chol_drop_warp<LP>(G, R, dropped, p, rank_tol);
       tri_inverse_warp<LP>(R, dropped, Td, T, p);

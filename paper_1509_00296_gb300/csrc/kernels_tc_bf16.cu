@@ -384,9 +384,11 @@ k_tb_sc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     w.W[e] = v;
   }
   __syncthreads();
-  const int s = orth_block<LP>(w, n, keep, l, rank_tol, passes);
+  float rp_res = -1.f;
+  const int s = orth_block<LP>(w, n, keep, l, rank_tol, passes, &rp_res);
   for (int e = threadIdx.x; e < n * LP; e += kScThr) Qout[e] = w.W[e];
   if (threadIdx.x == 0) {
+    if (use_rp) dst->rp_res = rp_res;
     dst->s = s;
     if (s < l) dst->status |= kDevRankDeficient;
   }

@@ -213,11 +213,14 @@ __device__ void block_trsm_rows(SmallWs<LP>& w, float* W, int64_t ns, int c0, in
 
 // Orthonormal basis (Alg. 1 steps 6 / 10-11 / 14).  W (ns x LP, shared) holds
 // [Qt[:, :keep] | Y[:, :l - keep] | 0]; on return W holds Q.  Returns s (surviving columns).
+// rp_res (optional, written by thread 0): the norm of the first new column once it has been
+// projected out of the propagated basis, ||(I - Qt Qt^T) y_0|| (Prop. 4); -1 when keep = 0.
 // passes = 2 is Cholesky QR2 (orthonormal to FP32 rounding); passes = 1 gives a basis of the
 // same span whose orthogonality error is ~u kappa(Y), enough for a basis that only feeds the
 // next power step (only its span matters there).
 template <int LP>
-__device__ int orth_block(SmallWs<LP>& w, int64_t ns, int keep, int l, double rank_tol, int passes) {
+__device__ int orth_block(SmallWs<LP>& w, int64_t ns, int keep, int l, double rank_tol, int passes,
+                          float* rp_res = nullptr) {
   float* W = w.W;
   const int p = l - keep;
   if (keep > 0 && p > 0) {
@@ -244,8 +247,10 @@ __device__ int orth_block(SmallWs<LP>& w, int64_t ns, int keep, int l, double ra
     }
   }
   int kept = 0;
+  if (rp_res != nullptr && threadIdx.x == 0 && (keep == 0 || p == 0)) *rp_res = -1.f;
   for (int pass = 0; pass < passes && p > 0; ++pass) {
     block_inner<LP>(W, ns, keep, keep, p, p, true, w.G, w.gacc, w.gacc_n);
+    if (pass == 0 && keep > 0 && rp_res != nullptr && threadIdx.x == 0) *rp_res = sqrtf(static_cast<float>(w.G[0]));
     block_cholesky<LP>(w, p, rank_tol);
     block_trsm_rows<LP>(w, W, ns, keep, p);
     kept = 0;

@@ -32,7 +32,8 @@ struct DevState {
   int32_t ap_pn;        // Eq. 7: ceil(rho n), the over-sampling when r >= l
   int32_t ap_b;         // Eq. 7: the bound b = ceil(gamma n) (<= the panel width)
   int32_t partial_k;    // leading singular values kept unshrunk (partial SVT, Table 6 Type B)
-  int32_t pad2;
+  float rp_res;         // Prop. 4: ||(I - Q~ Q~^T) y|| of the first new sample column of the last
+                        // range-propagated sketch (-1: the last sketch had no propagated basis)
   float sigma[kMaxL];   // singular values of B of the last SVT, descending
 };
 

@@ -8,6 +8,7 @@ there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from dataclasses import dataclass
 
@@ -41,7 +42,8 @@ class Config(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int32), ("s", ctypes.c_int32), ("keep", ctypes.c_int32),
                 ("device_status", ctypes.c_uint32), ("counter", ctypes.c_uint64), ("alm_iter", ctypes.c_int32),
-                ("sweeps", ctypes.c_int32), ("mu", ctypes.c_double), ("residual", ctypes.c_double)]
+                ("sweeps", ctypes.c_int32), ("mu", ctypes.c_double), ("residual", ctypes.c_double),
+                ("rp_residual", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -129,6 +131,14 @@ class SVTInfo:
     mu: float
     residual: float
     sweeps: int = 0
+    rp_residual: float = -1.0
+
+    def residual_estimate(self, alpha: float = 20.0) -> float:
+        """Prop. 4 / Eq. 14: alpha sqrt(2/pi) ||(I - Q~ Q~^T) A^T omega||, an upper bound on
+        sigma_{k+1} with probability >= 1 - 1/alpha (-1 when unavailable)."""
+        if self.rp_residual < 0:
+            return -1.0
+        return alpha * math.sqrt(2.0 / math.pi) * self.rp_residual
 
 
 class Handle:
@@ -221,7 +231,7 @@ class Handle:
         inf = Info()
         self._chk(lib().frsvt_get_info(self._h, ctypes.byref(inf)))
         return SVTInfo(inf.r, inf.s, inf.keep, inf.device_status, inf.counter, inf.alm_iter, inf.mu, inf.residual,
-                       inf.sweeps)
+                       inf.sweeps, inf.rp_residual)
 
     def enable_timing(self, on: bool = True):
         self._chk(lib().frsvt_enable_timing(self._h, 1 if on else 0))

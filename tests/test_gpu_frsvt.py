@@ -80,9 +80,12 @@ def test_frsvt_exact_for_low_rank(fr):
     assert rel_fro(X, Xe) <= TOL
 
 
-def test_frsvt_range_propagation_sequence(fr):
-    """Three calls on a slowly moving iterate: the propagated basis (Alg. 1 steps 8-11) matches the oracle."""
-    m, n, l, q = 1500, 120, 12, 1
+@pytest.mark.parametrize("m,n", [(1500, 120), (1500, 300)])
+def test_frsvt_range_propagation_sequence(fr, m, n):
+    """Three calls on a slowly moving iterate: the propagated basis (Alg. 1 steps 8-11) matches the oracle,
+    and so does the Prop. 4 residual ||(I - Q~ Q~^T) A^T omega_0|| of the first new sample column
+    (n = 120: tensor-core sketch tail; n = 300: CUDA-core path)."""
+    l, q = 12, 1
     A0, s = spectrum_matrix(m, n, 30, 0.75, 0.001, seed=77)
     rng = np.random.default_rng(78)
     Dlt = rng.standard_normal((m, n)) * 0.01
@@ -91,6 +94,7 @@ def test_frsvt_range_propagation_sequence(fr):
     Qp = None
     for t in range(3):
         A = (A0 + t * Dlt).astype(np.float32).astype(np.float64)
+        kept = 0 if Qp is None else Qp.shape[1]
         ref = svt.frsvt(A, tau, l, q, seed=21, stream=t, Q_prev=Qp)
         Qp = ref.Q_tilde
         X = h.svt(to_gpu(A), tau, l).cpu().numpy()
@@ -98,6 +102,13 @@ def test_frsvt_range_propagation_sequence(fr):
         assert info.r == ref.r and info.keep == ref.Q_tilde.shape[1]
         assert info.counter == t + 1
         assert rel_fro(X, ref.X) <= TOL, t
+        want = ref.extra["rp_residual"]
+        if kept == 0:
+            assert want == -1.0 and info.rp_residual == -1.0 and info.residual_estimate() == -1.0, t
+        else:
+            # a difference of FP32 quantities of size ||y||: 1e-3 of the residual plus 1e-5 ||y||
+            y = A.T @ philox.gaussian_matrix(m, l - kept, 21, t, 0)[:, 0]
+            assert abs(info.rp_residual - want) <= 1e-3 * want + 1e-5 * np.linalg.norm(y), (t, info.rp_residual, want)
 
 
 def test_tau_above_sigma_max_gives_zero(fr):

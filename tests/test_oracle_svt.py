@@ -378,3 +378,77 @@ def test_svt_vjp_tau_zero_is_identity_map():
     assert np.allclose(Abar, Xbar, atol=1e-12)
     U, s, Vt = np.linalg.svd(A, full_matrices=False)
     assert abs(taubar + np.trace(U.T @ Xbar @ Vt.T)) < 1e-12
+
+
+def _residual_problem(ns, nl, spectrum, k, seed):
+    """Ah = U diag(spectrum) V^T (ns x nl) and Q = U[:, :k]: (I - Q Q^T) Ah has the spectrum[k:] tail."""
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((ns, len(spectrum))))
+    V, _ = np.linalg.qr(rng.standard_normal((nl, len(spectrum))))
+    return (U * np.asarray(spectrum, dtype=np.float64)) @ V.T, U[:, :k]
+
+
+def test_prop4_rank_one_residual_failure_rate():
+    """Prop. 4 with a rank-one residual sigma u v^T: ||(I - QQ^T) A omega|| = sigma |g|, g ~ N(0, 1), so the
+    bound alpha sqrt(2/pi) sigma |g| >= sigma fails exactly when |g| < c = 1 / (alpha sqrt(2/pi)),
+    with probability erf(c / sqrt(2)).  At alpha = 2 that is 0.469 (0.383 without the sqrt(2/pi) factor,
+    0.683 with 1 / alpha dropped), so the count over 4000 draws pins the constant."""
+    from scipy.special import erf
+    Ah, Q = _residual_problem(30, 200, [9.0, 4.0, 2.5], 2, seed=401)
+    tail = 2.5                                        # ||(I - QQ^T) Ah||_2
+    assert np.linalg.norm(Ah - Q @ (Q.T @ Ah), 2) == pytest.approx(tail, rel=1e-12)
+    rng = np.random.default_rng(402)
+    N, alpha = 4000, 2.0
+    fails = sum(svt.residual_estimate(Q, Ah @ rng.standard_normal(200), alpha) < tail for _ in range(N))
+    p = erf(1.0 / (alpha * np.sqrt(2.0 / np.pi)) / np.sqrt(2.0))
+    assert p == pytest.approx(0.469, abs=1e-3)
+    assert abs(fails - N * p) <= 4.0 * np.sqrt(N * p * (1 - p)), (fails, N * p)
+
+
+def test_prop4_mean_residual_and_guarantee():
+    """E ||(I - QQ^T) A omega|| = sqrt(2/pi) sigma for a rank-one residual (E|g| = sqrt(2/pi)); with a
+    rank-three residual the alpha = 20 bound holds in at least 1 - 1/alpha = 95 % of the draws."""
+    Ah, Q = _residual_problem(30, 200, [9.0, 4.0, 2.5], 2, seed=403)
+    rng = np.random.default_rng(404)
+    r = np.array([svt.residual_norm(Q, Ah @ rng.standard_normal(200)) for _ in range(4000)])
+    se = 2.5 * np.sqrt(1.0 - 2.0 / np.pi) / np.sqrt(r.size)
+    assert abs(r.mean() - 2.5 * np.sqrt(2.0 / np.pi)) <= 4.0 * se
+    Ah3, Q3 = _residual_problem(30, 200, [9.0, 4.0, 1.0, 0.8, 0.5], 2, seed=405)
+    bound = np.linalg.norm(Ah3 - Q3 @ (Q3.T @ Ah3), 2)
+    assert bound == pytest.approx(1.0, rel=1e-12)
+    ok = np.mean([svt.residual_estimate(Q3, Ah3 @ rng.standard_normal(200), 20.0) >= bound for _ in range(2000)])
+    assert ok >= 0.95
+
+
+def test_prop4_zero_residual_when_basis_spans_range():
+    """rank(A) <= k and Q = the leading left singular vectors: the residual vanishes, so does the estimate."""
+    Ah, Q = _residual_problem(30, 200, [9.0, 4.0, 2.5], 3, seed=406)
+    y = Ah @ np.random.default_rng(407).standard_normal(200)
+    assert svt.residual_estimate(Q, y) <= 1e-13 * np.linalg.norm(y)
+
+
+def test_frsvt_reports_prop4_residual_of_first_new_column():
+    """Under range propagation frsvt reports ||(I - Q~ Q~^T) A^T omega_0|| for the first new Omega column
+    (short side = columns of a tall A); without a propagated basis it reports -1.  A propagated basis
+    that spans the whole row space leaves no residual."""
+    rng = np.random.default_rng(408)
+    m, n, l = 300, 40, 10
+    U, _ = np.linalg.qr(rng.standard_normal((m, 6)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, 6)))
+    s = np.array([50.0, 30.0, 20.0, 12.0, 3.0, 1.0])
+    A = (U * s) @ V.T + 1e-3 * rng.standard_normal((m, n))
+    first = svt.frsvt(A, 2.0, l, 1, seed=5, stream=0)
+    assert first.extra["rp_residual"] == -1.0
+    Qp = first.Q_tilde
+    assert Qp.shape[1] == 5                                     # min(r, l - 2) with r = #{sigma > 2} = 5
+    second = svt.frsvt(A, 2.0, l, 1, seed=5, stream=1, Q_prev=Qp)
+    omega0 = gaussian_matrix(m, l - Qp.shape[1], 5, 1, 0)[:, 0]
+    y = A.T @ omega0
+    direct = np.linalg.norm(y - Qp @ np.linalg.lstsq(Qp, y, rcond=None)[0])
+    assert second.extra["rp_residual"] == pytest.approx(direct, rel=1e-10)
+    # the residual is what the five kept directions miss: sigma_6 and the noise
+    assert 0.5 < second.extra["rp_residual"] / np.linalg.norm(y - V[:, :5] @ (V[:, :5].T @ y)) < 2.0
+    low = (U[:, :3] * s[:3]) @ V[:, :3].T
+    f1 = svt.frsvt(low, 2.0, l, 1, seed=5, stream=0)
+    f2 = svt.frsvt(low, 2.0, l, 1, seed=5, stream=1, Q_prev=f1.Q_tilde)
+    assert f1.Q_tilde.shape[1] == 3 and f2.extra["rp_residual"] <= 1e-12 * np.linalg.norm(low)
