@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kAdThr) k_ad_core(const float* __restrict__ Z,
   extern __shared__ __align__(16) unsigned char dsm[];
   SmallWs<LP> w = carve_small_ws<LP>(dsm, kAdGacc);
   const int tid = threadIdx.x;
-  for (int e = tid; e < LP * LP; e += kAdThr) w.G[e] = 0.0;
+  for (int e = tid; e < LP * LP; e += kAdThr) w.G[e] = df64{0.f, 0.f};
   __syncthreads();
   block_inner<LP>(Z, m, 0, 0, l, l, true, w.G, w.gacc, w.gacc_n);
   const int sweeps = core_svd_block<LP>(w, l, rank_tol, max_sweeps);

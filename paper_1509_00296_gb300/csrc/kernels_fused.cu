@@ -97,14 +97,7 @@ k_sc_orth(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const 
   SmallWs<LP> w = carve_small_ws<LP>(dsm, kGacc);
   int keep = use_rp ? dst->keep : 0;
   keep = max(0, min(keep, l));
-  for (int64_t e = threadIdx.x; e < n * LP; e += kThreads) {
-    const int c = static_cast<int>(e % LP);
-    const int64_t i = e / LP;
-    float v = 0.f;
-    if (c < keep) v = Qt[e];
-    else if (c < l) v = __ldcg(Y + i * LP + (c - keep));
-    w.W[e] = v;
-  }
+  load_basis_block<LP>(w.W, static_cast<int>(n), keep, l, Qt, Y);
   __syncthreads();
   float rp_res = -1.f;
   const int s = orth_block<LP>(w, n, keep, l, rank_tol, 2, &rp_res);
@@ -220,7 +213,7 @@ k_lr(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const float
       const int lo = a < b ? a : b, hi = a < b ? b : a;
       v = __ldcg(Gout + (lo * LP - lo * (lo - 1) / 2 + (hi - lo)));
     }
-    w.G[e] = v;
+    w.G[e] = df_from_double(v);
   }
   __syncthreads();
   const float tau = tau_from_mu ? static_cast<float>(1.0 / dst->mu) : tau_host;

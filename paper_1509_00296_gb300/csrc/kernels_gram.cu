@@ -99,9 +99,9 @@ k_gram_core(const float* __restrict__ Z, int64_t m, int n, int64_t rpc, const fl
       const int lo = a < b ? a : b, hi = a < b ? b : a;
       v = __ldcg(Gout + (lo * LP - lo * (lo - 1) / 2 + (hi - lo)));
     }
-    w.G[e] = v;
+    w.G[e] = df_from_double(v);
   }
-  for (int e = threadIdx.x; e < n * LP; e += kGThr) w.W[e] = Q[e];
+  block_copy(w.W, Q, n * LP);
   __syncthreads();
   const float tau = tau_from_mu ? static_cast<float>(1.0 / dst->mu) : tau_host;
   core_block<LP>(w, w.W, n, l, tau, update_rp, advance_counter, Rf, Qt, dst, rank_tol, max_sweeps);

@@ -55,7 +55,7 @@ k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, 
         float* __restrict__ Z, DevState* __restrict__ dst) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kMaxNS], hidone[kMaxNS], lo_ready[kMaxNS], empty[kMaxNS], acc_full[2],
-      acc_empty[2], fin;
+      acc_empty[2], fin, qready;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkc = (n + kBK - 1) / kBK;
@@ -69,17 +69,6 @@ k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, 
   const int total = nb * nkc;
   constexpr int kDrainQ = LP / 16;                                 // lane quarters holding stacked rows
 
-  for (int e = threadIdx.x; e < static_cast<int>(qbytes / 4); e += kTcThreads) reinterpret_cast<float*>(Qs)[e] = 0.f;
-  __syncthreads();
-  for (int e = threadIdx.x; e < nkc * kBK * LP; e += kTcThreads) {
-    const int k = e % LP, j = e / LP;                  // j: column of A (K index)
-    const float q = (j < n) ? Q[static_cast<int64_t>(j) * LP + k] : 0.f;
-    const float h = tf32_hi(q);
-    unsigned char* qc = Qs + static_cast<uint32_t>(j / kBK) * qchunk;
-    *reinterpret_cast<float*>(qc + sw128_offset(stack_row(k, 0), j % kBK)) = h;
-    *reinterpret_cast<float*>(qc + sw128_offset(stack_row(k, 1), j % kBK)) = q - h;
-  }
-  fence_proxy_async();
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
@@ -92,12 +81,45 @@ k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, 
       mbar_init(&acc_empty[b], kDrainQ);
     }
     mbar_init(&fin, 1);
+    mbar_init(&qready, kDrainWarps + kSplitWarps);
     fence_mbar_init();
   }
   if (warp == 1) tmem_alloc(&tmem_base, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // The producer starts streaming A at once; meanwhile the drain and split warps stage Q^T
+  // (hi / lo, stacked) and zero the rest of the M window, then release the MMA issuer.
+  if (warp >= 2) {
+    const int t = threadIdx.x - 64, nst = kTcThreads - 64;
+    const int tail0 = nkc * static_cast<int>(qchunk) / 4;
+    for (int e = tail0 + t; e < static_cast<int>(qbytes / 4); e += nst) reinterpret_cast<float*>(Qs)[e] = 0.f;
+    constexpr int U = 8;
+    const int count = nkc * kBK * LP;
+    for (int e0 = t; e0 < count; e0 += U * nst) {
+      float q[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * nst;
+        const int k = e % LP, j = e / LP;              // j: column of A (K index)
+        q[u] = (e < count && j < n) ? Q[static_cast<int64_t>(j) * LP + k] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * nst;
+        if (e < count) {
+          const int k = e % LP, j = e / LP;
+          const float h = tf32_hi(q[u]);
+          unsigned char* qc = Qs + static_cast<uint32_t>(j / kBK) * qchunk;
+          *reinterpret_cast<float*>(qc + sw128_offset(stack_row(k, 0), j % kBK)) = h;
+          *reinterpret_cast<float*>(qc + sw128_offset(stack_row(k, 1), j % kBK)) = q[u] - h;
+        }
+      }
+    }
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&qready);
+  }
   const uint32_t tbase = tmem_base;
   bool ok = true;
 
@@ -119,6 +141,12 @@ k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, 
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_tf32(128, kBN);
+      if (!mbar_wait(&qready, 0u)) {
+        ok = false;
+        atomicOr(&dst->status, kDevTimeout);
+      }
+      // K-steps (8 columns each) that hold columns of A: the last chunk may be partly padding
+      auto ksteps = [&](int c) { const int rem = n - c * kBK; return rem >= kBK ? kBK / 8 : (rem + 7) / 8; };
       // A_lo MMAs of chunk g (after the split warps rewrote its stage); closes the block.
       auto issue_lo = [&](int g) {
         const int s = g % ns, u = g / ns, c = g % nkc, b = g / nkc;
@@ -128,10 +156,12 @@ k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, 
         }
         tc_fence_after();
         const uint32_t d = tbase + static_cast<uint32_t>((b & 1) * kBN);
+        const int nks = ksteps(c);
 #pragma unroll
         for (int ks = 0; ks < kBK / 8; ++ks)
-          tc_mma_tf32(d, smem_desc_sw128(Qs + c * qchunk + 32 * ks, 16, 1024),
-                      smem_desc_sw128(ring + s * kChunkBytes + 32 * ks, 16, 1024), idesc, true);
+          if (ks < nks)
+            tc_mma_tf32(d, smem_desc_sw128(Qs + c * qchunk + 32 * ks, 16, 1024),
+                        smem_desc_sw128(ring + s * kChunkBytes + 32 * ks, 16, 1024), idesc, true);
         tc_commit(&empty[s]);
         if (c == nkc - 1) tc_commit(&acc_full[b & 1]);
       };
@@ -148,10 +178,12 @@ k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, 
         }
         tc_fence_after();
         const uint32_t d = tbase + static_cast<uint32_t>((b & 1) * kBN);
+        const int nks = ksteps(c);
 #pragma unroll
         for (int ks = 0; ks < kBK / 8; ++ks)
-          tc_mma_tf32(d, smem_desc_sw128(Qs + c * qchunk + 32 * ks, 16, 1024),
-                      smem_desc_sw128(ring + s * kChunkBytes + 32 * ks, 16, 1024), idesc, c > 0 || ks > 0);
+          if (ks < nks)
+            tc_mma_tf32(d, smem_desc_sw128(Qs + c * qchunk + 32 * ks, 16, 1024),
+                        smem_desc_sw128(ring + s * kChunkBytes + 32 * ks, 16, 1024), idesc, c > 0 || ks > 0);
         tc_commit(&hidone[s]);
         if (g > 0) issue_lo(g - 1);
       }
@@ -199,11 +231,15 @@ k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, 
         atomicOr(&dst->status, kDevTimeout);
       }
       float4* a = reinterpret_cast<float4*>(ring + s * kChunkBytes);
+      // 16-byte unit e: row e / 8 of the tile, logical column group (e % 8) ^ (row % 8) (128-byte swizzle)
+      const int cvalid = n - (g % nkc) * kBK;
 #pragma unroll
       for (int i = 0; i < static_cast<int>(kChunkBytes / 16 / (32 * kSplitWarps)); ++i) {
         const int e = t + 32 * kSplitWarps * i;
-        const float4 v = a[e];
-        a[e] = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+        if (4 * ((e & 7) ^ ((e >> 3) & 7)) < cvalid) {
+          const float4 v = a[e];
+          a[e] = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+        }
       }
       fence_proxy_async();
       __syncwarp();

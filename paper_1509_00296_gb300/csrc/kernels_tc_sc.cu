@@ -269,14 +269,7 @@ k_tc_sc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   if (l <= 0) l = min(max(dst->l_cur, 1), LP);            // adaptive rank prediction: l lives on the device
   int keep = use_rp ? dst->keep : 0;
   keep = max(0, min(keep, l));
-  for (int e = threadIdx.x; e < n * LP; e += kThr) {
-    const int col = e % LP;
-    const int i = e / LP;
-    float v = 0.f;
-    if (col < keep) v = Qt[e];
-    else if (col < l) v = __ldcg(Y + i * LP + (col - keep));
-    w.W[e] = v;
-  }
+  load_basis_block<LP>(w.W, n, keep, l, Qt, Y);
   __syncthreads();
   float rp_res = -1.f;
   const int s = orth_block<LP>(w, n, keep, l, rank_tol, passes, &rp_res);

@@ -217,14 +217,7 @@ k_tp_sc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   SmallWs<LP> w = carve_small_ws<LP>(dsm, kGacc);
   int keep = use_rp ? dst->keep : 0;
   keep = max(0, min(keep, l));
-  for (int e = threadIdx.x; e < n * LP; e += NT) {
-    const int col = e % LP;
-    const int i = e / LP;
-    float v = 0.f;
-    if (col < keep) v = Qt[e];
-    else if (col < l) v = __ldcg(Y + i * LP + (col - keep));
-    w.W[e] = v;
-  }
+  load_basis_block<LP>(w.W, n, keep, l, Qt, Y);
   __syncthreads();
   float rp_res = -1.f;
   const int s = orth_block<LP>(w, n, keep, l, rank_tol, passes, &rp_res);
@@ -354,9 +347,9 @@ k_tp_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int np4, int6
       const int lo = a < b ? a : b, hi = a < b ? b : a;
       v = __ldcg(Gout + (lo * LP - lo * (lo - 1) / 2 + (hi - lo)));
     }
-    w.G[e] = v;
+    w.G[e] = df_from_double(v);
   }
-  for (int e = threadIdx.x; e < n * LP; e += NT) w.W[e] = Q[e];       // the basis, staged
+  block_copy(w.W, Q, n * LP);                                         // the basis, staged
   __syncthreads();
   const float tau = tau_from_mu ? static_cast<float>(1.0 / dst->mu) : tau_host;
   core_block<LP>(w, w.W, n, l, tau, update_rp, advance_counter, Rf, Qt, dst, rank_tol, max_sweeps);

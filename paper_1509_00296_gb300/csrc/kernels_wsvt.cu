@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(NT) k_wsvt_frsvt(WsvtArgs p) {
       orth_block<LP>(w, s, 0, ls, p.rank_tol, 2);
     }
     mul_aht();                                     // Z = A_h^T Q = B^T
-    for (int e = tid; e < LP * LP; e += NT) w.G[e] = 0.0;
+    for (int e = tid; e < LP * LP; e += NT) w.G[e] = df64{0.f, 0.f};
     __syncthreads();
     block_inner<LP>(Zb, L, 0, 0, ls, ls, true, w.G, w.gacc, w.gacc_n);
     core_svd_block<LP>(w, ls, p.rank_tol, p.max_sweeps);

@@ -25,10 +25,10 @@ namespace frsvt {
 // Shared-memory workspace of orth_block / core_block, carved from one buffer.
 template <int LP>
 struct SmallWs {
-  double* G;        // LP x LP
-  double* R;        // LP x LP
-  double* gdiag;    // LP (original diagonal)
-  double* gacc;     // gacc_n partial sums
+  df64* G;          // LP x LP (double-float)
+  df64* R;          // LP x LP (double-float)
+  double* gdiag;    // LP (spare)
+  df64* gacc;       // gacc_n partial sums (double-float)
   float* Rf32;      // LP x LP  (FP32 copy of R / Jacobi columns)
   float* rinv;      // LP       (FP32 1 / R_jj, 0 for dropped)
   float* Cm;        // LP x LP  (projection coefficients / M)
@@ -54,11 +54,11 @@ template <int LP>
 __device__ SmallWs<LP> carve_small_ws(unsigned char* base, int gacc_n) {
   SmallWs<LP> w;
   w.gacc_n = gacc_n;
-  double* d = reinterpret_cast<double*>(base);
+  df64* d = reinterpret_cast<df64*>(base);                  // 8-byte entries, same layout as double
   w.G = d;
   w.R = w.G + LP * LP;
-  w.gdiag = w.R + LP * LP;
-  w.gacc = w.gdiag + LP;
+  w.gdiag = reinterpret_cast<double*>(w.R + LP * LP);
+  w.gacc = reinterpret_cast<df64*>(w.gdiag + LP);
   float* f = reinterpret_cast<float*>(w.gacc + gacc_n);
   w.Rf32 = f;
   w.rinv = w.Rf32 + LP * LP;
@@ -78,109 +78,152 @@ __device__ __forceinline__ void decode_pair_sym(int pr, int p, int& a, int& b) {
 
 // G[a][b] = sum_i X[i][ca + a] * X[i][cb + b] for the (a, b) pairs requested, accumulated
 // in double-float over the rows i < ns of X (row stride LP).  sym: a <= b < na (symmetric, both
-// triangles written); otherwise a < na, b < nb.  Block-wide; ends with __syncthreads.
+// triangles written); otherwise a < na, b < nb.  Up to eight row groups split the rows (four
+// independent chains each); their partial sums are added in double-float too: no FP64
+// instruction runs here (GB300's FP64 pipe issues a warp instruction in many cycles).
+// Block-wide; ends with __syncthreads.
 template <int LP>
-__device__ void block_inner(const float* X, int64_t ns, int ca, int cb, int na, int nb, bool sym, double* G,
-                            double* gacc, int gacc_n) {
+__device__ void block_inner(const float* X, int64_t ns, int ca, int cb, int na, int nb, bool sym, df64* G,
+                            df64* gacc, int gacc_n) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int np = sym ? na * (na + 1) / 2 : na * nb;
   if (np == 0) { __syncthreads(); return; }
   int groups = gacc_n / np;
   if (groups > nt / np) groups = nt / np;
+  if (groups > 8) groups = 8;
   if (groups < 1) groups = 1;
   for (int t = tid; t < np * groups; t += nt) {
     const int pr = t % np, g = t / np;
     int a, b;
     if (sym) decode_pair_sym(pr, na, a, b);
     else { a = pr / nb; b = pr % nb; }
+    const float* xa = X + ca + a;
+    const float* xb = X + cb + b;
     df64 acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // 4 independent chains
     int64_t i = g;
     for (; i + 3 * groups < ns; i += 4 * groups) {
+      float va[4], vb[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        df64_add_prod(acc[u], X[(i + u * groups) * LP + ca + a], X[(i + u * groups) * LP + cb + b]);
+      for (int u = 0; u < 4; ++u) {
+        va[u] = xa[(i + u * groups) * LP];
+        vb[u] = xb[(i + u * groups) * LP];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) df64_add_prod(acc[u], va[u], vb[u]);
     }
-    for (; i < ns; i += groups) df64_add_prod(acc[0], X[i * LP + ca + a], X[i * LP + cb + b]);
-    gacc[t] = df64_value(df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3])));
+    for (; i < ns; i += groups) df64_add_prod(acc[0], xa[i * LP], xb[i * LP]);
+    gacc[t] = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
   }
   __syncthreads();
   for (int pr = tid; pr < np; pr += nt) {
     int a, b;
     if (sym) decode_pair_sym(pr, na, a, b);
     else { a = pr / nb; b = pr % nb; }
-    double s = 0.0;
-    for (int g = 0; g < groups; ++g) s += gacc[g * np + pr];
-    G[a * LP + b] = s;
-    if (sym) G[b * LP + a] = s;
+    df64 v = gacc[pr];
+    for (int g = 1; g < groups; ++g) v = df_add(v, gacc[g * np + pr]);
+    G[a * LP + b] = v;
+    if (sym) G[b * LP + a] = v;
   }
   __syncthreads();
 }
 
-// Right-looking Cholesky G = R^T R (upper R) of the leading p x p block, by warp 0, with
-// column drops: column j is dropped (row j of R zero, rinv[j] = 0) when its pivot is not
-// above rank_tol * (original G_jj), when G_jj is below 1e-15 of the largest diagonal, or when
-// it is not a finite positive number.  G is overwritten.  Returns via iv[0..p) the drop flags.
-// Block-wide (contains __syncthreads).
+// W (ns x LP, shared) <- [Qt[:, :keep] | Y[:, :l - keep] | 0] (global; Y is read through L2).
+// Each thread issues U independent loads before its shared stores, so the copy costs one memory
+// latency per U elements instead of one per element.
+template <int LP, int U = 8>
+__device__ void load_basis_block(float* W, int ns, int keep, int l, const float* Qt, const float* Y) {
+  const int count = ns * LP, nt = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < count; e0 += U * nt) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nt;
+      const int col = e % LP, i = e / LP;
+      v[u] = 0.f;
+      if (e < count) {
+        if (col < keep) v[u] = Qt[e];
+        else if (col < l) v[u] = __ldcg(Y + i * LP + (col - keep));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nt;
+      if (e < count) W[e] = v[u];
+    }
+  }
+}
+
+// dst[e] = src[e], e < count (U loads in flight per thread).
+template <int U = 8>
+__device__ void block_copy(float* dst, const float* src, int count) {
+  const int nt = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < count; e0 += U * nt) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nt;
+      v[u] = (e < count) ? src[e] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nt;
+      if (e < count) dst[e] = v[u];
+    }
+  }
+}
+
+// Right-looking Cholesky G = R^T R (upper R) of the leading p x p block of the double-float
+// G, by warp 0, with column drops: column j is dropped (row j of R zero, rinv[j] = 0) when its
+// pivot is not above rank_tol * (original G_jj), when G_jj is below 1e-15 of the largest
+// diagonal, or when it is not a finite positive number.  G is overwritten.  Returns via
+// iv[0..p) the drop flags.  Block-wide (contains __syncthreads).
 //
 // The factorization runs in double-float arithmetic on the FP32 pipes (~48 significant bits):
 // on GB300 every FP64 operation of this serial chain costs far more latency than the dozen
-// FP32 operations of its double-float counterpart.  G (double) is converted in place.
+// FP32 operations of its double-float counterpart.  Lane b owns column b of the trailing
+// block: at step j it forms R[j][b] and subtracts R[j][a] R[j][b] from G[a][b] for j < a <= b.
 template <int LP>
 __device__ void block_cholesky(SmallWs<LP>& w, int p, double rank_tol) {
+  static_assert(LP <= 32, "one lane per column");
   const int tid = threadIdx.x;
-  df64* Gd = reinterpret_cast<df64*>(w.G);        // same 8 bytes per entry as the double
-  df64* Rd = reinterpret_cast<df64*>(w.R);
-  float* thr = w.vec + 2 * LP;                    // drop thresholds on the pivots
-  float* g0f = w.vec + 3 * LP;                    // original diagonal
+  df64* Gd = w.G;
+  df64* Rd = w.R;
   int* dropped = w.iv;
-  if (tid < LP) {
-    const double g0 = (tid < p) ? w.G[tid * LP + tid] : 0.0;
-    thr[tid] = static_cast<float>(rank_tol * g0);
-    g0f[tid] = static_cast<float>(g0);
-  }
-  __syncthreads();
-  for (int e = tid; e < LP * LP; e += blockDim.x) {
-    const double v = w.G[e];
-    Gd[e] = df_from_double(v);
-    Rd[e] = df64{0.f, 0.f};
-  }
-  __syncthreads();
   if (tid < 32) {
     const int lane = tid;
-    float maxdiag = 0.f;
-    for (int a = 0; a < p; ++a) maxdiag = fmaxf(maxdiag, g0f[a]);
+    const float tolf = static_cast<float>(rank_tol);
+    const float g0 = (lane < p) ? Gd[lane * LP + lane].hi : 0.f;   // original diagonal
+    float maxdiag = g0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxdiag = fmaxf(maxdiag, __shfl_xor_sync(0xffffffffu, maxdiag, o));
     for (int j = 0; j < p; ++j) {
       const df64 d = Gd[j * LP + j];
-      const bool drop = !(d.hi > thr[j]) || !(g0f[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
+      const float g0j = __shfl_sync(0xffffffffu, g0, j);
+      const df64 gjb = (lane > j && lane < p) ? Gd[j * LP + lane] : df64{0.f, 0.f};
+      const bool drop = !(d.hi > tolf * g0j) || !(g0j > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
       df64 inv{0.f, 0.f}, rjj{0.f, 0.f};
       if (!drop) {
         inv = df_rsqrt(d);
         rjj = df_mul(d, inv);
       }
-      if (lane < LP) {
-        df64 v{0.f, 0.f};
-        if (lane == j) v = rjj;
-        else if (lane > j && lane < p && !drop) v = df_mul(Gd[j * LP + lane], inv);
-        Rd[j * LP + lane] = v;
-        if (lane == j) {
-          dropped[j] = drop ? 1 : 0;
-          w.rinv[j] = inv.hi;
-        }
+      df64 rjb{0.f, 0.f};
+      if (lane > j && lane < p && !drop) rjb = df_mul(gjb, inv);
+      if (lane < LP) Rd[j * LP + lane] = (lane == j) ? rjj : rjb;
+      if (lane == j) {
+        dropped[j] = drop ? 1 : 0;
+        w.rinv[j] = inv.hi;
       }
       __syncwarp();
-      // trailing update G[a][b] -= R[j][a] R[j][b] over the pairs j < a <= b < p, spread over the
-      // lanes: pair t of the q x q trailing triangle is (a, b) = (j + 1 + t / q', ...) decoded below
-      if (!drop) {
-        const int q = p - j - 1;
-        for (int t = lane; t < q * q; t += 32) {
-          const int a = j + 1 + t / q, b = j + 1 + t % q;
-          if (a <= b) Gd[a * LP + b] = df_add(Gd[a * LP + b], df_neg(df_mul(Rd[j * LP + a], Rd[j * LP + b])));
-        }
+      if (!drop && lane > j && lane < p) {
+#pragma unroll 4
+        for (int a = j + 1; a <= lane; ++a)
+          Gd[a * LP + lane] = df_add(Gd[a * LP + lane], df_neg(df_mul(Rd[j * LP + a], rjb)));
       }
       __syncwarp();
     }
     if (lane < LP) {
-      for (int a = 0; a < LP; ++a) w.Rf32[a * LP + lane] = Rd[a * LP + lane].hi;
+      for (int a = p; a < LP; ++a) Rd[a * LP + lane] = df64{0.f, 0.f};
+      for (int a = 0; a < LP; ++a) w.Rf32[a * LP + lane] = (a < p) ? Rd[a * LP + lane].hi : 0.f;
       if (lane >= p) w.rinv[lane] = 0.f;
     }
   }
@@ -228,7 +271,7 @@ __device__ int orth_block(SmallWs<LP>& w, int64_t ns, int keep, int l, double ra
       block_inner<LP>(W, ns, 0, keep, keep, p, false, w.G, w.gacc, w.gacc_n);
       for (int e = threadIdx.x; e < keep * p; e += blockDim.x) {
         const int a = e / p, b = e % p;
-        w.Cm[a * LP + b] = static_cast<float>(w.G[a * LP + b]);
+        w.Cm[a * LP + b] = w.G[a * LP + b].hi;
       }
       __syncthreads();
       for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
@@ -250,7 +293,7 @@ __device__ int orth_block(SmallWs<LP>& w, int64_t ns, int keep, int l, double ra
   if (rp_res != nullptr && threadIdx.x == 0 && (keep == 0 || p == 0)) *rp_res = -1.f;
   for (int pass = 0; pass < passes && p > 0; ++pass) {
     block_inner<LP>(W, ns, keep, keep, p, p, true, w.G, w.gacc, w.gacc_n);
-    if (pass == 0 && keep > 0 && rp_res != nullptr && threadIdx.x == 0) *rp_res = sqrtf(static_cast<float>(w.G[0]));
+    if (pass == 0 && keep > 0 && rp_res != nullptr && threadIdx.x == 0) *rp_res = sqrtf(w.G[0].hi);
     block_cholesky<LP>(w, p, rank_tol);
     block_trsm_rows<LP>(w, W, ns, keep, p);
     kept = 0;
@@ -395,18 +438,52 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
   const int l_next = ap_a > 0 ? min(r + (r < l ? ap_a : dst->ap_pn), dst->ap_b) : l;
   const int keep = update_rp ? max(0, min(r, l_next - (ap_a > 0 ? ap_a : 2))) : 0;
   __syncthreads();
-  for (int64_t e = tid; e < ns * LP; e += nt) {
-    const int64_t i = e / LP;
-    const int k = static_cast<int>(e % LP);
-    float acc = 0.f, accq = 0.f;
-    const int pk = (k < keep) ? perm[k] : 0;
-    for (int a = 0; a < LP; ++a) {
-      const float qa = Q[i * LP + a];
-      acc = fmaf(qa, M[a * LP + k], acc);
-      accq = fmaf(qa, w.U[a * LP + pk], accq);
+  // Q~ columns in order: Up[a][k] = U[a][perm[k]] for k < keep (the Jacobi columns in Rf32 are dead)
+  float* Up = w.Rf32;
+  for (int e = tid; e < LP * LP; e += nt) {
+    const int a = e / LP, k = e % LP;
+    Up[e] = (k < keep) ? w.U[a * LP + perm[k]] : 0.f;
+  }
+  __syncthreads();
+  // one row of Q per thread: Rf[i] = Q[i] M and Q~[i] = Q[i] Up, M / Up rows read as float4 broadcasts
+  for (int64_t i = tid; i < ns; i += nt) {
+    float q[LP], rf[LP], qt[LP];
+#pragma unroll
+    for (int a4 = 0; a4 < LP / 4; ++a4) {
+      const float4 v = reinterpret_cast<const float4*>(Q + i * LP)[a4];
+      q[4 * a4] = v.x; q[4 * a4 + 1] = v.y; q[4 * a4 + 2] = v.z; q[4 * a4 + 3] = v.w;
     }
-    Rf[e] = acc;
-    if (update_rp && k < keep) Qt[e] = accq;
+#pragma unroll
+    for (int k = 0; k < LP; ++k) rf[k] = qt[k] = 0.f;
+#pragma unroll
+    for (int a = 0; a < LP; ++a) {
+#pragma unroll
+      for (int k4 = 0; k4 < LP / 4; ++k4) {
+        const float4 m4 = reinterpret_cast<const float4*>(M + a * LP)[k4];
+        rf[4 * k4] = fmaf(q[a], m4.x, rf[4 * k4]);
+        rf[4 * k4 + 1] = fmaf(q[a], m4.y, rf[4 * k4 + 1]);
+        rf[4 * k4 + 2] = fmaf(q[a], m4.z, rf[4 * k4 + 2]);
+        rf[4 * k4 + 3] = fmaf(q[a], m4.w, rf[4 * k4 + 3]);
+      }
+      if (update_rp) {
+#pragma unroll
+        for (int k4 = 0; k4 < LP / 4; ++k4) {
+          const float4 u4 = reinterpret_cast<const float4*>(Up + a * LP)[k4];
+          qt[4 * k4] = fmaf(q[a], u4.x, qt[4 * k4]);
+          qt[4 * k4 + 1] = fmaf(q[a], u4.y, qt[4 * k4 + 1]);
+          qt[4 * k4 + 2] = fmaf(q[a], u4.z, qt[4 * k4 + 2]);
+          qt[4 * k4 + 3] = fmaf(q[a], u4.w, qt[4 * k4 + 3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k4 = 0; k4 < LP / 4; ++k4)
+      reinterpret_cast<float4*>(Rf + i * LP)[k4] =
+          make_float4(rf[4 * k4], rf[4 * k4 + 1], rf[4 * k4 + 2], rf[4 * k4 + 3]);
+    if (update_rp)
+#pragma unroll
+      for (int k = 0; k < LP; ++k)
+        if (k < keep) Qt[i * LP + k] = qt[k];
   }
   if (tid == 0) {
     dst->r = r;
