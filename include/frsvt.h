@@ -71,6 +71,11 @@ typedef enum frsvt_precision {
 } frsvt_precision;
 
 #define FRSVT_CFG_ADJOINT 1      /* allocate the workspace of frsvt_svt_save / frsvt_backward */
+#define FRSVT_CFG_ORTH_LAST 2    /* orthonormalise only after the last power step (Sec. 2.5): the
+                                    intermediate steps of Alg. 1 step 14 pass A A^T Q on unnormalised.
+                                    X is the same in exact arithmetic (only span(Q) enters it); honoured
+                                    by the FP32 tensor-core path of the narrow basis, the other paths
+                                    orthonormalise every step. */
 
 typedef struct frsvt_config {
   int64_t m_max;                 /* largest row count served by the handle */

@@ -75,13 +75,14 @@ def ialm_rpca(O: np.ndarray, lam: float | None = None, mu0: float | None = None,
               max_iter: int = 500, method: str = "exact", l: int = 0, q: int = 0,
               seed: int = 0, range_prop: bool = True, fixed_iters: int | None = None,
               normO2: float | None = None, rank_tol: float = 1e-12,
-              ap: dict | None = None, partial_k: int = 0) -> RPCAResult:
+              ap: dict | None = None, partial_k: int = 0, orth_last: bool = False) -> RPCAResult:
     """Inexact ALM RPCA.  With ``ap`` (keys a, rho, gamma; FRSVT with range propagation) the
     sampling rate follows the adaptive rank prediction of Eq. 7: l_0 = ceil(0.1 b), b =
     ceil(gamma n) for the short side n, l_{i+1} = predict_rank(r_i, l_i, ...); the propagated
     basis keeps min(r_i, l_{i+1} - a) columns (r_i in the paper, capped so that at least a new
     Gaussian columns are drawn) and the call draws l_{i+1} - keep new ones.  The sampling rates
-    used are recorded in ``res.ls``."""
+    used are recorded in ``res.ls``.  ``orth_last`` is passed to every FRSVT call (orthonormalise
+    only after the last power step, Sec. 2.5)."""
     O = np.asarray(O, dtype=np.float64)
     m, n = O.shape
     if lam is None:
@@ -112,7 +113,8 @@ def ialm_rpca(O: np.ndarray, lam: float | None = None, mu0: float | None = None,
         elif method == "frsvt":
             l_k = l if ap is None else l_cur
             out = svt_mod.frsvt(Ain, 1.0 / mu, l_k, q, seed, k,
-                                Q_prev=Qt if range_prop else None, rank_tol=rank_tol, partial_k=partial_k)
+                                Q_prev=Qt if range_prop else None, rank_tol=rank_tol, partial_k=partial_k,
+                                orth_last=orth_last)
             L, r = out.X, out.r
             if ap is None:
                 Qt = out.Q_tilde

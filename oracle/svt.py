@@ -133,7 +133,7 @@ class FRSVTResult:
 
 def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
           Q_prev: np.ndarray | None = None, rank_tol: float = 1e-12,
-          problem: int = 0, weights=None, partial_k: int = 0) -> FRSVTResult:
+          problem: int = 0, weights=None, partial_k: int = 0, orth_last: bool = False) -> FRSVTResult:
     """Fast randomized SVT, Alg. 1, on A (m x n) in FP64.
 
     Omega is the (seed, stream, problem) Philox Gaussian matrix with max(m, n)
@@ -144,6 +144,9 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
     D_j > w_j.  With ``partial_k`` > 0 step 19 is the partial thresholding of
     the truncated nuclear norm (Table 6, Type B): the partial_k leading values
     of D are kept, the others soft-thresholded; r counts the non-zero ones.
+    With ``orth_last`` the power iteration orthonormalises only after its last
+    step (Sec. 2.5, Table 2 line 4): the intermediate steps carry A A^T Q on
+    as it is.  The span, hence X, is the same in exact arithmetic.
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
@@ -171,8 +174,9 @@ def frsvt(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,
 
     # Steps 13-15: power iteration Q = QR(A A^T Q), eta = q times.  The rank is
     # re-checked with a pivoted QR (Sec. 2.1, range propagation paragraph).
-    for _ in range(q):
-        Q = linalg.qr_cp(Ah @ (Ah.T @ Q), rank_tol)
+    for it in range(q):
+        Y = Ah @ (Ah.T @ Q)
+        Q = Y if (orth_last and it < q - 1) else linalg.qr_cp(Y, rank_tol)
 
     s = Q.shape[1]
     if s == 0:

@@ -103,7 +103,7 @@ cudaError_t launch_gram_core(int LP, const float* Z, int64_t m, int64_t n, int g
                              int max_sweeps, cudaStream_t st);
 cudaError_t prepare_tc_kernels(int smem_limit);
 cudaError_t launch_tc_lr(int LP, const CUtensorMap& tmA, int64_t m, int64_t n, int grid, int ns, const float* Q, float* Z,
-                         DevState* dst, cudaStream_t st);
+                         DevState* dst, cudaStream_t st, int normalize = 0);
 int tc_box_cols();
 int tc_box_rows();
 int tc_sc_stages(int LP, int64_t n, bool omega, size_t limit);
@@ -466,6 +466,7 @@ frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t 
     CUtensorMap tmAs;                       // 128-byte swizzled boxes for the tensor-core row pass
     if (!make_row_map_sw128(&tmAs, A, m, n, lda, tc_box_rows()))
       return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed for A (swizzled)");
+    const float* qin = h->Qs;                 // basis read by the next A Q pass
     for (int it = 0; it < q; ++it) {
       const int passes = it == q - 1 ? 2 : 1;
       if (bf && it < q - 1) {
@@ -475,11 +476,16 @@ frsvt_status range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t 
                                                          0, passes, h->Qt, h->Qs, tol, st));
         continue;
       }
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_tc_lr(LP, tmAs, m, n, h->sms, h->tc_lr_ns, h->Qs, h->Zl, h->dst, st));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_tc_lr(LP, tmAs, m, n, h->sms, h->tc_lr_ns, qin, h->Zl, h->dst, st,
+                                                      qin == h->Ys ? 1 : 0));
+      // Sec. 2.5: with FRSVT_CFG_ORTH_LAST the intermediate power steps skip the orthonormalisation
+      // and the next A Q pass reads Y = A^T Z itself (same span)
+      const bool skip = tcc && (h->cfg.flags & FRSVT_CFG_ORTH_LAST) && it < q - 1;
+      qin = skip ? h->Ys : h->Qs;
       if (tcc)
         FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_tc_sc(LP, tmAc, &tmZc, m, n, h->tc_sc_grid, h->tc_sc_ns,
                                                          h->cfg.seed, ctr, h->dst, h->cpart_sc, h->Ys, h->tickets,
-                                                         true, l, 0, passes, h->Qt, h->Qs, tol, st));
+                                                         !skip, l, 0, passes, h->Qt, h->Qs, tol, st));
       else
         FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_tp_sc(LP, tmA, &tmZ, m, n, rpc, G, h->cfg.seed, ctr, h->dst,
                                                          h->cpart_sc, h->Ys, h->tickets, l, 0, passes, h->Qt, h->Qs,

@@ -52,11 +52,12 @@ __host__ __device__ inline uint32_t lr_q_bytes(int LP, int n) {
 template <int LP>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, int ns, const float* __restrict__ Q,
-        float* __restrict__ Z, DevState* __restrict__ dst) {
+        float* __restrict__ Z, DevState* __restrict__ dst, int normalize) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kMaxNS], hidone[kMaxNS], lo_ready[kMaxNS], empty[kMaxNS], acc_full[2],
       acc_empty[2], fin, qready;
   __shared__ uint32_t tmem_base;
+  __shared__ float qmax[kDrainWarps + kSplitWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkc = (n + kBK - 1) / kBK;
   const uint32_t qchunk = 2u * LP * 128u;                          // stacked rows of one K-chunk
@@ -96,13 +97,33 @@ k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, 
     for (int e = tail0 + t; e < static_cast<int>(qbytes / 4); e += nst) reinterpret_cast<float*>(Qs)[e] = 0.f;
     constexpr int U = 8;
     const int count = nkc * kBK * LP;
+    // normalize: Q is an unnormalised power-step block (A^T A Q, Sec. 2.5); it is staged times the
+    // power of two 2^-e that brings its largest entry into [1/2, 1) (the same in every CTA: the max
+    // is exact), so repeated steps cannot leave the float range.  Z = A Q 2^-e has the same span.
+    float scale = 1.f;
+    if (normalize) {
+      float mx = 0.f;
+      for (int e = t; e < n * LP; e += nst) mx = fmaxf(mx, fabsf(Q[e]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) qmax[warp - 2] = mx;
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * (kDrainWarps + kSplitWarps)) : "memory");
+      mx = 0.f;
+#pragma unroll
+      for (int w = 0; w < kDrainWarps + kSplitWarps; ++w) mx = fmaxf(mx, qmax[w]);
+      if (mx > 0.f && mx < INFINITY) {
+        int ex;
+        (void)frexpf(mx, &ex);
+        scale = ldexpf(1.f, -ex);
+      }
+    }
     for (int e0 = t; e0 < count; e0 += U * nst) {
       float q[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int e = e0 + u * nst;
         const int k = e % LP, j = e / LP;              // j: column of A (K index)
-        q[u] = (e < count && j < n) ? Q[static_cast<int64_t>(j) * LP + k] : 0.f;
+        q[u] = (e < count && j < n) ? Q[static_cast<int64_t>(j) * LP + k] * scale : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -275,13 +296,13 @@ cudaError_t prepare_tc_kernels(int smem_limit) {
 
 // Z = A Q (A: m x n through tmA with 32-column x 256-row boxes and the 128-byte swizzle).
 cudaError_t launch_tc_lr(int LP, const CUtensorMap& tmA, int64_t m, int64_t n, int grid, int ns, const float* Q,
-                         float* Z, DevState* dst, cudaStream_t st) {
+                         float* Z, DevState* dst, cudaStream_t st, int normalize) {
   int64_t rpc = (m + grid - 1) / grid;
   rpc = (rpc + kBN - 1) / kBN * kBN;
   const size_t smem = tc_lr_smem(LP, n, ns);
   const int nn = static_cast<int>(n);
-  if (LP == 16) k_tc_lr<16><<<grid, kTcThreads, smem, st>>>(tmA, m, nn, rpc, ns, Q, Z, dst);
-  else k_tc_lr<32><<<grid, kTcThreads, smem, st>>>(tmA, m, nn, rpc, ns, Q, Z, dst);
+  if (LP == 16) k_tc_lr<16><<<grid, kTcThreads, smem, st>>>(tmA, m, nn, rpc, ns, Q, Z, dst, normalize);
+  else k_tc_lr<32><<<grid, kTcThreads, smem, st>>>(tmA, m, nn, rpc, ns, Q, Z, dst, normalize);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "FRSVT_OK", 1: "FRSVT_ERR_INVALID_ARG", 2: "FRSVT_ERR_UNSUPPO
 DEV_RANK_DEFICIENT, DEV_NOT_CONVERGED, DEV_NONFINITE, DEV_TIMEOUT, DEV_BAD_PROBLEM = 1, 2, 4, 8, 16
 WSVT_EXACT, WSVT_FRSVT = 0, 1
 CFG_ADJOINT = 1
+CFG_ORTH_LAST = 2
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 NPHASE = 10
 
@@ -146,9 +147,10 @@ class Handle:
 
     def __init__(self, m_max: int, n_max: int, l_max: int, q: int = 2, range_prop: bool = True,
                  seed: int = 0, max_jacobi_sweeps: int = 30, rank_tol: float = 1e-12, stream=None,
-                 adjoint: bool = False, precision: int = 0):
+                 adjoint: bool = False, precision: int = 0, orth_last: bool = False):
+        flags = (CFG_ADJOINT if adjoint else 0) | (CFG_ORTH_LAST if orth_last else 0)
         cfg = Config(m_max, n_max, l_max, q, 1 if range_prop else 0, precision, seed, max_jacobi_sweeps,
-                     CFG_ADJOINT if adjoint else 0, rank_tol)
+                     flags, rank_tol)
         h = _P()
         self._stream = stream
         st = lib().frsvt_create(ctypes.byref(h), ctypes.byref(cfg), _stream_ptr(stream))

@@ -111,6 +111,26 @@ def test_frsvt_range_propagation_sequence(fr, m, n):
             assert abs(info.rp_residual - want) <= 1e-3 * want + 1e-5 * np.linalg.norm(y), (t, info.rp_residual, want)
 
 
+@pytest.mark.parametrize("q", [2, 3])
+def test_frsvt_orth_last_matches_oracle(fr, q):
+    """FRSVT_CFG_ORTH_LAST (Sec. 2.5): the tensor-core path skips the orthonormalisation of the
+    intermediate power steps; X matches the oracle running the same variant, over a range-propagated
+    sequence of two calls."""
+    m, n, l = 3000, 200, 12
+    A, s = spectrum_matrix(m, n, 40, 0.85, 0.001, seed=91)
+    A = A.astype(np.float32).astype(np.float64)
+    tau = float(0.5 * (s[6] + s[7]))
+    h = fr.Handle(m, n, l, q=q, range_prop=True, seed=31, orth_last=True)
+    Qp = None
+    for t in range(2):
+        ref = svt.frsvt(A, tau, l, q, seed=31, stream=t, Q_prev=Qp, orth_last=True)
+        Qp = ref.Q_tilde
+        X = h.svt(to_gpu(A), tau, l).cpu().numpy()
+        info = h.info()
+        assert info.r == ref.r, t
+        assert rel_fro(X, ref.X) <= TOL, t
+
+
 def test_tau_above_sigma_max_gives_zero(fr):
     A, s = spectrum_matrix(400, 50, 10, 0.8, 0.0, seed=9)
     h = fr.Handle(400, 50, 8, q=1, range_prop=False)

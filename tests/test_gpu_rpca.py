@@ -19,14 +19,14 @@ def fr():
     return frsvt
 
 
-def run_gpu(fr, O, l, q, iters, seed, range_prop=True):
+def run_gpu(fr, O, l, q, iters, seed, range_prop=True, orth_last=False):
     import torch
     m, n = O.shape
     Og = torch.from_numpy(np.ascontiguousarray(O, dtype=np.float32)).cuda()
     S = torch.empty_like(Og)
     A = torch.empty_like(Og)
     L = torch.empty_like(Og)
-    h = fr.Handle(m, n, l, q=q, range_prop=range_prop, seed=seed)
+    h = fr.Handle(m, n, l, q=q, range_prop=range_prop, seed=seed, orth_last=orth_last)
     h.rpca_init(Og, S, A, 1.0 / np.sqrt(max(m, n)), 1.5, 1e7)
     hist = []
     for k in range(iters):
@@ -56,4 +56,19 @@ def test_rpca_video_full_size_parity(fr):
     L, S, hist, info = run_gpu(fr, O64, 10, 2, 6, 2002)
     assert rel_fro(L, ref.L) <= TOL
     assert rel_fro(S, ref.S) <= TOL
+    assert np.allclose(hist, ref.history, rtol=1e-3)
+
+
+def test_rpca_video_orth_last_parity(fr):
+    """The video workload with the orthonormalisation only after the last power step (Sec. 2.5) on the
+    tensor-core path: 6 iterations against the oracle running the same variant, and against the
+    default (orthonormalise every step) oracle run."""
+    O, _, _ = synth.video()
+    O64 = O.astype(np.float64)
+    ref = orpca.ialm_rpca(O64, method="frsvt", l=10, q=2, seed=2002, fixed_iters=6, orth_last=True)
+    ref_every = orpca.ialm_rpca(O64, method="frsvt", l=10, q=2, seed=2002, fixed_iters=6)
+    L, S, hist, info = run_gpu(fr, O64, 10, 2, 6, 2002, orth_last=True)
+    assert rel_fro(L, ref.L) <= TOL
+    assert rel_fro(S, ref.S) <= TOL
+    assert rel_fro(L, ref_every.L) <= TOL
     assert np.allclose(hist, ref.history, rtol=1e-3)

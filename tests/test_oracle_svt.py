@@ -452,3 +452,36 @@ def test_frsvt_reports_prop4_residual_of_first_new_column():
     f1 = svt.frsvt(low, 2.0, l, 1, seed=5, stream=0)
     f2 = svt.frsvt(low, 2.0, l, 1, seed=5, stream=1, Q_prev=f1.Q_tilde)
     assert f1.Q_tilde.shape[1] == 3 and f2.extra["rp_residual"] <= 1e-12 * np.linalg.norm(low)
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_frsvt_orth_last_same_result(q):
+    """Sec. 2.5: skipping the orthonormalisation of the intermediate power steps leaves span(Q), hence X,
+    unchanged in exact arithmetic; in FP64 on a moderately conditioned spectrum the two agree to 1e-9.
+    The basis handed to the core is still orthonormal (the last step keeps its QR)."""
+    rng = np.random.default_rng(501)
+    m, n, l = 400, 60, 12
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = 10.0 * 0.8 ** np.arange(n)
+    A = (U * s) @ V.T
+    tau = float(0.5 * (s[5] + s[6]))
+    ref = svt.frsvt(A, tau, l, q, seed=3, stream=0)
+    alt = svt.frsvt(A, tau, l, q, seed=3, stream=0, orth_last=True)
+    assert alt.r == ref.r
+    assert np.linalg.norm(alt.X - ref.X) <= 1e-9 * np.linalg.norm(ref.X)
+    QV = alt.extra["QV"]
+    assert np.abs(QV.T @ QV - np.eye(QV.shape[1])).max() <= 1e-12
+    # with range propagation as well
+    ref2 = svt.frsvt(A, tau, l, q, seed=3, stream=1, Q_prev=ref.Q_tilde)
+    alt2 = svt.frsvt(A, tau, l, q, seed=3, stream=1, Q_prev=ref.Q_tilde, orth_last=True)
+    assert np.linalg.norm(alt2.X - ref2.X) <= 1e-9 * np.linalg.norm(ref2.X)
+
+
+def test_frsvt_orth_last_q1_identical():
+    """q = 1 has no intermediate power step: the option changes nothing."""
+    rng = np.random.default_rng(502)
+    A = rng.standard_normal((120, 40))
+    a = svt.frsvt(A, 1.0, 8, 1, seed=4, stream=0)
+    b = svt.frsvt(A, 1.0, 8, 1, seed=4, stream=0, orth_last=True)
+    assert np.array_equal(a.X, b.X)
