@@ -62,14 +62,14 @@ __device__ bool cluster_split_reduce(T* part_sm, int count, T* cpart, T* out, un
         const int j = w % nv, h = w / nv;
         const float4* src = reinterpret_cast<const float4*>(cpart) + (e0 / 4 + j);
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int c0 = h; c0 < nclusters; c0 += 8 * H) {
-          float4 v[8];
+        for (int c0 = h; c0 < nclusters; c0 += 16 * H) {          // 16 loads in flight per thread
+          float4 v[16];
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
+          for (int u = 0; u < 16; ++u)
             v[u] = (c0 + u * H < nclusters) ? __ldcg(src + static_cast<int64_t>(c0 + u * H) * (count / 4))
                                             : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < 16; ++u) {
             acc.x += v[u].x;
             acc.y += v[u].y;
             acc.z += v[u].z;

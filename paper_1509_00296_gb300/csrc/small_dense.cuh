@@ -341,11 +341,17 @@ __device__ int core_svd_block(SmallWs<LP>& w, int l, double rank_tol, int max_sw
     for (int a = 0; a < LP; ++a) x[a] = (lane < N) ? Xt[lane * LP + a] : 0.f;
     for (int sweep = 0; sweep < max_sweeps && N >= 2; ++sweep) {
       bool rotated = false;
-      for (int rnd = 0; rnd < N - 1; ++rnd) {
+      const int N1 = N - 1;
+      for (int rnd = 0; rnd < N1; ++rnd) {
         int partner;
-        if (lane == N - 1) partner = rnd;
-        else if (lane == rnd) partner = N - 1;
-        else partner = ((2 * rnd - lane) % (N - 1) + (N - 1)) % (N - 1);
+        if (lane == N1) partner = rnd;
+        else if (lane == rnd) partner = N1;
+        else {                                   // (2 rnd - lane) mod (N - 1), argument in [-(N - 2), 2N - 4]
+          int v = 2 * rnd - lane;
+          v += (v < 0) ? N1 : 0;
+          v -= (v >= N1) ? N1 : 0;
+          partner = v;
+        }
         if (lane >= N) partner = lane;
         float y[LP];
 #pragma unroll
@@ -364,11 +370,17 @@ __device__ int core_svd_block(SmallWs<LP>& w, int l, double rank_tol, int max_sw
         }
         const float so = so0 + so1, sp = sp0 + sp1, gamma = g0 + g1;
         const float alpha = is_p ? so : sp, beta = is_p ? sp : so;  // column p, column q
-        if (lane < N && partner != lane && fabsf(gamma) > tol * sqrtf(alpha * beta) && alpha > 1e-30f &&
-            beta > 1e-30f) {
-          const float zeta = (beta - alpha) / (2.f * gamma);
-          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          const float c = rsqrtf(1.f + t * t);
+        // rotation test |gamma| > tol sqrt(alpha beta) with hardware reciprocal square roots, and
+        // the angle (Rutishauser's tan formula) with fast reciprocals: both lanes of a pair evaluate
+        // the same expressions on the same operands, so they still agree bit for bit; the rotation
+        // stays orthogonal to rounding through c = 1 / sqrt(1 + t^2), s = c t
+        if (lane < N && partner != lane && alpha > 1e-30f && beta > 1e-30f && alpha < 1e30f && beta < 1e30f &&
+            fabsf(gamma) * rsqrtf(alpha) * rsqrtf(beta) > tol) {
+          const float zeta = __fdividef(beta - alpha, 2.f * gamma);
+          const float az = fabsf(zeta);
+          const float t = az < 1e18f ? copysignf(__fdividef(1.f, az + sqrtf(fmaf(zeta, zeta, 1.f))), zeta)
+                                     : __fdividef(0.5f, zeta);
+          const float c = rsqrtf(fmaf(t, t, 1.f));
           const float sy = is_p ? -(c * t) : (c * t);           // x_p' = c x_p - s x_q, x_q' = s x_p + c x_q
 #pragma unroll
           for (int a = 0; a < LP; ++a) x[a] = fmaf(sy, y[a], c * x[a]);
@@ -445,45 +457,40 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
     Up[e] = (k < keep) ? w.U[a * LP + perm[k]] : 0.f;
   }
   __syncthreads();
-  // one row of Q per thread: Rf[i] = Q[i] M and Q~[i] = Q[i] Up, M / Up rows read as float4 broadcasts
-  for (int64_t i = tid; i < ns; i += nt) {
-    float q[LP], rf[LP], qt[LP];
+  // one row of Q per thread: Rf[i] = Q[i] M, then Q~[i] = Q[i] Up; the rows of M / Up are read as
+  // float4 broadcasts and the result row stays in registers (the loop over a is only partly
+  // unrolled so that the loads hoisted ahead of it do not exhaust the register file)
+  for (int pass = 0; pass < (update_rp && keep > 0 ? 2 : 1); ++pass) {
+    const float* F = pass == 0 ? M : Up;
+    float* out = pass == 0 ? Rf : Qt;
+    for (int64_t i = tid; i < ns; i += nt) {
+      const float* qrow = Q + i * LP;
+      float acc[LP];
 #pragma unroll
-    for (int a4 = 0; a4 < LP / 4; ++a4) {
-      const float4 v = reinterpret_cast<const float4*>(Q + i * LP)[a4];
-      q[4 * a4] = v.x; q[4 * a4 + 1] = v.y; q[4 * a4 + 2] = v.z; q[4 * a4 + 3] = v.w;
-    }
-#pragma unroll
-    for (int k = 0; k < LP; ++k) rf[k] = qt[k] = 0.f;
-#pragma unroll
-    for (int a = 0; a < LP; ++a) {
-#pragma unroll
-      for (int k4 = 0; k4 < LP / 4; ++k4) {
-        const float4 m4 = reinterpret_cast<const float4*>(M + a * LP)[k4];
-        rf[4 * k4] = fmaf(q[a], m4.x, rf[4 * k4]);
-        rf[4 * k4 + 1] = fmaf(q[a], m4.y, rf[4 * k4 + 1]);
-        rf[4 * k4 + 2] = fmaf(q[a], m4.z, rf[4 * k4 + 2]);
-        rf[4 * k4 + 3] = fmaf(q[a], m4.w, rf[4 * k4 + 3]);
-      }
-      if (update_rp) {
+      for (int k = 0; k < LP; ++k) acc[k] = 0.f;
+#pragma unroll 4
+      for (int a = 0; a < LP; ++a) {
+        const float qa = qrow[a];
 #pragma unroll
         for (int k4 = 0; k4 < LP / 4; ++k4) {
-          const float4 u4 = reinterpret_cast<const float4*>(Up + a * LP)[k4];
-          qt[4 * k4] = fmaf(q[a], u4.x, qt[4 * k4]);
-          qt[4 * k4 + 1] = fmaf(q[a], u4.y, qt[4 * k4 + 1]);
-          qt[4 * k4 + 2] = fmaf(q[a], u4.z, qt[4 * k4 + 2]);
-          qt[4 * k4 + 3] = fmaf(q[a], u4.w, qt[4 * k4 + 3]);
+          const float4 f4 = reinterpret_cast<const float4*>(F + a * LP)[k4];
+          acc[4 * k4] = fmaf(qa, f4.x, acc[4 * k4]);
+          acc[4 * k4 + 1] = fmaf(qa, f4.y, acc[4 * k4 + 1]);
+          acc[4 * k4 + 2] = fmaf(qa, f4.z, acc[4 * k4 + 2]);
+          acc[4 * k4 + 3] = fmaf(qa, f4.w, acc[4 * k4 + 3]);
         }
       }
+      if (pass == 0) {
+#pragma unroll
+        for (int k4 = 0; k4 < LP / 4; ++k4)
+          reinterpret_cast<float4*>(out + i * LP)[k4] =
+              make_float4(acc[4 * k4], acc[4 * k4 + 1], acc[4 * k4 + 2], acc[4 * k4 + 3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < LP; ++k)
+          if (k < keep) out[i * LP + k] = acc[k];
+      }
     }
-#pragma unroll
-    for (int k4 = 0; k4 < LP / 4; ++k4)
-      reinterpret_cast<float4*>(Rf + i * LP)[k4] =
-          make_float4(rf[4 * k4], rf[4 * k4 + 1], rf[4 * k4 + 2], rf[4 * k4 + 3]);
-    if (update_rp)
-#pragma unroll
-      for (int k = 0; k < LP; ++k)
-        if (k < keep) Qt[i * LP + k] = qt[k];
   }
   if (tid == 0) {
     dst->r = r;
