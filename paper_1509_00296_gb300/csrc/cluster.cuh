@@ -111,8 +111,7 @@ __device__ bool cluster_split_reduce(T* part_sm, int count, T* cpart, T* out, un
       out[e] = s;
     }
   }
-  __threadfence();
-  cl.sync();
+  cl.sync();                                   // the cluster barrier publishes out to the cluster
   if (rank == 0 && threadIdx.x == 0) *ticket = 0;   // ready for the next launch
   return true;
 }

@@ -960,7 +960,7 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
     const int64_t ntl = ntiles_max;
     const int64_t ncl_sc = cdiv(cdiv(h->target_ctas, 1), 8) + 1;          // clusters per tile, upper bound
     h->cpart_sc_elems = ntl * ncl_sc * 256 * LP;
-    h->cpart_alm_elems = ntl * ncl_sc;
+    h->cpart_alm_elems = ntl * ncl_sc + 2 * static_cast<int64_t>(h->sms);   // >= one partial per epilogue CTA
     const int64_t np = LP * (LP + 1) / 2;
     alloc(reinterpret_cast<void**>(&h->cpart_sc), sizeof(float) * h->cpart_sc_elems);
     alloc(reinterpret_cast<void**>(&h->cpart_lr), sizeof(double) * (h->lr_blocks / 8) * np);

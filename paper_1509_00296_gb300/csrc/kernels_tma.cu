@@ -356,16 +356,15 @@ k_tp_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int np4, int6
 }
 
 // ---------------------------------------------------------------- fused reconstruction + iALM update
-// Clusters of 4 (the cluster only serves the final one-value residual reduction): more of them
-// fit at once than clusters of 8, so the streaming kernel covers (nearly) every SM.
-constexpr int kAlmCL = 4;
+// One CTA per SM and no cluster: the kernel only reduces one value (the residual) across CTAs,
+// by per-CTA partials and a ticket, so every SM streams.
 // 256 consumer threads for either basis width: each holds four rows of Rf (4 LP registers), which
 // 512 threads (at most 96 registers each) would spill.
 constexpr int kAlmNC = 256;
 constexpr int kAlmNT = kAlmNC + 32;
 
 template <int LP>
-__global__ void __cluster_dims__(kAlmCL, 1, 1) __launch_bounds__(kAlmNT, 1)
+__global__ void __launch_bounds__(kAlmNT, 1)
 k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmS,
          const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ, int64_t m, int n, int np4,
          int64_t rpc, const float* __restrict__ Rf, float* __restrict__ S, float* __restrict__ A, int64_t ld,
@@ -531,14 +530,20 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w2 = 0; w2 < NT / 32; ++w2) t += red[w2];
-    mine = t;
+    cpart[blockIdx.x] = t;                       // this CTA's share of ||O - L - S'||^2
   }
-  const int nclusters = gridDim.x / kAlmCL;
-  if (!cluster_split_reduce<double, kAlmCL>(&mine, 1, cpart, rsum, tickets, blockIdx.x / kAlmCL, nclusters, &flag))
-    return;
-  if (cooperative_groups::this_cluster().block_rank() != 0) return;
+  if (!last_of(tickets, gridDim.x, &flag)) return;
+  // the CTA that finishes last adds the per-CTA partials in a fixed order (lane-strided, then the
+  // warp tree): the result does not depend on which CTA that is
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int b = lane; b < static_cast<int>(gridDim.x); b += 32) t += __ldcg(cpart + b);
+    t = warp_sum(t);
+    if (lane == 0) mine = t;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const double s2 = __ldcg(rsum);
+    const double s2 = mine;
     const double rr = (dst->normO_F > 0.0) ? sqrt(s2) / dst->normO_F : 0.0;
     dst->resid_ratio = rr;
     if (!isfinite(rr)) dst->status |= kDevNonfinite;
@@ -641,24 +646,18 @@ int tma_resident_grid(int LP, int64_t n) {
   return best * kCL;
 }
 
-// Resident grid of the epilogue kernel (clusters of kAlmCL).
+// Resident grid of the epilogue kernel (blocks per SM times SMs).
 int tma_alm_resident_grid(int LP, int64_t n) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kAlmCL, 1, 1);
-  cfg.blockDim = dim3(kAlmNT, 1, 1);
-  cfg.dynamicSmemBytes = tma_alm_smem(LP, n);
-  cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = kAlmCL;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
-  int nc = 0;
+  int per = 0, dev = 0, sms = 0;
   const void* fn = LP == 16 ? reinterpret_cast<const void*>(k_tp_alm<16>) : reinterpret_cast<const void*>(k_tp_alm<32>);
-  if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) nc = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kAlmNT, tma_alm_smem(LP, n)) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    per = 0;
+    sms = 0;
+  }
   (void)cudaGetLastError();
-  return nc * kAlmCL;
+  return per * sms;
 }
 
 cudaError_t prepare_tma_kernels(int smem_limit) {
