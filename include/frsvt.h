@@ -179,6 +179,13 @@ frsvt_status rpca_init(frsvt_handle* h, const float* O, float* S, float* A,
  * ldl) receives the low-rank iterate when given; otherwise L is never
  * materialised.  O, S, A share the leading dimension ld.  When residual is not
  * NULL the call synchronizes and writes ||O - L - S'||_F / ||O||_F there.
+ * The first call with a given (O, S, A, m, n, ld, l, L, ldl) captures the
+ * iteration's kernels into a CUDA graph on a stream private to the handle;
+ * later calls with the same arguments replay it on the handle's stream (the
+ * iteration's state lives on the device).  rpca_init, frsvt_reset,
+ * frsvt_set_stream, frsvt_set_rank_prediction and frsvt_set_partial retire
+ * the graph.  While the handle's stream is being captured by the caller, or
+ * with phase timing on, the kernels are launched directly.
  */
 frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
                             int64_t m, int64_t n, int64_t ld, int32_t l,

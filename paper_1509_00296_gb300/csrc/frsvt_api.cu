@@ -193,6 +193,27 @@ struct frsvt_handle {
   int lr_blocks = 8;
   int64_t last_m = -1, last_n = -1;
   int last_l = -1;
+  // rpca_ialm_step replays its launches from a CUDA graph captured on the first call with a given
+  // argument tuple (capture_stream is private to the handle; the graph runs on the user's stream).
+  // epoch changes whenever a setter changes what a step launches, which retires the graph.
+  struct StepKey {
+    const float* O;
+    float* S;
+    float* A;
+    int64_t m, n, ld;
+    int32_t l;
+    float* L;
+    int64_t ldl;
+    uint64_t epoch;
+    bool operator==(const StepKey& o) const {
+      return O == o.O && S == o.S && A == o.A && m == o.m && n == o.n && ld == o.ld && l == o.l && L == o.L &&
+             ldl == o.ldl && epoch == o.epoch;
+    }
+  };
+  uint64_t epoch = 1;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  StepKey step_key{};
   // wide basis (cfg.l_max > 32, LP = 128, any short side): basis-side matrices transposed
   // (128 x ld_m / ld_n), Z and Rf row-major (len x 128), K-split partials, Gram partials
   bool wide = false;
@@ -551,6 +572,10 @@ frsvt_status sync_rp_shape(frsvt_handle* h, int64_t m, int64_t n, int l) {
 }
 
 void free_all(frsvt_handle* h) {
+  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+  h->step_exec = nullptr;
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  h->capture_stream = nullptr;
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   h->ev_pool.clear();
   void* ptrs[] = {h->dst, h->Ys,       h->Qs,       h->Qt,        h->Zl,   h->Rf,   h->part,    h->gpart,
@@ -1015,11 +1040,13 @@ frsvt_status frsvt_destroy(frsvt_handle* h) {
 frsvt_status frsvt_set_stream(frsvt_handle* h, void* stream) {
   if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
   h->stream = static_cast<cudaStream_t>(stream);
+  h->epoch += 1;
   return FRSVT_OK;
 }
 
 frsvt_status frsvt_reset(frsvt_handle* h, uint64_t counter) {
   if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  h->epoch += 1;
   FRSVT_CK(cudaMemsetAsync(&h->dst->keep, 0, sizeof(int32_t), h->stream));
   FRSVT_CK(cudaMemcpyAsync(&h->dst->counter, &counter, sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
   FRSVT_CK(cudaStreamSynchronize(h->stream));   // the host value lives on this stack frame
@@ -1093,6 +1120,7 @@ frsvt_status frsvt_spectral_norm(frsvt_handle* h, const float* A, int64_t m, int
 frsvt_status rpca_init(frsvt_handle* h, const float* O, float* S, float* A, int64_t m, int64_t n, int64_t ld,
                        double lambda, double rho, double mu_bar_factor, double normO2, int32_t power_iters) {
   if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  h->epoch += 1;                                     // what a step launches may change
   frsvt_status s = check_shape(h, m, n);
   if (s != FRSVT_OK) return s;
   if ((s = check_matrix(h, O, m, n, ld, "O")) != FRSVT_OK) return s;
@@ -1124,27 +1152,16 @@ frsvt_status rpca_init(frsvt_handle* h, const float* O, float* S, float* A, int6
   return FRSVT_OK;
 }
 
-frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A, int64_t m, int64_t n, int64_t ld,
-                            int32_t l, float* L, int64_t ldl, double* residual) {
-  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
-  frsvt_status s = check_shape(h, m, n);
-  if (s != FRSVT_OK) return s;
-  if ((s = check_matrix(h, O, m, n, ld, "O")) != FRSVT_OK) return s;
-  if ((s = check_matrix(h, S, m, n, ld, "S")) != FRSVT_OK) return s;
-  if ((s = check_matrix(h, A, m, n, ld, "A")) != FRSVT_OK) return s;
-  if (L != nullptr && (s = check_matrix(h, L, m, n, ldl, "L")) != FRSVT_OK) return s;
-  if (l < 1 || l > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "l must be in [1, l_max]");
-  if (m == 0 || n == 0) return FRSVT_OK;
-  if (l > n) l = static_cast<int32_t>(n);
-  if (h->ap_a > 0) {                                   // adaptive rank prediction: l on the device
-    if (!(h->tma && n <= 256)) return fail(h, FRSVT_ERR_UNSUPPORTED, "rank prediction needs n <= 256");
-    if (h->ap_n != n && (s = ap_setup(h, n)) != FRSVT_OK) return s;
-    h->last_m = m;
-    h->last_n = n;
-    l = -1;
-  } else if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) {
-    return s;
-  }
+// The kernels of one iALM iteration (range finder, core, fused epilogue) on h->stream.
+static frsvt_status ialm_launches(frsvt_handle* h, const frsvt_handle::StepKey& k) {
+  const float* O = k.O;
+  float* S = k.S;
+  float* A = k.A;
+  const int64_t m = k.m, n = k.n, ld = k.ld;
+  const int l = k.l;
+  float* L = k.L;
+  const int64_t ldl = k.ldl;
+  frsvt_status s = FRSVT_OK;
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;   // the shadow is kept current by rpca_init / the epilogue
   if (h->wide) {
@@ -1178,6 +1195,78 @@ frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
   FRSVT_LAUNCH(FRSVT_PHASE_FINISH, launch_alm_finish(h->rpart, sp.nsplit * sp.ntiles, h->dst, h->stream));
   }
   }
+  return FRSVT_OK;
+}
+
+// Runs ialm_launches through a CUDA graph: captured on the handle's private stream the first time
+// a StepKey is seen, then replayed on the user's stream (one launch instead of eight or more, and
+// no tensor-map encoding on the host).  When the user's stream is itself being captured, or phase
+// timing is on, the kernels are launched directly; a capture that fails falls back the same way.
+static frsvt_status ialm_step_launch(frsvt_handle* h, const frsvt_handle::StepKey& key) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (h->timing || cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    return ialm_launches(h, key);
+  }
+  if (h->step_exec == nullptr || !(h->step_key == key)) {
+    if (h->step_exec) {                        // a replay of the old graph may still be queued
+      FRSVT_CK(cudaStreamSynchronize(h->stream));
+      cudaGraphExecDestroy(h->step_exec);
+      h->step_exec = nullptr;
+    }
+    if (h->capture_stream == nullptr &&
+        cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      h->capture_stream = nullptr;
+      (void)cudaGetLastError();
+      return ialm_launches(h, key);
+    }
+    cudaStream_t user = h->stream;
+    h->stream = h->capture_stream;
+    frsvt_status s = FRSVT_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      s = ialm_launches(h, key);
+      e = cudaStreamEndCapture(h->capture_stream, &g);
+    }
+    h->stream = user;
+    if (e == cudaSuccess && s == FRSVT_OK && g != nullptr) e = cudaGraphInstantiate(&h->step_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (s != FRSVT_OK) return s;
+    if (e != cudaSuccess || h->step_exec == nullptr) {
+      h->step_exec = nullptr;
+      (void)cudaGetLastError();
+      return ialm_launches(h, key);
+    }
+    h->step_key = key;
+  }
+  FRSVT_CK(cudaGraphLaunch(h->step_exec, h->stream));
+  return FRSVT_OK;
+}
+
+frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A, int64_t m, int64_t n, int64_t ld,
+                            int32_t l, float* L, int64_t ldl, double* residual) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = check_shape(h, m, n);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, O, m, n, ld, "O")) != FRSVT_OK) return s;
+  if ((s = check_matrix(h, S, m, n, ld, "S")) != FRSVT_OK) return s;
+  if ((s = check_matrix(h, A, m, n, ld, "A")) != FRSVT_OK) return s;
+  if (L != nullptr && (s = check_matrix(h, L, m, n, ldl, "L")) != FRSVT_OK) return s;
+  if (l < 1 || l > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "l must be in [1, l_max]");
+  if (m == 0 || n == 0) return FRSVT_OK;
+  if (l > n) l = static_cast<int32_t>(n);
+  if (h->ap_a > 0) {                                   // adaptive rank prediction: l on the device
+    if (!(h->tma && n <= 256)) return fail(h, FRSVT_ERR_UNSUPPORTED, "rank prediction needs n <= 256");
+    if (h->ap_n != n && (s = ap_setup(h, n)) != FRSVT_OK) return s;
+    h->last_m = m;
+    h->last_n = n;
+    l = -1;
+  } else if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) {
+    return s;
+  }
+  const frsvt_handle::StepKey key{O, S, A, m, n, ld, l, L, ldl, h->epoch};
+  if ((s = ialm_step_launch(h, key)) != FRSVT_OK) return s;
   if (residual != nullptr) {
     double v = 0.0;
     FRSVT_CK(cudaMemcpyAsync(&v, &h->dst->resid_ratio, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1396,6 +1485,7 @@ frsvt_status ap_setup(frsvt_handle* h, int64_t n) {
 
 frsvt_status frsvt_set_rank_prediction(frsvt_handle* h, int32_t a, double rho, double gamma) {
   if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  h->epoch += 1;                                     // what a step launches may change
   if (a < 0 || (a > 0 && (!(rho > 0.0) || rho > 1.0 || !(gamma > 0.0) || gamma > 1.0)))
     return fail(h, FRSVT_ERR_INVALID_ARG, "need a >= 0, 0 < rho <= 1, 0 < gamma <= 1");
   if (a > 0 && (h->wide || !h->cfg.range_prop || h->cfg.precision != FRSVT_PREC_FP32 || !h->tma ||
@@ -1412,6 +1502,7 @@ frsvt_status frsvt_set_rank_prediction(frsvt_handle* h, int32_t a, double rho, d
 
 frsvt_status frsvt_set_partial(frsvt_handle* h, int32_t k) {
   if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  h->epoch += 1;                                     // what a step launches may change
   if (k < 0 || k > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "k must be in [0, l_max]");
   FRSVT_CK(cudaMemcpyAsync(&h->dst->partial_k, &k, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
   FRSVT_CK(cudaStreamSynchronize(h->stream));          // k lives on this stack frame
