@@ -44,7 +44,7 @@ WORKLOAD = "video-background RPCA 76800x200 (320x240 px x 200 frames), FRSVT l=1
 
 # DRAM bytes per launch from one ncu capture of the kernel that serves the phase (video
 # workload); None once that kernel has changed since the capture.
-NCU_TRAFFIC = {"power_AtZ": 66.77e6}
+NCU_TRAFFIC = {"power_AtZ": 66.71e6}
 PHASE_KERNEL = {"sketch": "k_tc_sc<16,1,1>", "power_AQ": "k_tc_lr<16>", "power_AtZ": "k_tc_sc<16,0,1>",
                 "project": "k_tc_lr<16>", "core": "k_gram_core<16>", "epilogue": "k_tp_alm<16>"}
 # sm__pipe_tensor_cycles_active of the tensor-core passes, same capture (percent of peak, elapsed)
