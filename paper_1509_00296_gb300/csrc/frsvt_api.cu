@@ -53,7 +53,7 @@ cudaError_t launch_tp_lr(int LP, bool gram, const CUtensorMap& tmA, int64_t m, i
 cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS, const CUtensorMap& tmA,
                           const CUtensorMap& tmZ, int64_t m, int64_t n, int64_t rpc, int grid, const float* Rf,
                           float* S, float* A, int64_t ld, float* L, int64_t ldl, DevState* dst, double* cpart,
-                          double* rsum, unsigned* tickets, void* Ab, int64_t ldb, cudaStream_t st);
+                          unsigned* tickets, void* Ab, int64_t ldb, cudaStream_t st);
 int tb_lr_stages(int LP, int64_t n, size_t limit);
 int tb_sc_stages(int LP, int64_t n, bool omega, size_t limit);
 size_t tb_sc_smem(int LP, int64_t n, bool omega, int ns);
@@ -1182,7 +1182,7 @@ static frsvt_status ialm_launches(frsvt_handle* h, const frsvt_handle::StepKey& 
     const int G = h->alm_grid;
     const int64_t rpc = cdiv(cdiv(m, G), re) * re;
     FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_tp_alm(h->LP, tO, tS, tA, tZ, m, n, rpc, G, h->Rf, S, A, ld, L, ldl,
-                                                     h->dst, h->cpart_alm, h->rsum, h->tickets, bf ? h->Ab : nullptr,
+                                                     h->dst, h->cpart_alm, h->tickets, bf ? h->Ab : nullptr,
                                                      h->ldb, h->stream));
   } else if (h->fused) {
     const Splits fs = fused_splits(h, m, n);

@@ -20,8 +20,9 @@
 // swizzle (the K-major B operand).  Warp roles: 0 TMA producer; 1 tensor-memory owner and MMA
 // issuer (A_hi MMAs of chunk g, then the A_lo MMAs of chunk g - 1); 2-5 drain the
 // double-buffered accumulator into Z (the warps of lane quarters 0 / 1 hold the stacked
-// rows); 6-13 split.  Every wait is bounded; a timeout sets FRSVT_DEV_TIMEOUT and the kernel
-// still releases its tensor memory.
+// rows); 6-13 split.  Warps 2-13 first stage Q^T while the producer already streams A.
+// Every wait is bounded; a timeout sets FRSVT_DEV_TIMEOUT and the kernel still releases its
+// tensor memory.
 #include <cuda.h>
 
 #include "common.cuh"
@@ -107,7 +108,7 @@ k_tc_lr(const __grid_constant__ CUtensorMap tmA, int64_t m, int n, int64_t rpc, 
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if (lane == 0) qmax[warp - 2] = mx;
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * (kDrainWarps + kSplitWarps)) : "memory");
+      named_bar(1, 32 * (kDrainWarps + kSplitWarps));
       mx = 0.f;
 #pragma unroll
       for (int w = 0; w < kDrainWarps + kSplitWarps; ++w) mx = fmaxf(mx, qmax[w]);

@@ -7,7 +7,8 @@
 // (512 for l <= 16, 256 for l <= 32) compute on the tiles; the ring keeps ~100 KB of
 // loads in flight per SM without register cost.  Each pass ends with a cluster
 // split-K reduction (cluster.cuh) whose last cluster runs the small dense step of
-// Alg. 1 that depends on the reduced result:
+// Alg. 1 that depends on the reduced result (k_tp_alm, which reduces a single value,
+// runs without clusters on every SM and with 256 consumer threads):
 //   k_tp_sc  : Y = A^T Omega (sketch, steps 4-5 / 8-9) or Y = A^T Z (power step 14),
 //              then the orthonormal basis (steps 6, 10-11, 14)
 //   k_tp_lr  : Z = A Q (power step 14 / projection step 16); with GRAM also B B^T = Z^T Z
@@ -369,8 +370,7 @@ k_tp_alm(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtens
          const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ, int64_t m, int n, int np4,
          int64_t rpc, const float* __restrict__ Rf, float* __restrict__ S, float* __restrict__ A, int64_t ld,
          float* __restrict__ L, int64_t ldl, DevState* __restrict__ dst, double* __restrict__ cpart,
-         double* __restrict__ rsum, unsigned* __restrict__ tickets, __nv_bfloat16* __restrict__ Ab, int64_t ldb,
-         int nse) {
+         unsigned* __restrict__ tickets, __nv_bfloat16* __restrict__ Ab, int64_t ldb, int nse) {
   constexpr int NC = kAlmNC, NT = kAlmNT;
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kStagesE], empty[kStagesE];
@@ -720,7 +720,7 @@ cudaError_t launch_tp_lr(int LP, bool gram, const CUtensorMap& tmA, int64_t m, i
 cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS, const CUtensorMap& tmA,
                           const CUtensorMap& tmZ, int64_t m, int64_t n, int64_t rpc, int grid, const float* Rf,
                           float* S, float* A, int64_t ld, float* L, int64_t ldl, DevState* dst, double* cpart,
-                          double* rsum, unsigned* tickets, void* Ab, int64_t ldb, cudaStream_t st) {
+                          unsigned* tickets, void* Ab, int64_t ldb, cudaStream_t st) {
   const int np4 = tma_np4(n);
   const size_t smem = tma_alm_smem(LP, n);
   const int nse = tma_alm_stages(LP, n);
@@ -729,10 +729,10 @@ cudaError_t launch_tp_alm(int LP, const CUtensorMap& tmO, const CUtensorMap& tmS
   __nv_bfloat16* ab = static_cast<__nv_bfloat16*>(Ab);
   if (LP == 16)
     k_tp_alm<16><<<grid, kAlmNT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
-                                                   cpart, rsum, tickets, ab, ldb, nse);
+                                                   cpart, tickets, ab, ldb, nse);
   else
     k_tp_alm<32><<<grid, kAlmNT, smem, st>>>(tmO, tmS, tmA, tmZ, m, nn, np4, rpc, Rf, S, A, ld, L, ldl, dst,
-                                                   cpart, rsum, tickets, ab, ldb, nse);
+                                                   cpart, tickets, ab, ldb, nse);
   return cudaGetLastError();
 }
 

@@ -6,13 +6,13 @@
 // reduction last.
 //
 // orth_block : orthonormal basis of the sketch, Alg. 1 steps 6, 10-11, 14.
-//              Cholesky QR applied twice (CholeskyQR2): Gram matrix in
-//              double-float, FP64 Cholesky with a pivot drop (s = min(l, rank)),
+//              Cholesky QR applied twice (CholeskyQR2): Gram matrix and Cholesky
+//              with a pivot drop (s = min(l, rank)) in double-float arithmetic,
 //              FP32 triangular solves.  Under range propagation the new block is
 //              projected out of the propagated basis twice first (the partial
 //              orthogonalization of step 10).  Only span(Q) matters (Prop. 1).
 // core_block : singular values / vectors of B = Q^T A from B B^T = Z^T Z
-//              (Z = A Q): FP64 Cholesky R^T R = Z^T Z, FP32 one-sided Jacobi SVD
+//              (Z = A Q): double-float Cholesky R^T R = Z^T Z, FP32 one-sided Jacobi SVD
 //              of R^T (the D and V of Alg. 1 steps 16-18), soft shrinkage,
 //              M = U diag(S_tau(D) / D) U^T (Eq. 6: X = Z M Q^T), Rf = Q M and
 //              the propagated basis Q~ = Q U[:, :keep] (step 21).
