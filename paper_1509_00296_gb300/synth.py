@@ -20,6 +20,12 @@ generators stand in for it with the shapes and structures below.
   Gaussian product plus N(0, 0.05^2) noise (WNNM, Sec. 1 footnote on WSVT).
 - ``unrolled_batch``: 8 x (2048 x 512), rank 8 (factors scaled 1/sqrt(8)),
   5 % outliers in [-20, 20].
+- ``subspaces``: columns drawn from a union of independent low-dimensional
+  subspaces (orthonormal random bases, Gaussian coefficients), ordered by
+  subspace, with a fraction of whole columns corrupted by a large Gaussian
+  vector (the sample-specific corruption that the l2,1 term of the
+  low-rank-representation problem, Table 6 Type A, models; stands in for the
+  motion-segmentation and face data of Sec. 4.3).
 """
 from __future__ import annotations
 
@@ -150,3 +156,22 @@ def snow_video(seed: int = 1006, h: int = 288, w: int = 384, frames: int = 20, d
         o[flakes] = rng.uniform(0.85, 1.0, size=int(flakes.sum()))
         O[:, t] = o
     return O.astype(np.float32), clean, mask
+
+
+def subspaces(seed: int = 1007, d: int = 60, k: int = 4, dim: int = 3, per: int = 15, frac: float = 0.1,
+              amp: float = 3.0):
+    """O (d x k*per): `per` columns from each of `k` random `dim`-dimensional subspaces of R^d
+    (coefficients N(0, 1)), ordered by subspace; round(frac * n) columns, chosen at random, get
+    amp * N(0, I_d) / sqrt(d) added.  Returns (O, the clean columns, labels, the corrupted mask)."""
+    rng = np.random.default_rng(seed)
+    n = k * per
+    clean = np.empty((d, n))
+    labels = np.repeat(np.arange(k), per)
+    for i in range(k):
+        B, _ = np.linalg.qr(rng.standard_normal((d, dim)))
+        clean[:, i * per:(i + 1) * per] = B @ rng.standard_normal((dim, per))
+    mask = np.zeros(n, dtype=bool)
+    mask[rng.choice(n, size=int(round(frac * n)), replace=False)] = True
+    O = clean.copy()
+    O[:, mask] += amp * rng.standard_normal((d, int(mask.sum()))) / np.sqrt(d)
+    return O, clean, labels, mask
