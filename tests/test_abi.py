@@ -68,3 +68,45 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
+
+
+def _header_text():
+    return re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+
+
+def _struct_fields(name):
+    """(type, field) pairs of `typedef struct name { ... } name;` in the header."""
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), _header_text(), flags=re.S).group(1)
+    return re.findall(r"^\s*([a-z0-9_]+)\s+([a-z0-9_]+)\s*;", body, flags=re.M)
+
+
+_CTYPES = {"int32_t": ctypes.c_int32, "uint32_t": ctypes.c_uint32, "int64_t": ctypes.c_int64,
+           "uint64_t": ctypes.c_uint64, "double": ctypes.c_double, "float": ctypes.c_float}
+
+
+@pytest.mark.parametrize("cname,pyname", [("frsvt_config", "Config"), ("frsvt_info", "Info")])
+def test_binding_structs_match_header(cname, pyname):
+    """The ctypes structures of the binding list the header's fields in order with the same types."""
+    from paper_1509_00296_gb300 import frsvt
+    want = [(f, _CTYPES[t]) for t, f in _struct_fields(cname)]
+    got = list(getattr(frsvt, pyname)._fields_)
+    assert got == want
+
+
+def test_binding_constants_match_header():
+    """Status codes, device status bits, configuration flags, precisions, phases and WSVT variants."""
+    from paper_1509_00296_gb300 import frsvt
+    src = _header_text()
+    macros = {k: v for k, v in re.findall(r"#define (FRSVT_\w+)\s+\(?([0-9]+u?(?:\s*<<\s*[0-9]+)?)\)?", src)}
+    val = lambda k: eval(macros[k].replace("u", ""))
+    assert frsvt.CFG_ADJOINT == val("FRSVT_CFG_ADJOINT") and frsvt.CFG_ORTH_LAST == val("FRSVT_CFG_ORTH_LAST")
+    assert (frsvt.DEV_RANK_DEFICIENT, frsvt.DEV_NOT_CONVERGED, frsvt.DEV_NONFINITE, frsvt.DEV_TIMEOUT,
+            frsvt.DEV_BAD_PROBLEM) == tuple(val("FRSVT_DEV_" + k) for k in
+                                            ("RANK_DEFICIENT", "NOT_CONVERGED", "NONFINITE", "TIMEOUT", "BAD_PROBLEM"))
+    assert (frsvt.WSVT_EXACT, frsvt.WSVT_FRSVT) == (val("FRSVT_WSVT_EXACT"), val("FRSVT_WSVT_FRSVT"))
+    assert frsvt.NPHASE == val("FRSVT_NPHASE")
+    enums = dict((k, int(v)) for k, v in re.findall(r"(FRSVT_(?:ERR_\w+|OK|PREC_\w+))\s*=\s*([0-9]+)", src))
+    assert {v: k for k, v in frsvt.STATUS_NAMES.items()} == {k: v for k, v in enums.items()
+                                                           if k == "FRSVT_OK" or k.startswith("FRSVT_ERR_")}
+    assert (frsvt.PREC_FP32, frsvt.PREC_BF16, frsvt.PREC_FP8) == (enums["FRSVT_PREC_FP32"], enums["FRSVT_PREC_BF16"],
+                                                                 enums["FRSVT_PREC_FP8"])
