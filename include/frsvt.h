@@ -86,7 +86,7 @@ typedef struct frsvt_config {
   int32_t precision;             /* frsvt_precision */
   uint64_t seed;                 /* Philox4x64-10 key of Omega */
   int32_t max_jacobi_sweeps;     /* cap of the l x l Jacobi SVD (<= 0: 30) */
-  int32_t flags;                 /* FRSVT_CFG_* bits */
+  int32_t flags;                 /* FRSVT_CFG_* bits (other bits: FRSVT_ERR_INVALID_ARG) */
   double rank_tol;               /* relative pivot cut of the Cholesky QR (<= 0: 1e-12) */
 } frsvt_config;
 

@@ -873,6 +873,7 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   *out = nullptr;
   if (cfg->m_max < 1 || cfg->n_max < 1 || cfg->l_max < 1 || cfg->l_max > kMaxL || cfg->q < 0 || cfg->q > 64)
     return FRSVT_ERR_INVALID_ARG;
+  if ((cfg->flags & ~(FRSVT_CFG_ADJOINT | FRSVT_CFG_ORTH_LAST)) != 0) return FRSVT_ERR_INVALID_ARG;
   if (cfg->precision != FRSVT_PREC_FP32 && cfg->precision != FRSVT_PREC_BF16 &&
       !(cfg->precision == FRSVT_PREC_FP8 && cfg->l_max > 32))
     return FRSVT_ERR_UNSUPPORTED;
