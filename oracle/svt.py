@@ -33,6 +33,12 @@
 - ``svt_vjp``        adjoint of the exact SVT (divided-difference form of the derivative
                      of a spectral function, and the tau derivative).  Pinned by central
                      finite differences of ``exact_svt`` in FP64.
+- ``frsvt_vjp``      adjoint of the FRSVT map with a fixed Omega (Alg. 1 run backwards: the
+                     SVT adjoint of the small problem, the QR adjoint of every
+                     orthonormalisation, the transposed products).  Pinned by entrywise
+                     central differences of ``frsvt`` (every entry of A and tau, tall and
+                     wide inputs, q = 0..2) and by equality with ``svt_vjp`` when the basis
+                     spans the short side (l = min(m, n): FRSVT is then the exact SVT).
 - ``psvt``           partial SVT of the truncated nuclear norm (Table 6, Type B):
                      the k leading singular values are kept, the rest shrunk.
 
@@ -262,6 +268,81 @@ def svt_vjp(A: np.ndarray, tau: float, Xbar: np.ndarray):
     Abar += U @ (D[:, None] * (U.T @ Xbar - (U.T @ Xbar @ V) @ V.T))
     taubar = -float(np.sum(np.diag(Ub)[s > tau]))
     return Abar, taubar
+
+
+def _qr_pos(Y: np.ndarray):
+    """Thin QR with a non-negative diagonal of R (the unique factor of a full-rank Y)."""
+    Q, R = linalg.qr(Y)
+    sg = np.where(np.diag(R) < 0.0, -1.0, 1.0)
+    return Q * sg[None, :], R * sg[:, None]
+
+
+def _qr_vjp(Q: np.ndarray, R: np.ndarray, Qbar: np.ndarray) -> np.ndarray:
+    """Adjoint of the thin QR Y = Q R (full column rank) for a cotangent of Q alone.
+
+    With M = -Qbar^T Q (the R R-bar^T term is absent: R feeds nothing downstream) and
+    copyltu(M) = tril(M) + tril(M, -1)^T, Ybar = (Qbar + Q copyltu(M)) R^{-T}.
+    """
+    M = -(Qbar.T @ Q)
+    C = np.tril(M) + np.tril(M, -1).T
+    return np.linalg.solve(R, (Qbar + Q @ C).T).T
+
+
+def frsvt_vjp(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int, Xbar: np.ndarray,
+              problem: int = 0):
+    """Vector-Jacobian product of the FRSVT map with a fixed Omega (Alg. 1, no range propagation).
+
+    Returns (Abar, taubar, X) for the cotangent Xbar of X = FRSVT_tau(A).  The forward is Alg. 1
+    in the orientation of ``frsvt`` (Ah = the short x long view of A), with every
+    orthonormalisation a thin QR (X depends only on the spans, Prop. 1, so this is the map
+    ``frsvt`` computes with pivoted QR wherever no column is dropped):
+        Y_0 = Ah Omega,  Q_0 R_0 = Y_0                              (steps 4-6)
+        Z_i = Ah^T Q_{i-1},  Y_i = Ah Z_i,  Q_i R_i = Y_i, i = 1..q   (steps 13-15)
+        B = Q_q^T Ah,  Xh = Q_q S_tau(B)                             (steps 16-19, Eq. 6)
+    and the reverse pass takes the same steps backwards: the exact SVT adjoint of the small
+    problem (``svt_vjp`` on B, divided differences), the QR adjoint of each factorisation
+    (``_qr_vjp``), and the products' transposes.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    Xbar = np.asarray(Xbar, dtype=np.float64)
+    m, n = A.shape
+    transposed = m >= n
+    Ah = A.T if transposed else A
+    Xbh = Xbar.T if transposed else Xbar
+    ns, nl = Ah.shape
+    l = min(l, ns)
+    Omega = gaussian_matrix(nl, l, seed, stream, problem)
+    # forward, keeping what the reverse pass reads
+    Qs, Rs, Zs = [], [], []
+    Q, R = _qr_pos(Ah @ Omega)
+    Qs.append(Q)
+    Rs.append(R)
+    for _ in range(q):
+        Z = Ah.T @ Q
+        Q, R = _qr_pos(Ah @ Z)
+        Zs.append(Z)
+        Qs.append(Q)
+        Rs.append(R)
+    B = Q.T @ Ah
+    W, _ = exact_svt(B, tau)
+    Xh = Q @ W
+    # reverse
+    Qbar = Xbh @ W.T                                  # Xh = Q W
+    Wbar = Q.T @ Xbh
+    Bbar, taubar = svt_vjp(B, tau, Wbar)              # W = S_tau(B)
+    Qbar = Qbar + Ah @ Bbar.T                         # B = Q^T Ah
+    Ahbar = Q @ Bbar
+    for i in range(q, 0, -1):
+        Ybar = _qr_vjp(Qs[i], Rs[i], Qbar)            # Q_i R_i = Y_i
+        Ahbar += Ybar @ Zs[i - 1].T                   # Y_i = Ah Z_i
+        Zbar = Ah.T @ Ybar
+        Ahbar += Qs[i - 1] @ Zbar.T                   # Z_i = Ah^T Q_{i-1}
+        Qbar = Ah @ Zbar
+    Ybar = _qr_vjp(Qs[0], Rs[0], Qbar)                # Q_0 R_0 = Y_0
+    Ahbar += Ybar @ Omega.T                           # Y_0 = Ah Omega
+    Abar = Ahbar.T if transposed else Ahbar
+    X = Xh.T if transposed else Xh
+    return np.ascontiguousarray(Abar), float(taubar), np.ascontiguousarray(X)
 
 
 def frsvt_directional_fd(A: np.ndarray, tau: float, l: int, q: int, seed: int, stream: int,

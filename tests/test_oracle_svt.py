@@ -485,3 +485,55 @@ def test_frsvt_orth_last_q1_identical():
     a = svt.frsvt(A, 1.0, 8, 1, seed=4, stream=0)
     b = svt.frsvt(A, 1.0, 8, 1, seed=4, stream=0, orth_last=True)
     assert np.array_equal(a.X, b.X)
+
+
+# ---------------------------------------------------------------- FRSVT-map adjoint
+
+def _frsvt_tau(A, l, q, seed, stream):
+    """tau halfway across the widest gap among the leading singular values of FRSVT's B."""
+    d = svt.frsvt(A, 0.0, l, q, seed, stream).sigma
+    gaps = d[:-1] - d[1:]
+    i = int(np.argmax(gaps[: max(1, len(gaps) - 1)]))
+    return float(0.5 * (d[i] + d[i + 1]))
+
+
+@pytest.mark.parametrize("shape,l,q", [((9, 6), 3, 0), ((9, 6), 3, 1), ((11, 7), 4, 2), ((6, 10), 3, 1),
+                                       ((8, 8), 5, 2)])
+def test_frsvt_vjp_entrywise_central_differences(shape, l, q):
+    """Every entry of Abar and taubar of the FRSVT-map adjoint against one-entry central differences
+    of the oracle's Alg. 1 (pivoted QR, Newton polar and Jacobi route) with the same Omega."""
+    rng = np.random.default_rng(71 + shape[0] + q)
+    m, n = shape
+    A = rng.standard_normal((m, n)) * 2.0
+    seed, stream = 13, 4
+    tau = _frsvt_tau(A, l, q, seed, stream)
+    Xbar = rng.standard_normal((m, n))
+    Abar, taubar, X = svt.frsvt_vjp(A, tau, l, q, seed, stream, Xbar)
+    assert np.linalg.norm(X - svt.frsvt(A, tau, l, q, seed, stream).X) < 1e-12 * np.linalg.norm(A)
+    h = 1e-6
+    fd = np.empty((m, n))
+    for i in range(m):
+        for j in range(n):
+            E = np.zeros((m, n))
+            E[i, j] = h
+            fd[i, j] = np.sum(Xbar * (svt.frsvt(A + E, tau, l, q, seed, stream).X
+                                      - svt.frsvt(A - E, tau, l, q, seed, stream).X)) / (2 * h)
+    assert np.max(np.abs(Abar - fd)) < 1e-6 * max(1.0, np.max(np.abs(fd)))
+    fdt = np.sum(Xbar * (svt.frsvt(A, tau + h, l, q, seed, stream).X
+                         - svt.frsvt(A, tau - h, l, q, seed, stream).X)) / (2 * h)
+    assert abs(taubar - fdt) < 1e-6 * max(1.0, abs(fdt))
+
+
+@pytest.mark.parametrize("shape,q", [((9, 5), 0), ((9, 5), 2), ((5, 8), 1)])
+def test_frsvt_vjp_full_basis_is_exact_svt_adjoint(shape, q):
+    """With l = min(m, n) the basis spans the short side, FRSVT is the exact SVT, and the FRSVT-map
+    adjoint reduces to the divided-difference adjoint of the exact SVT (every QR adjoint cancels)."""
+    rng = np.random.default_rng(81 + q)
+    A = rng.standard_normal(shape)
+    s = np.linalg.svd(A, compute_uv=False)
+    tau = 0.5 * (s[1] + s[2])
+    Xbar = rng.standard_normal(shape)
+    Abar, taubar, _ = svt.frsvt_vjp(A, tau, min(shape), q, 3, 1, Xbar)
+    Ae, te = svt.svt_vjp(A, tau, Xbar)
+    assert np.max(np.abs(Abar - Ae)) < 1e-10 * max(1.0, np.max(np.abs(Ae)))
+    assert abs(taubar - te) < 1e-10 * max(1.0, abs(te))
