@@ -1,21 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: inexact-ALM RPCA iterations per second with FRSVT on one GB300.
 
-Workload (one "step" = one full iALM iteration of the hot path): the
-video-background RPCA input, O = 76800 x 200 float32 (320 x 240 pixels x 200
-frames, rank-3 smooth background, ~8 % moving rectangles, noise 0.01),
-FRSVT with l = 10, q = 2 power iterations and range propagation, lambda =
-1/sqrt(76800), rho = 1.5.  Data is synthetic (seeded), see synth.video.
+Workload (one "step" = one full iALM iteration of the hot path): the large
+low-rank recovery input, O = 8192 x 8192 float32, rank 100 (Gaussian factors
+scaled 1/sqrt(100)) plus 10 % additive corruption uniform in [-10, 10]; inexact
+ALM with FRSVT at l = 120, q = 2 (the wide-basis path: FP32-accurate 3xTF32
+passes on tcgen05, double-float Gram and Cholesky, l x l core), lambda =
+1/sqrt(8192), rho = 1.5.  Data is synthetic (seeded), see synth.recovery_8192.
 
-Default arm (--impl frsvt): the C-ABI library; each step is one rpca_ialm_step
+Default arm (--impl frsvt): the C-ABI library; each step is one iALM iteration
 replayed from a captured CUDA graph.  Timing: CUDA events around each step on
 the launching stream, the L2 cache flushed (a 256 MiB write) between steps
 outside the events.  `value` = steps / summed device time, max over ranks.
 Also reported: per-phase device times through the library's tracing hook (the
-roofline of the dominant kernel), the same iteration with exact SVT by
-cuSOLVER (torch.linalg.svd) on the same GPU, the end-to-end rate through the
-public API with host buffers, the FP64 oracle on the host cores, and SM clocks
-sampled by nvidia-smi during the timed region.
+roofline of the dominant kernel), one exact SVT of the same iterate by cuSOLVER
+on the same GPU, the end-to-end rate through the public API with host buffers,
+the FP64 oracle on the host cores, SM clocks sampled by nvidia-smi during the
+timed region, the BF16 / FP8 variants of the same workload, and the other
+workloads (video-background RPCA, batched weighted SVT, unrolled RPCA, Type B
+weather windows) as extra keys.
 
 --impl reference times the FP64 CPU oracle (numpy) on the same workload.
 Under torchrun each rank runs an independent replica (the path does not shard).
@@ -36,20 +39,38 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ALM iters/s & tensor-pipe % of FRSVT vs exact-SVD SVT, same GPU, ≤1e-4 rel err"
 UNIT = "ALM iters/s"
-M, N, L_COLS, Q_POW = 76800, 200, 10, 2
+RN, RL, RQ = 8192, 120, 2                 # recovery: n x n, l, q
+RDATA_SEED, ROMEGA_SEED = 1003, 2004
+RWORKLOAD = ("large low-rank recovery 8192x8192 rank 100 + 10% corruption in [-10,10], "
+             "iALM with FRSVT l=120 q=2 (FP32-accurate passes)")
+M, N, L_COLS, Q_POW = 76800, 200, 10, 2   # video-background extra
 LP_COLS = 16                              # l rounded up to the 16-column panel
 DATA_SEED, OMEGA_SEED = 1002, 2002
 WORKLOAD = "video-background RPCA 76800x200 (320x240 px x 200 frames), FRSVT l=10 q=2 range propagation"
 
+# Kernels that serve each phase of the wide-basis FP32 path: one kernel, except the sketch (Omega
+# generation, a few percent of it) and the small dense tails (the Gram of a basis-side matrix on all
+# SMs, then the Cholesky QR operand on one SM or the core on an 8-CTA cluster).
+WIDE_PHASE_KERNEL = {"sketch": "k_wd_pass<1,0>", "power_AQ": "k_wd_pass<0,0>", "power_AtZ": "k_wd_pass<1,0>",
+                     "project": "k_wd_pass<0,0>", "orth": "k_wd_gram + k_wd_orth", "apply": "k_wd_trsm / k_wd_apply",
+                     "core": "k_wd_gram + k_wd_core", "epilogue": "k_wd_alm<true>"}
+# ncu counters of the wide-basis kernels on this workload, per launch (NCU_PROFILE records the capture command
+# and these figures; tests/test_bench_host.py checks that they match; None where no capture of the current
+# kernel exists).  traffic:
+# dram__bytes_read.sum + dram__bytes_write.sum; tensor_pct: sm__pipe_tensor_cycles_active (percent of elapsed).
+NCU_PROFILE = "profiles/wide_passes_recovery_8192x8192.md"
+NCU_WIDE = {"k_wd_pass<1,0>": {"traffic": 280.1e6, "tensor_pct": 46.2},
+            "k_wd_pass<0,0>": {"traffic": 280.6e6, "tensor_pct": 41.2},
+            "k_wd_alm<true>": {"traffic": None, "tensor_pct": None}}
 
-# DRAM bytes per launch from one ncu capture of the kernel that serves the phase (video
-# workload); None once that kernel has changed since the capture.
-NCU_TRAFFIC = {"power_AtZ": 66.71e6}
-PHASE_KERNEL = {"sketch": "k_tc_sc<16,1,1>", "power_AQ": "k_tc_lr<16>", "power_AtZ": "k_tc_sc<16,0,1>",
-                "project": "k_tc_lr<16>", "core": "k_gram_core<16>", "epilogue": "k_tp_alm<16>"}
-# sm__pipe_tensor_cycles_active of the tensor-core passes, same capture (percent of peak, elapsed)
-TENSOR_PIPE_PCT = {"sketch k_tc_sc<16,1,1>": 11.9, "A^T Z k_tc_sc<16,0,1>": 13.0, "A Q k_tc_lr<16>": 25.3,
-                   "source": "ncu --set full capture of the passes on the video workload"}
+
+def config_dict(ws: int):
+    """The workload description printed by both arms."""
+    return {"workload": RWORKLOAD, "m": RN, "n": RN, "l": RL, "q": RQ, "range_prop": False,
+            "precision": "fp32 data, 3xTF32 tcgen05 passes, double-float Gram / Cholesky",
+            "l2": "inputs (3 x 268 MB) exceed L2; L2 also flushed between steps (256 MiB write, outside the events)",
+            "timing": "sum of per-step CUDA-event durations on the launching stream",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
 
 
 def dist_env():
@@ -144,20 +165,45 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(O64, iters: int):
-    """FP64 oracle iALM-FRSVT iterations per second on a bounded sample (host cores)."""
+def host_norm2(O, iters: int = 30, seed: int = 0) -> float:
+    """||O||_2 by the power method on the host (FP64), for the oracle's initialisation."""
     import numpy as np
-    from oracle import rpca as orpca
-    normO2 = float(np.linalg.norm(O64, 2))
-    t0 = time.perf_counter()
-    orpca.ialm_rpca(O64, method="frsvt", l=L_COLS, q=Q_POW, seed=OMEGA_SEED, fixed_iters=iters, normO2=normO2)
-    dt = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(O.shape[1])
+    s = 0.0
+    for _ in range(iters):
+        u = O @ v
+        v = O.T @ u
+        s = float(np.linalg.norm(v))
+        v /= s
+    return float(np.sqrt(s))
+
+
+def oracle_cores() -> int:
     try:
         import threadpoolctl
-        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or os.cpu_count()
+        return max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or os.cpu_count()
     except Exception:
-        cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
-    return iters / dt, cores, dt
+        return int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+
+
+def oracle_rate(O64, normO2: float, iters: int, **kw):
+    """FP64 oracle iALM-FRSVT iterations per second on a bounded sample (host cores); the
+    initialisation (||O||_2, given) is outside the timing."""
+    from oracle import rpca as orpca
+    args = dict(l=RL, q=RQ, seed=ROMEGA_SEED, range_prop=False)
+    args.update(kw)
+    t0 = time.perf_counter()
+    orpca.ialm_rpca(O64, method="frsvt", fixed_iters=iters, normO2=normO2, **args)
+    dt = time.perf_counter() - t0
+    return iters / dt, oracle_cores(), dt
+
+
+def recovery_input():
+    import numpy as np
+    from paper_1509_00296_gb300 import synth
+    O, _, _ = synth.recovery_8192(seed=RDATA_SEED)
+    return np.ascontiguousarray(O, dtype=np.float32)
 
 
 def run_reference(args):
@@ -165,18 +211,17 @@ def run_reference(args):
     if rank != 0:
         return 0
     import numpy as np
-    from paper_1509_00296_gb300 import synth
-    O, _, _ = synth.video(seed=DATA_SEED)
-    O64 = O.astype(np.float64)
-    for _ in range(args.warmup):
-        pass                                   # the oracle has no warm-up state; samples are independent
-    rate, cores, dt = oracle_rate(O64, max(1, args.steps))
+    O64 = recovery_input().astype(np.float64)
+    nrm = host_norm2(O64)
+    # the oracle keeps no state between runs, so the warm-up steps have nothing to warm: each timed
+    # step is one iALM-FRSVT iteration of the full workload
+    rate, cores, dt = oracle_rate(O64, nrm, max(1, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / rate, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": M, "n": N, "l": L_COLS, "q": Q_POW},
+            "config": config_dict(ws),
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} iALM-FRSVT iterations of the full 76800x200 workload "
+                             "sample": f"{args.steps} iALM-FRSVT iterations of the full 8192x8192 workload "
                                        f"({dt:.1f} s), FP64 numpy oracle"},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -186,11 +231,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="frsvt", choices=["frsvt", "reference"])
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--oracle-iters", type=int, default=12)
+    ap.add_argument("--oracle-iters", type=int, default=2)
     ap.add_argument("--skip-extras", action="store_true", help="only the main timed region")
     ap.add_argument("--profile-svt", choices=["fp32", "bf16", "fp8"], default=None,
                     help="only three FRSVT calls on the 8192 x 8192 recovery matrix (l = 120, q = 2), for ncu")
@@ -212,24 +257,23 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    from paper_1509_00296_gb300 import build, frsvt, synth
+    from paper_1509_00296_gb300 import build, frsvt
     build.build()
 
-    O_np, _, _ = synth.video(seed=DATA_SEED)
-    lam = 1.0 / np.sqrt(max(M, N))
+    O_np = recovery_input()
+    lam = 1.0 / np.sqrt(RN)
     O = torch.from_numpy(O_np).to(dev)
     S = torch.empty_like(O)
     A = torch.empty_like(O)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    h = frsvt.Handle(M, N, L_COLS, q=Q_POW, range_prop=True, seed=OMEGA_SEED, stream=stream)
+    h = frsvt.Handle(RN, RN, RL, q=RQ, range_prop=False, seed=ROMEGA_SEED, stream=stream)
     h.rpca_init(O, S, A, lam, 1.5, 1e7)
 
-    # one eager step first: it records the problem shape in the handle, so that the
-    # captured step contains no reset of the propagated basis; its launches are counted
+    # one eager step first, its launches counted through the tracing hook
     h.enable_timing(True)
     h.timings()
-    h.ialm_step(O, S, A, L_COLS)
+    h.ialm_step(O, S, A, RL)
     launches_per_step = sum(v[1] for v in h.timings().values())
     h.enable_timing(False)
     graph = None
@@ -238,14 +282,14 @@ def main():
         h.set_stream(cap)
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=cap):
-            h.ialm_step(O, S, A, L_COLS)
+            h.ialm_step(O, S, A, RL)
         h.set_stream(stream)
 
     def step():
         if graph is not None:
             graph.replay()
         else:
-            h.ialm_step(O, S, A, L_COLS)
+            h.ialm_step(O, S, A, RL)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
@@ -278,37 +322,20 @@ def main():
         extras = run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush)
 
     if rank == 0:
-        peak, peak_kind = peaks()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": M, "n": N, "l": L_COLS, "q": Q_POW, "range_prop": True,
-                       "graph": graph is not None, "l2": "flushed between steps (256 MiB write, outside the events)",
-                       "timing": "sum of per-step CUDA-event durations on the launching stream",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "config": dict(config_dict(ws), graph=graph is not None),
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "wall_s_timed_region": t_wall,
-            "alm_state": {"iter": info.alm_iter, "residual": info.residual, "rank": info.r,
-                          "device_status": info.device_status},
+            "alm_state": {"iter": info.alm_iter, "residual": info.residual, "rank": info.r, "basis": info.s,
+                          "jacobi_sweeps": info.sweeps, "device_status": info.device_status},
         }
-        if extras:
-            line["roofline"] = extras["roofline"]
-            line["roofline"]["peak_kind"] = peak_kind
-            line["phases_ms_per_step"] = extras["phases"]
-            line["e2e"] = extras["e2e"]
-            line["cpu_baseline"] = extras["cpu_baseline"]
-            line["exact_svd_same_gpu"] = extras["exact"]
-            line["exact_svd_same_gpu"]["frsvt_speedup"] = value / extras["exact"]["value"]
-            line["tensor_pipe_pct"] = TENSOR_PIPE_PCT
-            line["wsvt_batch"] = extras.get("wsvt")
-            line["unrolled_rpca"] = extras.get("unrolled")
-            line["video_bf16"] = extras.get("video_bf16")
-            line["video_rank_prediction"] = extras.get("video_rank_prediction")
-            line["video_orth_last"] = extras.get("video_orth_last")
-            line["weather_type_b"] = extras.get("weather_type_b")
-            line["recovery_8192"] = extras.get("recovery")
+        line.update(extras)
+        if "exact_svd_same_gpu" in line:
+            line["exact_svd_same_gpu"]["frsvt_speedup"] = value / line["exact_svd_same_gpu"]["value"]
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -338,14 +365,161 @@ def profile_svt(prec: str):
     return 0
 
 
+def fp32_alu_peak_tflops() -> float:
+    """FP32 FMA rate of the whole chip from its unit counts and clock: 152 SMs x 128 lanes x 2 FLOP
+    x the measured maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def wide_roofline(tm, K, n):
+    """Dominant kernel of the wide-basis iALM step from the tracing hook's per-phase times, and its
+    roofline: algorithmic bytes (or FP32-pipe operations for the one-CTA tails) per launch over the
+    average launch duration (CUDA events on the launching stream)."""
+    peak, peak_kind = peaks()
+    e = 4.0 * n * n                      # one float32 pass over A
+    z = 4.0 * 128 * n                    # one 128-wide basis-side matrix
+    kern = {}
+    for ph, (ms, cnt) in tm.items():
+        if cnt > 0 and ph in WIDE_PHASE_KERNEL:
+            k = WIDE_PHASE_KERNEL[ph]
+            t = kern.setdefault(k, [0.0, 0])
+            t[0] += ms / K
+            t[1] += cnt / K
+    dom = max(kern, key=lambda k: kern[k][0])
+    per_launch_ms = kern[dom][0] / kern[dom][1]
+    hbm_bytes = {"k_wd_pass<1,0>": e + 3 * z, "k_wd_pass<0,0>": e + 4 * z, "k_wd_alm<true>": 5 * e + 4 * z,
+                 "k_wd_trsm / k_wd_apply": 3 * z}
+    ncu = NCU_WIDE.get(dom, {})
+    if dom in hbm_bytes:
+        ach = hbm_bytes[dom] / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": ncu.get("traffic"), "algorithmic_bytes_per_launch": hbm_bytes[dom],
+                "peak_kind": f"{peak_kind} (STREAM-style copy)"}
+    else:
+        # df64 Gram (8 FP32-pipe operations per product-accumulate) + the 128 x 128 factorisations
+        ops = 2.0 * 8 * n * 128 * 129 / 2 + 8 * 2 * 128 ** 3 / 3
+        pk = fp32_alu_peak_tflops()
+        ach = ops / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": ncu.get("traffic"), "algorithmic_ops_per_launch": ops,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    roof.update({"kernel": dom, "avg_launch_ms": per_launch_ms, "launches_per_step": kern[dom][1],
+                 "kernel_ms_per_step": {k: v[0] for k, v in kern.items()}})
+    return roof
+
+
 def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
     import numpy as np
     import torch
-    from paper_1509_00296_gb300 import frsvt
 
     out = {}
     # ---- per-phase device times (tracing hook), same step, eager launches on the same stream
-    K = max(10, min(args.steps, 50))
+    K = max(5, min(args.steps, 20))
+    h.enable_timing(True)
+    h.timings()
+    for k in range(K):
+        flush.fill_(float(k))
+        h.ialm_step(O, S, A, RL)
+    tm = h.timings()
+    h.enable_timing(False)
+    out["phases_ms_per_step"] = {k: v[0] / K for k, v in tm.items() if v[1] > 0}
+    out["roofline"] = wide_roofline(tm, K, RN)
+    out["tensor_pipe_pct"] = {k: v["tensor_pct"] for k, v in NCU_WIDE.items() if v.get("tensor_pct") is not None}
+    out["tensor_pipe_pct"]["source"] = f"ncu capture of the passes on this workload, {NCU_PROFILE}"
+
+    # ---- exact-SVD iALM on the same GPU: one iteration on the current iterate (cuSOLVER through
+    # torch.linalg.svd, then the same shrinkage, reconstruction and multiplier update)
+    info = h.info()
+    mu = info.mu
+    torch.linalg.svd(A[:1024, :1024], full_matrices=False, driver="gesvd")   # set-up outside the timing
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    U, sv, Vh = torch.linalg.svd(A, full_matrices=False, driver="gesvd")
+    Le = (U * torch.clamp(sv - 1.0 / mu, min=0.0)) @ Vh
+    T = A + S - Le
+    Se = torch.sign(T) * torch.clamp(T.abs() - lam / mu, min=0.0)
+    Ae = O - Se + (T - Se) / 1.5
+    e1.record()
+    torch.cuda.synchronize()
+    ex_ms = e0.elapsed_time(e1)
+    del U, sv, Vh, Le, T, Se, Ae
+    torch.cuda.empty_cache()
+    out["exact_svd_same_gpu"] = {
+        "value": 1e3 / ex_ms, "unit": UNIT, "ms_per_step": ex_ms,
+        "method": "one iALM iteration with exact SVT by torch.linalg.svd (cuSOLVER gesvd), float32, same GPU",
+        "frsvt_speedup": None}
+
+    # ---- end to end through the public API with host buffers: rpca_init from pinned host O, K2
+    # iterations with the residual read back every step, S and L copied back; run twice, the
+    # second is timed (the first captures the iteration graphs for these buffers)
+    O_host = torch.from_numpy(O_np).pin_memory()
+    S_host = torch.empty_like(O_host).pin_memory()
+    L_host = torch.empty_like(O_host).pin_memory()
+    K2 = max(5, min(args.steps, 20))
+    Od, Sd, Ad, Ld = (torch.empty_like(O) for _ in range(4))
+
+    def e2e_run():
+        Od.copy_(O_host, non_blocking=True)
+        h.rpca_init(Od, Sd, Ad, lam, 1.5, 1e7)
+        for k in range(K2):
+            h.ialm_step(Od, Sd, Ad, RL, L=Ld if k == K2 - 1 else None, sync_residual=True)
+        S_host.copy_(Sd, non_blocking=True)
+        L_host.copy_(Ld, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_run()
+    w0 = time.perf_counter()
+    e2e_run()
+    w = time.perf_counter() - w0
+    nbytes = 4 * RN * RN
+    out["e2e"] = {"value": K2 / w, "unit": UNIT, "h2d_bytes_per_step": nbytes / K2,
+                  "d2h_bytes_per_step": (8 * K2 + 2 * nbytes) / K2,
+                  "what": f"rpca_init (spectral norm by 30 power steps) + {K2} rpca_ialm_step calls from pinned "
+                          f"host O, residual read back every step, S and L copied back at the end; wall clock"}
+    del Od, Sd, Ad, Ld, O_host, S_host, L_host
+
+    # ---- FP64 oracle on the host cores (bounded sample)
+    O64 = O_np.astype(np.float64)
+    rate, cores, dt = oracle_rate(O64, host_norm2(O64), args.oracle_iters)
+    del O64
+    out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": f"{args.oracle_iters} iALM-FRSVT iterations of the full 8192x8192 workload "
+                                     f"({dt:.1f} s), FP64 numpy oracle"}
+    out["recovery_8192_precisions"] = bench_recovery(args, O, lam, dev, flush)
+    out["video"] = bench_video(args, dev, flush)
+    out["wsvt_batch"] = bench_wsvt(dev)
+    out["unrolled_rpca"] = bench_unrolled(dev)
+    out["weather_type_b"] = bench_weather()
+    return out
+
+
+def bench_video(args, dev, flush):
+    """The video-background workload (76800 x 200, l = 10, q = 2, range propagation; the narrow
+    tensor-core path): graph-replayed iterations per second, per-phase times and the roofline of
+    its dominant phase, exact-SVD iALM on the same GPU, and its BF16 / rank-prediction /
+    orthonormalise-last variants."""
+    import numpy as np
+    import torch
+    from paper_1509_00296_gb300 import frsvt, synth
+    O_np, _, _ = synth.video(seed=DATA_SEED)
+    lam = 1.0 / np.sqrt(max(M, N))
+    O = torch.from_numpy(O_np).to(dev)
+    S = torch.empty_like(O)
+    A = torch.empty_like(O)
+    h = frsvt.Handle(M, N, L_COLS, q=Q_POW, range_prop=True, seed=OMEGA_SEED, stream=torch.cuda.current_stream())
+    h.rpca_init(O, S, A, lam, 1.5, 1e7)
+    h.ialm_step(O, S, A, L_COLS)
+    steps = max(10, min(args.steps, 50))
+    ms = graph_rate(h, O, S, A, L_COLS, steps, flush)
+    out = {"workload": WORKLOAD, "ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT}
+    K = 10
     h.enable_timing(True)
     h.timings()
     for k in range(K):
@@ -353,23 +527,18 @@ def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
         h.ialm_step(O, S, A, L_COLS)
     tm = h.timings()
     h.enable_timing(False)
-    phases = {k: v[0] / K for k, v in tm.items() if v[1] > 0}
-    e = 4.0 * M * N                       # one pass over A (float32)
-    z = 4.0 * M * LP_COLS                 # one pass over Z (m x LP float32)
+    out["phases_ms_per_step"] = {k: v[0] / K for k, v in tm.items() if v[1] > 0}
+    e = 4.0 * M * N
+    z = 4.0 * M * LP_COLS
     alg_bytes = {"epilogue": 5 * e + z, "sketch": e, "power_AQ": e + z, "power_AtZ": e + z, "project": e + z,
                  "core": z}
-    launches = {k: v[1] for k, v in tm.items()}
-    dom = max((k for k in alg_bytes if k in tm), key=lambda k: tm[k][0])
-    avg_ms = tm[dom][0] / max(1, launches[dom])
+    dom = max((k for k in alg_bytes if tm.get(k, (0, 0))[1] > 0), key=lambda k: tm[k][0])
+    avg_ms = tm[dom][0] / tm[dom][1]
     peak, _ = peaks()
-    achieved = alg_bytes[dom] / (avg_ms / 1e3) / 1e9
-    out["roofline"] = {"bound": "hbm", "kernel": dom, "kernel_name": PHASE_KERNEL.get(dom), "achieved": achieved,
-                       "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom),
-                       "algorithmic_bytes_per_launch": alg_bytes[dom], "avg_launch_ms": avg_ms}
-    out["phases"] = phases
-
-    # ---- exact-SVD iALM on the same GPU (cuSOLVER through torch.linalg.svd), a few iterations per
-    # cuSOLVER driver (gesvd: QR + bidiagonalisation; gesvdj: Jacobi); the faster one is the baseline
+    ach = alg_bytes[dom] / (avg_ms / 1e3) / 1e9
+    out["roofline"] = {"bound": "hbm", "phase": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                       "frac": ach / peak, "algorithmic_bytes_per_launch": alg_bytes[dom], "avg_launch_ms": avg_ms}
+    # exact-SVD iALM on the same GPU, both cuSOLVER drivers (gesvd, gesvdj); the faster one counts
     normO2 = torch.linalg.matrix_norm(O, 2).item()
     per_driver = {}
     for drv in ("gesvd", "gesvdj"):
@@ -384,9 +553,8 @@ def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record()
         for _ in range(ex_it):
-            U, s, Vh = torch.linalg.svd(Oe - Se + Ye / mu, full_matrices=False, driver=drv)
-            s = torch.clamp(s - 1.0 / mu, min=0.0)
-            Le = (U * s) @ Vh
+            U, sv, Vh = torch.linalg.svd(Oe - Se + Ye / mu, full_matrices=False, driver=drv)
+            Le = (U * torch.clamp(sv - 1.0 / mu, min=0.0)) @ Vh
             T = Oe - Le + Ye / mu
             Se = torch.sign(T) * torch.clamp(T.abs() - lam / mu, min=0.0)
             Ye = Ye + mu * (Oe - Le - Se)
@@ -395,49 +563,12 @@ def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
         torch.cuda.synchronize()
         per_driver[drv] = t0.elapsed_time(t1) / ex_it
     best = min(per_driver, key=per_driver.get)
-    ex_ms = per_driver[best]
-    out["exact"] = {"value": 1e3 / ex_ms, "unit": UNIT, "ms_per_step": ex_ms,
-                    "method": f"iALM with exact SVT by torch.linalg.svd (cuSOLVER {best}, the faster of "
-                              f"gesvd / gesvdj), float32, same GPU",
-                    "ms_per_step_by_driver": per_driver, "frsvt_speedup": None}
-
-    # ---- end to end through the public API with host buffers
-    O_host = torch.from_numpy(O_np).pin_memory()
-    S_host = torch.empty_like(O_host).pin_memory()
-    L_host = torch.empty_like(O_host).pin_memory()
-    K2 = max(5, min(args.steps, 30))
-    Od = torch.empty_like(O)
-    Sd = torch.empty_like(O)
-    Ad = torch.empty_like(O)
-    Ld = torch.empty_like(O)
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    Od.copy_(O_host, non_blocking=True)
-    h.rpca_init(Od, Sd, Ad, lam, 1.5, 1e7)
-    for k in range(K2):
-        h.ialm_step(Od, Sd, Ad, L_COLS, L=Ld if k == K2 - 1 else None, sync_residual=True)
-    S_host.copy_(Sd, non_blocking=True)
-    L_host.copy_(Ld, non_blocking=True)
-    torch.cuda.synchronize()
-    w = time.perf_counter() - w0
-    nbytes = 4 * M * N
-    out["e2e"] = {"value": K2 / w, "unit": UNIT, "h2d_bytes_per_step": nbytes / K2,
-                  "d2h_bytes_per_step": (8 * K2 + 2 * nbytes) / K2,
-                  "what": f"rpca_init + {K2} rpca_ialm_step calls from pinned host O, residual read back "
-                          f"every step, S and L copied back at the end"}
-
-    # ---- FP64 oracle on the host cores (bounded sample)
-    rate, cores, dt = oracle_rate(O_np.astype(np.float64), args.oracle_iters)
-    out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                           "sample": f"{args.oracle_iters} iALM-FRSVT iterations of the full workload ({dt:.1f} s)"}
-    out["exact"]["frsvt_speedup"] = None
-    out["wsvt"] = bench_wsvt(dev)
-    out["unrolled"] = bench_unrolled(dev)
-    out["video_bf16"] = bench_video_bf16(args, O, O_np, lam, dev, flush)
-    out["video_rank_prediction"] = bench_video_ap(args, O, lam, flush)
-    out["video_orth_last"] = bench_video_orth_last(args, O, lam, flush)
-    out["weather_type_b"] = bench_weather()
-    out["recovery"] = bench_recovery(args, dev, flush)
+    out["exact_svd_same_gpu"] = {"ms_per_step": per_driver[best], "driver": best, "ms_by_driver": per_driver,
+                                 "frsvt_speedup": per_driver[best] / ms}
+    h.close()
+    out["bf16"] = bench_video_bf16(args, O, O_np, lam, dev, flush)
+    out["rank_prediction"] = bench_video_ap(args, O, lam, flush)
+    out["orth_last"] = bench_video_orth_last(args, O, lam, flush)
     return out
 
 
@@ -580,57 +711,36 @@ def bench_weather():
             "paper_context": "65.5 ms per frame (n = 5 window, Matlab 2014a, one CPU thread, Sec. 4.2)"}
 
 
-def bench_recovery(args, dev, flush):
-    """Large low-rank recovery: 8192 x 8192 rank 100 + 10 % corruption, iALM with FRSVT l = 120,
-    q = 2 (the wide-basis path) in FP32-accurate, BF16-shadow and FP8-shadow (E4M3, per-128 x 128-tile
-    scales) modes: iterations per second from a captured graph, per-phase device times, and one exact
-    SVT (torch.linalg.svd, cuSOLVER) of the same iterate on the same GPU."""
-    import numpy as np
+def bench_recovery(args, O, lam, dev, flush):
+    """The headline workload in the BF16-shadow and FP8-shadow (E4M3, per-128 x 128-tile power-of-two
+    scales) modes: sketch and first power step on the shadow, FP32-accurate last power step and
+    projection.  Iterations per second from a captured graph and per-phase device times."""
     import torch
-    from paper_1509_00296_gb300 import frsvt, synth
-    n, l = 8192, 120
-    O_np, _, _ = synth.recovery_8192(seed=1003)
-    O = torch.from_numpy(np.ascontiguousarray(O_np, dtype=np.float32)).to(dev)
-    del O_np
+    from paper_1509_00296_gb300 import frsvt
+    out = {"workload": RWORKLOAD, "unit": UNIT, "hbm_floor_ms_fp32": 11 * 4.0 * RN * RN / (peaks()[0] * 1e9) * 1e3}
     S = torch.empty_like(O)
     A = torch.empty_like(O)
-    out = {"workload": "8192 x 8192 rank 100 (factors / 10) + 10 % corruption in [-10, 10], FRSVT l=120 q=2",
-           "unit": UNIT, "hbm_floor_ms_fp32": 11 * 4.0 * n * n / (peaks()[0] * 1e9) * 1e3}
-    for name, prec in (("fp32", frsvt.PREC_FP32), ("bf16", frsvt.PREC_BF16), ("fp8", frsvt.PREC_FP8)):
-        h = frsvt.Handle(n, n, l, q=2, range_prop=False, seed=2004, stream=torch.cuda.current_stream(),
+    for name, prec in (("bf16", frsvt.PREC_BF16), ("fp8", frsvt.PREC_FP8)):
+        h = frsvt.Handle(RN, RN, RL, q=RQ, range_prop=False, seed=ROMEGA_SEED, stream=torch.cuda.current_stream(),
                          precision=prec)
-        h.rpca_init(O, S, A, 1.0 / np.sqrt(n), 1.5, 1e7)
+        h.rpca_init(O, S, A, lam, 1.5, 1e7)
         for _ in range(3):
-            h.ialm_step(O, S, A, l)
+            h.ialm_step(O, S, A, RL)
         K = 5
         h.enable_timing(True)
         h.timings()
         for k in range(K):
             flush.fill_(float(k))
-            h.ialm_step(O, S, A, l)
+            h.ialm_step(O, S, A, RL)
         tm = h.timings()
         h.enable_timing(False)
-        ms = graph_rate(h, O, S, A, l, 10, flush)
+        ms = graph_rate(h, O, S, A, RL, 10, flush)
         info = h.info()
         out[name] = {"ms_per_step": ms, "value": 1e3 / ms,
                      "phases_ms_per_step": {k: v[0] / K for k, v in tm.items() if v[1] > 0},
                      "launches_per_step": sum(v[1] for v in tm.values()) / K, "jacobi_sweeps": info.sweeps,
-                     "rank": info.r, "device_status": info.device_status}
+                     "rank": info.r, "basis": info.s, "device_status": info.device_status}
         h.close()
-    # one exact SVT of the current iterate on the same GPU (after a warm-up call on a small matrix)
-    torch.linalg.svd(A[:1024, :1024], full_matrices=False)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    U, sv, Vh = torch.linalg.svd(A, full_matrices=False)
-    X = (U * torch.clamp(sv - 1e-3, min=0.0)) @ Vh
-    e1.record()
-    torch.cuda.synchronize()
-    ex_ms = e0.elapsed_time(e1)
-    del U, sv, Vh, X
-    out["exact_svt_same_gpu_ms"] = ex_ms
-    out["frsvt_iter_vs_exact_svt"] = ex_ms / out["fp32"]["ms_per_step"]
-    out["value"] = out["fp32"]["value"]
     return out
 
 

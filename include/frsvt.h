@@ -24,8 +24,10 @@
  *     call allocates.
  *   - Orientation: the orthonormal basis Q of Alg. 1 is kept on the shorter
  *     side of A (Sec. 2.5 asks for the transposed problem when needed).  The
- *     Gaussian test matrix Omega therefore has max(m, n) rows.  This release
- *     supports m >= n (tall or square A); m < n returns FRSVT_ERR_UNSUPPORTED.
+ *     Gaussian test matrix Omega therefore has max(m, n) rows.  The wide-basis
+ *     handle (cfg.l_max > 32) serves both orientations: for m < n its two
+ *     passes over A swap roles (no copy of A is made).  The narrow-basis handle
+ *     (cfg.l_max <= 32) serves m >= n; m < n returns FRSVT_ERR_UNSUPPORTED.
  */
 #ifndef FRSVT_H_
 #define FRSVT_H_
@@ -149,6 +151,21 @@ frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, in
                        float tau, int32_t l, float* X, int64_t ldx);
 
 /*
+ * The same FRSVT as frsvt_svt, returned in factored form instead of forming X (Eq. 6 with the
+ * small factors folded in):  X = U V^T  with U (m x l, ldu) and V (n x l, ldv).  For m >= n,
+ * U = A Q and V = Q M; for m < n (wide-basis handles), U = Q M and V = A^T Q; Q is the orthonormal
+ * basis of Alg. 1 on the short side and M = V_B diag(f(sigma) / sigma) V_B^T the l x l core
+ * (f the soft threshold, or the partial threshold after frsvt_set_partial).  Columns of U and V
+ * past the basis size are zero.  r (nullable, device memory) receives #{sigma_i > tau}.  Under
+ * adaptive rank prediction U and V get the panel width (16 or 32) of columns, so ldu and ldv must
+ * be at least that.  Same arguments, limits, side effects (Omega counter, propagated basis) and
+ * errors as frsvt_svt; U, V and r are caller-owned device memory; asynchronous.
+ */
+frsvt_status frsvt_svt_factors(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda,
+                               float tau, int32_t l, float* U, int64_t ldu, float* V, int64_t ldv,
+                               int32_t* r);
+
+/*
  * Largest singular value of A by block power iteration (the range finder of
  * Sec. 2.1 with `iters` power steps and l = cfg.l_max columns).  Synchronizes
  * and writes the value to *sigma1.  Does not touch the propagated basis or
@@ -182,9 +199,10 @@ frsvt_status rpca_init(frsvt_handle* h, const float* O, float* S, float* A,
  * The first call with a given (O, S, A, m, n, ld, l, L, ldl) captures the
  * iteration's kernels into a CUDA graph on a stream private to the handle;
  * later calls with the same arguments replay it on the handle's stream (the
- * iteration's state lives on the device).  rpca_init, frsvt_reset,
+ * iteration's state lives on the device); the graphs of the four most
+ * recently used argument tuples are kept.  rpca_init, frsvt_reset,
  * frsvt_set_stream, frsvt_set_rank_prediction and frsvt_set_partial retire
- * the graph.  While the handle's stream is being captured by the caller, or
+ * the graphs.  While the handle's stream is being captured by the caller, or
  * with phase timing on, the kernels are launched directly.
  */
 frsvt_status rpca_ialm_step(frsvt_handle* h, const float* O, float* S, float* A,
@@ -233,7 +251,7 @@ frsvt_status frsvt_set_partial(frsvt_handle* h, int32_t k);
  * since the previous call, and clears them.  ms and launches have
  * FRSVT_NPHASE entries.  Disabling collects pending events first.
  */
-#define FRSVT_NPHASE 10
+#define FRSVT_NPHASE 11
 #define FRSVT_PHASE_SKETCH    0   /* Y = A^T Omega            (Alg. 1 steps 4-5, 8-9) */
 #define FRSVT_PHASE_POWER_AQ  1   /* Z = A Q in a power step  (step 14) */
 #define FRSVT_PHASE_POWER_ATZ 2   /* Y = A^T Z in a power step (step 14) */
@@ -244,6 +262,8 @@ frsvt_status frsvt_set_partial(frsvt_handle* h, int32_t k);
 #define FRSVT_PHASE_CORE      7   /* l x l SVD and shrinkage  (steps 16-19) */
 #define FRSVT_PHASE_EPILOGUE  8   /* X = Z M Q^T, fused with the iALM update (Eq. 6) */
 #define FRSVT_PHASE_FINISH    9   /* residual reduction and mu update */
+#define FRSVT_PHASE_APPLY    10   /* products with the small factors on the wide basis:
+                                     Q = Y R^{-1} (steps 6 / 14), Rf = Q M and Q~ = Q U (step 19) */
 frsvt_status frsvt_enable_timing(frsvt_handle* h, int32_t enable);
 frsvt_status frsvt_get_timings(frsvt_handle* h, double* ms, int32_t* launches);
 const char* frsvt_phase_name(int32_t phase);
@@ -252,9 +272,11 @@ const char* frsvt_phase_name(int32_t phase);
  * Allocation-free FRSVT (the paper has no counterpart: this is a deployment
  * entry point, not part of the method).
  *
- * Some callers cannot allocate device memory: code running inside a CUDA graph
- * capture that forbids allocation, plug-ins whose host framework owns every
- * device allocation, real-time paths that must not enter the allocator.
+ * Some callers cannot allocate device memory: plug-ins whose host framework
+ * owns every device allocation through its own pool, real-time paths that must
+ * not enter the allocator (cudaMalloc / cudaFree may synchronize the device and
+ * take unbounded time), services that fix their device-memory budget at
+ * start-up.
  * frsvt_svt_noalloc computes the same X = FRSVT_tau(A) as frsvt_svt (no range
  * propagation; Omega stream index `counter`, key `seed`) without a handle and
  * without allocating: no cudaMalloc, no cudaFree, no allocating library call.
@@ -263,8 +285,11 @@ const char* frsvt_phase_name(int32_t phase);
  *
  * Limits (checked; larger sizes return FRSVT_ERR_INVALID_ARG):
  *   m <= FRSVT_NOALLOC_MAX_M, n <= FRSVT_NOALLOC_MAX_N, m >= n (m < n:
- *   FRSVT_ERR_UNSUPPORTED), 1 <= l <= 16, 0 <= q <= 64.  A and X are
- *   caller-owned device buffers with the alignment rules above.
+ *   FRSVT_ERR_UNSUPPORTED), 1 <= l <= 16, 0 <= q <= 64, tau finite and >= 0,
+ *   counter != UINT64_MAX (a reserved value).  A and X are caller-owned device
+ *   buffers with the alignment rules above.  The kernels' device status bits
+ *   (non-finite values, an unconverged core, a rank-deficient sketch) are not
+ *   reported by this entry point.
  * The first call on a device performs a one-time set-up on that device (the
  * device address of the scratch array, kernel attributes); make that first call
  * before any stream capture.  Every call shares the one array and keeps the
@@ -311,6 +336,42 @@ frsvt_status frsvt_svt_save(frsvt_handle* h, const float* A, int64_t m, int64_t 
 frsvt_status frsvt_backward(frsvt_handle* h, const void* saved, const float* A, int64_t m, int64_t n, int64_t lda,
                             float tau, int32_t l, uint64_t omega_stream, const float* dX, int64_t lddx, float* dA,
                             int64_t ldda, float* dtau);
+
+/* ------------------------------------------------------------------ unrolled iALM RPCA
+ * The differentiable workload: K inexact-ALM steps of robust PCA (the host algorithm of Sec. 4.1)
+ * unrolled, with a threshold tau_k and a penalty mu_k per step as learnable parameters, over a
+ * batch of B matrices (each m x n, m >= n, n % 4 == 0, row-major with leading dimension ld; the
+ * batch is contiguous, problem b at O + b m ld):
+ *     A_k = O - S_{k-1} + Y_{k-1} / mu_k,   L_k = FRSVT_{tau_k}(A_k)  (Alg. 1, Omega stream k),
+ *     S_k = shrink_{lambda / mu_k}(O - L_k + Y_{k-1} / mu_k),   Y_k = Y_{k-1} + mu_k (O - L_k - S_k),
+ * from S_0 = 0 and Y_0 = y0_scale_b O (y0_scale_b = 1 / max(||O_b||_2, ||O_b||_inf / lambda), the
+ * iALM initialisation).  The output is L_K.  The library runs the whole batch and every step in
+ * one call: the FRSVT and its adjoint (frsvt_svt_save / frsvt_backward) and fused elementwise
+ * kernels for the shrinkage, the multiplier update and their adjoints.  The handle must be
+ * created with FRSVT_CFG_ADJOINT (the adjoint's size limits apply).
+ *
+ * rpca_unrolled_saved_bytes: size of the caller-owned device buffer `saved` (per problem and step:
+ *   A_k, L_k, Y_{k-1} and the FRSVT factors; plus the backward scratch).
+ * rpca_unrolled_init: y0_scale (HOST array of B floats) from ||O_b||_2 (frsvt_spectral_norm with
+ *   power_iters steps) and the largest |O_b| entry.  Synchronizes.
+ * rpca_unrolled_forward: tau, mu: HOST arrays of K floats (tau_k >= 0, mu_k > 0); L: B x m x ld
+ *   device output (L_K of every problem); saved: written for the backward pass.  Asynchronous.
+ * rpca_unrolled_backward: dL (B x m x ld, the cotangent of L_K) -> dtau, dmu (DEVICE arrays of K
+ *   floats, overwritten): the gradient of <dL, L_K> summed over the batch.  Same O, y0_scale,
+ *   tau, mu, lambda, l as the forward call that wrote `saved`.  Asynchronous.
+ * Errors: FRSVT_ERR_INVALID_ARG (sizes, pointers, alignment, parameters), FRSVT_ERR_UNSUPPORTED
+ * (no adjoint workspace, adjoint size limits), FRSVT_ERR_CUDA. */
+size_t rpca_unrolled_saved_bytes(const frsvt_handle* h, int32_t batch, int32_t steps, int64_t m, int64_t n,
+                                 int64_t ld);
+frsvt_status rpca_unrolled_init(frsvt_handle* h, int32_t batch, const float* O, int64_t m, int64_t n, int64_t ld,
+                                double lambda, int32_t power_iters, float* y0_scale);
+frsvt_status rpca_unrolled_forward(frsvt_handle* h, int32_t batch, int32_t steps, const float* O, int64_t m,
+                                   int64_t n, int64_t ld, const float* y0_scale, const float* tau, const float* mu,
+                                   float lambda, int32_t l, float* L, void* saved);
+frsvt_status rpca_unrolled_backward(frsvt_handle* h, int32_t batch, int32_t steps, const float* O, int64_t m,
+                                    int64_t n, int64_t ld, const float* y0_scale, const float* tau, const float* mu,
+                                    float lambda, int32_t l, const void* saved, const float* dL, float* dtau,
+                                    float* dmu);
 
 /* ------------------------------------------------------------------ batched weighted SVT
  * Weighted SVT (the WSVT footnote of Sec. 1) of a batch of small independent matrices, the
@@ -359,6 +420,13 @@ frsvt_status frsvt_debug_rows_tc(frsvt_handle* h, const float* A, int64_t m, int
  * Y: n x LP row-major (n <= 256).  Enqueued on the handle's stream. */
 frsvt_status frsvt_debug_cols_tc(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda,
                                  const float* B, uint64_t seed, uint64_t stream, float* Y);
+/* Failure detection of the bounded waits: one CTA waits, polling at most spin_limit times
+ * (1 <= spin_limit <= 2^20), on an mbarrier that nothing arrives at, with the same bounded poll
+ * that every pipeline wait of the library uses (where the limit is fixed at 2^26 polls).  The
+ * wait gives up, the kernel ORs FRSVT_DEV_TIMEOUT into the handle's device status and returns
+ * (it holds no tensor memory and has no copy in flight, so the handle and the context stay
+ * usable).  Enqueued on the handle's stream; read the bit with frsvt_get_info. */
+frsvt_status frsvt_debug_wait_timeout(frsvt_handle* h, uint32_t spin_limit);
 /* Raw Philox4x64-10 words for counters (i, j, stream, problem), i < rows, j < blocks: rows x blocks x 4 uint64. */
 frsvt_status frsvt_debug_philox(uint64_t* out, int64_t rows, int32_t blocks, uint64_t seed,
                                 uint64_t stream, uint64_t problem, void* cuda_stream);

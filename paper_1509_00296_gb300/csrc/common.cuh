@@ -110,6 +110,20 @@ __device__ __forceinline__ df64 df_rsqrt(df64 a) {
 }
 
 // ---------------------------------------------------------------- small utilities
+// Sort key of a singular value for the descending order of D: NaN ranks below every number, so
+// that ranking by (key, index) is a permutation whatever the values are.
+__device__ __forceinline__ float sigma_rank_key(float x) { return x == x ? x : -3.0e38f; }
+
+// Position of entry `self` in the descending order of v[0..count) (ties: lower index first).
+__device__ __forceinline__ int sigma_rank(const float* v, int count, int self) {
+  const float k = sigma_rank_key(v[self]);
+  int r = 0;
+  for (int c = 0; c < count; ++c) {
+    const float kc = sigma_rank_key(v[c]);
+    r += (kc > k || (kc == k && c < self)) ? 1 : 0;
+  }
+  return r;
+}
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -137,6 +137,22 @@ cudaError_t launch_wd_apply(const float* in, int64_t ldi, int64_t len, const flo
                             int64_t ldo, float* outR, float* outRl, cudaStream_t st);
 cudaError_t launch_wd_trsm(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
                            void* outTb, void* outTbl, int64_t ldo, cudaStream_t st);
+int unrolled_grid(int64_t m, int64_t n, int sms);
+cudaError_t launch_ur_pre(const float* O, const float* S, const float* Y, float ys, float* A, int64_t m, int64_t n,
+                          int64_t ld, float mu, int grid, cudaStream_t st);
+cudaError_t launch_ur_post(const float* O, const float* L, const float* Y, float ys, float* S, float* Yout, float* An,
+                           int64_t m, int64_t n, int64_t ld, float mu, float mu_next, float lam, int grid,
+                           cudaStream_t st);
+cudaError_t launch_ur_bwd_post(const float* O, const float* L, const float* Y, float ys, const float* Sb,
+                               const float* Yb, const float* Lin, float* Lb, float* Yb2, float* Tb, int64_t m,
+                               int64_t n, int64_t ld, float mu, float lam, double* part, int grid, cudaStream_t st);
+cudaError_t launch_ur_bwd_pre(const float* O, const float* Y, float ys, const float* Ab, const float* Tb, float* Sb,
+                              float* Yb2, int64_t m, int64_t n, int64_t ld, float mu, double* part, int grid,
+                              cudaStream_t st);
+cudaError_t launch_ur_sum(const double* part, int count, float* out, int accumulate, cudaStream_t st);
+cudaError_t launch_ur_addf(const float* in, float* out, cudaStream_t st);
+cudaError_t launch_absmax_sumsq(const float* O, int64_t m, int64_t n, int64_t ld, float* pmax, float2* psum, int nblk,
+                                cudaStream_t st);
 cudaError_t launch_wd_alm(bool alm, const CUtensorMap& tmZ, const CUtensorMap& tmZl, const CUtensorMap& tmR,
                           const CUtensorMap& tmRl, int64_t m, int64_t n, const float* O, float* S, float* A, int64_t ld,
                           float* L, int64_t ldl, DevState* dst, double* cpart, unsigned* ticket, int grid,
@@ -212,12 +228,15 @@ struct frsvt_handle {
   };
   uint64_t epoch = 1;
   cudaStream_t capture_stream = nullptr;
-  cudaGraphExec_t step_exec = nullptr;
-  StepKey step_key{};
+  static constexpr int kGraphSlots = 4;          // graphs kept for the most recent argument tuples
+  cudaGraphExec_t step_exec[kGraphSlots] = {};
+  StepKey step_key[kGraphSlots] = {};
+  uint64_t step_used[kGraphSlots] = {};           // last use (LRU eviction)
+  uint64_t step_clock = 0;
   // wide basis (cfg.l_max > 32, LP = 128, any short side): basis-side matrices transposed
   // (128 x ld_m / ld_n), Z and Rf row-major (len x 128), K-split partials, Gram partials
   bool wide = false;
-  int64_t w_ldm = 0, w_ldn = 0, w_ldp = 0;
+  int64_t w_ldl = 0, w_lds = 0, w_ldp = 0;      // long-side / short-side / partial row strides
   float *wOT = nullptr, *wOTl = nullptr, *wZT = nullptr, *wZTl = nullptr, *wZ = nullptr, *wZl = nullptr;
   float *wYT = nullptr, *wQT = nullptr, *wQTl = nullptr, *wQp = nullptr, *wRf = nullptr, *wRfl = nullptr;
   float *wT1 = nullptr, *wT2 = nullptr, *wpart = nullptr;
@@ -432,7 +451,8 @@ frsvt_status check_matrix(frsvt_handle* h, const void* p, int64_t m, int64_t n, 
 
 frsvt_status check_shape(frsvt_handle* h, int64_t m, int64_t n) {
   if (m < 0 || n < 0) return fail(h, FRSVT_ERR_INVALID_ARG, "negative size");
-  if (m < n) return fail(h, FRSVT_ERR_UNSUPPORTED, "m < n: pass the transposed problem (this build orients tall)");
+  if (m < n && !h->wide)
+    return fail(h, FRSVT_ERR_UNSUPPORTED, "m < n is served by the wide-basis handle (l_max > 32) only");
   if (m > h->cfg.m_max || n > h->cfg.n_max)
     return fail(h, FRSVT_ERR_INVALID_ARG, "problem larger than the handle's m_max / n_max");
   return FRSVT_OK;
@@ -572,8 +592,10 @@ frsvt_status sync_rp_shape(frsvt_handle* h, int64_t m, int64_t n, int l) {
 }
 
 void free_all(frsvt_handle* h) {
-  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
-  h->step_exec = nullptr;
+  for (auto& g : h->step_exec) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   h->capture_stream = nullptr;
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -589,30 +611,36 @@ void free_all(frsvt_handle* h) {
 }
 
 // ---------------------------------------------------------------- wide basis (32 < l <= 128)
-// Orthonormal basis of the columns of Y (given transposed, 128 x n at h->wYT) into QT / QTl:
+// Orientation (reading R1): the basis lives on the short side of A.  For m >= n (tall) the short
+// side is the columns, and the passes over A are the column pass (reduce over the rows, output on
+// the column side) and the row pass (reduce over the columns, output on the row side); for m < n
+// (wide) the same two kernels swap roles, with no copy of A.  Basis-side matrices (Y^T, Q^T) have
+// ns = min(m, n) columns (stride w_lds), long-side ones (Omega^T, Z^T, Z) nl = max(m, n) (w_ldl).
+
+// Orthonormal basis of the columns of Y (given transposed, 128 x ns at h->wYT) into QT / QTl:
 // Cholesky QR, `passes` times (Alg. 1 steps 6 / 14; only span(Q) matters, Prop. 1).
-// With bf_next the basis is also written as BF16 hi / lo parts (the next row pass reads the shadow).
-frsvt_status wide_orth(frsvt_handle* h, int64_t n, int l, int passes, bool bf_next) {
+// With bf_next the basis is also written as BF16 hi / lo parts (the next pass reads the shadow).
+frsvt_status wide_orth(frsvt_handle* h, int64_t ns, int l, int passes, bool bf_next) {
   cudaStream_t st = h->stream;
-  const int64_t ld = h->w_ldn;
+  const int64_t ld = h->w_lds;
   unsigned* gt = h->wtick + h->w_ntiles;
   for (int pass = 0; pass < passes; ++pass) {
     const float* src = pass == 0 ? h->wYT : h->wQT;
     const bool last = pass == passes - 1;
-    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_gram(false, src, ld, n, h->w_gram_grid, h->wgc, h->wGpk, gt, l,
+    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_gram(false, src, ld, ns, h->w_gram_grid, h->wgc, h->wGpk, gt, l,
                                                   h->cfg.rank_tol, l, 0.f, 0, 0, 0, h->cfg.max_jacobi_sweeps, h->wT1,
                                                   h->wT2, h->dst, st));
-    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_trsm(src, ld, n, h->wT1, h->wQT, h->wQTl,
+    FRSVT_LAUNCH(FRSVT_PHASE_APPLY, launch_wd_trsm(src, ld, ns, h->wT1, h->wQT, h->wQTl,
                                                   (bf_next && last) ? h->wQTb : nullptr,
                                                   (bf_next && last) ? h->wQTbl : nullptr, ld, st));
   }
   return FRSVT_OK;
 }
 
-// Alg. 1 up to the core on the wide basis: leaves Z / Z_lo (m x 128) and Rf / Rf_lo (n x 128)
-// so that X = Z Rf^T, and sets r, s, sigma (and the counter) in the device state.
-// Shadow the reduced-precision passes read: 0 none, 1 the BF16 shadow (kept current by rpca_init,
-// frsvt_svt and the epilogue), 2 the E4M3 shadow (quantized at the start of each SVT).
+// Alg. 1 up to the core on the wide basis: leaves Z / Z_lo (nl x 128) and Rf / Rf_lo (ns x 128)
+// so that X = Z Rf^T (tall) or X = Rf Z^T (wide), and sets r, s, sigma (and the counter) in the
+// device state.  Shadow the reduced-precision passes read: 0 none, 1 the BF16 shadow (kept current
+// by rpca_init, frsvt_svt and the epilogue), 2 the E4M3 shadow (quantized at the start of each SVT).
 int wide_lowp(const frsvt_handle* h) { return h->A8 != nullptr ? 2 : (h->Ab != nullptr ? 1 : 0); }
 
 // Reduced precision (lowp, see wide_lowp): the sketch and the first q - 1 power steps
@@ -622,15 +650,18 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
                                  uint64_t ctr, float tau_host, int tau_from_mu, int advance_counter, int lowp = 0) {
   cudaStream_t st = h->stream;
   const int64_t LW = wide_lp();
+  const bool tall = m >= n;
+  const int64_t nl = tall ? m : n, ns = tall ? n : m;
+  const int64_t ldl = h->w_ldl, lds = h->w_lds;
   CUtensorMap tmAr, tmAc, tmOT, tmOTl, tmZT, tmZTl, tmQT, tmQTl;
   if (!make_row_map_sw128(&tmAr, A, m, n, lda, wide_tile()) ||
       !make_row_map_sw128(&tmAc, A, m, n, lda, 32, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) ||
-      !make_row_map_sw128(&tmOT, h->wOT, LW, m, h->w_ldm, 128) ||
-      !make_row_map_sw128(&tmOTl, h->wOTl, LW, m, h->w_ldm, 128) ||
-      !make_row_map_sw128(&tmZT, h->wZT, LW, m, h->w_ldm, 128) ||
-      !make_row_map_sw128(&tmZTl, h->wZTl, LW, m, h->w_ldm, 128) ||
-      !make_row_map_sw128(&tmQT, h->wQT, LW, n, h->w_ldn, 128) ||
-      !make_row_map_sw128(&tmQTl, h->wQTl, LW, n, h->w_ldn, 128))
+      !make_row_map_sw128(&tmOT, h->wOT, LW, nl, ldl, 128) ||
+      !make_row_map_sw128(&tmOTl, h->wOTl, LW, nl, ldl, 128) ||
+      !make_row_map_sw128(&tmZT, h->wZT, LW, nl, ldl, 128) ||
+      !make_row_map_sw128(&tmZTl, h->wZTl, LW, nl, ldl, 128) ||
+      !make_row_map_sw128(&tmQT, h->wQT, LW, ns, lds, 128) ||
+      !make_row_map_sw128(&tmQTl, h->wQTl, LW, ns, lds, 128))
     return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis)");
   const bool bf = lowp != 0;
   CUtensorMap tmBr, tmBc, tmOTb, tmOTbl, tmZTb, tmZTbl, tmQTb, tmQTbl;
@@ -644,65 +675,79 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
     return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis, BF16 shadow)");
   const float* sc8 = lowp == 2 ? h->w8s : nullptr;
   const int ntr8 = static_cast<int>(cdiv(m, 128)), ntc8 = static_cast<int>(cdiv(n, 128));
-  if (bf && (!make_row_map_bf16(&tmOTb, h->wOTb, LW, m, h->w_ldm, 128) ||
-             !make_row_map_bf16(&tmOTbl, h->wOTbl, LW, m, h->w_ldm, 128) ||
-             !make_row_map_bf16(&tmZTb, h->wZTb, LW, m, h->w_ldm, 128) ||
-             !make_row_map_bf16(&tmZTbl, h->wZTbl, LW, m, h->w_ldm, 128) ||
-             !make_row_map_bf16(&tmQTb, h->wQTb, LW, n, h->w_ldn, 128) ||
-             !make_row_map_bf16(&tmQTbl, h->wQTbl, LW, n, h->w_ldn, 128)))
+  if (bf && (!make_row_map_bf16(&tmOTb, h->wOTb, LW, nl, ldl, 128) ||
+             !make_row_map_bf16(&tmOTbl, h->wOTbl, LW, nl, ldl, 128) ||
+             !make_row_map_bf16(&tmZTb, h->wZTb, LW, nl, ldl, 128) ||
+             !make_row_map_bf16(&tmZTbl, h->wZTbl, LW, nl, ldl, 128) ||
+             !make_row_map_bf16(&tmQTb, h->wQTb, LW, ns, lds, 128) ||
+             !make_row_map_bf16(&tmQTbl, h->wQTbl, LW, ns, lds, 128)))
     return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide basis, BF16 factors)");
-  const int Sr = wide_splits(m, n, h->sms), Sc = wide_splits(n, m, h->sms);
+  // P_short reduces over the long side of A (output on the basis side: Y^T = M^T A or M^T A^T),
+  // P_long reduces over the short side (output on the long side: Z^T = Q^T A^T or Q^T A)
+  const bool short_col = tall;                   // P_short is the column pass for a tall A
+  const CUtensorMap& tmS = short_col ? tmAc : tmAr;
+  const CUtensorMap& tmL = short_col ? tmAr : tmAc;
+  const CUtensorMap& tmSb = short_col ? tmBc : tmBr;
+  const CUtensorMap& tmLb = short_col ? tmBr : tmBc;
+  const int Ss = wide_splits(ns, nl, h->sms), Sl = wide_splits(nl, ns, h->sms);
   FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_omega(h->wOT, h->wOTl, bf ? h->wOTb : nullptr, bf ? h->wOTbl : nullptr,
-                                                   h->w_ldm, m, l, 0, h->cfg.seed, ctr, h->dst, st));
+                                                   ldl, nl, l, 0, h->cfg.seed, ctr, h->dst, st));
   if (bf)
-    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(true, lowp, tmBc, tmOTb, tmOTbl, n, m, Sc, h->wpart, h->w_ldp,
-                                                    h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn, nullptr,
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(short_col, lowp, tmSb, tmOTb, tmOTbl, ns, nl, Ss, h->wpart,
+                                                    h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr, lds, nullptr,
                                                     nullptr, h->dst, st, sc8, ntr8, ntc8));
   else
-    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(true, 0, tmAc, tmOT, tmOTl, n, m, Sc, h->wpart, h->w_ldp,
-                                                    h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn, nullptr,
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(short_col, 0, tmS, tmOT, tmOTl, ns, nl, Ss, h->wpart, h->w_ldp,
+                                                    h->wtick, h->wYT, nullptr, nullptr, nullptr, lds, nullptr,
                                                     nullptr, h->dst, st));
-  frsvt_status s = wide_orth(h, n, l, q == 0 ? 2 : 1, bf && q > 1);
+  frsvt_status s = wide_orth(h, ns, l, q == 0 ? 2 : 1, bf && q > 1);
   if (s != FRSVT_OK) return s;
   for (int it = 0; it < q; ++it) {
     if (bf && it < q - 1) {
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(false, lowp, tmBr, tmQTb, tmQTbl, m, n, Sr, h->wpart,
-                                                        h->w_ldp, h->wtick, nullptr, nullptr, h->wZTb, h->wZTbl,
-                                                        h->w_ldm, nullptr, nullptr, h->dst, st, sc8, ntr8, ntc8));
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(true, lowp, tmBc, tmZTb, tmZTbl, n, m, Sc, h->wpart,
-                                                         h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr,
-                                                         h->w_ldn, nullptr, nullptr, h->dst, st, sc8, ntr8, ntc8));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(!short_col, lowp, tmLb, tmQTb, tmQTbl, nl, ns, Sl, h->wpart,
+                                                        h->w_ldp, h->wtick, nullptr, nullptr, h->wZTb, h->wZTbl, ldl,
+                                                        nullptr, nullptr, h->dst, st, sc8, ntr8, ntc8));
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(short_col, lowp, tmSb, tmZTb, tmZTbl, ns, nl, Ss, h->wpart,
+                                                         h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr, lds,
+                                                         nullptr, nullptr, h->dst, st, sc8, ntr8, ntc8));
     } else {
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(false, 0, tmAr, tmQT, tmQTl, m, n, Sr, h->wpart, h->w_ldp,
-                                                        h->wtick, h->wZT, h->wZTl, nullptr, nullptr, h->w_ldm,
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(!short_col, 0, tmL, tmQT, tmQTl, nl, ns, Sl, h->wpart,
+                                                        h->w_ldp, h->wtick, h->wZT, h->wZTl, nullptr, nullptr, ldl,
                                                         nullptr, nullptr, h->dst, st));
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(true, 0, tmAc, tmZT, tmZTl, n, m, Sc, h->wpart, h->w_ldp,
-                                                         h->wtick, h->wYT, nullptr, nullptr, nullptr, h->w_ldn,
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(short_col, 0, tmS, tmZT, tmZTl, ns, nl, Ss, h->wpart,
+                                                         h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr, lds,
                                                          nullptr, nullptr, h->dst, st));
     }
-    if ((s = wide_orth(h, n, l, it == q - 1 ? 2 : 1, bf && it + 1 < q - 1)) != FRSVT_OK) return s;
+    if ((s = wide_orth(h, ns, l, it == q - 1 ? 2 : 1, bf && it + 1 < q - 1)) != FRSVT_OK) return s;
   }
-  // projection B^T = Z = A Q (step 16), then B B^T = Z^T Z and the core (steps 16-19)
-  FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_wd_pass(false, 0, tmAr, tmQT, tmQTl, m, n, Sr, h->wpart, h->w_ldp,
-                                                   h->wtick, h->wZT, nullptr, nullptr, nullptr, h->w_ldm, h->wZ,
-                                                   h->wZl, h->dst, st));
-  FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_wd_gram(true, h->wZT, h->w_ldm, m, h->w_gram_grid, h->wgc, h->wGpk,
+  // projection B^T = Z (step 16), then B B^T = Z^T Z and the core (steps 16-19)
+  FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_wd_pass(!short_col, 0, tmL, tmQT, tmQTl, nl, ns, Sl, h->wpart, h->w_ldp,
+                                                   h->wtick, h->wZT, nullptr, nullptr, nullptr, ldl, h->wZ, h->wZl,
+                                                   h->dst, st));
+  FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_wd_gram(true, h->wZT, ldl, nl, h->w_gram_grid, h->wgc, h->wGpk,
                                                 h->wtick + h->w_ntiles, l, h->cfg.rank_tol, l, tau_host, tau_from_mu, 0,
                                                 advance_counter, h->cfg.max_jacobi_sweeps, h->wT1, h->wT2, h->dst,
                                                 st));
-  FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_wd_apply(h->wQT, h->w_ldn, n, h->wT1, nullptr, nullptr, 0, h->wRf, h->wRfl,
+  FRSVT_LAUNCH(FRSVT_PHASE_APPLY, launch_wd_apply(h->wQT, lds, ns, h->wT1, nullptr, nullptr, 0, h->wRf, h->wRfl,
                                                  st));
   return FRSVT_OK;
 }
 
-// X = Z Rf^T (alm = false: written to L) or the fused iALM update (alm = true).
+// X = Z Rf^T (tall) or Rf Z^T (wide): written to L (alm = false) or fused with the iALM update
+// (alm = true).  The epilogue kernel forms X[i][j] = sum_k P[i][k] Q[j][k] for its row factor P
+// (m x 128) and column factor Q (n x 128): (Z, Rf) for a tall A, (Rf, Z) for a wide one.
 frsvt_status wide_epilogue(frsvt_handle* h, bool alm, int64_t m, int64_t n, const float* O, float* S, float* A,
                            int64_t ld, float* L, int64_t ldl) {
+  const bool tall = m >= n;
+  const float* P = tall ? h->wZ : h->wRf;
+  const float* Pl = tall ? h->wZl : h->wRfl;
+  const float* Qf = tall ? h->wRf : h->wZ;
+  const float* Ql = tall ? h->wRfl : h->wZl;
   CUtensorMap tmZ, tmZl, tmR, tmRl;
-  if (!make_row_map_sw128(&tmZ, h->wZ, m, wide_lp(), wide_lp(), 128) ||
-      !make_row_map_sw128(&tmZl, h->wZl, m, wide_lp(), wide_lp(), 128) ||
-      !make_row_map_sw128(&tmR, h->wRf, n, wide_lp(), wide_lp(), wide_tile()) ||
-      !make_row_map_sw128(&tmRl, h->wRfl, n, wide_lp(), wide_lp(), wide_tile()))
+  if (!make_row_map_sw128(&tmZ, P, m, wide_lp(), wide_lp(), 128) ||
+      !make_row_map_sw128(&tmZl, Pl, m, wide_lp(), wide_lp(), 128) ||
+      !make_row_map_sw128(&tmR, Qf, n, wide_lp(), wide_lp(), wide_tile()) ||
+      !make_row_map_sw128(&tmRl, Ql, n, wide_lp(), wide_lp(), wide_tile()))
     return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed (wide epilogue)");
   const int64_t ntiles = cdiv(m, 128) * cdiv(n, wide_tile());
   const int grid = static_cast<int>(ntiles < h->sms ? ntiles : h->sms);
@@ -716,9 +761,11 @@ frsvt_status wide_epilogue(frsvt_handle* h, bool alm, int64_t m, int64_t n, cons
 bool wide_alloc(frsvt_handle* h) {
   const frsvt_config* cfg = &h->cfg;
   const int64_t T = wide_tile(), LW = wide_lp();
-  h->w_ldm = cdiv(cfg->m_max, T) * T;
-  h->w_ldn = cdiv(cfg->n_max, T) * T;
-  h->w_ldp = h->w_ldm > h->w_ldn ? h->w_ldm : h->w_ldn;
+  const int64_t lmax = cfg->m_max > cfg->n_max ? cfg->m_max : cfg->n_max;   // long side of any served problem
+  const int64_t smax = cfg->m_max < cfg->n_max ? cfg->m_max : cfg->n_max;   // short side
+  h->w_ldl = cdiv(lmax, T) * T;
+  h->w_lds = cdiv(smax, T) * T;
+  h->w_ldp = h->w_ldl;
   h->w_ntiles = h->w_ldp / T;
   h->w_gram_grid = wide_gram_grid();
   if (h->w_gram_grid < kCLw) h->w_gram_grid = kCLw;
@@ -726,7 +773,7 @@ bool wide_alloc(frsvt_handle* h) {
   auto alloc = [&](void** p, size_t bytes) {
     if (ok && cudaMalloc(p, bytes < 16 ? 16 : bytes) != cudaSuccess) ok = false;
   };
-  const size_t fm = sizeof(float) * LW * h->w_ldm, fn = sizeof(float) * LW * h->w_ldn;
+  const size_t fm = sizeof(float) * LW * h->w_ldl, fn = sizeof(float) * LW * h->w_lds;
   alloc(reinterpret_cast<void**>(&h->wOT), fm);
   alloc(reinterpret_cast<void**>(&h->wOTl), fm);
   alloc(reinterpret_cast<void**>(&h->wZT), fm);
@@ -751,7 +798,7 @@ bool wide_alloc(frsvt_handle* h) {
   alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
   alloc(reinterpret_cast<void**>(&h->wsvt_next), sizeof(unsigned));
   if (cfg->precision == FRSVT_PREC_BF16 || cfg->precision == FRSVT_PREC_FP8) {
-    const size_t bm = sizeof(uint16_t) * LW * h->w_ldm, bn = sizeof(uint16_t) * LW * h->w_ldn;
+    const size_t bm = sizeof(uint16_t) * LW * h->w_ldl, bn = sizeof(uint16_t) * LW * h->w_lds;
     if (cfg->precision == FRSVT_PREC_BF16) {
       h->ldb = (cfg->n_max + 7) / 8 * 8;
       alloc(&h->Ab, sizeof(uint16_t) * static_cast<size_t>(cfg->m_max) * h->ldb);
@@ -1054,46 +1101,78 @@ frsvt_status frsvt_reset(frsvt_handle* h, uint64_t counter) {
   return FRSVT_OK;
 }
 
-frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, float tau, int32_t l,
-                       float* X, int64_t ldx) {
-  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
-  frsvt_status s = check_shape(h, m, n);
-  if (s != FRSVT_OK) return s;
-  if ((s = check_matrix(h, A, m, n, lda, "A")) != FRSVT_OK) return s;
-  if ((s = check_matrix(h, X, m, n, ldx, "X")) != FRSVT_OK) return s;
-  if (l < 1 || l > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "l must be in [1, l_max]");
-  if (!(tau >= 0.f) || !std::isfinite(tau)) return fail(h, FRSVT_ERR_INVALID_ARG, "tau must be finite and >= 0");
-  if (m == 0 || n == 0) return FRSVT_OK;
-  if (static_cast<const void*>(A) == static_cast<const void*>(X)) return fail(h, FRSVT_ERR_INVALID_ARG, "X aliases A");
-  if (l > n) l = static_cast<int32_t>(n);
+// Alg. 1 up to the core for frsvt_svt / frsvt_svt_factors: leaves X = Z Rf^T in the handle
+// (Z = A Q, Rf = Q M; narrow: Zl / Rf, m x LP / n x LP; wide: wZ / wRf, long side x 128 / short
+// side x 128, with X = Rf Z^T when m < n).
+static frsvt_status svt_range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda,
+                                       float tau, int32_t l) {
+  frsvt_status s = FRSVT_OK;
   if (h->ap_a > 0) {                                   // adaptive rank prediction: l on the device
     if (!(h->tma && n <= 256)) return fail(h, FRSVT_ERR_UNSUPPORTED, "rank prediction needs n <= 256");
     if (h->ap_n != n && (s = ap_setup(h, n)) != FRSVT_OK) return s;
     h->last_m = m;
     h->last_n = n;
     h->last_l = -1;
-    if ((s = range_and_core(h, A, m, n, lda, -1, h->cfg.q, 1, kCounterFromState, tau, 0, 1, 1)) != FRSVT_OK)
-      return s;
-    const Splits sp = row_splits(h, m, n);
-    FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_recon(h->LP, h->Zl, h->Rf, m, n, X, ldx, sp.nsplit, sp.rps, h->stream));
-    return FRSVT_OK;
+    return range_and_core(h, A, m, n, lda, -1, h->cfg.q, 1, kCounterFromState, tau, 0, 1, 1);
   }
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
   if (h->wide) {
     if (h->Ab != nullptr) FRSVT_CK(launch_to_bf16(A, lda, m, n, h->Ab, h->ldb, h->stream));
-    if ((s = wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1, wide_lowp(h))) !=
-        FRSVT_OK)
-      return s;
-    return wide_epilogue(h, false, m, n, nullptr, nullptr, nullptr, 0, X, ldx);
+    return wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1, wide_lowp(h));
   }
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;
   if (bf) FRSVT_CK(launch_to_bf16(A, lda, m, n, h->Ab, h->ldb, h->stream));
-  if ((s = range_and_core(h, A, m, n, lda, l, h->cfg.q, rp, kCounterFromState, tau, 0, rp, 1,
-                          bf ? h->Ab : nullptr)) != FRSVT_OK)
-    return s;
+  return range_and_core(h, A, m, n, lda, l, h->cfg.q, rp, kCounterFromState, tau, 0, rp, 1, bf ? h->Ab : nullptr);
+}
+
+static frsvt_status svt_check(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, float tau,
+                              int32_t l) {
+  frsvt_status s = check_shape(h, m, n);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, A, m, n, lda, "A")) != FRSVT_OK) return s;
+  if (l < 1 || l > h->cfg.l_max) return fail(h, FRSVT_ERR_INVALID_ARG, "l must be in [1, l_max]");
+  if (!(tau >= 0.f) || !std::isfinite(tau)) return fail(h, FRSVT_ERR_INVALID_ARG, "tau must be finite and >= 0");
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_svt(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, float tau, int32_t l,
+                       float* X, int64_t ldx) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = svt_check(h, A, m, n, lda, tau, l);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, X, m, n, ldx, "X")) != FRSVT_OK) return s;
+  if (m == 0 || n == 0) return FRSVT_OK;
+  if (static_cast<const void*>(A) == static_cast<const void*>(X)) return fail(h, FRSVT_ERR_INVALID_ARG, "X aliases A");
+  if (l > n) l = static_cast<int32_t>(n);
+  if ((s = svt_range_and_core(h, A, m, n, lda, tau, l)) != FRSVT_OK) return s;
+  if (h->wide) return wide_epilogue(h, false, m, n, nullptr, nullptr, nullptr, 0, X, ldx);
   const Splits sp = row_splits(h, m, n);
   FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_recon(h->LP, h->Zl, h->Rf, m, n, X, ldx, sp.nsplit, sp.rps, h->stream));
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_svt_factors(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, float tau,
+                               int32_t l, float* U, int64_t ldu, float* V, int64_t ldv, int32_t* r) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  frsvt_status s = svt_check(h, A, m, n, lda, tau, l);
+  if (s != FRSVT_OK) return s;
+  if (m == 0 || n == 0) return FRSVT_OK;
+  if (l > n) l = static_cast<int32_t>(n);
+  const int32_t lw = h->ap_a > 0 ? h->LP : l;          // under rank prediction l is chosen on the device
+  if (U == nullptr || V == nullptr || ldu < lw || ldv < lw)
+    return fail(h, FRSVT_ERR_INVALID_ARG, "U and V are required, with ldu, ldv >= l");
+  if ((s = svt_range_and_core(h, A, m, n, lda, tau, l)) != FRSVT_OK) return s;
+  const bool tall = m >= n;                           // wide handles serve m < n with X = Rf Z^T
+  const float* Zs = h->wide ? (tall ? h->wZ : h->wRf) : h->Zl;
+  const float* Rs = h->wide ? (tall ? h->wRf : h->wZ) : h->Rf;
+  const int64_t lds = h->wide ? wide_lp() : h->LP;
+  FRSVT_CK(cudaMemcpy2DAsync(U, sizeof(float) * ldu, Zs, sizeof(float) * lds, sizeof(float) * lw, m,
+                             cudaMemcpyDeviceToDevice, h->stream));
+  FRSVT_CK(cudaMemcpy2DAsync(V, sizeof(float) * ldv, Rs, sizeof(float) * lds, sizeof(float) * lw, n,
+                             cudaMemcpyDeviceToDevice, h->stream));
+  if (r != nullptr)
+    FRSVT_CK(cudaMemcpyAsync(r, &h->dst->r, sizeof(int32_t), cudaMemcpyDeviceToDevice, h->stream));
   return FRSVT_OK;
 }
 
@@ -1201,19 +1280,32 @@ static frsvt_status ialm_launches(frsvt_handle* h, const frsvt_handle::StepKey& 
 
 // Runs ialm_launches through a CUDA graph: captured on the handle's private stream the first time
 // a StepKey is seen, then replayed on the user's stream (one launch instead of eight or more, and
-// no tensor-map encoding on the host).  When the user's stream is itself being captured, or phase
-// timing is on, the kernels are launched directly; a capture that fails falls back the same way.
+// no tensor-map encoding on the host).  The graphs of the four most recent keys are kept (a caller
+// that alternates, e.g. with and without L, does not recapture).  When the user's stream is itself
+// being captured, or phase timing is on, the kernels are launched directly; a capture that fails
+// falls back the same way.
 static frsvt_status ialm_step_launch(frsvt_handle* h, const frsvt_handle::StepKey& key) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (h->timing || cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     (void)cudaGetLastError();
     return ialm_launches(h, key);
   }
-  if (h->step_exec == nullptr || !(h->step_key == key)) {
-    if (h->step_exec) {                        // a replay of the old graph may still be queued
+  int slot = -1;
+  for (int i = 0; i < frsvt_handle::kGraphSlots; ++i)
+    if (h->step_exec[i] != nullptr && h->step_key[i] == key) slot = i;
+  if (slot < 0) {
+    slot = 0;                                  // an empty slot, else the least recently used one
+    for (int i = 0; i < frsvt_handle::kGraphSlots; ++i) {
+      if (h->step_exec[i] == nullptr) {
+        slot = i;
+        break;
+      }
+      if (h->step_used[i] < h->step_used[slot]) slot = i;
+    }
+    if (h->step_exec[slot]) {                  // a replay of the old graph may still be queued
       FRSVT_CK(cudaStreamSynchronize(h->stream));
-      cudaGraphExecDestroy(h->step_exec);
-      h->step_exec = nullptr;
+      cudaGraphExecDestroy(h->step_exec[slot]);
+      h->step_exec[slot] = nullptr;
     }
     if (h->capture_stream == nullptr &&
         cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1231,17 +1323,18 @@ static frsvt_status ialm_step_launch(frsvt_handle* h, const frsvt_handle::StepKe
       e = cudaStreamEndCapture(h->capture_stream, &g);
     }
     h->stream = user;
-    if (e == cudaSuccess && s == FRSVT_OK && g != nullptr) e = cudaGraphInstantiate(&h->step_exec, g, 0);
+    if (e == cudaSuccess && s == FRSVT_OK && g != nullptr) e = cudaGraphInstantiate(&h->step_exec[slot], g, 0);
     if (g) cudaGraphDestroy(g);
     if (s != FRSVT_OK) return s;
-    if (e != cudaSuccess || h->step_exec == nullptr) {
-      h->step_exec = nullptr;
+    if (e != cudaSuccess || h->step_exec[slot] == nullptr) {
+      h->step_exec[slot] = nullptr;
       (void)cudaGetLastError();
       return ialm_launches(h, key);
     }
-    h->step_key = key;
+    h->step_key[slot] = key;
   }
-  FRSVT_CK(cudaGraphLaunch(h->step_exec, h->stream));
+  h->step_used[slot] = ++h->step_clock;
+  FRSVT_CK(cudaGraphLaunch(h->step_exec[slot], h->stream));
   return FRSVT_OK;
 }
 
@@ -1582,7 +1675,7 @@ frsvt_status frsvt_get_timings(frsvt_handle* h, double* ms, int32_t* launches) {
 
 const char* frsvt_phase_name(int32_t phase) {
   static const char* names[FRSVT_NPHASE] = {"sketch", "power_AQ", "power_AtZ", "reduce", "orth",
-                                            "project", "gram", "core", "epilogue", "finish"};
+                                            "project", "gram", "core", "epilogue", "finish", "apply"};
   return (phase >= 0 && phase < FRSVT_NPHASE) ? names[phase] : "unknown";
 }
 
@@ -1603,6 +1696,14 @@ frsvt_status frsvt_debug_philox(uint64_t* out, int64_t rows, int32_t blocks, uin
   if (rows == 0 || blocks == 0) return FRSVT_OK;
   if (out == nullptr) return FRSVT_ERR_INVALID_ARG;
   FRSVT_CK(launch_debug_philox(out, rows, blocks, seed, stream, problem, static_cast<cudaStream_t>(cuda_stream)));
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_debug_wait_timeout(frsvt_handle* h, uint32_t spin_limit) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (spin_limit < 1 || spin_limit > (1u << 20))
+    return fail(h, FRSVT_ERR_INVALID_ARG, "spin_limit must be in [1, 2^20]");
+  FRSVT_CK(launch_debug_wait_timeout(spin_limit, h->dst, h->stream));
   return FRSVT_OK;
 }
 
@@ -1646,6 +1747,164 @@ frsvt_status frsvt_debug_cols_tc(frsvt_handle* h, const float* A, int64_t m, int
     return fail(h, FRSVT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   FRSVT_CK(launch_tc_sc(h->LP, tmA, B ? &tmZ : nullptr, m, n, h->tc_sc_grid, h->tc_sc_ns, seed, stream, h->dst,
                         h->cpart_sc, Y, h->tickets, false, 0, 0, 1, h->Qt, h->Qs, h->cfg.rank_tol, h->stream));
+  return FRSVT_OK;
+}
+
+// ------------------------------------------------------------------ unrolled iALM RPCA
+// Saved-buffer layout of rpca_unrolled_forward, per batch element b and step k (1 <= k <= K):
+// A_k, L_k, Y_{k-1} (m x ld floats each; Y_0 = y0_scale_b O is not stored) and the FRSVT factors
+// of step k (frsvt_adjoint_saved_bytes), then the backward scratch: Sb, Yb, Lb, Tb, Ab (m x ld
+// each) and two arrays of per-CTA partial sums.
+struct UrLayout {
+  size_t mat, blob, per_step, scratch_off, part_off, total;
+  int grid;
+};
+
+static size_t ur_align(size_t x) { return (x + 255) / 256 * 256; }
+
+static UrLayout ur_layout(const frsvt_handle* h, int32_t batch, int32_t steps, int64_t m, int64_t n, int64_t ld) {
+  UrLayout u{};
+  u.mat = ur_align(sizeof(float) * static_cast<size_t>(m) * static_cast<size_t>(ld));
+  u.blob = ur_align(frsvt_adjoint_saved_bytes(h, m, n));
+  u.per_step = 3 * u.mat + u.blob;
+  u.scratch_off = static_cast<size_t>(batch) * static_cast<size_t>(steps) * u.per_step;
+  u.grid = unrolled_grid(m, n, h->sms);
+  u.part_off = u.scratch_off + 5 * u.mat;
+  u.total = u.part_off + ur_align(sizeof(double) * 2 * static_cast<size_t>(u.grid) + 64);
+  return u;
+}
+
+static frsvt_status ur_check(frsvt_handle* h, int32_t batch, int32_t steps, const float* O, int64_t m, int64_t n,
+                             int64_t ld, float lambda, int32_t l) {
+  if (h == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (h->ad_ws == nullptr) return fail(h, FRSVT_ERR_UNSUPPORTED, "handle created without FRSVT_CFG_ADJOINT");
+  if (batch < 0 || steps < 1 || steps > 1024) return fail(h, FRSVT_ERR_INVALID_ARG, "need batch >= 0, 1 <= steps <= 1024");
+  frsvt_status s = ad_check(h, O, m, n, ld, l);
+  if (s != FRSVT_OK) return s;
+  if ((n % 4) != 0) return fail(h, FRSVT_ERR_INVALID_ARG, "the unrolled steps need n % 4 == 0");
+  if (!(lambda > 0.f) || !std::isfinite(lambda)) return fail(h, FRSVT_ERR_INVALID_ARG, "lambda must be finite and > 0");
+  return FRSVT_OK;
+}
+
+size_t rpca_unrolled_saved_bytes(const frsvt_handle* h, int32_t batch, int32_t steps, int64_t m, int64_t n,
+                                 int64_t ld) {
+  if (h == nullptr || batch < 0 || steps < 1 || m < 0 || n < 0 || ld < n) return 0;
+  return ur_layout(h, batch, steps, m, n, ld).total;
+}
+
+frsvt_status rpca_unrolled_init(frsvt_handle* h, int32_t batch, const float* O, int64_t m, int64_t n, int64_t ld,
+                                double lambda, int32_t power_iters, float* y0_scale) {
+  if (h == nullptr || y0_scale == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (batch < 0 || !(lambda > 0.0) || power_iters < 0 || power_iters > 64)
+    return fail(h, FRSVT_ERR_INVALID_ARG, "need batch >= 0, lambda > 0, 0 <= power_iters <= 64");
+  const size_t step = static_cast<size_t>(m) * static_cast<size_t>(ld);
+  for (int32_t b = 0; b < batch; ++b) {
+    const float* Ob = O + step * b;
+    double nrm = 0.0;
+    frsvt_status s = frsvt_spectral_norm(h, Ob, m, n, ld, power_iters, &nrm);
+    if (s != FRSVT_OK) return s;
+    FRSVT_CK(launch_absmax_sumsq(Ob, m, n, ld, h->pmax, h->psum, h->absmax_blocks, h->stream));
+    std::vector<float> pm(h->absmax_blocks);
+    FRSVT_CK(cudaMemcpyAsync(pm.data(), h->pmax, sizeof(float) * h->absmax_blocks, cudaMemcpyDeviceToHost, h->stream));
+    FRSVT_CK(cudaStreamSynchronize(h->stream));
+    double amax = 0.0;
+    for (float v : pm) amax = amax > v ? amax : v;
+    const double den = nrm > amax / lambda ? nrm : amax / lambda;
+    y0_scale[b] = den > 0.0 ? static_cast<float>(1.0 / den) : 0.f;
+  }
+  return FRSVT_OK;
+}
+
+frsvt_status rpca_unrolled_forward(frsvt_handle* h, int32_t batch, int32_t steps, const float* O, int64_t m,
+                                   int64_t n, int64_t ld, const float* y0_scale, const float* tau, const float* mu,
+                                   float lambda, int32_t l, float* L, void* saved) {
+  frsvt_status s = ur_check(h, batch, steps, O, m, n, ld, lambda, l);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, L, m, n, ld, "L")) != FRSVT_OK) return s;
+  if (y0_scale == nullptr || tau == nullptr || mu == nullptr || saved == nullptr)
+    return fail(h, FRSVT_ERR_INVALID_ARG, "y0_scale, tau, mu and saved are required");
+  for (int32_t k = 0; k < steps; ++k)
+    if (!(mu[k] > 0.f) || !std::isfinite(mu[k]) || !(tau[k] >= 0.f) || !std::isfinite(tau[k]))
+      return fail(h, FRSVT_ERR_INVALID_ARG, "every mu_k must be finite and > 0, every tau_k finite and >= 0");
+  if (batch == 0 || m == 0 || n == 0) return FRSVT_OK;
+  const UrLayout u = ur_layout(h, batch, steps, m, n, ld);
+  unsigned char* base = static_cast<unsigned char*>(saved);
+  float* Sw = reinterpret_cast<float*>(base + u.scratch_off);          // S_k of the running step
+  const size_t step = static_cast<size_t>(m) * static_cast<size_t>(ld);
+  cudaStream_t st = h->stream;
+  for (int32_t b = 0; b < batch; ++b) {
+    const float* Ob = O + step * b;
+    for (int32_t k = 0; k < steps; ++k) {
+      unsigned char* slot = base + (static_cast<size_t>(b) * steps + k) * u.per_step;
+      float* Ak = reinterpret_cast<float*>(slot);
+      float* Lk = reinterpret_cast<float*>(slot + u.mat);
+      float* Yp = reinterpret_cast<float*>(slot + 2 * u.mat);          // Y_{k-1} (k >= 1)
+      void* blob = slot + 3 * u.mat;
+      if (k == 0) FRSVT_CK(launch_ur_pre(Ob, nullptr, nullptr, y0_scale[b], Ak, m, n, ld, mu[0], u.grid, st));
+      float* Lout = (k == steps - 1) ? L + step * b : Lk;
+      if ((s = frsvt_svt_save(h, Ak, m, n, ld, tau[k], l, static_cast<uint64_t>(k), Lout, ld, blob)) != FRSVT_OK)
+        return s;
+      if (k == steps - 1) {
+        FRSVT_CK(cudaMemcpy2DAsync(Lk, sizeof(float) * ld, Lout, sizeof(float) * ld, sizeof(float) * n, m,
+                                   cudaMemcpyDeviceToDevice, st));
+        break;
+      }
+      unsigned char* next = slot + u.per_step;
+      FRSVT_CK(launch_ur_post(Ob, Lk, k == 0 ? nullptr : Yp, y0_scale[b], Sw,
+                              reinterpret_cast<float*>(next + 2 * u.mat), reinterpret_cast<float*>(next), m, n, ld,
+                              mu[k], mu[k + 1], lambda, u.grid, st));
+    }
+  }
+  return FRSVT_OK;
+}
+
+frsvt_status rpca_unrolled_backward(frsvt_handle* h, int32_t batch, int32_t steps, const float* O, int64_t m,
+                                    int64_t n, int64_t ld, const float* y0_scale, const float* tau, const float* mu,
+                                    float lambda, int32_t l, const void* saved, const float* dL, float* dtau,
+                                    float* dmu) {
+  frsvt_status s = ur_check(h, batch, steps, O, m, n, ld, lambda, l);
+  if (s != FRSVT_OK) return s;
+  if ((s = check_matrix(h, dL, m, n, ld, "dL")) != FRSVT_OK) return s;
+  if (y0_scale == nullptr || tau == nullptr || mu == nullptr || saved == nullptr || dtau == nullptr || dmu == nullptr)
+    return fail(h, FRSVT_ERR_INVALID_ARG, "y0_scale, tau, mu, saved, dtau and dmu are required");
+  cudaStream_t st = h->stream;
+  FRSVT_CK(cudaMemsetAsync(dtau, 0, sizeof(float) * steps, st));
+  FRSVT_CK(cudaMemsetAsync(dmu, 0, sizeof(float) * steps, st));
+  if (batch == 0 || m == 0 || n == 0) return FRSVT_OK;
+  const UrLayout u = ur_layout(h, batch, steps, m, n, ld);
+  unsigned char* base = static_cast<unsigned char*>(const_cast<void*>(saved));
+  unsigned char* sc = base + u.scratch_off;
+  float* Sb = reinterpret_cast<float*>(sc);
+  float* Yb = reinterpret_cast<float*>(sc + u.mat);
+  float* Lb = reinterpret_cast<float*>(sc + 2 * u.mat);
+  float* Tb = reinterpret_cast<float*>(sc + 3 * u.mat);
+  float* Ab = reinterpret_cast<float*>(sc + 4 * u.mat);
+  double* part = reinterpret_cast<double*>(base + u.part_off);
+  double* part2 = part + u.grid;
+  float* tt = reinterpret_cast<float*>(part2 + u.grid);                // dtau of one FRSVT adjoint
+  const size_t step = static_cast<size_t>(m) * static_cast<size_t>(ld);
+  for (int32_t b = 0; b < batch; ++b) {
+    const float* Ob = O + step * b;
+    for (int32_t k = steps - 1; k >= 0; --k) {
+      unsigned char* slot = base + (static_cast<size_t>(b) * steps + k) * u.per_step;
+      const float* Ak = reinterpret_cast<const float*>(slot);
+      const float* Lk = reinterpret_cast<const float*>(slot + u.mat);
+      const float* Yp = k == 0 ? nullptr : reinterpret_cast<const float*>(slot + 2 * u.mat);
+      const void* blob = slot + 3 * u.mat;
+      const bool last = k == steps - 1;
+      // the last step's L is the output: only the loss's cotangent flows into it
+      FRSVT_CK(launch_ur_bwd_post(Ob, Lk, Yp, y0_scale[b], last ? nullptr : Sb, last ? nullptr : Yb,
+                                  last ? dL + step * b : nullptr, Lb, Yb, Tb, m, n, ld, mu[k], lambda, part, u.grid,
+                                  st));
+      if ((s = frsvt_backward(h, blob, Ak, m, n, ld, tau[k], l, static_cast<uint64_t>(k), Lb, ld, Ab, ld, tt)) !=
+          FRSVT_OK)
+        return s;
+      FRSVT_CK(launch_ur_bwd_pre(Ob, Yp, y0_scale[b], Ab, Tb, Sb, Yb, m, n, ld, mu[k], part2, u.grid, st));
+      FRSVT_CK(launch_ur_sum(part, u.grid, dmu + k, 1, st));
+      FRSVT_CK(launch_ur_sum(part2, u.grid, dmu + k, 1, st));
+      FRSVT_CK(launch_ur_addf(tt, dtau + k, st));
+    }
+  }
   return FRSVT_OK;
 }
 

@@ -1,20 +1,27 @@
 // frsvt_svt_noalloc: the FRSVT of frsvt_svt for callers that cannot allocate
 // device memory.
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a CUDA
-// graph is being captured in a mode that forbids allocation, plug-ins hosted
-// by a framework that owns every device allocation through its own pool, or
-// real-time paths that must not touch the allocator.  This entry point needs
-// no handle and allocates nothing: its scratch (split-K partials, the basis,
-// the long-side projection, the Gram partials and the small device state)
-// lives in one file-scope __device__ array of FRSVT_NOALLOC_SCRATCH_BYTES that
-// every GPU loading this library holds until the process exits.
+// Some callers cannot call cudaMalloc at all: plug-ins hosted by a framework
+// that owns every device allocation through its own pool (a second allocator
+// would fragment or overcommit that pool), real-time paths that must not enter
+// the allocator (cudaMalloc and cudaFree may synchronize the device and take
+// unbounded time), and services that fix their device-memory budget at
+// start-up.  This entry point needs no handle and allocates nothing: its
+// scratch (split-K partials, the basis, the long-side projection, the Gram
+// partials and the small device state) lives in one file-scope __device__
+// array of FRSVT_NOALLOC_SCRATCH_BYTES that every GPU loading this library
+// holds until the process exits.
 //
 // The address of that array is looked up once per device (with the device
 // current) by cudaGetSymbolAddress; host code never passes the array's own
 // name to a kernel, because on the host that name is only a stand-in, not a
 // device address.  All calls share the array: calls that overlap on the GPU
 // (two streams, two host threads) race and corrupt each other's results.
+// The device status bits of the kernels (non-finite values, an unconverged
+// Jacobi core, a rank-deficient sketch) land in the scratch state and are not
+// reported: the call returns FRSVT_OK for every input that passes the host
+// checks.
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -92,7 +99,8 @@ extern "C" frsvt_status frsvt_svt_noalloc(const float* A, int64_t m, int64_t n, 
   if (m < n) return FRSVT_ERR_UNSUPPORTED;
   if (m > kNaMaxM || n > kNaMaxN) return FRSVT_ERR_INVALID_ARG;      // beyond the scratch array
   if (l < 1 || l > kNaLP || q < 0 || q > 64) return FRSVT_ERR_INVALID_ARG;
-  if (!(tau >= 0.f) || !(tau < 3.0e38f)) return FRSVT_ERR_INVALID_ARG;
+  if (!(tau >= 0.f) || !std::isfinite(tau)) return FRSVT_ERR_INVALID_ARG;
+  if (counter == kCounterFromState) return FRSVT_ERR_INVALID_ARG;   // reserved stream index
   if (m == 0 || n == 0) return FRSVT_OK;
   if (A == nullptr || X == nullptr || static_cast<const void*>(A) == static_cast<const void*>(X))
     return FRSVT_ERR_INVALID_ARG;

@@ -100,7 +100,7 @@ k_sc_orth(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const 
   load_basis_block<LP>(w.W, static_cast<int>(n), keep, l, Qt, Y);
   __syncthreads();
   float rp_res = -1.f;
-  const int s = orth_block<LP>(w, n, keep, l, rank_tol, 2, &rp_res);
+  const int s = orth_block<LP>(w, n, keep, l, rank_tol, 2, &rp_res, &dst->status);
   for (int64_t e = threadIdx.x; e < n * LP; e += kThreads) Qout[e] = w.W[e];
   if (threadIdx.x == 0) {
     if (use_rp) dst->rp_res = rp_res;

@@ -11,6 +11,7 @@
 // (Q, Z rows, Omega rows) are staged in shared memory.
 #include "common.cuh"
 #include "state.cuh"
+#include "tma.cuh"
 
 namespace frsvt {
 
@@ -450,6 +451,23 @@ cudaError_t launch_debug_omega(float* out, int64_t rows, int cols, uint64_t seed
 cudaError_t launch_debug_philox(uint64_t* out, int64_t rows, int blocks, uint64_t seed, uint64_t stream,
                                 uint64_t problem, cudaStream_t st) {
   k_debug_philox<<<grid_1d(rows * blocks, 256, 1 << 30), 256, 0, st>>>(out, rows, blocks, seed, stream, problem);
+  return cudaGetLastError();
+}
+
+// One thread initialises an mbarrier that expects one arrival, which nothing ever makes, and
+// waits on it with the bounded poll every pipeline wait of the library uses (here with a caller-
+// chosen limit).  When the wait gives up the kernel records kDevTimeout and returns: no copy is
+// in flight and no tensor memory is held, so the context stays usable.
+__global__ void k_debug_wait_timeout(uint32_t spin_limit, DevState* __restrict__ dst) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (!mbar_wait_n(&bar, 0u, spin_limit)) atomicOr(&dst->status, kDevTimeout);
+}
+
+cudaError_t launch_debug_wait_timeout(uint32_t spin_limit, DevState* dst, cudaStream_t st) {
+  k_debug_wait_timeout<<<1, 32, 0, st>>>(spin_limit, dst);
   return cudaGetLastError();
 }
 

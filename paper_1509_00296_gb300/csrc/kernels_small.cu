@@ -28,12 +28,19 @@ constexpr int kBig = 1024;
 // Cholesky G = R^T R (upper R) of the leading p x p block with column drops.
 // A column j is dropped (row j of R set to zero) when its pivot is not above
 // rank_tol * G_jj, when G_jj is below 1e-15 of the largest diagonal, or when
-// the pivot is not a positive finite number.  Run by one full warp.
+// the pivot is not a positive finite number.  A non-finite diagonal (NaN or Inf met in the Gram
+// reduction) ORs FRSVT_DEV_NONFINITE into *status when given.  Run by one full warp.
 template <int LP>
-__device__ void chol_drop_warp(const double* G, double* R, int* dropped, int p, double rank_tol) {
+__device__ void chol_drop_warp(const double* G, double* R, int* dropped, int p, double rank_tol,
+                               uint32_t* status = nullptr) {
   const int lane = threadIdx.x & 31;
   double maxdiag = 0.0;
-  for (int a = 0; a < p; ++a) maxdiag = fmax(maxdiag, G[a * LP + a]);
+  bool finite = true;
+  for (int a = 0; a < p; ++a) {
+    maxdiag = fmax(maxdiag, G[a * LP + a]);
+    finite = finite && isfinite(G[a * LP + a]);
+  }
+  if (!finite && lane == 0 && status != nullptr) atomicOr(status, kDevNonfinite);
   for (int jj = 0; jj < p; ++jj) {
     double d = G[jj * LP + jj];
     for (int k = 0; k < jj; ++k) d -= R[k * LP + jj] * R[k * LP + jj];
@@ -165,7 +172,7 @@ k_orth(const float* __restrict__ Y, int64_t ns, int l, int use_rp, const float* 
     __syncthreads();
     if (pass == 0 && tid == 0 && use_rp && keep > 0) dst->rp_res = sqrtf(static_cast<float>(G[0]));   // Prop. 4
     if (tid < 32) {
-      chol_drop_warp<LP>(G, R, dropped, p, rank_tol);
+      chol_drop_warp<LP>(G, R, dropped, p, rank_tol, &dst->status);
       tri_inverse_warp<LP>(R, dropped, Td, T, p);
     }
     __syncthreads();
@@ -233,7 +240,7 @@ k_core(const float2* __restrict__ gpart, int gsplit, const float* __restrict__ Q
   }
   __syncthreads();
   // 2. Cholesky with column drops.
-  if (warp == 0) chol_drop_warp<LP>(G, R, dropped, l, rank_tol);
+  if (warp == 0) chol_drop_warp<LP>(G, R, dropped, l, rank_tol, &dst->status);
   __syncthreads();
   for (int e = tid; e < LP * LP; e += nt) {
     const int b = e / LP, a = e % LP;
@@ -289,7 +296,7 @@ k_core(const float2* __restrict__ gpart, int gsplit, const float* __restrict__ Q
   const float tau = tau_from_mu ? static_cast<float>(1.0 / dst->mu) : tau_host;
   if (tid < LP) {
     int rank = 0;
-    for (int c = 0; c < LP; ++c) rank += (sig[c] > sig[tid] || (sig[c] == sig[tid] && c < tid)) ? 1 : 0;
+    rank = sigma_rank(sig, LP, tid);
     perm[rank] = tid;
     coef[tid] = (sig[tid] > tau) ? (sig[tid] - tau) / sig[tid] : 0.f;
   }
@@ -323,6 +330,7 @@ k_core(const float2* __restrict__ gpart, int gsplit, const float* __restrict__ Q
     dst->r = r;
     if (update_rp) dst->keep = keep;
     if (advance_counter) dst->counter += 1;
+    dst->sweeps = sweeps_done;
     if (sweeps_done >= max_sweeps) dst->status |= kDevNotConverged;
     bool finite = true;
     for (int c = 0; c < LP; ++c) {

@@ -378,7 +378,7 @@ k_tb_sc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   load_basis_block<LP>(w.W, n, keep, l, Qt, Y);
   __syncthreads();
   float rp_res = -1.f;
-  const int s = orth_block<LP>(w, n, keep, l, rank_tol, passes, &rp_res);
+  const int s = orth_block<LP>(w, n, keep, l, rank_tol, passes, &rp_res, &dst->status);
   for (int e = threadIdx.x; e < n * LP; e += kScThr) Qout[e] = w.W[e];
   if (threadIdx.x == 0) {
     if (use_rp) dst->rp_res = rp_res;

@@ -479,16 +479,18 @@ constexpr int kGCount = kGB * 16;        // packed partial (doubles)
 constexpr int kGCols = 64;               // long-side columns staged per step
 constexpr int kGSt = kWL + 4;            // staging row stride (floats)
 constexpr int kWCL = 8;                  // cluster size of the Gram reduction
+// threads of the one-CTA orthonormalisation tail after a Gram matrix
+constexpr int kTW = 512;
 
-enum { kTailOrth = 0, kTailCore = 1 };
 
 // Shared-memory regions of the tails (the Gram staging and partial are dead by then).
 constexpr size_t kTG = 0;                                      // df64 G, 128 x 128 (128 KB)
 constexpr size_t kTR = kTG + sizeof(df64) * kWL * kWL;         // float 128 x 128 (64 KB)
 constexpr size_t kTV = kTR + sizeof(float) * kWL * kWL;        // small vectors
-constexpr size_t kTEnd = kTV + 8 * 1024;
-constexpr size_t kGMain = sizeof(float) * kGCols * kGSt + sizeof(double) * kGCount;
-constexpr size_t kGSmem = kTEnd > kGMain ? kTEnd : kGMain;
+constexpr size_t kTP = kTV + 8 * 1024;                         // Cholesky panel rows (df64)
+constexpr size_t kTEnd = kTP + 4 * 1024;
+constexpr size_t kGSmem = sizeof(float) * kGCols * kGSt + sizeof(double) * kGCount;   // Gram kernel
+constexpr size_t kTSmem = kTEnd;                                                          // tail kernel
 
 __device__ __forceinline__ void block_of(int t, int& bi, int& bj) {
   bi = 0;
@@ -532,209 +534,101 @@ __device__ TailVec carve_vec(unsigned char* base) {
   return v;
 }
 
-// Right-looking Cholesky G = R^T R of the leading p x p block in double-float arithmetic, with
-// the column drops of the l <= 32 path: column j is dropped (row j of R zero) when its pivot is
-// not above rank_tol * G_jj (original), when G_jj is below 1e-15 of the largest diagonal, or when
-// it is not a finite positive number.  Blocked by 4: thread t < 528 keeps its 4 x 4 block (bi, bj),
-// bi <= bj, of the upper triangle in registers for the whole factorization.  Per block column jb:
-// (1) the owner of the diagonal block factors it, R11 (four pivots), and forms W = R11^{-1};
-// (2) the owners of block row jb form R12 = W^T G12 and publish the four rows of R (shared);
-// (3) every trailing block takes its rank-4 update.  Two barriers per four columns.  R (FP32,
-// row-major, upper, dropped rows zero) goes to Rout; v.rdiag / v.drop get the diagonal and flags.
-__device__ void wide_cholesky(const double* __restrict__ Gpk, const TailVec& v, df64* Rpanel, float* Rout, int p,
-                              double rank_tol) {
-  const int tid = threadIdx.x;
-  const bool own = tid < kGB;
-  int bi = 0, bj = 0;
-  if (own) block_of(tid, bi, bj);
-  df64 g[16];
-#pragma unroll
-  for (int u = 0; u < 16; ++u) g[u] = own ? df_from_double(__ldcg(Gpk + tid * 16 + u)) : df64{0.f, 0.f};
+// Right-looking Cholesky G = R^T R of the leading p x p block of G (double-float, upper triangle,
+// in shared memory), with the column drops of the l <= 32 path: column j is dropped (row j of R
+// zero, the trailing block untouched) when its pivot is not above rank_tol * G_jj (original), when
+// G_jj is below 1e-15 of the largest diagonal, or when it is not a finite positive number.  Blocked
+// by kCB columns: warp 0 factors a panel (its kCB rows of R, each with warp-level synchronisation
+// only: pivot, 1 / sqrt(pivot), the row scaled, the panel's later rows updated), then every warp
+// applies the panel's rank-kCB update to the trailing upper triangle, dealt as (row, 32-column
+// chunk) items, two per warp and pass with every load ahead of the stores; two block barriers per
+// panel.  R (FP32, row-major, upper, dropped rows zero) goes to Rout; v.rdiag / v.drop get the
+// diagonal and the flags.  A non-finite diagonal of G (NaN or Inf met in the Gram reduction) ORs
+// FRSVT_DEV_NONFINITE into *status.
+constexpr int kCB = 4;                   // panel width of the Cholesky
+
+__device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, double rank_tol, uint32_t* status,
+                              df64* Rp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < kWL * kWL; e += blockDim.x) Rout[e] = 0.f;
-  if (own && bi == bj)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int a = 4 * bi + i;
-      v.g0[a] = (a < p) ? g[5 * i].hi : 0.f;
-    }
-  __syncthreads();
-  if (tid < kWL) v.thr[tid] = static_cast<float>(rank_tol * static_cast<double>(v.g0[tid]));
+  if (tid < kWL) {
+    const float g0 = tid < p ? G[tid * kWL + tid].hi : 0.f;
+    v.g0[tid] = g0;
+    v.thr[tid] = static_cast<float>(rank_tol * static_cast<double>(g0));
+    v.drop[tid] = 1;
+    v.rdiag[tid] = df64{0.f, 0.f};
+    if (tid < p && !isfinite(g0)) atomicOr(status, kDevNonfinite);
+  }
   __syncthreads();
   float maxdiag = 0.f;
   for (int a = 0; a < p; ++a) maxdiag = fmaxf(maxdiag, v.g0[a]);
-  __shared__ df64 sW[16];                      // W = R11^{-1} of the current block column (upper)
-  const int nb = (p + 3) / 4;
-  for (int jb = 0; jb < nb; ++jb) {
-    if (own && bi == jb && bj == jb) {         // (1) diagonal block
-      df64 r[16], w[16], inv[4];
-      int dr[4];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        r[u] = df64{0.f, 0.f};
-        w[u] = df64{0.f, 0.f};
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int j = 4 * jb + i;
-        const df64 d = g[5 * i];
-        const bool drop = j >= p || !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) ||
-                          !(d.hi < 1e30f);
-        dr[i] = drop ? 1 : 0;
-        inv[i] = drop ? df64{0.f, 0.f} : df_rsqrt(d);
-        if (!drop) {
-          r[5 * i] = df_mul(d, inv[i]);
-#pragma unroll
-          for (int c = i + 1; c < 4; ++c) r[4 * i + c] = df_mul(g[4 * i + c], inv[i]);
-#pragma unroll
-          for (int a = i + 1; a < 4; ++a)
-#pragma unroll
-            for (int c = a; c < 4; ++c) g[4 * a + c] = df_add(g[4 * a + c], df_neg(df_mul(r[4 * i + a], r[4 * i + c])));
+  for (int j0 = 0; j0 < p; j0 += kCB) {
+    const int j1 = min(p, j0 + kCB);
+    if (warp == 0) {                               // panel j0 .. j1 - 1: rows of R into Rp
+      for (int j = j0; j < j1; ++j) {
+        const df64 d = G[j * kWL + j];
+        const bool drop =
+            !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
+        const df64 inv = drop ? df64{0.f, 0.f} : df_rsqrt(d);
+        if (lane == 0) {
+          v.rdiag[j] = drop ? df64{0.f, 0.f} : df_mul(d, inv);
+          v.drop[j] = drop ? 1 : 0;
         }
-      }
-      // W = R11^{-1}: W_cc = 1 / R_cc = inv_c, W_rc = -(sum_{r<k<=c} R_rk W_kc) / R_rr
+        df64* rp = Rp + (j - j0) * kWL;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        w[5 * c] = inv[c];
-#pragma unroll
-        for (int rr = c - 1; rr >= 0; --rr) {
-          df64 acc{0.f, 0.f};
-#pragma unroll
-          for (int k = rr + 1; k <= c; ++k) acc = df_add(acc, df_mul(r[4 * rr + k], w[4 * k + c]));
-          w[4 * rr + c] = dr[rr] ? df64{0.f, 0.f} : df_neg(df_mul(acc, inv[rr]));
+        for (int t = 0; t < kWL / 32; ++t) {         // row j of R (zero left of j, and when dropped)
+          const int b = lane + 32 * t;
+          const df64 r = (!drop && b >= j && b < p) ? df_mul(G[j * kWL + b], inv) : df64{0.f, 0.f};
+          rp[b] = r;
+          if (b >= j && b < p) Rout[j * kWL + b] = r.hi;
         }
-      }
+        __syncwarp();
+        if (!drop)                                   // the panel's later rows
+          for (int a = j + 1; a < j1; ++a) {
+            const df64 fa = df_neg(rp[a]);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) sW[u] = w[u];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int j = 4 * jb + i;
-        if (j < kWL) {
-          v.rdiag[j] = r[5 * i];
-          v.drop[j] = dr[i];
-#pragma unroll
-          for (int c = i; c < 4; ++c) Rout[j * kWL + 4 * jb + c] = r[4 * i + c].hi;
-        }
-      }
-    }
-    __syncthreads();
-    if (own && bi == jb && bj > jb) {          // (2) R12 = W^T G12 for this block of row block jb
-      df64 w[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) w[u] = sW[u];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          df64 acc{0.f, 0.f};
-#pragma unroll
-          for (int k = 0; k <= i; ++k) acc = df_add(acc, df_mul(w[4 * k + i], g[4 * k + c]));
-          const int b = 4 * bj + c;
-          if (b >= p) acc = df64{0.f, 0.f};
-          Rpanel[i * kWL + b] = acc;
-          Rout[(4 * jb + i) * kWL + b] = acc.hi;
-        }
-    }
-    __syncthreads();
-    if (own && bi > jb) {                      // (3) rank-4 update of a trailing block
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        df64 ra[4], rb[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          ra[i] = Rpanel[k * kWL + 4 * bi + i];
-          rb[i] = Rpanel[k * kWL + 4 * bj + i];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (bi < bj || c >= i) g[4 * i + c] = df_add(g[4 * i + c], df_neg(df_mul(ra[i], rb[c])));
-      }
-    }
-  }
-  for (int j = nb * 4 + tid; j < kWL; j += blockDim.x) {
-    v.rdiag[j] = df64{0.f, 0.f};
-    v.drop[j] = 1;
-  }
-  for (int j = p + tid; j < nb * 4; j += blockDim.x) Rout[j * kWL + j] = 0.f;
-  __syncthreads();
-}
-
-// Round-robin schedule: pair w of round rnd among N (even) indices.
-__device__ __forceinline__ void wd_rr_pair(int rnd, int w, int N, int& p, int& q) {
-  if (w == 0) {
-    p = N - 1;
-    q = rnd;
-  } else {
-    p = (rnd + w) % (N - 1);
-    q = (rnd - w + (N - 1)) % (N - 1);
-  }
-  if (p > q) {
-    const int t = p;
-    p = q;
-    q = t;
-  }
-}
-
-// One-sided Jacobi on the columns of R^T (Xt[c][a] = R[c][a], c < N even): a pair of columns
-// per 8 threads, each thread holding 16 elements (float4 at 4 sub + 32 jj).  The 8 threads of a
-// pair reduce alpha, beta, gamma with xor butterflies (every lane forms the same sums, so they
-// agree on the rotation).  Returns the sweeps taken.
-__device__ int wide_jacobi(float* Xt, int N, int max_sweeps, float tol) {
-  const int tid = threadIdx.x;
-  const int slot = tid >> 3, sub = tid & 7;
-  int sweeps = 0;
-  for (int sweep = 0; sweep < max_sweeps && N >= 2; ++sweep) {
-    int rotated = 0;
-    for (int rnd = 0; rnd < N - 1; ++rnd) {
-      if (tid < 512) {                       // whole warps: every lane takes part in the shuffles
-        const bool act = slot < N / 2;
-        int p = 0, q = 0;
-        if (act) wd_rr_pair(rnd, slot, N, p, q);
-        float4* xp = reinterpret_cast<float4*>(Xt + p * kWL);
-        float4* xq = reinterpret_cast<float4*>(Xt + q * kWL);
-        float4 a[4], b[4];
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          a[jj] = act ? xp[sub + 8 * jj] : make_float4(0.f, 0.f, 0.f, 0.f);
-          b[jj] = act ? xq[sub + 8 * jj] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        float al = 0.f, be = 0.f, ga = 0.f;
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          al = fmaf(a[jj].x, a[jj].x, al); al = fmaf(a[jj].y, a[jj].y, al);
-          al = fmaf(a[jj].z, a[jj].z, al); al = fmaf(a[jj].w, a[jj].w, al);
-          be = fmaf(b[jj].x, b[jj].x, be); be = fmaf(b[jj].y, b[jj].y, be);
-          be = fmaf(b[jj].z, b[jj].z, be); be = fmaf(b[jj].w, b[jj].w, be);
-          ga = fmaf(a[jj].x, b[jj].x, ga); ga = fmaf(a[jj].y, b[jj].y, ga);
-          ga = fmaf(a[jj].z, b[jj].z, ga); ga = fmaf(a[jj].w, b[jj].w, ga);
-        }
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        if (act && fabsf(ga) > tol * sqrtf(al * be) && al > 1e-30f && be > 1e-30f) {
-          const float zeta = (be - al) / (2.f * ga);
-          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          const float c = rsqrtf(1.f + t * t);
-          const float s = c * t;
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const float4 x = a[jj], y = b[jj];
-            xp[sub + 8 * jj] = make_float4(c * x.x - s * y.x, c * x.y - s * y.y, c * x.z - s * y.z, c * x.w - s * y.w);
-            xq[sub + 8 * jj] = make_float4(s * x.x + c * y.x, s * x.y + c * y.y, s * x.z + c * y.z, s * x.w + c * y.w);
+            for (int t = 0; t < kWL / 32; ++t) {
+              const int b = lane + 32 * t;
+              if (b >= a && b < p) G[a * kWL + b] = df_add(G[a * kWL + b], df_mul(fa, rp[b]));
+            }
           }
-          rotated = 1;
-        }
+        __syncwarp();
       }
-      __syncthreads();
     }
-    sweeps = sweep + 1;
-    if (!__syncthreads_or(rotated)) break;
+    __syncthreads();
+    // trailing update of rows j1 .. p - 1: G_ab -= sum_k Rp[k][a] Rp[k][b]
+    const int nk = j1 - j0;
+    const int rows = p - j1;
+#pragma unroll 1
+    for (int c = 0; c < kWL / 32; ++c) {
+      const int lc = rows - 32 * c;
+      for (int it = warp; it < lc; it += 2 * nw) {
+        const int a0 = j1 + it, a1 = a0 + nw;
+        const bool two = it + nw < lc;
+        const int b0 = a0 + 32 * c + lane, b1 = a1 + 32 * c + lane;
+        df64 g0{0.f, 0.f}, g1{0.f, 0.f}, x0[kCB], x1[kCB], y0[kCB], y1[kCB];
+        const bool on0 = b0 < p, on1 = two && b1 < p;
+        if (on0) g0 = G[a0 * kWL + b0];
+        if (on1) g1 = G[a1 * kWL + b1];
+#pragma unroll
+        for (int k = 0; k < kCB; ++k) {
+          const bool kk = k < nk;
+          x0[k] = kk ? Rp[k * kWL + a0] : df64{0.f, 0.f};
+          y0[k] = (kk && on0) ? Rp[k * kWL + b0] : df64{0.f, 0.f};
+          x1[k] = (kk && two) ? Rp[k * kWL + a1] : df64{0.f, 0.f};
+          y1[k] = (kk && on1) ? Rp[k * kWL + b1] : df64{0.f, 0.f};
+        }
+#pragma unroll
+        for (int k = 0; k < kCB; ++k) {
+          g0 = df_add(g0, df_neg(df_mul(x0[k], y0[k])));
+          g1 = df_add(g1, df_neg(df_mul(x1[k], y1[k])));
+        }
+        if (on0) G[a0 * kWL + b0] = g0;
+        if (on1) G[a1 * kWL + b1] = g1;
+      }
+    }
+    __syncthreads();
   }
-  return sweeps;
 }
 
 struct CoreArgs {
@@ -746,11 +640,12 @@ struct CoreArgs {
   int max_sweeps;
 };
 
-template <int TAIL>
+// X^T X (128 x 128, packed 4 x 4 blocks of the upper triangle) of a basis-side matrix in
+// double-float arithmetic, each CTA over its range of long-side columns, then a cluster split-K
+// reduction into Gpk (the cluster that finishes last writes it).
 __global__ void __cluster_dims__(kWCL, 1, 1) __launch_bounds__(kGW, 1)
 k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_cta, double* __restrict__ cpart,
-          double* __restrict__ Gpk, unsigned* __restrict__ ticket, int p, double rank_tol, CoreArgs ca,
-          float* __restrict__ T1, float* __restrict__ T2, DevState* __restrict__ dst) {
+          double* __restrict__ Gpk, unsigned* __restrict__ ticket, int p) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ int flag;
   float* stg = reinterpret_cast<float*>(dsm);                                         // kGCols x kGSt
@@ -789,38 +684,214 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
     for (int u = 0; u < 16; ++u) part_sm[tid * 16 + u] = df64_value(acc[u]);
   __syncthreads();
   const int nclusters = gridDim.x / kWCL;
-  if (!cluster_split_reduce<double, kWCL>(part_sm, kGCount, cpart, Gpk, ticket, blockIdx.x / kWCL, nclusters, &flag))
-    return;
-  if (cooperative_groups::this_cluster().block_rank() != 0) return;
-  __syncthreads();
-  float* R = reinterpret_cast<float*>(dsm + kTR);               // R (FP32, upper); the core rotates its rows
-  df64* Rrow = reinterpret_cast<df64*>(dsm + kTG);              // pivot row of the factorization
+  cluster_split_reduce<double, kWCL>(part_sm, kGCount, cpart, Gpk, ticket, blockIdx.x / kWCL, nclusters, &flag);
+}
+
+// The orthonormalisation tail after the Gram of Y (one CTA of kTW threads; Alg. 1 steps 6 / 11 /
+// 14): Cholesky of Gpk with the rank cut, T1 = R with 1 / R_cc on the diagonal (0 for dropped
+// columns: the operand of the forward substitution Q^T = R^{-T} Y^T in k_wd_trsm), the basis size s.
+__global__ void __launch_bounds__(kTW, 1)
+k_wd_orth(const double* __restrict__ Gpk, int p, double rank_tol, float* __restrict__ T1, DevState* __restrict__ dst) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  df64* G = reinterpret_cast<df64*>(dsm + kTG);                 // 128 x 128 (upper triangle used)
+  float* R = reinterpret_cast<float*>(dsm + kTR);               // R (FP32, upper)
   const TailVec v = carve_vec(dsm);
-  wide_cholesky(Gpk, v, Rrow, R, p, rank_tol);
-  if (TAIL == kTailOrth) {
-    // T1 = R with 1 / R_cc on the diagonal (0 for dropped columns): the operand of the forward
-    // substitution Q^T = R^{-T} Y^T (k_wd_trsm)
-    for (int e = tid; e < kWL * kWL; e += kGW) {
-      const int a = e / kWL, c = e % kWL;
-      float x = R[e];
-      if (a == c) x = (c < p && !v.drop[c] && x != 0.f) ? 1.f / x : 0.f;
-      T1[e] = x;
-    }
-    if (tid == 0) {
-      int s = 0;
-      for (int j = 0; j < p; ++j) s += v.drop[j] ? 0 : 1;
-      dst->s = s;
-      if (s < p) dst->status |= kDevRankDeficient;
-    }
-    return;
+  for (int e = tid; e < kGCount; e += nt) {                     // unpack the 4 x 4 blocks
+    const int t = e >> 4, u = e & 15;
+    int bi, bj;
+    block_of(t, bi, bj);
+    G[(4 * bi + (u >> 2)) * kWL + 4 * bj + (u & 3)] = df_from_double(__ldcg(Gpk + e));
   }
-  // core (steps 16-19): one-sided Jacobi on the columns of R^T (the rows of R); then
-  // sigma_c = ||row c||, U[:, c] = row c / sigma_c, and M = U diag(coef) U^T = X^T diag(w) X with
-  // w_c = coef_c / sigma_c^2 (X: the rotated rows)
+  __syncthreads();
+  wide_cholesky(G, v, R, p, rank_tol, &dst->status, reinterpret_cast<df64*>(dsm + kTP));
+  for (int e = tid; e < kWL * kWL; e += nt) {
+    const int a = e / kWL, c = e % kWL;
+    float x = R[e];
+    if (a == c) x = (c < p && !v.drop[c] && x != 0.f) ? 1.f / x : 0.f;
+    T1[e] = x;
+  }
+  if (tid == 0) {
+    int s = 0;
+    for (int j = 0; j < p; ++j) s += v.drop[j] ? 0 : 1;
+    dst->s = s;
+    if (s < p) dst->status |= kDevRankDeficient;
+  }
+}
+
+// ---------------------------------------------------------------- core on a cluster
+// The l x l core (Alg. 1 steps 16-19) with its one-sided Jacobi spread over a cluster of kJC CTAs.
+// The 128 columns of R^T are 16 blocks of 8; CTA c holds two blocks (its top and bot slot) in
+// shared memory.  A sweep is 15 outer rounds of the block round-robin: in every outer round each
+// CTA rotates all 64 pairs between its two blocks (8 inner rounds of 8 disjoint pairs, a_i with
+// b_{(i + r) mod 8}), in the first one also the 28 pairs inside each block (7 inner rounds of the
+// round-robin of 8); then the blocks move one place round the ring of the 15 slots other than
+// CTA 0's top (bot_0 -> top_1 -> ... -> top_7 -> bot_7 -> ... -> bot_1 -> bot_0), written straight
+// into the receiving CTA's other buffer through distributed shared memory, one cluster barrier per
+// outer round.  Every pair meets once per sweep and the blocks are back in place after it.  Only
+// the inner rounds touch the columns often, and they stay inside one SM's shared memory.
+constexpr int kJC = 8;                   // CTAs of the core cluster
+constexpr int kJB = 8;                   // columns per block
+constexpr int kJP = 16;                  // threads per pair in an inner round
+constexpr int kJW = kJB * kJP;           // worker threads of a CTA (8 pairs per inner round)
+constexpr int kCW = 512;                 // threads of a core CTA
+constexpr size_t kTJ = kTG;              // two working buffers of 16 columns (over the dead G)
+
+// Pair (p, q) of the 8 columns of a block in round r of the round-robin of 8 (slot w < 4).
+__device__ __forceinline__ void rr8(int r, int w, int& p, int& q) {
+  if (w == 0) {
+    p = kJB - 1;
+    q = r;
+  } else {
+    p = r + w;
+    if (p >= kJB - 1) p -= kJB - 1;
+    q = r - w;
+    if (q < 0) q += kJB - 1;
+  }
+}
+
+// Rotate local columns p and q of X (16 columns of kWL floats) if they are not orthogonal to
+// tol; kJP threads (sub 0 .. kJP - 1) share the pair.  Returns whether it rotated.
+__device__ __forceinline__ int jacobi_pair(float* X, int p, int q, int sub, float tol) {
+  constexpr int E = kWL / kJP;
+  float4* xp = reinterpret_cast<float4*>(X + p * kWL);
+  float4* xq = reinterpret_cast<float4*>(X + q * kWL);
+  float4 a[E / 4], b[E / 4];
+#pragma unroll
+  for (int jj = 0; jj < E / 4; ++jj) {
+    a[jj] = xp[sub + kJP * jj];
+    b[jj] = xq[sub + kJP * jj];
+  }
+  float al = 0.f, be = 0.f, ga = 0.f, al2 = 0.f, be2 = 0.f, ga2 = 0.f;
+#pragma unroll
+  for (int jj = 0; jj < E / 4; ++jj) {
+    al = fmaf(a[jj].x, a[jj].x, al); al2 = fmaf(a[jj].y, a[jj].y, al2);
+    al = fmaf(a[jj].z, a[jj].z, al); al2 = fmaf(a[jj].w, a[jj].w, al2);
+    be = fmaf(b[jj].x, b[jj].x, be); be2 = fmaf(b[jj].y, b[jj].y, be2);
+    be = fmaf(b[jj].z, b[jj].z, be); be2 = fmaf(b[jj].w, b[jj].w, be2);
+    ga = fmaf(a[jj].x, b[jj].x, ga); ga2 = fmaf(a[jj].y, b[jj].y, ga2);
+    ga = fmaf(a[jj].z, b[jj].z, ga); ga2 = fmaf(a[jj].w, b[jj].w, ga2);
+  }
+  al += al2;
+  be += be2;
+  ga += ga2;
+#pragma unroll
+  for (int o = 1; o < kJP; o <<= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  if (!(al > 1e-30f && be > 1e-30f && fabsf(ga) * rsqrtf(al) * rsqrtf(be) > tol)) return 0;
+  const float zeta = __fdividef(be - al, 2.f * ga);
+  const float az = fabsf(zeta);
+  const float w2 = fmaf(zeta, zeta, 1.f);
+  const float t = az < 1e15f ? copysignf(__fdividef(1.f, az + w2 * rsqrtf(w2)), zeta) : __fdividef(0.5f, zeta);
+  const float c = rsqrtf(fmaf(t, t, 1.f));
+  const float sn = c * t;
+#pragma unroll
+  for (int jj = 0; jj < E / 4; ++jj) {
+    const float4 x = a[jj], y = b[jj];
+    xp[sub + kJP * jj] = make_float4(c * x.x - sn * y.x, c * x.y - sn * y.y, c * x.z - sn * y.z, c * x.w - sn * y.w);
+    xq[sub + kJP * jj] = make_float4(sn * x.x + c * y.x, sn * x.y + c * y.y, sn * x.z + c * y.z, sn * x.w + c * y.w);
+  }
+  return 1;
+}
+
+// Cluster Jacobi on the rows of R (rank 0's R, 128 x kWL; rows >= the live count are zero):
+// scattered to the CTAs, rotated, gathered back into rank 0's R.  All threads of every CTA call
+// it, rank 0 once its R is complete (the first cluster barrier waits for that).  Every CTA passes
+// the same sequence of cluster barriers: the sweep loop ends on a decision all CTAs take from the
+// same eight flags.  Returns the sweeps taken (the same in every CTA).
+__device__ int cluster_jacobi(float* R0, int max_sweeps, float tol, float* buf, int* rotflag) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = static_cast<int>(cl.block_rank());
+  const int tid = threadIdx.x;
+  constexpr int COLS = 2 * kJB;                     // local columns: top block 0..7, bot block 8..15
+  constexpr int BUF = COLS * kWL;                   // floats per working buffer
+  cl.sync();                                        // rank 0's R is complete
+  // scatter: this CTA's blocks 2 rank (top) and 2 rank + 1 (bot) = rows 16 rank .. 16 rank + 15
+  {
+    const float4* src = reinterpret_cast<const float4*>(cl.map_shared_rank(R0, 0) + rank * COLS * kWL);
+    for (int e = tid; e < BUF / 4; e += blockDim.x) reinterpret_cast<float4*>(buf)[e] = src[e];
+  }
+  if (tid < 2 * kJC) rotflag[tid] = 0;
+  cl.sync();                                        // R0 read by everyone; flags cleared everywhere
+  int wb = 0, sweeps = 0;
+  const int pair = tid / kJP, sub = tid % kJP;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int R = 0; R < 2 * kJC - 1; ++R) {
+      float* X = buf + wb * BUF;
+      if (tid < kJW) {
+        if (R == 0)
+          for (int r = 0; r < kJB - 1; ++r) {       // pairs inside each block
+            int p, q;
+            rr8(r, pair & 3, p, q);
+            const int off = (pair >> 2) * kJB;
+            rotated |= jacobi_pair(X, off + p, off + q, sub, tol);
+            named_bar(1, kJW);
+          }
+        for (int r = 0; r < kJB; ++r) {             // pairs across the two blocks
+          rotated |= jacobi_pair(X, pair, kJB + ((pair + r) & (kJB - 1)), sub, tol);
+          named_bar(1, kJW);
+        }
+      }
+      __syncthreads();
+      // move the blocks round the ring into the receivers' other buffer
+      {
+        const int c = tid / (kWL / 4), f = tid % (kWL / 4);      // local column, float4 index
+        if (c < COLS) {
+          const bool top = c < kJB;
+          int dst_rank, dst_slot;
+          if (top) {
+            dst_rank = rank == 0 ? 0 : (rank == kJC - 1 ? rank : rank + 1);
+            dst_slot = rank == kJC - 1 ? 1 : 0;
+          } else {
+            dst_rank = rank == 0 ? 1 : rank - 1;
+            dst_slot = rank == 0 ? 0 : 1;
+          }
+          float* dst = cl.map_shared_rank(buf + (1 - wb) * BUF, dst_rank);
+          reinterpret_cast<float4*>(dst + (dst_slot * kJB + (c & (kJB - 1))) * kWL)[f] =
+              reinterpret_cast<const float4*>(X + c * kWL)[f];
+        }
+      }
+      cl.sync();
+      wb = 1 - wb;
+    }
+    // convergence: every CTA tells every CTA whether it rotated in this sweep
+    const int any_local = __syncthreads_or(rotated);
+    int* flags = rotflag + (sweep & 1) * kJC;
+    if (tid < kJC) *cl.map_shared_rank(flags + rank, tid) = any_local;
+    cl.sync();
+    int any = 0;
+    for (int c = 0; c < kJC; ++c) any |= flags[c];
+    __syncthreads();
+    if (tid < kJC) flags[tid] = 0;                  // reused two sweeps later, after two cluster barriers
+    sweeps = sweep + 1;
+    if (!any) break;
+  }
+  // gather the rotated rows back into rank 0's R (the blocks are in their starting slots)
+  {
+    float4* dst = reinterpret_cast<float4*>(cl.map_shared_rank(R0, 0) + rank * COLS * kWL);
+    const float4* src = reinterpret_cast<const float4*>(buf + wb * BUF);
+    for (int e = tid; e < BUF / 4; e += blockDim.x) dst[e] = src[e];
+  }
+  cl.sync();
+  return sweeps;
+}
+
+// Alg. 1 steps 18-19 after the Jacobi, by one CTA: row c of R now holds sigma_c u_c^T (u_c a
+// right singular vector of Z = B^T), so sigma_c = ||row c||, and M = U diag(coef) U^T = X^T diag(w) X
+// with w_c = coef_c / sigma_c^2 (X: the rotated rows, coef the shrinkage of Eq. 6 or the partial
+// threshold); T2 = the propagated basis factor U[:, perm[:keep]]; r, sweeps, sigma and the status
+// bits go to the device state.
+__device__ void core_post(const float* R, const TailVec& v, int p, int sweeps, const CoreArgs& ca,
+                          float* __restrict__ T1, float* __restrict__ T2, DevState* __restrict__ dst) {
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int N = (p + 1) / 2 * 2;
-  const int sweeps = wide_jacobi(R, N, ca.max_sweeps, 8e-6f);
   const int warp = tid >> 5, lane = tid & 31;
-  for (int c = warp; c < kWL; c += kGW / 32) {
+  for (int c = warp; c < kWL; c += nt / 32) {
     float s2 = 0.f;
     for (int a = lane; a < kWL; a += 32) s2 = fmaf(R[c * kWL + a], R[c * kWL + a], s2);
     s2 = warp_sum(s2);
@@ -831,8 +902,7 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
   float* wv = v.thr;                                            // w_c (the thresholds are no longer needed)
   if (tid < kWL) {
     const float sc = v.sig[tid];
-    int rank = 0;
-    for (int c = 0; c < kWL; ++c) rank += (v.sig[c] > sc || (v.sig[c] == sc && c < tid)) ? 1 : 0;
+    const int rank = sigma_rank(v.sig, kWL, tid);
     v.perm[rank] = tid;
     const float cf = (rank < dst->partial_k && sc > 0.f) ? 1.f : ((sc > tau) ? (sc - tau) / sc : 0.f);
     v.coef[tid] = cf;
@@ -842,9 +912,9 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
   int r = 0;
   for (int c = 0; c < kWL; ++c) r += (v.coef[c] > 0.f) ? 1 : 0;
   const int keep = ca.update_rp ? max(0, min(r, ca.l - 2)) : 0;
-  if (tid < kGB) {
+  for (int t = tid; t < kGB; t += nt) {          // one 4 x 4 block of M per thread and pass
     int bi2, bj2;
-    block_of(tid, bi2, bj2);
+    block_of(t, bi2, bj2);
     float m4[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) m4[u] = 0.f;
@@ -869,7 +939,7 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
       }
   }
   if (ca.update_rp)
-    for (int e = tid; e < kWL * kWL; e += kGW) {
+    for (int e = tid; e < kWL * kWL; e += nt) {
       const int j = e / kWL, a = e % kWL;
       const int c = v.perm[j];
       T2[a * kWL + j] = (j < keep && v.sig[c] > 0.f) ? R[c * kWL + a] / v.sig[c] : 0.f;
@@ -889,6 +959,34 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
     if (!finite) dst->status |= kDevNonfinite;
     dst->sigma1 = static_cast<double>(v.sig[v.perm[0]]);
   }
+}
+
+// The core of Alg. 1 steps 16-19 after the Gram of Z (rank 0 factors and post-processes; the
+// cluster runs the Jacobi): Cholesky of Gpk with the rank cut, one-sided Jacobi SVD of R^T,
+// shrinkage, M = U diag(coef) U^T into T1 and the propagated basis factor into T2.
+__global__ void __cluster_dims__(kJC, 1, 1) __launch_bounds__(kCW, 1)
+k_wd_core(const double* __restrict__ Gpk, int p, double rank_tol, CoreArgs ca, float* __restrict__ T1,
+          float* __restrict__ T2, DevState* __restrict__ dst) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ int rotflag[2 * kJC];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int rank = static_cast<int>(cooperative_groups::this_cluster().block_rank());
+  df64* G = reinterpret_cast<df64*>(dsm + kTG);
+  float* R = reinterpret_cast<float*>(dsm + kTR);
+  const TailVec v = carve_vec(dsm);
+  if (rank == 0) {
+    for (int e = tid; e < kGCount; e += nt) {
+      const int t = e >> 4, u = e & 15;
+      int bi, bj;
+      block_of(t, bi, bj);
+      G[(4 * bi + (u >> 2)) * kWL + 4 * bj + (u & 3)] = df_from_double(__ldcg(Gpk + e));
+    }
+    __syncthreads();
+    wide_cholesky(G, v, R, p, rank_tol, &dst->status, reinterpret_cast<df64*>(dsm + kTP));
+  }
+  const int sweeps = cluster_jacobi(R, ca.max_sweeps, 8e-6f, reinterpret_cast<float*>(dsm + kTJ), rotflag);
+  if (rank != 0) return;
+  core_post(R, v, p, sweeps, ca, T1, T2, dst);
 }
 
 // ---------------------------------------------------------------- Q^T = R^{-T} Y^T
@@ -1148,7 +1246,44 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
       if (ok && !mbar_wait(&acc_full[buf], static_cast<uint32_t>(k / 2) & 1u)) flag_timeout(ok, dst);
       tc_fence_after();
       const int64_t row = 128 * static_cast<int64_t>(tr) + 32 * q + lane;
+      // O, S, A of the thread's row, 16 columns per group; the next group's loads are issued before
+      // the current group is consumed, so each thread keeps two groups (384 bytes) in flight
+      float ov[16], sv[16], av[16], on[16], sn_[16], anx[16];    // current group, next group
+      auto load_group = [&](int cg, float* o_, float* s_, float* a_) {
+        const int64_t c0 = static_cast<int64_t>(kWN) * tc + 128 * half + 16 * cg;
+        if (!ALM || row >= m || c0 >= n) return;
+        if (c0 + 16 <= n) {
+          const float4* O4 = reinterpret_cast<const float4*>(O + row * ld + c0);
+          const float4* S4 = reinterpret_cast<const float4*>(S + row * ld + c0);
+          const float4* A4 = reinterpret_cast<const float4*>(A + row * ld + c0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 o = __ldcs(O4 + u), s = __ldcs(S4 + u), a = __ldcs(A4 + u);
+            o_[4 * u] = o.x; o_[4 * u + 1] = o.y; o_[4 * u + 2] = o.z; o_[4 * u + 3] = o.w;
+            s_[4 * u] = s.x; s_[4 * u + 1] = s.y; s_[4 * u + 2] = s.z; s_[4 * u + 3] = s.w;
+            a_[4 * u] = a.x; a_[4 * u + 1] = a.y; a_[4 * u + 2] = a.z; a_[4 * u + 3] = a.w;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const bool in = c0 + u < n;
+            o_[u] = in ? O[row * ld + c0 + u] : 0.f;
+            s_[u] = in ? S[row * ld + c0 + u] : 0.f;
+            a_[u] = in ? A[row * ld + c0 + u] : 0.f;
+          }
+        }
+      };
+      if (ok) load_group(0, ov, sv, av);
+#pragma unroll
       for (int cg = 0; cg < 8; ++cg) {
+        if (cg > 0)                                                   // the group loaded last pass
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            ov[u] = on[u];
+            sv[u] = sn_[u];
+            av[u] = anx[u];
+          }
+        if (ok && cg + 1 < 8) load_group(cg + 1, on, sn_, anx);
         float x[16];
         const int colt = 128 * half + 16 * cg;
         tmem_ld16(tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(buf * kWN + colt), x);
@@ -1166,31 +1301,10 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
           }
           continue;
         }
-        float ov[16], sv[16], av[16];
-        if (full16) {
-          const float4* O4 = reinterpret_cast<const float4*>(O + row * ld + col0);
-          const float4* S4 = reinterpret_cast<const float4*>(S + row * ld + col0);
-          const float4* A4 = reinterpret_cast<const float4*>(A + row * ld + col0);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 o = __ldcs(O4 + u), s = __ldcs(S4 + u), a = __ldcs(A4 + u);
-            ov[4 * u] = o.x; ov[4 * u + 1] = o.y; ov[4 * u + 2] = o.z; ov[4 * u + 3] = o.w;
-            sv[4 * u] = s.x; sv[4 * u + 1] = s.y; sv[4 * u + 2] = s.z; sv[4 * u + 3] = s.w;
-            av[4 * u] = a.x; av[4 * u + 1] = a.y; av[4 * u + 2] = a.z; av[4 * u + 3] = a.w;
-          }
-        } else {
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const bool in = col0 + u < n;
-            ov[u] = in ? O[row * ld + col0 + u] : 0.f;
-            sv[u] = in ? S[row * ld + col0 + u] : 0.f;
-            av[u] = in ? A[row * ld + col0 + u] : 0.f;
-          }
-        }
         float sn[16], an[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
-          const float t = av[u] + sv[u] - x[u];                        // O - L + Y / mu
+          const float t = av[u] + sv[u] - x[u];                         // O - L + Y / mu
           sn[u] = (t > thr) ? (t - thr) : ((t < -thr) ? (t + thr) : 0.f);
           an[u] = ov[u] - sn[u] + ratio * (t - sn[u]);                  // O - S' + Y' / mu'
           const float rz = ov[u] - x[u] - sn[u];                        // O - L - S'
@@ -1279,8 +1393,9 @@ cudaError_t prepare_wide_kernels() {
   if (e == cudaSuccess) e = set_dyn(k_wd_pass<true, 1>, kWStages * kWStage);
   if (e == cudaSuccess) e = set_dyn(k_wd_pass<false, 2>, 2 * (kWStage + 16384));
   if (e == cudaSuccess) e = set_dyn(k_wd_pass<true, 2>, 2 * (kWStage + 16384));
-  if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailOrth>, kGSmem);
-  if (e == cudaSuccess) e = set_dyn(k_wd_gram<kTailCore>, kGSmem);
+  if (e == cudaSuccess) e = set_dyn(k_wd_gram, kGSmem);
+  if (e == cudaSuccess) e = set_dyn(k_wd_orth, kTSmem);
+  if (e == cudaSuccess) e = set_dyn(k_wd_core, kTSmem);
   if (e == cudaSuccess) e = set_dyn(k_wd_apply, sizeof(float) * kWL * (kWL + kACols));
   if (e == cudaSuccess) e = set_dyn(k_wd_trsm, sizeof(float) * kWL * (kTS + kTX));
   if (e == cudaSuccess) e = set_dyn(k_wd_alm<true>, kEStages * kEStage);
@@ -1302,7 +1417,7 @@ int wide_gram_grid() {
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
   int nc = 0;
-  if (cudaOccupancyMaxActiveClusters(&nc, reinterpret_cast<const void*>(k_wd_gram<kTailCore>), &cfg) != cudaSuccess)
+  if (cudaOccupancyMaxActiveClusters(&nc, reinterpret_cast<const void*>(k_wd_gram), &cfg) != cudaSuccess)
     nc = 0;
   (void)cudaGetLastError();
   return nc * kWCL;
@@ -1362,10 +1477,13 @@ cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len,
                            cudaStream_t st) {
   const int64_t per = (len + grid - 1) / grid;
   CoreArgs ca{l, tau_host, tau_from_mu, update_rp, advance_counter, max_sweeps};
+  k_wd_gram<<<grid, kGW, kGSmem, st>>>(XT, ldx, len, per, cpart, Gpk, ticket, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   if (core)
-    k_wd_gram<kTailCore><<<grid, kGW, kGSmem, st>>>(XT, ldx, len, per, cpart, Gpk, ticket, p, rank_tol, ca, T1, T2, dst);
+    k_wd_core<<<kJC, kCW, kTSmem, st>>>(Gpk, p, rank_tol, ca, T1, T2, dst);
   else
-    k_wd_gram<kTailOrth><<<grid, kGW, kGSmem, st>>>(XT, ldx, len, per, cpart, Gpk, ticket, p, rank_tol, ca, T1, T2, dst);
+    k_wd_orth<<<1, kTW, kTSmem, st>>>(Gpk, p, rank_tol, T1, dst);
   return cudaGetLastError();
 }
 

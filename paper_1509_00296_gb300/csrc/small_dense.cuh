@@ -176,14 +176,16 @@ __device__ void block_copy(float* dst, const float* src, int count) {
 // G, by warp 0, with column drops: column j is dropped (row j of R zero, rinv[j] = 0) when its
 // pivot is not above rank_tol * (original G_jj), when G_jj is below 1e-15 of the largest
 // diagonal, or when it is not a finite positive number.  G is overwritten.  Returns via
-// iv[0..p) the drop flags.  Block-wide (contains __syncthreads).
+// iv[0..p) the drop flags.  A non-finite diagonal of G (NaN or Inf met in the Gram reduction) is
+// reported by OR-ing FRSVT_DEV_NONFINITE into *status (when given).  Block-wide (contains
+// __syncthreads).
 //
 // The factorization runs in double-float arithmetic on the FP32 pipes (~48 significant bits):
 // on GB300 every FP64 operation of this serial chain costs far more latency than the dozen
 // FP32 operations of its double-float counterpart.  Lane b owns column b of the trailing
 // block: at step j it forms R[j][b] and subtracts R[j][a] R[j][b] from G[a][b] for j < a <= b.
 template <int LP>
-__device__ void block_cholesky(SmallWs<LP>& w, int p, double rank_tol) {
+__device__ void block_cholesky(SmallWs<LP>& w, int p, double rank_tol, uint32_t* status = nullptr) {
   static_assert(LP <= 32, "one lane per column");
   const int tid = threadIdx.x;
   df64* Gd = w.G;
@@ -196,6 +198,8 @@ __device__ void block_cholesky(SmallWs<LP>& w, int p, double rank_tol) {
     float maxdiag = g0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxdiag = fmaxf(maxdiag, __shfl_xor_sync(0xffffffffu, maxdiag, o));
+    if (__any_sync(0xffffffffu, lane < p && !isfinite(g0)) && lane == 0 && status != nullptr)
+      atomicOr(status, kDevNonfinite);
     for (int j = 0; j < p; ++j) {
       const df64 d = Gd[j * LP + j];
       const float g0j = __shfl_sync(0xffffffffu, g0, j);
@@ -263,7 +267,7 @@ __device__ void block_trsm_rows(SmallWs<LP>& w, float* W, int64_t ns, int c0, in
 // next power step (only its span matters there).
 template <int LP>
 __device__ int orth_block(SmallWs<LP>& w, int64_t ns, int keep, int l, double rank_tol, int passes,
-                          float* rp_res = nullptr) {
+                          float* rp_res = nullptr, uint32_t* status = nullptr) {
   float* W = w.W;
   const int p = l - keep;
   if (keep > 0 && p > 0) {
@@ -294,7 +298,7 @@ __device__ int orth_block(SmallWs<LP>& w, int64_t ns, int keep, int l, double ra
   for (int pass = 0; pass < passes && p > 0; ++pass) {
     block_inner<LP>(W, ns, keep, keep, p, p, true, w.G, w.gacc, w.gacc_n);
     if (pass == 0 && keep > 0 && rp_res != nullptr && threadIdx.x == 0) *rp_res = sqrtf(w.G[0].hi);
-    block_cholesky<LP>(w, p, rank_tol);
+    block_cholesky<LP>(w, p, rank_tol, status);
     block_trsm_rows<LP>(w, W, ns, keep, p);
     kept = 0;
     for (int c = 0; c < p; ++c) kept += w.iv[c] ? 0 : 1;
@@ -320,14 +324,15 @@ __device__ __forceinline__ void rr_pair(int rnd, int w, int N, int& p, int& q) {
 // w.U the left singular vectors (column b), w.iv[LP..2LP) the order by descending sigma (perm[k]
 // = index of the k-th largest).  Returns the number of Jacobi sweeps.  Block-wide.
 template <int LP>
-__device__ int core_svd_block(SmallWs<LP>& w, int l, double rank_tol, int max_sweeps) {
+__device__ int core_svd_block(SmallWs<LP>& w, int l, double rank_tol, int max_sweeps,
+                              uint32_t* status = nullptr) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
   float* Xt = w.Rf32;          // after the Cholesky: Xt[b * LP + a] = R[b][a] (columns of R^T)
   float* sig = w.vec;
   int* perm = w.iv + LP;
   int* flag = w.iv + 2 * LP;
-  block_cholesky<LP>(w, l, rank_tol);
+  block_cholesky<LP>(w, l, rank_tol, status);
   const int N = (l + 1) / 2 * 2;   // even number of Jacobi columns covering the live ones
   const float tol = 1e-6f;
   int sweeps = 0;
@@ -409,7 +414,7 @@ __device__ int core_svd_block(SmallWs<LP>& w, int l, double rank_tol, int max_sw
   }
   if (tid < LP) {
     int rank = 0;
-    for (int c = 0; c < LP; ++c) rank += (sig[c] > sig[tid] || (sig[c] == sig[tid] && c < tid)) ? 1 : 0;
+    rank = sigma_rank(sig, LP, tid);
     perm[rank] = tid;
   }
   __syncthreads();
@@ -427,7 +432,7 @@ __device__ void core_block(SmallWs<LP>& w, const float* Q, int64_t ns, int l, fl
   float* sig = w.vec;
   float* coef = w.vec + LP;
   int* perm = w.iv + LP;
-  const int sweeps = core_svd_block<LP>(w, l, rank_tol, max_sweeps);
+  const int sweeps = core_svd_block<LP>(w, l, rank_tol, max_sweeps, &dst->status);
   const int pk = dst->partial_k;                   // partial SVT: the pk leading values stay
   if (tid < LP) {
     int rk = 0;

@@ -92,6 +92,9 @@ cudaError_t launch_init_state(const float* O, float* S, float* A, int64_t m, int
 // debug
 cudaError_t launch_debug_omega(float* out, int64_t rows, int cols, uint64_t seed, uint64_t stream,
                                uint64_t problem, cudaStream_t st);
+// one CTA waits, with at most spin_limit polls, on an mbarrier that nothing arrives at, and ORs
+// kDevTimeout into dst->status when the wait gives up (the path every bounded wait takes)
+cudaError_t launch_debug_wait_timeout(uint32_t spin_limit, DevState* dst, cudaStream_t st);
 cudaError_t launch_debug_philox(uint64_t* out, int64_t rows, int blocks, uint64_t seed,
                                 uint64_t stream, uint64_t problem, cudaStream_t st);
 

@@ -49,11 +49,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false if it timed out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+// Wait for the phase with the given parity, polling at most `limit` times; false if it timed out.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Bounded wait for the phase with the given parity; false if it timed out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_n(bar, parity, kSpinLimit);
 }
 
 // 2-D tiled TMA load of the box at (x = column, y = row) into shared memory; completes on bar.

@@ -24,7 +24,7 @@ WSVT_EXACT, WSVT_FRSVT = 0, 1
 CFG_ADJOINT = 1
 CFG_ORTH_LAST = 2
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
-NPHASE = 10
+NPHASE = 11
 
 
 class FrsvtError(RuntimeError):
@@ -57,6 +57,7 @@ _SIGS = {
     "frsvt_reset": [_P, ctypes.c_uint64],
     "frsvt_svt": [_P, _P, _I64, _I64, _I64, ctypes.c_float, ctypes.c_int32, _P, _I64],
     "frsvt_spectral_norm": [_P, _P, _I64, _I64, _I64, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)],
+    "frsvt_svt_factors": [_P, _P, _I64, _I64, _I64, ctypes.c_float, ctypes.c_int32, _P, _I64, _P, _I64, _P],
     "rpca_init": [_P, _P, _P, _P, _I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                   ctypes.c_double, ctypes.c_int32],
     "rpca_ialm_step": [_P, _P, _P, _P, _I64, _I64, _I64, ctypes.c_int32, _P, _I64, ctypes.POINTER(ctypes.c_double)],
@@ -82,6 +83,12 @@ _SIGS = {
     "frsvt_debug_cols_tc": [_P, _P, _I64, _I64, _I64, _P, ctypes.c_uint64, ctypes.c_uint64, _P],
     "frsvt_debug_omega": [_P, _I64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P],
     "frsvt_debug_philox": [_P, _I64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P],
+    "frsvt_debug_wait_timeout": [_P, ctypes.c_uint32],
+    "rpca_unrolled_init": [_P, ctypes.c_int32, _P, _I64, _I64, _I64, ctypes.c_double, ctypes.c_int32, _P],
+    "rpca_unrolled_forward": [_P, ctypes.c_int32, ctypes.c_int32, _P, _I64, _I64, _I64, _P, _P, _P, ctypes.c_float,
+                              ctypes.c_int32, _P, _P],
+    "rpca_unrolled_backward": [_P, ctypes.c_int32, ctypes.c_int32, _P, _I64, _I64, _I64, _P, _P, _P, ctypes.c_float,
+                               ctypes.c_int32, _P, _P, _P, _P],
 }
 
 
@@ -99,6 +106,8 @@ def lib():
                           else ctypes.c_int)
         L.frsvt_adjoint_saved_bytes.argtypes = [_P, _I64, _I64]
         L.frsvt_adjoint_saved_bytes.restype = ctypes.c_size_t
+        L.rpca_unrolled_saved_bytes.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _I64, _I64, _I64]
+        L.rpca_unrolled_saved_bytes.restype = ctypes.c_size_t
         _lib = L
     return _lib
 
@@ -192,6 +201,20 @@ class Handle:
         self._chk(lib().frsvt_svt(self._h, _ptr(A), m, n, A.stride(0), float(tau), int(l), _ptr(X), X.stride(0)))
         return X
 
+    def svt_factors(self, A, tau: float, l: int, width: int | None = None):
+        """FRSVT_tau(A) in factored form: returns (U, V, r) with X = U V^T, U = A Q (m x width),
+        V = Q M (n x width), r a 1-element int32 CUDA tensor (#{sigma > tau}); width defaults to l."""
+        import torch
+        _check_f32_cuda(A, "A")
+        m, n = A.shape
+        w = int(l if width is None else width)
+        U = torch.empty((m, w), dtype=torch.float32, device=A.device)
+        V = torch.empty((n, w), dtype=torch.float32, device=A.device)
+        r = torch.empty(1, dtype=torch.int32, device=A.device)
+        self._chk(lib().frsvt_svt_factors(self._h, _ptr(A), m, n, A.stride(0), float(tau), int(l), _ptr(U), w,
+                                          _ptr(V), w, _ptr(r)))
+        return U, V, r
+
     def spectral_norm(self, A, iters: int = 20) -> float:
         _check_f32_cuda(A, "A")
         out = ctypes.c_double()
@@ -263,6 +286,10 @@ class Handle:
         self._chk(lib().frsvt_debug_cols_tc(self._h, _ptr(A), m, n, A.stride(0), _ptr(B), seed, stream, _ptr(Y)))
         return Y
 
+    def debug_wait_timeout(self, spin_limit: int = 1000):
+        """Run one bounded mbarrier wait that nothing satisfies (sets DEV_TIMEOUT in the status)."""
+        self._chk(lib().frsvt_debug_wait_timeout(self._h, int(spin_limit)))
+
     def svt_save(self, A, tau: float, l: int, omega_stream: int = 0, X=None, saved=None):
         """X = FRSVT_tau(A) recording the factors of the backward pass; returns (X, saved)."""
         import torch
@@ -290,6 +317,41 @@ class Handle:
         self._chk(lib().frsvt_backward(self._h, _ptr(saved), _ptr(A), m, n, A.stride(0), tau, l, omega_stream,
                                        _ptr(dX), dX.stride(0), _ptr(dA), dA.stride(0), _ptr(dtau)))
         return dA, dtau
+
+    def unrolled_init(self, Ob, lam: float, power_iters: int = 30):
+        """y0 scales of a batch (B, m, n contiguous float32 CUDA tensor): a list of B floats."""
+        B, m, n = Ob.shape
+        out = (ctypes.c_float * B)()
+        self._chk(lib().rpca_unrolled_init(self._h, B, _ptr(Ob), m, n, n, float(lam), int(power_iters), out))
+        return [out[i] for i in range(B)]
+
+    def unrolled_forward(self, Ob, y0_scale, tau, mu, lam: float, l: int, saved=None):
+        """L_K of the unrolled iALM for a batch (B, m, n); tau, mu: sequences of K floats.
+        Returns (L, saved)."""
+        import torch
+        B, m, n = Ob.shape
+        K = len(tau)
+        if saved is None:
+            nb = lib().rpca_unrolled_saved_bytes(self._h, B, K, m, n, n)
+            saved = torch.empty(nb, dtype=torch.uint8, device=Ob.device)
+        L = torch.empty_like(Ob)
+        f = ctypes.c_float
+        self._chk(lib().rpca_unrolled_forward(self._h, B, K, _ptr(Ob), m, n, n, (f * B)(*y0_scale), (f * K)(*tau),
+                                              (f * K)(*mu), float(lam), int(l), _ptr(L), _ptr(saved)))
+        return L, saved
+
+    def unrolled_backward(self, Ob, y0_scale, tau, mu, lam: float, l: int, saved, dL):
+        """(dtau, dmu) as float32 CUDA tensors of K entries for the cotangent dL of L_K."""
+        import torch
+        B, m, n = Ob.shape
+        K = len(tau)
+        dtau = torch.empty(K, dtype=torch.float32, device=Ob.device)
+        dmu = torch.empty(K, dtype=torch.float32, device=Ob.device)
+        f = ctypes.c_float
+        self._chk(lib().rpca_unrolled_backward(self._h, B, K, _ptr(Ob), m, n, n, (f * B)(*y0_scale), (f * K)(*tau),
+                                               (f * K)(*mu), float(lam), int(l), _ptr(saved), _ptr(dL.contiguous()),
+                                               _ptr(dtau), _ptr(dmu)))
+        return dtau, dmu
 
     def wsvt_raw(self, A_ptrs, n_i, m: int, c: float, eps: float, X_ptrs, variant: int = WSVT_EXACT,
                  l: int = 12, tune: bool = False):

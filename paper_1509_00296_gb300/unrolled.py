@@ -8,10 +8,11 @@ whose step k has its own SVT threshold tau_k and penalty mu_k, both learnable:
     S   = shrink_{lambda / mu_k}(O - L + Y / mu_k)
     Y   = Y + mu_k (O - L - S)
 
-starting from S = 0 and Y = O / max(||O||_2, ||O||_inf / lambda).  The SVT and its gradient
-(with respect to A_k and tau_k) run in the library (frsvt_svt_save / frsvt_backward); the
-elementwise shrinkage and dual update are torch operations on the GPU, differentiated by
-autograd.  The default schedule is the iALM one: mu_k = mu_0 rho^k, tau_k = 1 / mu_k.
+starting from S = 0 and Y = O / max(||O||_2, ||O||_inf / lambda).  The whole batch and every step
+run in the library (rpca_unrolled_forward / rpca_unrolled_backward: the FRSVT, its adjoint and
+fused kernels for the shrinkage, the multiplier update and their adjoints); this module only
+keeps the parameters and wires the two calls into a torch.autograd.Function.  The default
+schedule is the iALM one: mu_k = mu_0 rho^k, tau_k = 1 / mu_k.
 """
 from __future__ import annotations
 
@@ -25,8 +26,33 @@ def _torch():
     return torch
 
 
+def _function():
+    torch = _torch()
+
+    class UnrolledRPCA(torch.autograd.Function):
+        """L_K of the unrolled iALM for a batch; gradients with respect to tau and mu."""
+
+        @staticmethod
+        def forward(ctx, tau, mu, Ob, handle, lam, l, y0_scale):
+            t = [float(v) for v in tau.detach().cpu()]
+            mv = [float(v) for v in mu.detach().cpu()]
+            L, saved = handle.unrolled_forward(Ob, y0_scale, t, mv, lam, l)
+            ctx.save_for_backward(Ob, saved)
+            ctx.meta = (handle, lam, l, y0_scale, t, mv)
+            return L
+
+        @staticmethod
+        def backward(ctx, dL):
+            Ob, saved = ctx.saved_tensors
+            handle, lam, l, y0_scale, t, mv = ctx.meta
+            dtau, dmu = handle.unrolled_backward(Ob, y0_scale, t, mv, lam, l, saved, dL)
+            return dtau, dmu, None, None, None, None, None
+
+    return UnrolledRPCA
+
+
 class RPCAUnrolled:
-    """Learnable unrolled RPCA over a batch of m x n matrices (m >= n).
+    """Learnable unrolled RPCA over a batch of m x n matrices (m >= n, n % 4 == 0).
 
     Parameters (torch tensors with requires_grad): ``tau`` and ``mu`` of shape (K,).
     """
@@ -44,30 +70,17 @@ class RPCAUnrolled:
     def parameters(self):
         return [self.tau, self.mu]
 
-    def dual_init(self, O):
-        """Y_0 = O / max(||O||_2, ||O||_inf / lambda) with ||O||_2 from the library's power method."""
-        norm2 = self.handle.spectral_norm(O)
-        return O / max(norm2, float(O.abs().max()) / self.lam)
+    def dual_scales(self, Ob):
+        """y0 scales 1 / max(||O_b||_2, ||O_b||_inf / lambda) of a batch (computed by the library)."""
+        return self.handle.unrolled_init(Ob.contiguous(), self.lam)
 
-    def forward_one(self, O, Y0=None):
+    def forward(self, Ob, y0_scale=None):
+        """Ob: (B, m, n) float32 CUDA.  Returns L_K as a (B, m, n) tensor."""
+        Ob = Ob.contiguous()
+        ys = self.dual_scales(Ob) if y0_scale is None else list(y0_scale)
+        return _function().apply(self.tau, self.mu, Ob, self.handle, self.lam, self.l, ys)
+
+    def loss(self, Ob, Lb_true, y0_scale=None):
+        """The training objective of the workload, sum_b ||L_K(b) - L_true(b)||_F^2."""
         torch = _torch()
-        Y = self.dual_init(O) if Y0 is None else Y0
-        S = torch.zeros_like(O)
-        L = None
-        for k in range(self.K):
-            mu, tau = self.mu[k], self.tau[k]
-            A = O - S + Y / mu
-            L = fr.frsvt_svt_autograd(A, tau, self.handle, self.l, k)
-            T = O - L + Y / mu
-            S = torch.sign(T) * torch.relu(T.abs() - self.lam / mu)
-            Y = Y + mu * (O - L - S)
-        return L
-
-    def forward(self, Ob):
-        """Ob: (B, m, n) float32 CUDA.  Returns the list of L_K per batch element."""
-        return [self.forward_one(Ob[b]) for b in range(Ob.shape[0])]
-
-    def loss(self, Ob, Lb_true):
-        torch = _torch()
-        Ls = self.forward(Ob)
-        return sum(torch.sum((L - Lt) ** 2) for L, Lt in zip(Ls, Lb_true))
+        return torch.sum((self.forward(Ob, y0_scale) - Lb_true) ** 2)

@@ -49,7 +49,9 @@ def test_rank_prediction_matches_oracle(fr, case):
         l_max, q, iters, seed, ap = 32, 1, 12, 17, dict(a=2, rho=0.05, gamma=0.2)
     ref = orpca.ialm_rpca(O, method="frsvt", q=q, seed=seed, fixed_iters=iters, ap=ap)
     L, S, ls, info = run(fr, O, l_max, q, iters, seed, ap)
-    assert info.device_status & ~1 == 0
+    # only the informational rank bit may be set: the sampled basis (r + a columns) reaches past the
+    # iterate's numerical rank as the iALM converges, and the Cholesky QR then drops those columns
+    assert info.device_status & ~fr.DEV_RANK_DEFICIENT == 0, info
     assert ls[:iters] == ref.ls                     # l_0 .. l_{iters-1}
     assert rel_fro(L, ref.L) <= TOL
     assert rel_fro(S, ref.S) <= TOL
