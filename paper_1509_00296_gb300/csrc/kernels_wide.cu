@@ -538,11 +538,11 @@ __device__ TailVec carve_vec(unsigned char* base) {
 // in shared memory), with the column drops of the l <= 32 path: column j is dropped (row j of R
 // zero, the trailing block untouched) when its pivot is not above rank_tol * G_jj (original), when
 // G_jj is below 1e-15 of the largest diagonal, or when it is not a finite positive number.  Blocked
-// by kCB columns: warp 0 factors a panel (its kCB rows of R, each with warp-level synchronisation
-// only: pivot, 1 / sqrt(pivot), the row scaled, the panel's later rows updated), then every warp
-// applies the panel's rank-kCB update to the trailing upper triangle, dealt as (row, 32-column
-// chunk) items, two per warp and pass with every load ahead of the stores; two block barriers per
-// panel.  R (FP32, row-major, upper, dropped rows zero) goes to Rout; v.rdiag / v.drop get the
+// by kCB columns: warp 0 factors the panel's kCB x kCB diagonal block and inverts it (every lane
+// alike, in registers: the only serial part), every thread then forms one column of the panel's
+// rows of R (R12 = R11^{-T} G12), and every warp applies the panel's rank-kCB update to the
+// trailing upper triangle, dealt as (row, 32-column chunk) items, two per warp and pass with every
+// load ahead of the stores; three block barriers per panel.  R (FP32, row-major, upper, dropped rows zero) goes to Rout; v.rdiag / v.drop get the
 // diagonal and the flags.  A non-finite diagonal of G (NaN or Inf met in the Gram reduction) ORs
 // FRSVT_DEV_NONFINITE into *status.
 constexpr int kCB = 4;                   // panel width of the Cholesky
@@ -562,42 +562,84 @@ __device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, dou
   __syncthreads();
   float maxdiag = 0.f;
   for (int a = 0; a < p; ++a) maxdiag = fmaxf(maxdiag, v.g0[a]);
+  __shared__ df64 sW[kCB * kCB];                     // W = R11^{-1} of the current panel (upper)
   for (int j0 = 0; j0 < p; j0 += kCB) {
     const int j1 = min(p, j0 + kCB);
-    if (warp == 0) {                               // panel j0 .. j1 - 1: rows of R into Rp
-      for (int j = j0; j < j1; ++j) {
-        const df64 d = G[j * kWL + j];
-        const bool drop =
-            !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
-        const df64 inv = drop ? df64{0.f, 0.f} : df_rsqrt(d);
-        if (lane == 0) {
-          v.rdiag[j] = drop ? df64{0.f, 0.f} : df_mul(d, inv);
-          v.drop[j] = drop ? 1 : 0;
-        }
-        df64* rp = Rp + (j - j0) * kWL;
+    const int nk = j1 - j0;
+    if (warp == 0) {                               // the kCB x kCB diagonal block, every lane alike
+      df64 g[kCB * kCB], r[kCB * kCB], w[kCB * kCB], inv[kCB];
+      int dr[kCB];
 #pragma unroll
-        for (int t = 0; t < kWL / 32; ++t) {         // row j of R (zero left of j, and when dropped)
-          const int b = lane + 32 * t;
-          const df64 r = (!drop && b >= j && b < p) ? df_mul(G[j * kWL + b], inv) : df64{0.f, 0.f};
-          rp[b] = r;
-          if (b >= j && b < p) Rout[j * kWL + b] = r.hi;
-        }
-        __syncwarp();
-        if (!drop)                                   // the panel's later rows
-          for (int a = j + 1; a < j1; ++a) {
-            const df64 fa = df_neg(rp[a]);
+      for (int u = 0; u < kCB * kCB; ++u) {
+        const int i = u / kCB, c = u % kCB;
+        g[u] = (i <= c && c < nk) ? G[(j0 + i) * kWL + j0 + c] : df64{0.f, 0.f};
+        r[u] = df64{0.f, 0.f};
+        w[u] = df64{0.f, 0.f};
+      }
 #pragma unroll
-            for (int t = 0; t < kWL / 32; ++t) {
-              const int b = lane + 32 * t;
-              if (b >= a && b < p) G[a * kWL + b] = df_add(G[a * kWL + b], df_mul(fa, rp[b]));
-            }
+      for (int i = 0; i < kCB; ++i) {
+        const int j = j0 + i;
+        const df64 d = g[i * kCB + i];
+        const bool drop = i >= nk || !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) ||
+                          !(d.hi < 1e30f);
+        dr[i] = drop ? 1 : 0;
+        inv[i] = drop ? df64{0.f, 0.f} : df_rsqrt(d);
+        if (!drop) {
+          r[i * kCB + i] = df_mul(d, inv[i]);
+#pragma unroll
+          for (int c = i + 1; c < kCB; ++c) r[i * kCB + c] = df_mul(g[i * kCB + c], inv[i]);
+#pragma unroll
+          for (int a = i + 1; a < kCB; ++a)
+#pragma unroll
+            for (int c = a; c < kCB; ++c)
+              g[a * kCB + c] = df_add(g[a * kCB + c], df_neg(df_mul(r[i * kCB + a], r[i * kCB + c])));
+        }
+      }
+      // W = R11^{-1}: W_cc = inv_c, W_rc = -(sum_{r < k <= c} R_rk W_kc) inv_r (zero rows for drops)
+#pragma unroll
+      for (int c = 0; c < kCB; ++c) {
+        w[c * kCB + c] = inv[c];
+#pragma unroll
+        for (int rr = c - 1; rr >= 0; --rr) {
+          df64 acc{0.f, 0.f};
+#pragma unroll
+          for (int k = rr + 1; k <= c; ++k) acc = df_add(acc, df_mul(r[rr * kCB + k], w[k * kCB + c]));
+          w[rr * kCB + c] = dr[rr] ? df64{0.f, 0.f} : df_neg(df_mul(acc, inv[rr]));
+        }
+      }
+      if (lane == 0) {                             // compile-time indices keep the block in registers
+#pragma unroll
+        for (int u = 0; u < kCB * kCB; ++u) sW[u] = w[u];
+#pragma unroll
+        for (int i = 0; i < kCB; ++i)
+          if (i < nk) {
+            v.rdiag[j0 + i] = r[i * kCB + i];
+            v.drop[j0 + i] = dr[i];
           }
-        __syncwarp();
       }
     }
     __syncthreads();
+    // the panel's rows of R, R[j0 + i][b] = sum_{k <= i} W[k][i] G[j0 + k][b] for b >= j0 (one column b
+    // per thread; the diagonal block this way equals R11): into Rp (df64) and Rout (FP32)
+    for (int b = j0 + tid; b < kWL; b += blockDim.x) {
+      df64 gk[kCB];
+#pragma unroll
+      for (int k = 0; k < kCB; ++k) gk[k] = (k < nk && b < p) ? G[(j0 + k) * kWL + b] : df64{0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < kCB; ++i) {
+        df64 acc{0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k <= i; ++k) acc = df_add(acc, df_mul(sW[k * kCB + i], gk[k]));
+        if (i >= nk || b >= p || b < j0 + i) acc = df64{0.f, 0.f};
+        Rp[i * kWL + b] = acc;
+        if (i < nk && b < p && b >= j0 + i) Rout[(j0 + i) * kWL + b] = acc.hi;
+      }
+    }
+    for (int b = tid; b < j0; b += blockDim.x)      // left of the panel: zero
+#pragma unroll
+      for (int i = 0; i < kCB; ++i) Rp[i * kWL + b] = df64{0.f, 0.f};
+    __syncthreads();
     // trailing update of rows j1 .. p - 1: G_ab -= sum_k Rp[k][a] Rp[k][b]
-    const int nk = j1 - j0;
     const int rows = p - j1;
 #pragma unroll 1
     for (int c = 0; c < kWL / 32; ++c) {
@@ -1246,44 +1288,7 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
       if (ok && !mbar_wait(&acc_full[buf], static_cast<uint32_t>(k / 2) & 1u)) flag_timeout(ok, dst);
       tc_fence_after();
       const int64_t row = 128 * static_cast<int64_t>(tr) + 32 * q + lane;
-      // O, S, A of the thread's row, 16 columns per group; the next group's loads are issued before
-      // the current group is consumed, so each thread keeps two groups (384 bytes) in flight
-      float ov[16], sv[16], av[16], on[16], sn_[16], anx[16];    // current group, next group
-      auto load_group = [&](int cg, float* o_, float* s_, float* a_) {
-        const int64_t c0 = static_cast<int64_t>(kWN) * tc + 128 * half + 16 * cg;
-        if (!ALM || row >= m || c0 >= n) return;
-        if (c0 + 16 <= n) {
-          const float4* O4 = reinterpret_cast<const float4*>(O + row * ld + c0);
-          const float4* S4 = reinterpret_cast<const float4*>(S + row * ld + c0);
-          const float4* A4 = reinterpret_cast<const float4*>(A + row * ld + c0);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 o = __ldcs(O4 + u), s = __ldcs(S4 + u), a = __ldcs(A4 + u);
-            o_[4 * u] = o.x; o_[4 * u + 1] = o.y; o_[4 * u + 2] = o.z; o_[4 * u + 3] = o.w;
-            s_[4 * u] = s.x; s_[4 * u + 1] = s.y; s_[4 * u + 2] = s.z; s_[4 * u + 3] = s.w;
-            a_[4 * u] = a.x; a_[4 * u + 1] = a.y; a_[4 * u + 2] = a.z; a_[4 * u + 3] = a.w;
-          }
-        } else {
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const bool in = c0 + u < n;
-            o_[u] = in ? O[row * ld + c0 + u] : 0.f;
-            s_[u] = in ? S[row * ld + c0 + u] : 0.f;
-            a_[u] = in ? A[row * ld + c0 + u] : 0.f;
-          }
-        }
-      };
-      if (ok) load_group(0, ov, sv, av);
-#pragma unroll
       for (int cg = 0; cg < 8; ++cg) {
-        if (cg > 0)                                                   // the group loaded last pass
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            ov[u] = on[u];
-            sv[u] = sn_[u];
-            av[u] = anx[u];
-          }
-        if (ok && cg + 1 < 8) load_group(cg + 1, on, sn_, anx);
         float x[16];
         const int colt = 128 * half + 16 * cg;
         tmem_ld16(tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(buf * kWN + colt), x);
@@ -1301,10 +1306,31 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
           }
           continue;
         }
+        float ov[16], sv[16], av[16];
+        if (full16) {
+          const float4* O4 = reinterpret_cast<const float4*>(O + row * ld + col0);
+          const float4* S4 = reinterpret_cast<const float4*>(S + row * ld + col0);
+          const float4* A4 = reinterpret_cast<const float4*>(A + row * ld + col0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 o = __ldcs(O4 + u), s = __ldcs(S4 + u), a = __ldcs(A4 + u);
+            ov[4 * u] = o.x; ov[4 * u + 1] = o.y; ov[4 * u + 2] = o.z; ov[4 * u + 3] = o.w;
+            sv[4 * u] = s.x; sv[4 * u + 1] = s.y; sv[4 * u + 2] = s.z; sv[4 * u + 3] = s.w;
+            av[4 * u] = a.x; av[4 * u + 1] = a.y; av[4 * u + 2] = a.z; av[4 * u + 3] = a.w;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const bool in = col0 + u < n;
+            ov[u] = in ? O[row * ld + col0 + u] : 0.f;
+            sv[u] = in ? S[row * ld + col0 + u] : 0.f;
+            av[u] = in ? A[row * ld + col0 + u] : 0.f;
+          }
+        }
         float sn[16], an[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
-          const float t = av[u] + sv[u] - x[u];                         // O - L + Y / mu
+          const float t = av[u] + sv[u] - x[u];                        // O - L + Y / mu
           sn[u] = (t > thr) ? (t - thr) : ((t < -thr) ? (t + thr) : 0.f);
           an[u] = ov[u] - sn[u] + ratio * (t - sn[u]);                  // O - S' + Y' / mu'
           const float rz = ov[u] - x[u] - sn[u];                        // O - L - S'
