@@ -247,9 +247,12 @@ frsvt_status frsvt_set_partial(frsvt_handle* h, int32_t k);
  * When timing is enabled every kernel launch is bracketed by CUDA events on
  * the handle's stream (recording events does not synchronize; it adds a few
  * microseconds per launch).  frsvt_get_timings synchronizes, then returns per
- * phase the summed device time in milliseconds and the number of launches
- * since the previous call, and clears them.  ms and launches have
- * FRSVT_NPHASE entries.  Disabling collects pending events first.
+ * phase the summed device time in milliseconds and the number of timed
+ * launch groups since the previous call, and clears them.  A group is one
+ * launcher call and may hold more than one kernel (the wide-basis Gram and
+ * the small dense factorisation that consumes it are one group).  ms and
+ * launches have FRSVT_NPHASE entries.  Disabling collects pending events
+ * first.
  */
 #define FRSVT_NPHASE 11
 #define FRSVT_PHASE_SKETCH    0   /* Y = A^T Omega            (Alg. 1 steps 4-5, 8-9) */
@@ -267,6 +270,15 @@ frsvt_status frsvt_set_partial(frsvt_handle* h, int32_t k);
 frsvt_status frsvt_enable_timing(frsvt_handle* h, int32_t enable);
 frsvt_status frsvt_get_timings(frsvt_handle* h, double* ms, int32_t* launches);
 const char* frsvt_phase_name(int32_t phase);
+
+/*
+ * Kernels per iALM step.  *kernels = the number of kernel launches in the CUDA
+ * graph that the most recent rpca_ialm_step call replayed (counted from the
+ * graph's kernel nodes when it was captured), or 0 when that call launched its
+ * kernels directly (phase timing on, or the caller's stream being captured).
+ * Host-only; does not synchronize.
+ */
+frsvt_status frsvt_step_kernels(frsvt_handle* h, int32_t* kernels);
 
 /*
  * Allocation-free FRSVT (the paper has no counterpart: this is a deployment

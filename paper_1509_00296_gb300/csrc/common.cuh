@@ -109,6 +109,33 @@ __device__ __forceinline__ df64 df_rsqrt(df64 a) {
   return df_add(y, c);
 }
 
+// The same Newton step with a shorter dependency chain: the residual h = 1 - a y0^2 is formed by
+// FMAs from the exact square y0^2 = t + te (te = fma(y0, y0, -t)), h = 1 - a.hi t - a.hi te -
+// a.lo t, and y1 = y0 + y0 h / 2 is returned as the pair (y0, y0 h / 2) renormalised.
+__device__ __forceinline__ df64 df_rsqrt_fma(df64 a) {
+  const float y = rsqrtf(a.hi);
+  const float t = __fmul_rn(y, y);
+  const float te = __fmaf_rn(y, y, -t);
+  float h = __fmaf_rn(-a.hi, t, 1.f);
+  h = __fmaf_rn(-a.hi, te, h);
+  h = __fmaf_rn(-a.lo, t, h);
+  return df_quick(y, __fmul_rn(__fmul_rn(0.5f, y), h));
+}
+
+// g - x y in double-float: the product split exactly with FMAs (the cross terms with the low
+// parts folded into its error), its high part taken off g.hi by two-sum, the low-order terms
+// gathered in one float, the pair renormalised.
+__device__ __forceinline__ df64 df_fms(df64 g, df64 x, df64 y) {
+  const float pr = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -pr);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const float s = __fsub_rn(g.hi, pr);
+  const float bb = __fsub_rn(s, g.hi);
+  const float err = __fsub_rn(__fsub_rn(g.hi, __fsub_rn(s, bb)), __fadd_rn(pr, bb));
+  return df_quick(s, __fadd_rn(g.lo, __fsub_rn(err, e)));
+}
+
 // ---------------------------------------------------------------- small utilities
 // Sort key of a singular value for the descending order of D: NaN ranks below every number, so
 // that ranking by (key, index) is a permutation whatever the values are.

@@ -130,8 +130,8 @@ cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUt
 cudaError_t launch_wd_quant8(const float* A, int64_t lda, int64_t m, int64_t n, void* A8, int64_t ld8, float* scales,
                              cudaStream_t st);
 cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len, int grid, double* cpart, double* Gpk,
-                           unsigned* ticket, int p, double rank_tol, int l, float tau_host, int tau_from_mu,
-                           int update_rp, int advance_counter, int max_sweeps, float* T1, float* T2, DevState* dst,
+                           int p, double rank_tol, int l, float tau_host, int tau_from_mu, int update_rp,
+                           int advance_counter, int max_sweeps, float* T1, float* T2, DevState* dst,
                            cudaStream_t st);
 cudaError_t launch_wd_apply(const float* in, int64_t ldi, int64_t len, const float* T, float* outT, float* outTl,
                             int64_t ldo, float* outR, float* outRl, cudaStream_t st);
@@ -232,6 +232,8 @@ struct frsvt_handle {
   cudaGraphExec_t step_exec[kGraphSlots] = {};
   StepKey step_key[kGraphSlots] = {};
   uint64_t step_used[kGraphSlots] = {};           // last use (LRU eviction)
+  int32_t step_kernels[kGraphSlots] = {};         // kernel nodes of each captured graph
+  int32_t last_step_kernels = 0;                  // ... of the graph the last step replayed
   uint64_t step_clock = 0;
   // wide basis (cfg.l_max > 32, LP = 128, any short side): basis-side matrices transposed
   // (128 x ld_m / ld_n), Z and Rf row-major (len x 128), K-split partials, Gram partials
@@ -265,7 +267,6 @@ struct frsvt_handle {
 namespace {
 
 constexpr size_t kSmemLimit = 227 * 1024;
-constexpr int kCLw = 8;            // cluster size of the wide-basis Gram reduction
 const float kNoResidual = -1.f;    // DevState::rp_res before any range-propagated sketch (static storage: async copy)
 
 frsvt_status fail(frsvt_handle* h, frsvt_status s, const std::string& msg) {
@@ -623,11 +624,10 @@ void free_all(frsvt_handle* h) {
 frsvt_status wide_orth(frsvt_handle* h, int64_t ns, int l, int passes, bool bf_next) {
   cudaStream_t st = h->stream;
   const int64_t ld = h->w_lds;
-  unsigned* gt = h->wtick + h->w_ntiles;
   for (int pass = 0; pass < passes; ++pass) {
     const float* src = pass == 0 ? h->wYT : h->wQT;
     const bool last = pass == passes - 1;
-    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_gram(false, src, ld, ns, h->w_gram_grid, h->wgc, h->wGpk, gt, l,
+    FRSVT_LAUNCH(FRSVT_PHASE_ORTH, launch_wd_gram(false, src, ld, ns, h->w_gram_grid, h->wgc, h->wGpk, l,
                                                   h->cfg.rank_tol, l, 0.f, 0, 0, 0, h->cfg.max_jacobi_sweeps, h->wT1,
                                                   h->wT2, h->dst, st));
     FRSVT_LAUNCH(FRSVT_PHASE_APPLY, launch_wd_trsm(src, ld, ns, h->wT1, h->wQT, h->wQTl,
@@ -725,7 +725,7 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
                                                    h->wtick, h->wZT, nullptr, nullptr, nullptr, ldl, h->wZ, h->wZl,
                                                    h->dst, st));
   FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_wd_gram(true, h->wZT, ldl, nl, h->w_gram_grid, h->wgc, h->wGpk,
-                                                h->wtick + h->w_ntiles, l, h->cfg.rank_tol, l, tau_host, tau_from_mu, 0,
+                                                l, h->cfg.rank_tol, l, tau_host, tau_from_mu, 0,
                                                 advance_counter, h->cfg.max_jacobi_sweeps, h->wT1, h->wT2, h->dst,
                                                 st));
   FRSVT_LAUNCH(FRSVT_PHASE_APPLY, launch_wd_apply(h->wQT, lds, ns, h->wT1, nullptr, nullptr, 0, h->wRf, h->wRfl,
@@ -768,7 +768,7 @@ bool wide_alloc(frsvt_handle* h) {
   h->w_ldp = h->w_ldl;
   h->w_ntiles = h->w_ldp / T;
   h->w_gram_grid = wide_gram_grid();
-  if (h->w_gram_grid < kCLw) h->w_gram_grid = kCLw;
+  if (h->w_gram_grid < 1) h->w_gram_grid = 1;
   bool ok = true;
   auto alloc = [&](void** p, size_t bytes) {
     if (ok && cudaMalloc(p, bytes < 16 ? 16 : bytes) != cudaSuccess) ok = false;
@@ -789,7 +789,7 @@ bool wide_alloc(frsvt_handle* h) {
   alloc(reinterpret_cast<void**>(&h->wT1), sizeof(float) * LW * LW);
   alloc(reinterpret_cast<void**>(&h->wT2), sizeof(float) * LW * LW);
   alloc(reinterpret_cast<void**>(&h->wpart), sizeof(float) * 8 * LW * h->w_ldp);
-  alloc(reinterpret_cast<void**>(&h->wgc), sizeof(double) * (h->w_gram_grid / kCLw) * wide_gram_count());
+  alloc(reinterpret_cast<void**>(&h->wgc), sizeof(double) * h->w_gram_grid * wide_gram_count());
   alloc(reinterpret_cast<void**>(&h->wGpk), sizeof(double) * wide_gram_count());
   alloc(reinterpret_cast<void**>(&h->wac), sizeof(double) * (h->sms > 0 ? h->sms : 1));
   alloc(reinterpret_cast<void**>(&h->wtick), sizeof(unsigned) * (h->w_ntiles + 2));
@@ -1323,7 +1323,20 @@ static frsvt_status ialm_step_launch(frsvt_handle* h, const frsvt_handle::StepKe
       e = cudaStreamEndCapture(h->capture_stream, &g);
     }
     h->stream = user;
-    if (e == cudaSuccess && s == FRSVT_OK && g != nullptr) e = cudaGraphInstantiate(&h->step_exec[slot], g, 0);
+    int32_t kernels = 0;
+    if (e == cudaSuccess && s == FRSVT_OK && g != nullptr) {
+      size_t nn = 0;
+      if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+          for (size_t i = 0; i < nn; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+          }
+      }
+      (void)cudaGetLastError();
+      e = cudaGraphInstantiate(&h->step_exec[slot], g, 0);
+    }
     if (g) cudaGraphDestroy(g);
     if (s != FRSVT_OK) return s;
     if (e != cudaSuccess || h->step_exec[slot] == nullptr) {
@@ -1332,8 +1345,10 @@ static frsvt_status ialm_step_launch(frsvt_handle* h, const frsvt_handle::StepKe
       return ialm_launches(h, key);
     }
     h->step_key[slot] = key;
+    h->step_kernels[slot] = kernels;
   }
   h->step_used[slot] = ++h->step_clock;
+  h->last_step_kernels = h->step_kernels[slot];
   FRSVT_CK(cudaGraphLaunch(h->step_exec[slot], h->stream));
   return FRSVT_OK;
 }
@@ -1657,6 +1672,12 @@ frsvt_status frsvt_enable_timing(frsvt_handle* h, int32_t enable) {
     if (s != FRSVT_OK) return s;
   }
   h->timing = enable ? 1 : 0;
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_step_kernels(frsvt_handle* h, int32_t* kernels) {
+  if (h == nullptr || kernels == nullptr) return FRSVT_ERR_INVALID_ARG;
+  *kernels = h->last_step_kernels;
   return FRSVT_OK;
 }
 

@@ -473,12 +473,17 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 }
 
 // ---------------------------------------------------------------- Gram + small dense tails
-constexpr int kGW = 544;                 // 17 warps; threads < 528 own a 4 x 4 block of the upper triangle
+// Gram kernel: warps 0-15 own the 496 strictly-upper 4 x 4 blocks (threads 496-511 idle), warp 16
+// the 32 diagonal blocks (10 products each), so that every scheduler carries four full warps and
+// the first one also the lighter diagonal warp.
+constexpr int kGW = 544;
+constexpr int kGOff = 496;               // strictly-upper 4 x 4 blocks
 constexpr int kGB = 528;                 // 4 x 4 blocks (bi <= bj) of a 128 x 128 symmetric matrix
-constexpr int kGCount = kGB * 16;        // packed partial (doubles)
+constexpr int kGCount = kGB * 16;        // packed partial (df64 entries)
 constexpr int kGCols = 64;               // long-side columns staged per step
 constexpr int kGSt = kWL + 4;            // staging row stride (floats)
-constexpr int kWCL = 8;                  // cluster size of the Gram reduction
+constexpr int kGSumE = 64;               // entries per CTA of the partial sum
+constexpr int kGSumT = 256;              // its threads: 4 quarters of the partials per entry
 // threads of the one-CTA orthonormalisation tail after a Gram matrix
 constexpr int kTW = 512;
 
@@ -487,9 +492,9 @@ constexpr int kTW = 512;
 constexpr size_t kTG = 0;                                      // df64 G, 128 x 128 (128 KB)
 constexpr size_t kTR = kTG + sizeof(df64) * kWL * kWL;         // float 128 x 128 (64 KB)
 constexpr size_t kTV = kTR + sizeof(float) * kWL * kWL;        // small vectors
-constexpr size_t kTP = kTV + 8 * 1024;                         // Cholesky panel rows (df64)
-constexpr size_t kTEnd = kTP + 4 * 1024;
-constexpr size_t kGSmem = sizeof(float) * kGCols * kGSt + sizeof(double) * kGCount;   // Gram kernel
+constexpr size_t kTP = kTV + 8 * 1024;                         // Cholesky panels of R (df64)
+constexpr size_t kTEnd = kTP + 8 * 1024;                       // two panels of R, 128 x 4 df64 each
+constexpr size_t kGSmem = sizeof(float) * kGCols * kGSt + sizeof(df64) * kGCount;     // Gram kernel
 constexpr size_t kTSmem = kTEnd;                                                          // tail kernel
 
 __device__ __forceinline__ void block_of(int t, int& bi, int& bj) {
@@ -537,19 +542,94 @@ __device__ TailVec carve_vec(unsigned char* base) {
 // Right-looking Cholesky G = R^T R of the leading p x p block of G (double-float, upper triangle,
 // in shared memory), with the column drops of the l <= 32 path: column j is dropped (row j of R
 // zero, the trailing block untouched) when its pivot is not above rank_tol * G_jj (original), when
-// G_jj is below 1e-15 of the largest diagonal, or when it is not a finite positive number.  Blocked
-// by kCB columns: warp 0 factors the panel's kCB x kCB diagonal block and inverts it (every lane
-// alike, in registers: the only serial part), every thread then forms one column of the panel's
-// rows of R (R12 = R11^{-T} G12), and every warp applies the panel's rank-kCB update to the
-// trailing upper triangle, dealt as (row, 32-column chunk) items, two per warp and pass with every
-// load ahead of the stores; three block barriers per panel.  R (FP32, row-major, upper, dropped rows zero) goes to Rout; v.rdiag / v.drop get the
-// diagonal and the flags.  A non-finite diagonal of G (NaN or Inf met in the Gram reduction) ORs
-// FRSVT_DEV_NONFINITE into *status.
+// G_jj is below 1e-15 of the largest diagonal, or when it is not a finite positive number.
+//
+// Blocked by kCB columns, with one panel of look-ahead and the warps split by role:
+//   - the factor warp factors the panel's kCB x kCB diagonal block (every lane alike, in
+//     registers) and forms the panel's rows of R, R12 = R11^{-T} G12 (forward substitution, one
+//     column per lane), into a double-buffered panel Rp;
+//   - 384 update threads own fixed elements of the upper triangle (thread (pair c, group g):
+//     columns c and 127 - c, rows g, g + 6, g + 12, ...) and apply each panel's rank-kCB update
+//     to theirs.  Each first updates its element in the next panel's rows (at most one per
+//     column, as the row stride 6 exceeds kCB) and arrives on a named barrier, which lets the
+//     factor warp start on the next panel while the rest of the trailing update runs.
+// Warps are dealt to the four schedulers by warp index mod 4: the update threads are the warps
+// on schedulers 0-2 and the factor warp is warp 3, alone on scheduler 3 (warps 7, 11, 15 idle),
+// so that the serial chain of the diagonal blocks never waits for issue slots behind update
+// warps that always have independent work.
+// Rp[(panel & 1)][b][k] holds row k of the panel's rows of R at column b.  Every wait is a
+// hardware barrier whose arrival counts are fixed by p alone: per panel one "panel of R ready"
+// phase (factor warp arrives, update threads wait) and, except after the last panel, one "next
+// rows ready" phase (update threads arrive, factor warp waits).
+// R (FP32, row-major, upper, dropped rows zero) goes to Rout; v.rdiag / v.drop get the diagonal
+// and the flags.  A non-finite diagonal of G (NaN or Inf met in the Gram reduction) ORs
+// FRSVT_DEV_NONFINITE into *status.  Needs blockDim.x = 512.
 constexpr int kCB = 4;                   // panel width of the Cholesky
+constexpr int kChG = 6;                  // row groups of the update threads (row stride > kCB)
+constexpr int kChU = 64 * kChG;          // update threads: 64 column pairs x 6 row groups (12 warps)
+constexpr int kChFactorWarp = 3;         // alone on its scheduler
+constexpr int kChBar = kChU + 32;        // threads taking part in each named barrier
+constexpr int kBarRowsReady = 1;         // named barrier ids (0 is __syncthreads)
+constexpr int kBarPanelReady = 2;
+static_assert(kChG > kCB, "one element per column and thread in the look-ahead rows");
+
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// g - sum_k x_k y_k in double-float: each product split exactly with FMAs (the cross terms of the
+// low parts folded into its error), its high part taken off g by two-sum, every low-order term
+// gathered in one float and the pair renormalised at the end.
+__device__ __forceinline__ df64 df_sub_dot(df64 g, const df64* x, const df64* y) {
+  float hi = g.hi, lo = g.lo;
+#pragma unroll
+  for (int k = 0; k < kCB; ++k) {
+    const float pr = __fmul_rn(x[k].hi, y[k].hi);
+    float e = __fmaf_rn(x[k].hi, y[k].hi, -pr);
+    e = __fmaf_rn(x[k].hi, y[k].lo, e);
+    e = __fmaf_rn(x[k].lo, y[k].hi, e);
+    const float s = __fsub_rn(hi, pr);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fsub_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fadd_rn(pr, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fsub_rn(err, e));
+  }
+  return df_quick(hi, lo);
+}
+
+__device__ __forceinline__ void load_panel_col(const df64* Rpb, int b, df64* x) {
+  const float4 u0 = *reinterpret_cast<const float4*>(Rpb + b * kCB);
+  const float4 u1 = *reinterpret_cast<const float4*>(Rpb + b * kCB + 2);
+  x[0] = df64{u0.x, u0.y};
+  x[1] = df64{u0.z, u0.w};
+  x[2] = df64{u1.x, u1.y};
+  x[3] = df64{u1.z, u1.w};
+}
+
+// The update of column `col` (rows a0, a0 + kChG, ... <= col), two elements per step.
+__device__ __forceinline__ void chol_update_col(df64* G, const df64* Rpb, int col, int a0, const df64* y) {
+  int a = a0;
+  for (; a + kChG <= col; a += 2 * kChG) {
+    df64 x0[kCB], x1[kCB];
+    load_panel_col(Rpb, a, x0);
+    load_panel_col(Rpb, a + kChG, x1);
+    const df64 g0 = G[a * kWL + col], g1 = G[(a + kChG) * kWL + col];
+    G[a * kWL + col] = df_sub_dot(g0, x0, y);
+    G[(a + kChG) * kWL + col] = df_sub_dot(g1, x1, y);
+  }
+  if (a <= col) {
+    df64 x0[kCB];
+    load_panel_col(Rpb, a, x0);
+    G[a * kWL + col] = df_sub_dot(G[a * kWL + col], x0, y);
+  }
+}
 
 __device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, double rank_tol, uint32_t* status,
                               df64* Rp) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < kWL * kWL; e += blockDim.x) Rout[e] = 0.f;
   if (tid < kWL) {
     const float g0 = tid < p ? G[tid * kWL + tid].hi : 0.f;
@@ -560,117 +640,128 @@ __device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, dou
     if (tid < p && !isfinite(g0)) atomicOr(status, kDevNonfinite);
   }
   __syncthreads();
-  float maxdiag = 0.f;
-  for (int a = 0; a < p; ++a) maxdiag = fmaxf(maxdiag, v.g0[a]);
-  __shared__ df64 sW[kCB * kCB];                     // W = R11^{-1} of the current panel (upper)
-  for (int j0 = 0; j0 < p; j0 += kCB) {
-    const int j1 = min(p, j0 + kCB);
-    const int nk = j1 - j0;
-    if (warp == 0) {                               // the kCB x kCB diagonal block, every lane alike
-      df64 g[kCB * kCB], r[kCB * kCB], w[kCB * kCB], inv[kCB];
+  if (warp == kChFactorWarp) {                       // ---- the factor warp
+    float maxdiag = 0.f;
+    for (int a = lane; a < p; a += 32) maxdiag = fmaxf(maxdiag, v.g0[a]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxdiag = fmaxf(maxdiag, __shfl_xor_sync(0xffffffffu, maxdiag, o));
+    for (int j0 = 0, jp = 0; j0 < p; j0 += kCB, ++jp) {
+      if (jp > 0) named_bar_sync(kBarRowsReady, kChBar);   // rows j0 .. j0 + kCB - 1 are final
+      const int j1 = min(p, j0 + kCB);
+      const int nk = j1 - j0;
+      df64 g[kCB * kCB], r[kCB * kCB], inv[kCB];
+      float thr[kCB], gd[kCB];
       int dr[kCB];
 #pragma unroll
       for (int u = 0; u < kCB * kCB; ++u) {
         const int i = u / kCB, c = u % kCB;
         g[u] = (i <= c && c < nk) ? G[(j0 + i) * kWL + j0 + c] : df64{0.f, 0.f};
         r[u] = df64{0.f, 0.f};
-        w[u] = df64{0.f, 0.f};
       }
 #pragma unroll
       for (int i = 0; i < kCB; ++i) {
-        const int j = j0 + i;
+        thr[i] = i < nk ? v.thr[j0 + i] : 0.f;
+        gd[i] = i < nk ? v.g0[j0 + i] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < kCB; ++i) {
         const df64 d = g[i * kCB + i];
-        const bool drop = i >= nk || !(d.hi > v.thr[j]) || !(v.g0[j] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) ||
+        const bool drop = i >= nk || !(d.hi > thr[i]) || !(gd[i] > 1e-15f * maxdiag) || !(d.hi > 1e-30f) ||
                           !(d.hi < 1e30f);
         dr[i] = drop ? 1 : 0;
-        inv[i] = drop ? df64{0.f, 0.f} : df_rsqrt(d);
+        inv[i] = drop ? df64{0.f, 0.f} : df_rsqrt_fma(d);
         if (!drop) {
-          r[i * kCB + i] = df_mul(d, inv[i]);
 #pragma unroll
           for (int c = i + 1; c < kCB; ++c) r[i * kCB + c] = df_mul(g[i * kCB + c], inv[i]);
 #pragma unroll
-          for (int a = i + 1; a < kCB; ++a)
+          for (int a = i + 1; a < kCB; ++a)              // the next pivot's entry first
 #pragma unroll
-            for (int c = a; c < kCB; ++c)
-              g[a * kCB + c] = df_add(g[a * kCB + c], df_neg(df_mul(r[i * kCB + a], r[i * kCB + c])));
+            for (int c = a; c < kCB; ++c) g[a * kCB + c] = df_fms(g[a * kCB + c], r[i * kCB + a], r[i * kCB + c]);
+          r[i * kCB + i] = df_mul(d, inv[i]);
         }
       }
-      // W = R11^{-1}: W_cc = inv_c, W_rc = -(sum_{r < k <= c} R_rk W_kc) inv_r (zero rows for drops)
-#pragma unroll
-      for (int c = 0; c < kCB; ++c) {
-        w[c * kCB + c] = inv[c];
-#pragma unroll
-        for (int rr = c - 1; rr >= 0; --rr) {
-          df64 acc{0.f, 0.f};
-#pragma unroll
-          for (int k = rr + 1; k <= c; ++k) acc = df_add(acc, df_mul(r[rr * kCB + k], w[k * kCB + c]));
-          w[rr * kCB + c] = dr[rr] ? df64{0.f, 0.f} : df_neg(df_mul(acc, inv[rr]));
-        }
-      }
-      if (lane == 0) {                             // compile-time indices keep the block in registers
-#pragma unroll
-        for (int u = 0; u < kCB * kCB; ++u) sW[u] = w[u];
+      if (lane == 0) {                               // compile-time indices keep the block in registers
 #pragma unroll
         for (int i = 0; i < kCB; ++i)
           if (i < nk) {
             v.rdiag[j0 + i] = r[i * kCB + i];
             v.drop[j0 + i] = dr[i];
+#pragma unroll
+            for (int c = i; c < kCB; ++c)
+              if (c < nk) Rout[(j0 + i) * kWL + j0 + c] = r[i * kCB + c].hi;
           }
       }
-    }
-    __syncthreads();
-    // the panel's rows of R, R[j0 + i][b] = sum_{k <= i} W[k][i] G[j0 + k][b] for b >= j0 (one column b
-    // per thread; the diagonal block this way equals R11): into Rp (df64) and Rout (FP32)
-    for (int b = j0 + tid; b < kWL; b += blockDim.x) {
-      df64 gk[kCB];
+      // rows j0 .. j1 - 1 of R right of the block: x_i = (g_ib - sum_{k<i} r_ki x_k) / r_ii, four
+      // columns per lane at once
+      df64* Rpb = Rp + (jp & 1) * (kWL * kCB);
+      for (int b0 = j1; b0 < p; b0 += 128) {
+        df64 x[4][kCB];
 #pragma unroll
-      for (int k = 0; k < kCB; ++k) gk[k] = (k < nk && b < p) ? G[(j0 + k) * kWL + b] : df64{0.f, 0.f};
+        for (int t = 0; t < 4; ++t) {
+          const int b = b0 + lane + 32 * t;
 #pragma unroll
-      for (int i = 0; i < kCB; ++i) {
-        df64 acc{0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k <= i; ++k) acc = df_add(acc, df_mul(sW[k * kCB + i], gk[k]));
-        if (i >= nk || b >= p || b < j0 + i) acc = df64{0.f, 0.f};
-        Rp[i * kWL + b] = acc;
-        if (i < nk && b < p && b >= j0 + i) Rout[(j0 + i) * kWL + b] = acc.hi;
-      }
-    }
-    for (int b = tid; b < j0; b += blockDim.x)      // left of the panel: zero
-#pragma unroll
-      for (int i = 0; i < kCB; ++i) Rp[i * kWL + b] = df64{0.f, 0.f};
-    __syncthreads();
-    // trailing update of rows j1 .. p - 1: G_ab -= sum_k Rp[k][a] Rp[k][b]
-    const int rows = p - j1;
-#pragma unroll 1
-    for (int c = 0; c < kWL / 32; ++c) {
-      const int lc = rows - 32 * c;
-      for (int it = warp; it < lc; it += 2 * nw) {
-        const int a0 = j1 + it, a1 = a0 + nw;
-        const bool two = it + nw < lc;
-        const int b0 = a0 + 32 * c + lane, b1 = a1 + 32 * c + lane;
-        df64 g0{0.f, 0.f}, g1{0.f, 0.f}, x0[kCB], x1[kCB], y0[kCB], y1[kCB];
-        const bool on0 = b0 < p, on1 = two && b1 < p;
-        if (on0) g0 = G[a0 * kWL + b0];
-        if (on1) g1 = G[a1 * kWL + b1];
-#pragma unroll
-        for (int k = 0; k < kCB; ++k) {
-          const bool kk = k < nk;
-          x0[k] = kk ? Rp[k * kWL + a0] : df64{0.f, 0.f};
-          y0[k] = (kk && on0) ? Rp[k * kWL + b0] : df64{0.f, 0.f};
-          x1[k] = (kk && two) ? Rp[k * kWL + a1] : df64{0.f, 0.f};
-          y1[k] = (kk && on1) ? Rp[k * kWL + b1] : df64{0.f, 0.f};
+          for (int i = 0; i < kCB; ++i) x[t][i] = (b < p && i < nk) ? G[(j0 + i) * kWL + b] : df64{0.f, 0.f};
         }
 #pragma unroll
-        for (int k = 0; k < kCB; ++k) {
-          g0 = df_add(g0, df_neg(df_mul(x0[k], y0[k])));
-          g1 = df_add(g1, df_neg(df_mul(x1[k], y1[k])));
+        for (int i = 0; i < kCB; ++i)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int k = 0; k < i; ++k) x[t][i] = df_fms(x[t][i], r[k * kCB + i], x[t][k]);
+            x[t][i] = dr[i] ? df64{0.f, 0.f} : df_mul(x[t][i], inv[i]);   // a dropped row stays 0, NaN or not
+          }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int b = b0 + lane + 32 * t;
+          if (b < p) {
+            *reinterpret_cast<float4*>(Rpb + b * kCB) = make_float4(x[t][0].hi, x[t][0].lo, x[t][1].hi, x[t][1].lo);
+            *reinterpret_cast<float4*>(Rpb + b * kCB + 2) =
+                make_float4(x[t][2].hi, x[t][2].lo, x[t][3].hi, x[t][3].lo);
+#pragma unroll
+            for (int i = 0; i < kCB; ++i)
+              if (i < nk) Rout[(j0 + i) * kWL + b] = x[t][i].hi;
+          }
         }
-        if (on0) G[a0 * kWL + b0] = g0;
-        if (on1) G[a1 * kWL + b1] = g1;
       }
+      __syncwarp();
+      named_bar_arrive(kBarPanelReady, kChBar);
     }
-    __syncthreads();
+  } else if ((warp & 3) != 3) {                      // ---- the update threads
+    const int ut = ((warp >> 2) * 3 + (warp & 3)) * 32 + lane;   // 0 .. kChU - 1
+    const int pc = ut & 63, grp = ut >> 6;
+    const int colA = pc, colB = kWL - 1 - pc;
+    for (int j0 = 0, jp = 0; j0 < p; j0 += kCB, ++jp) {
+      named_bar_sync(kBarPanelReady, kChBar);
+      const int j1 = j0 + kCB;                       // rows >= j1 take this panel's update
+      const df64* Rpb = Rp + (jp & 1) * (kWL * kCB);
+      const int a0 = j1 <= grp ? grp : grp + (j1 - grp + kChG - 1) / kChG * kChG;   // first row >= j1
+      const bool onA = colA < p && a0 <= colA, onB = colB < p && a0 <= colB;
+      df64 yA[kCB], yB[kCB];
+      if (onA) load_panel_col(Rpb, colA, yA);
+      if (onB) load_panel_col(Rpb, colB, yB);
+      const bool look = a0 < j1 + kCB;               // a0 lies in the next panel's rows
+      if (look && (onA || onB)) {                    // (a0 <= a column < p: inside the panel)
+        df64 x[kCB];
+        load_panel_col(Rpb, a0, x);
+        if (onA) G[a0 * kWL + colA] = df_sub_dot(G[a0 * kWL + colA], x, yA);
+        if (onB) G[a0 * kWL + colB] = df_sub_dot(G[a0 * kWL + colB], x, yB);
+      }
+      if (j1 < p) {
+        __syncwarp();
+        named_bar_arrive(kBarRowsReady, kChBar);
+      }
+      const int a1 = look ? a0 + kChG : a0;
+      if (onA) chol_update_col(G, Rpb, colA, a1, yA);
+      if (onB) chol_update_col(G, Rpb, colB, a1, yB);
+    }
   }
+  __syncthreads();
+}
+
+// Entry e of the packed Gram (a df64 pair stored where a double is declared).
+__device__ __forceinline__ df64 gram_entry(const double* Gpk, int e) {
+  const float2 w = __ldcg(reinterpret_cast<const float2*>(Gpk) + e);
+  return df64{w.x, w.y};
 }
 
 struct CoreArgs {
@@ -682,19 +773,33 @@ struct CoreArgs {
   int max_sweeps;
 };
 
+// Packed index of the 4 x 4 block (bi, bj), bi <= bj, in row-major order of the upper triangle.
+__device__ __forceinline__ int block_slot(int bi, int bj) { return 32 * bi - bi * (bi - 1) / 2 + (bj - bi); }
+
 // X^T X (128 x 128, packed 4 x 4 blocks of the upper triangle) of a basis-side matrix in
-// double-float arithmetic, each CTA over its range of long-side columns, then a cluster split-K
-// reduction into Gpk (the cluster that finishes last writes it).
-__global__ void __cluster_dims__(kWCL, 1, 1) __launch_bounds__(kGW, 1)
+// double-float arithmetic over this CTA's range of long-side columns, written as the CTA's
+// partial: cpart[blockIdx.x][kGCount] (df64 pairs, float hi then float lo, where a double is
+// declared).  k_wd_gsum adds the partials.
+__global__ void __launch_bounds__(kGW, 1)
 k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_cta, double* __restrict__ cpart,
-          double* __restrict__ Gpk, unsigned* __restrict__ ticket, int p) {
+          int p) {
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ int flag;
-  float* stg = reinterpret_cast<float*>(dsm);                                         // kGCols x kGSt
-  double* part_sm = reinterpret_cast<double*>(dsm + sizeof(float) * kGCols * kGSt);  // kGCount
-  const int tid = threadIdx.x;
+  float* stg = reinterpret_cast<float*>(dsm);                                          // kGCols x kGSt
+  df64* part_sm = reinterpret_cast<df64*>(dsm + sizeof(float) * kGCols * kGSt);       // kGCount
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool diag = warp == kGOff / 32 + 1;          // warp 16
   int bi = 0, bj = 0;
-  if (tid < kGB) block_of(tid, bi, bj);
+  if (diag) {
+    bi = bj = lane;
+  } else if (tid < kGOff) {                          // strictly-upper block number tid
+    int rem = tid;
+    while (rem >= 31 - bi) {
+      rem -= 31 - bi;
+      ++bi;
+    }
+    bj = bi + 1 + rem;
+  }
+  const bool on = diag || tid < kGOff;
   df64 acc[16];
 #pragma unroll
   for (int u = 0; u < 16; ++u) acc[u] = df64{0.f, 0.f};
@@ -702,12 +807,22 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
   const int64_t x1 = imin64(len, x0 + per_cta);
   for (int64_t xs = x0; xs < x1; xs += kGCols) {
     const int nxc = static_cast<int>(imin64(kGCols, x1 - xs));
+#pragma unroll 4                                     // four loads in flight per thread
     for (int e = tid; e < kWL * kGCols; e += kGW) {
       const int a = e / kGCols, x = e % kGCols;
       stg[x * kGSt + a] = (x < nxc && a < p) ? __ldcg(XT + a * ldx + xs + x) : 0.f;
     }
     __syncthreads();
-    if (tid < kGB) {
+    if (diag) {                                      // the upper triangle of a diagonal block
+      for (int x = 0; x < nxc; ++x) {
+        const float4 ua = *reinterpret_cast<const float4*>(stg + x * kGSt + 4 * bi);
+        const float va[4] = {ua.x, ua.y, ua.z, ua.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = i; j < 4; ++j) df64_add_prod(acc[4 * i + j], va[i], va[j]);
+      }
+    } else if (on) {
       for (int x = 0; x < nxc; ++x) {
         const float4 ua = *reinterpret_cast<const float4*>(stg + x * kGSt + 4 * bi);
         const float4 ub = *reinterpret_cast<const float4*>(stg + x * kGSt + 4 * bj);
@@ -721,12 +836,54 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
     }
     __syncthreads();
   }
-  if (tid < kGB)
+  if (on) {
+    const int slot = block_slot(bi, bj);
 #pragma unroll
-    for (int u = 0; u < 16; ++u) part_sm[tid * 16 + u] = df64_value(acc[u]);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const df64 a = (diag && i > j) ? acc[4 * j + i] : acc[4 * i + j];   // the lower half mirrored
+        part_sm[slot * 16 + 4 * i + j] = df_quick(a.hi, a.lo);
+      }
+  }
   __syncthreads();
-  const int nclusters = gridDim.x / kWCL;
-  cluster_split_reduce<double, kWCL>(part_sm, kGCount, cpart, Gpk, ticket, blockIdx.x / kWCL, nclusters, &flag);
+  float4* dst = reinterpret_cast<float4*>(cpart + static_cast<int64_t>(blockIdx.x) * kGCount);
+  const float4* src = reinterpret_cast<const float4*>(part_sm);
+  for (int e = tid; e < kGCount / 2; e += kGW) __stcg(dst + e, src[e]);
+}
+
+// Gpk = the sum of the nparts partials, entry by entry in a fixed order: each CTA takes kGSumE
+// entries; quarter q of its threads sums partials q, q + 4, q + 8, ... (16 loads in flight,
+// pairwise within a group), then the four quarter sums are added in quarter order.
+__global__ void __launch_bounds__(kGSumT)
+k_wd_gsum(const double* __restrict__ cpart, int nparts, double* __restrict__ Gpk) {
+  __shared__ df64 red[4][kGSumE];
+  const int t = threadIdx.x, el = t % kGSumE, q = t / kGSumE;
+  const int e = blockIdx.x * kGSumE + el;
+  const float2* cp = reinterpret_cast<const float2*>(cpart);
+  df64 sum{0.f, 0.f};
+  if (e < kGCount) {
+    for (int k0 = q; k0 < nparts; k0 += 4 * 16) {
+      df64 v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int k = k0 + 4 * u;
+        const float2 w = k < nparts ? __ldcg(cp + static_cast<int64_t>(k) * kGCount + e) : make_float2(0.f, 0.f);
+        v[u] = df64{w.x, w.y};
+      }
+#pragma unroll
+      for (int h = 1; h < 16; h *= 2)
+#pragma unroll
+        for (int u = 0; u + h < 16; u += 2 * h) v[u] = df_add(v[u], v[u + h]);
+      sum = df_add(sum, v[0]);
+    }
+  }
+  red[q][el] = sum;
+  __syncthreads();
+  if (q == 0 && e < kGCount) {
+    const df64 g = df_add(df_add(red[0][el], red[1][el]), df_add(red[2][el], red[3][el]));
+    reinterpret_cast<float2*>(Gpk)[e] = make_float2(g.hi, g.lo);
+  }
 }
 
 // The orthonormalisation tail after the Gram of Y (one CTA of kTW threads; Alg. 1 steps 6 / 11 /
@@ -743,7 +900,7 @@ k_wd_orth(const double* __restrict__ Gpk, int p, double rank_tol, float* __restr
     const int t = e >> 4, u = e & 15;
     int bi, bj;
     block_of(t, bi, bj);
-    G[(4 * bi + (u >> 2)) * kWL + 4 * bj + (u & 3)] = df_from_double(__ldcg(Gpk + e));
+    G[(4 * bi + (u >> 2)) * kWL + 4 * bj + (u & 3)] = gram_entry(Gpk, e);
   }
   __syncthreads();
   wide_cholesky(G, v, R, p, rank_tol, &dst->status, reinterpret_cast<df64*>(dsm + kTP));
@@ -1021,7 +1178,7 @@ k_wd_core(const double* __restrict__ Gpk, int p, double rank_tol, CoreArgs ca, f
       const int t = e >> 4, u = e & 15;
       int bi, bj;
       block_of(t, bi, bj);
-      G[(4 * bi + (u >> 2)) * kWL + 4 * bj + (u & 3)] = df_from_double(__ldcg(Gpk + e));
+      G[(4 * bi + (u >> 2)) * kWL + 4 * bj + (u & 3)] = gram_entry(Gpk, e);
     }
     __syncthreads();
     wide_cholesky(G, v, R, p, rank_tol, &dst->status, reinterpret_cast<df64*>(dsm + kTP));
@@ -1429,24 +1586,13 @@ cudaError_t prepare_wide_kernels() {
   return e;
 }
 
-// Resident clusters of the Gram kernel, in CTAs (a multiple of its cluster size).
+// CTAs of the Gram kernel: one per SM (each holds one partial).
 int wide_gram_grid() {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kWCL, 1, 1);
-  cfg.blockDim = dim3(kGW, 1, 1);
-  cfg.dynamicSmemBytes = kGSmem;
-  cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = kWCL;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
-  int nc = 0;
-  if (cudaOccupancyMaxActiveClusters(&nc, reinterpret_cast<const void*>(k_wd_gram), &cfg) != cudaSuccess)
-    nc = 0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 0;
   (void)cudaGetLastError();
-  return nc * kWCL;
+  return sms;
 }
 
 int wide_gram_count() { return kGCount; }
@@ -1498,13 +1644,16 @@ cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUt
 }
 
 cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len, int grid, double* cpart, double* Gpk,
-                           unsigned* ticket, int p, double rank_tol, int l, float tau_host, int tau_from_mu,
-                           int update_rp, int advance_counter, int max_sweeps, float* T1, float* T2, DevState* dst,
+                           int p, double rank_tol, int l, float tau_host, int tau_from_mu, int update_rp,
+                           int advance_counter, int max_sweeps, float* T1, float* T2, DevState* dst,
                            cudaStream_t st) {
   const int64_t per = (len + grid - 1) / grid;
   CoreArgs ca{l, tau_host, tau_from_mu, update_rp, advance_counter, max_sweeps};
-  k_wd_gram<<<grid, kGW, kGSmem, st>>>(XT, ldx, len, per, cpart, Gpk, ticket, p);
+  k_wd_gram<<<grid, kGW, kGSmem, st>>>(XT, ldx, len, per, cpart, p);
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_wd_gsum<<<(kGCount + kGSumE - 1) / kGSumE, kGSumT, 0, st>>>(cpart, grid, Gpk);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (core)
     k_wd_core<<<kJC, kCW, kTSmem, st>>>(Gpk, p, rank_tol, ca, T1, T2, dst);

@@ -70,6 +70,7 @@ _SIGS = {
     "frsvt_last_error": [_P],
     "frsvt_enable_timing": [_P, ctypes.c_int32],
     "frsvt_get_timings": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
+    "frsvt_step_kernels": [_P, ctypes.POINTER(ctypes.c_int32)],
     "frsvt_phase_name": [ctypes.c_int32],
     "frsvt_svt_save": [_P, _P, _I64, _I64, _I64, ctypes.c_float, ctypes.c_int32, ctypes.c_uint64, _P, _I64, _P],
     "frsvt_backward": [_P, _P, _P, _I64, _I64, _I64, ctypes.c_float, ctypes.c_int32, ctypes.c_uint64, _P, _I64, _P,
@@ -260,6 +261,12 @@ class Handle:
 
     def enable_timing(self, on: bool = True):
         self._chk(lib().frsvt_enable_timing(self._h, 1 if on else 0))
+
+    def step_kernels(self) -> int:
+        """Kernel launches of the graph the last ialm_step replayed (0 if it launched directly)."""
+        n = ctypes.c_int32(0)
+        self._chk(lib().frsvt_step_kernels(self._h, ctypes.byref(n)))
+        return n.value
 
     def timings(self):
         """{phase name: (device ms, launches)} since the last call (synchronizes)."""
