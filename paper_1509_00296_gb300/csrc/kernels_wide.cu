@@ -546,31 +546,34 @@ __device__ TailVec carve_vec(unsigned char* base) {
 //
 // Blocked by kCB columns, with one panel of look-ahead and the warps split by role:
 //   - the factor warp factors the panel's kCB x kCB diagonal block (every lane alike, in
-//     registers) and forms the panel's rows of R, R12 = R11^{-T} G12 (forward substitution, one
-//     column per lane), into a double-buffered panel Rp;
-//   - 384 update threads own fixed elements of the upper triangle (thread (pair c, group g):
-//     columns c and 127 - c, rows g, g + 6, g + 12, ...) and apply each panel's rank-kCB update
-//     to theirs.  Each first updates its element in the next panel's rows (at most one per
+//     registers) and publishes R11 and 1 / R_ii (double-buffered in shared memory);
+//   - 384 update threads then form the panel's rows of R right of the block, R12 = R11^{-T} G12
+//     (forward substitution, one column per thread), into a double-buffered panel Rp, meet on a
+//     barrier of their own, and apply the panel's rank-kCB update to the elements of the upper
+//     triangle they own (thread (pair c, group g): columns c and 127 - c, rows g, g + 6,
+//     g + 12, ...).  Each first updates its element in the next panel's rows (at most one per
 //     column, as the row stride 6 exceeds kCB) and arrives on a named barrier, which lets the
-//     factor warp start on the next panel while the rest of the trailing update runs.
-// Warps are dealt to the four schedulers by warp index mod 4: the update threads are the warps
-// on schedulers 0-2 and the factor warp is warp 3, alone on scheduler 3 (warps 7, 11, 15 idle),
-// so that the serial chain of the diagonal blocks never waits for issue slots behind update
-// warps that always have independent work.
+//     factor warp start on the next block while the rest of the trailing update runs.
+// The update threads are warps 0-11 and the factor warp is warp 15 (warps 12-14 idle): measured
+// on GB300, this layout lets the serial chain of the diagonal blocks wait least for issue behind
+// the update warps, which always have independent work (75 us against 81 us for a 120 x 120
+// Gram with the factor warp at warp 3 and the update warps on the other three schedulers).
 // Rp[(panel & 1)][b][k] holds row k of the panel's rows of R at column b.  Every wait is a
-// hardware barrier whose arrival counts are fixed by p alone: per panel one "panel of R ready"
-// phase (factor warp arrives, update threads wait) and, except after the last panel, one "next
-// rows ready" phase (update threads arrive, factor warp waits).
+// hardware barrier whose arrival counts are fixed by p alone: per panel one "block ready" phase
+// (factor warp arrives, update threads wait), one "panel ready" phase (update threads only) and,
+// except after the last panel, one "next rows ready" phase (update threads arrive, factor warp
+// waits).
 // R (FP32, row-major, upper, dropped rows zero) goes to Rout; v.rdiag / v.drop get the diagonal
 // and the flags.  A non-finite diagonal of G (NaN or Inf met in the Gram reduction) ORs
 // FRSVT_DEV_NONFINITE into *status.  Needs blockDim.x = 512.
 constexpr int kCB = 4;                   // panel width of the Cholesky
 constexpr int kChG = 6;                  // row groups of the update threads (row stride > kCB)
 constexpr int kChU = 64 * kChG;          // update threads: 64 column pairs x 6 row groups (12 warps)
-constexpr int kChFactorWarp = 3;         // alone on its scheduler
-constexpr int kChBar = kChU + 32;        // threads taking part in each named barrier
+constexpr int kChFactorWarp = 15;
+constexpr int kChBar = kChU + 32;        // threads on the barriers between the factor warp and the update threads
 constexpr int kBarRowsReady = 1;         // named barrier ids (0 is __syncthreads)
-constexpr int kBarPanelReady = 2;
+constexpr int kBarBlockReady = 2;
+constexpr int kBarPanelReady = 3;
 static_assert(kChG > kCB, "one element per column and thread in the look-ahead rows");
 
 __device__ __forceinline__ void named_bar_sync(int id, int n) {
@@ -639,6 +642,8 @@ __device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, dou
     v.rdiag[tid] = df64{0.f, 0.f};
     if (tid < p && !isfinite(g0)) atomicOr(status, kDevNonfinite);
   }
+  __shared__ df64 sBlk[2][kCB * kCB + kCB];         // the panel's diagonal block of R and 1 / R_ii
+  __shared__ int sDrop[2][kCB];
   __syncthreads();
   if (warp == kChFactorWarp) {                       // ---- the factor warp
     float maxdiag = 0.f;
@@ -650,19 +655,24 @@ __device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, dou
       const int j1 = min(p, j0 + kCB);
       const int nk = j1 - j0;
       df64 g[kCB * kCB], r[kCB * kCB], inv[kCB];
-      float thr[kCB], gd[kCB];
       int dr[kCB];
-#pragma unroll
-      for (int u = 0; u < kCB * kCB; ++u) {
-        const int i = u / kCB, c = u % kCB;
-        g[u] = (i <= c && c < nk) ? G[(j0 + i) * kWL + j0 + c] : df64{0.f, 0.f};
-        r[u] = df64{0.f, 0.f};
-      }
+      // few shared-memory instructions (the update warps keep the shared-memory pipe busy): the
+      // block's rows as 32-byte vectors, the thresholds as one float4 each
 #pragma unroll
       for (int i = 0; i < kCB; ++i) {
-        thr[i] = i < nk ? v.thr[j0 + i] : 0.f;
-        gd[i] = i < nk ? v.g0[j0 + i] : 0.f;
+        const float4* row = reinterpret_cast<const float4*>(G + (j0 + min(i, nk - 1)) * kWL + j0);
+        const float4 u0 = row[0], u1 = row[1];
+        const df64 e[4] = {df64{u0.x, u0.y}, df64{u0.z, u0.w}, df64{u1.x, u1.y}, df64{u1.z, u1.w}};
+#pragma unroll
+        for (int c = 0; c < kCB; ++c) {
+          g[i * kCB + c] = (i <= c && c < nk) ? e[c] : df64{0.f, 0.f};
+          r[i * kCB + c] = df64{0.f, 0.f};
+        }
       }
+      const float4 thr4 = *reinterpret_cast<const float4*>(v.thr + j0);
+      const float4 gd4 = *reinterpret_cast<const float4*>(v.g0 + j0);
+      const float thr[kCB] = {thr4.x, thr4.y, thr4.z, thr4.w};
+      const float gd[kCB] = {gd4.x, gd4.y, gd4.z, gd4.w};
 #pragma unroll
       for (int i = 0; i < kCB; ++i) {
         const df64 d = g[i * kCB + i];
@@ -680,60 +690,64 @@ __device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, dou
           r[i * kCB + i] = df_mul(d, inv[i]);
         }
       }
-      if (lane == 0) {                               // compile-time indices keep the block in registers
+      {                                              // one store instruction per output, lane u storing entry u
+        df64 ru = r[0];
+        int du = dr[0];
+#pragma unroll
+        for (int u = 1; u < kCB * kCB; ++u)
+          if (lane == u) ru = r[u];
 #pragma unroll
         for (int i = 0; i < kCB; ++i)
-          if (i < nk) {
-            v.rdiag[j0 + i] = r[i * kCB + i];
-            v.drop[j0 + i] = dr[i];
+          if (lane == kCB * kCB + i) ru = inv[i];
 #pragma unroll
-            for (int c = i; c < kCB; ++c)
-              if (c < nk) Rout[(j0 + i) * kWL + j0 + c] = r[i * kCB + c].hi;
-          }
-      }
-      // rows j0 .. j1 - 1 of R right of the block: x_i = (g_ib - sum_{k<i} r_ki x_k) / r_ii, four
-      // columns per lane at once
-      df64* Rpb = Rp + (jp & 1) * (kWL * kCB);
-      for (int b0 = j1; b0 < p; b0 += 128) {
-        df64 x[4][kCB];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int b = b0 + lane + 32 * t;
-#pragma unroll
-          for (int i = 0; i < kCB; ++i) x[t][i] = (b < p && i < nk) ? G[(j0 + i) * kWL + b] : df64{0.f, 0.f};
+        for (int i = 1; i < kCB; ++i)
+          if (lane == i) du = dr[i];
+        if (lane < kCB * kCB + kCB) sBlk[jp & 1][lane] = ru;     // R11 (row-major), then 1 / R_ii
+        const int i = lane / kCB, c = lane % kCB;
+        if (lane < kCB * kCB && i <= c && c < nk) Rout[(j0 + i) * kWL + j0 + c] = ru.hi;
+        if (lane < kCB) {
+          sDrop[jp & 1][lane] = du;
+          if (lane < nk) v.drop[j0 + lane] = du;
         }
+        df64 dg = r[0];
 #pragma unroll
-        for (int i = 0; i < kCB; ++i)
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-#pragma unroll
-            for (int k = 0; k < i; ++k) x[t][i] = df_fms(x[t][i], r[k * kCB + i], x[t][k]);
-            x[t][i] = dr[i] ? df64{0.f, 0.f} : df_mul(x[t][i], inv[i]);   // a dropped row stays 0, NaN or not
-          }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int b = b0 + lane + 32 * t;
-          if (b < p) {
-            *reinterpret_cast<float4*>(Rpb + b * kCB) = make_float4(x[t][0].hi, x[t][0].lo, x[t][1].hi, x[t][1].lo);
-            *reinterpret_cast<float4*>(Rpb + b * kCB + 2) =
-                make_float4(x[t][2].hi, x[t][2].lo, x[t][3].hi, x[t][3].lo);
-#pragma unroll
-            for (int i = 0; i < kCB; ++i)
-              if (i < nk) Rout[(j0 + i) * kWL + b] = x[t][i].hi;
-          }
-        }
+        for (int k = 1; k < kCB; ++k)
+          if (lane == k) dg = r[k * kCB + k];
+        if (lane < nk) v.rdiag[j0 + lane] = dg;
       }
       __syncwarp();
-      named_bar_arrive(kBarPanelReady, kChBar);
+      named_bar_arrive(kBarBlockReady, kChBar);
     }
-  } else if ((warp & 3) != 3) {                      // ---- the update threads
-    const int ut = ((warp >> 2) * 3 + (warp & 3)) * 32 + lane;   // 0 .. kChU - 1
+  } else if (warp < kChU / 32) {                     // ---- the update threads
+    const int ut = tid;
     const int pc = ut & 63, grp = ut >> 6;
     const int colA = pc, colB = kWL - 1 - pc;
     for (int j0 = 0, jp = 0; j0 < p; j0 += kCB, ++jp) {
-      named_bar_sync(kBarPanelReady, kChBar);
+      named_bar_sync(kBarBlockReady, kChBar);
       const int j1 = j0 + kCB;                       // rows >= j1 take this panel's update
-      const df64* Rpb = Rp + (jp & 1) * (kWL * kCB);
+      df64* Rpb = Rp + (jp & 1) * (kWL * kCB);
+      {                                              // rows j0 .. j0 + 3 of R at column b = j1 + ut
+        const int b = j1 + ut;
+        if (b < p) {
+          const df64* blk = sBlk[jp & 1];
+          const int nk = min(kCB, p - j0);
+          df64 x[kCB];
+#pragma unroll
+          for (int i = 0; i < kCB; ++i) x[i] = i < nk ? G[(j0 + i) * kWL + b] : df64{0.f, 0.f};
+#pragma unroll
+          for (int i = 0; i < kCB; ++i) {
+#pragma unroll
+            for (int k = 0; k < i; ++k) x[i] = df_fms(x[i], blk[k * kCB + i], x[k]);
+            x[i] = sDrop[jp & 1][i] ? df64{0.f, 0.f} : df_mul(x[i], blk[kCB * kCB + i]);   // dropped: 0, NaN or not
+          }
+          *reinterpret_cast<float4*>(Rpb + b * kCB) = make_float4(x[0].hi, x[0].lo, x[1].hi, x[1].lo);
+          *reinterpret_cast<float4*>(Rpb + b * kCB + 2) = make_float4(x[2].hi, x[2].lo, x[3].hi, x[3].lo);
+#pragma unroll
+          for (int i = 0; i < kCB; ++i)
+            if (i < nk) Rout[(j0 + i) * kWL + b] = x[i].hi;
+        }
+      }
+      named_bar_sync(kBarPanelReady, kChU);          // the panel's rows of R are in Rp
       const int a0 = j1 <= grp ? grp : grp + (j1 - grp + kChG - 1) / kChG * kChG;   // first row >= j1
       const bool onA = colA < p && a0 <= colA, onB = colB < p && a0 <= colB;
       df64 yA[kCB], yB[kCB];
