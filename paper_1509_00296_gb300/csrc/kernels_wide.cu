@@ -1344,14 +1344,18 @@ k_wd_apply(const float* in, int64_t ldi, int64_t len, const float* __restrict__ 
 // of Rf (columns of X), K = 128 in 4 chunks of 32; 3xTF32 as Z_hi Rf_hi + Z_lo Rf_hi + Z_hi Rf_lo
 // (Z_lo, Rf_lo precomputed).  Persistent CTAs walk the tiles; the accumulator is double
 // buffered in tensor memory so the epilogue of one tile overlaps the MMAs of the next.
-// Epilogue: 8 warps, two per lane quarter (columns 0-127 / 128-255 of the tile); a thread owns
-// row 32 q + L and reads O, S, A directly (16 consecutive columns per tcgen05.ld).
+// Epilogue: 8 warps, two per lane quarter (columns 0-127 / 128-255 of the tile).  A warp reads
+// its 32 rows x 32 columns of X from tensor memory (one row per lane), stages them through shared
+// memory and reads them back transposed, so that every global load of O, S, A and every store of
+// S', A' (and L) covers four rows x 128 contiguous bytes per warp instruction.
 constexpr int kEStages = 2;
 constexpr int kEW = 8;                                   // epilogue warps
 constexpr int kEThr = 64 + 32 * kEW;
 constexpr uint32_t kEZ = 128 * kWK * 4;                  // 16 KB
 constexpr uint32_t kER = kWN * kWK * 4;                  // 32 KB
 constexpr uint32_t kEStage = 2 * kEZ + 2 * kER;          // 96 KB
+constexpr int kEXs = 33;                                  // staged X chunk row stride (floats)
+constexpr uint32_t kESmem = kEStages * kEStage + kEW * 32 * kEXs * 4;   // + 8 x 4.2 KB for the transpose
 
 template <bool ALM>
 __global__ void __launch_bounds__(kEThr, 1)
@@ -1452,94 +1456,108 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
       thr = static_cast<float>(dst->lambda / mu);
       ratio = static_cast<float>(mu / mu_next);
     }
+    float* sX = reinterpret_cast<float*>(dsm + kEStages * kEStage) + (warp - 2) * (32 * kEXs);
+    const int rr = lane >> 3, c4 = 4 * (lane & 7);      // transposed read: row group, column quad
     for (int k = 0; k < mine; ++k) {
       const int buf = k & 1;
       const int tl = static_cast<int>(blockIdx.x) + k * static_cast<int>(gridDim.x);
       const int tr = tl / ntc, tc = tl % ntc;
       if (ok && !mbar_wait(&acc_full[buf], static_cast<uint32_t>(k / 2) & 1u)) flag_timeout(ok, dst);
       tc_fence_after();
-      const int64_t row = 128 * static_cast<int64_t>(tr) + 32 * q + lane;
-      for (int cg = 0; cg < 8; ++cg) {
-        float x[16];
-        const int colt = 128 * half + 16 * cg;
-        tmem_ld16(tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(buf * kWN + colt), x);
+      const int64_t rbase = 128 * static_cast<int64_t>(tr) + 32 * q;   // the warp's 32 rows
+      for (int cg = 0; cg < 4; ++cg) {
+        const int colt = 128 * half + 32 * cg;
+        {                                              // the 32 x 32 chunk of X, staged row-major
+          float x[16];
+          const uint32_t ta = tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(buf * kWN + colt);
+          tmem_ld16(ta, x);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sX[lane * kEXs + j] = x[j];
+          tmem_ld16(ta + 16, x);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sX[lane * kEXs + 16 + j] = x[j];
+        }
+        __syncwarp();
         const int64_t col0 = static_cast<int64_t>(kWN) * tc + colt;
-        if (row >= m || col0 >= n || !ok) continue;
-        const bool full16 = col0 + 16 <= n;
-        if (!ALM) {
-          if (full16) {
-            float4* o4 = reinterpret_cast<float4*>(L + row * ldl + col0);
+        if (ok && rbase < m && col0 < n) {
+          // lane (rr, c4) takes rows 4 i + rr, columns c4 .. c4 + 3: every load and store below
+          // covers four rows x 128 contiguous bytes per warp
+          const int64_t colg = col0 + c4;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) o4[u] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
-          } else {
-            for (int u = 0; u < 16; ++u)
-              if (col0 + u < n) L[row * ldl + col0 + u] = x[u];
-          }
-          continue;
-        }
-        float ov[16], sv[16], av[16];
-        if (full16) {
-          const float4* O4 = reinterpret_cast<const float4*>(O + row * ld + col0);
-          const float4* S4 = reinterpret_cast<const float4*>(S + row * ld + col0);
-          const float4* A4 = reinterpret_cast<const float4*>(A + row * ld + col0);
+          for (int i0 = 0; i0 < 8; i0 += 4) {
+            float ov[4][4], sv[4][4], av[4][4];
+            bool full[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 o = __ldcs(O4 + u), s = __ldcs(S4 + u), a = __ldcs(A4 + u);
-            ov[4 * u] = o.x; ov[4 * u + 1] = o.y; ov[4 * u + 2] = o.z; ov[4 * u + 3] = o.w;
-            sv[4 * u] = s.x; sv[4 * u + 1] = s.y; sv[4 * u + 2] = s.z; sv[4 * u + 3] = s.w;
-            av[4 * u] = a.x; av[4 * u + 1] = a.y; av[4 * u + 2] = a.z; av[4 * u + 3] = a.w;
-          }
-        } else {
+            for (int ii = 0; ii < 4; ++ii) {
+              const int64_t rowg = rbase + 4 * (i0 + ii) + rr;
+              full[ii] = rowg < m && colg + 4 <= n;
+              if (!ALM) continue;
+              if (full[ii]) {
+                const float4 o = __ldcs(reinterpret_cast<const float4*>(O + rowg * ld + colg));
+                const float4 s4 = __ldcs(reinterpret_cast<const float4*>(S + rowg * ld + colg));
+                const float4 a = __ldcs(reinterpret_cast<const float4*>(A + rowg * ld + colg));
+                ov[ii][0] = o.x; ov[ii][1] = o.y; ov[ii][2] = o.z; ov[ii][3] = o.w;
+                sv[ii][0] = s4.x; sv[ii][1] = s4.y; sv[ii][2] = s4.z; sv[ii][3] = s4.w;
+                av[ii][0] = a.x; av[ii][1] = a.y; av[ii][2] = a.z; av[ii][3] = a.w;
+              } else {
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const bool in = col0 + u < n;
-            ov[u] = in ? O[row * ld + col0 + u] : 0.f;
-            sv[u] = in ? S[row * ld + col0 + u] : 0.f;
-            av[u] = in ? A[row * ld + col0 + u] : 0.f;
-          }
-        }
-        float sn[16], an[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const float t = av[u] + sv[u] - x[u];                        // O - L + Y / mu
-          sn[u] = (t > thr) ? (t - thr) : ((t < -thr) ? (t + thr) : 0.f);
-          an[u] = ov[u] - sn[u] + ratio * (t - sn[u]);                  // O - S' + Y' / mu'
-          const float rz = ov[u] - x[u] - sn[u];                        // O - L - S'
-          if (col0 + u < n) res2 = fmaf(rz, rz, res2);
-        }
-        if (full16) {
-          float4* S4 = reinterpret_cast<float4*>(S + row * ld + col0);
-          float4* A4 = reinterpret_cast<float4*>(A + row * ld + col0);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            __stcs(S4 + u, make_float4(sn[4 * u], sn[4 * u + 1], sn[4 * u + 2], sn[4 * u + 3]));
-            __stcs(A4 + u, make_float4(an[4 * u], an[4 * u + 1], an[4 * u + 2], an[4 * u + 3]));
-          }
-          if (L != nullptr) {
-            float4* L4 = reinterpret_cast<float4*>(L + row * ldl + col0);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) L4[u] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
-          }
-          if (Ab != nullptr) {                                          // BF16 shadow of A' (two 16-byte stores)
-            uint32_t pk[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const __nv_bfloat162 b2 = __floats2bfloat162_rn(an[2 * u], an[2 * u + 1]);
-              pk[u] = *reinterpret_cast<const uint32_t*>(&b2);
+                for (int e = 0; e < 4; ++e) {
+                  const bool in = rowg < m && colg + e < n;
+                  ov[ii][e] = in ? O[rowg * ld + colg + e] : 0.f;
+                  sv[ii][e] = in ? S[rowg * ld + colg + e] : 0.f;
+                  av[ii][e] = in ? A[rowg * ld + colg + e] : 0.f;
+                }
+              }
             }
-            uint4* ab = reinterpret_cast<uint4*>(Ab + row * ldb + col0);
-            __stcs(ab, make_uint4(pk[0], pk[1], pk[2], pk[3]));
-            __stcs(ab + 1, make_uint4(pk[4], pk[5], pk[6], pk[7]));
-          }
-        } else {
-          for (int u = 0; u < 16; ++u)
-            if (col0 + u < n) {
-              S[row * ld + col0 + u] = sn[u];
-              A[row * ld + col0 + u] = an[u];
-              if (L != nullptr) L[row * ldl + col0 + u] = x[u];
-              if (Ab != nullptr) Ab[row * ldb + col0 + u] = __float2bfloat16_rn(an[u]);
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) {
+              const int r = 4 * (i0 + ii) + rr;
+              const int64_t rowg = rbase + r;
+              float xv[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) xv[e] = sX[r * kEXs + c4 + e];
+              if (!ALM) {
+                if (full[ii]) {
+                  *reinterpret_cast<float4*>(L + rowg * ldl + colg) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+                } else {
+                  for (int e = 0; e < 4; ++e)
+                    if (rowg < m && colg + e < n) L[rowg * ldl + colg + e] = xv[e];
+                }
+                continue;
+              }
+              float sn[4], an[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float t = av[ii][e] + sv[ii][e] - xv[e];                  // O - L + Y / mu
+                sn[e] = (t > thr) ? (t - thr) : ((t < -thr) ? (t + thr) : 0.f);
+                an[e] = ov[ii][e] - sn[e] + ratio * (t - sn[e]);                // O - S' + Y' / mu'
+                const float rz = ov[ii][e] - xv[e] - sn[e];                     // O - L - S'
+                if (rowg < m && colg + e < n) res2 = fmaf(rz, rz, res2);
+              }
+              if (full[ii]) {
+                __stcs(reinterpret_cast<float4*>(S + rowg * ld + colg), make_float4(sn[0], sn[1], sn[2], sn[3]));
+                __stcs(reinterpret_cast<float4*>(A + rowg * ld + colg), make_float4(an[0], an[1], an[2], an[3]));
+                if (L != nullptr)
+                  *reinterpret_cast<float4*>(L + rowg * ldl + colg) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+                if (Ab != nullptr) {                                            // BF16 shadow of A'
+                  const __nv_bfloat162 b0 = __floats2bfloat162_rn(an[0], an[1]);
+                  const __nv_bfloat162 b1 = __floats2bfloat162_rn(an[2], an[3]);
+                  __stcs(reinterpret_cast<uint2*>(Ab + rowg * ldb + colg),
+                         make_uint2(*reinterpret_cast<const uint32_t*>(&b0), *reinterpret_cast<const uint32_t*>(&b1)));
+                }
+              } else {
+                for (int e = 0; e < 4; ++e)
+                  if (rowg < m && colg + e < n) {
+                    S[rowg * ld + colg + e] = sn[e];
+                    A[rowg * ld + colg + e] = an[e];
+                    if (L != nullptr) L[rowg * ldl + colg + e] = xv[e];
+                    if (Ab != nullptr) Ab[rowg * ldb + colg + e] = __float2bfloat16_rn(an[e]);
+                  }
+              }
             }
+          }
         }
+        __syncwarp();                                  // sX is rewritten by the next chunk
       }
       tc_fence_before();
       __syncwarp();
@@ -1595,8 +1613,8 @@ cudaError_t prepare_wide_kernels() {
   if (e == cudaSuccess) e = set_dyn(k_wd_core, kTSmem);
   if (e == cudaSuccess) e = set_dyn(k_wd_apply, sizeof(float) * kWL * (kWL + kACols));
   if (e == cudaSuccess) e = set_dyn(k_wd_trsm, sizeof(float) * kWL * (kTS + kTX));
-  if (e == cudaSuccess) e = set_dyn(k_wd_alm<true>, kEStages * kEStage);
-  if (e == cudaSuccess) e = set_dyn(k_wd_alm<false>, kEStages * kEStage);
+  if (e == cudaSuccess) e = set_dyn(k_wd_alm<true>, kESmem);
+  if (e == cudaSuccess) e = set_dyn(k_wd_alm<false>, kESmem);
   return e;
 }
 
@@ -1706,7 +1724,7 @@ cudaError_t launch_wd_alm(bool alm, const CUtensorMap& tmZ, const CUtensorMap& t
                           const CUtensorMap& tmRl, int64_t m, int64_t n, const float* O, float* S, float* A, int64_t ld,
                           float* L, int64_t ldl, DevState* dst, double* cpart, unsigned* ticket, int grid,
                           void* Ab, int64_t ldb, cudaStream_t st) {
-  const size_t smem = kEStages * kEStage;
+  const size_t smem = kESmem;
   __nv_bfloat16* ab = static_cast<__nv_bfloat16*>(Ab);
   if (alm)
     k_wd_alm<true><<<grid, kEThr, smem, st>>>(tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, dst, cpart, ticket, ab,
