@@ -496,7 +496,7 @@ def run_extras(args, h, O, S, A, O_np, lam, dev, stream, flush):
     out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                            "sample": f"{args.oracle_iters} iALM-FRSVT iterations of the full 8192x8192 workload "
                                      f"({dt:.1f} s), FP64 numpy oracle"}
-    out["recovery_8192_precisions"] = bench_recovery(args, O, lam, dev, flush)
+    out["recovery_8192_variants"] = bench_recovery(args, O, lam, dev, flush)
     out["video"] = bench_video(args, dev, flush)
     out["wsvt_batch"] = bench_wsvt(dev)
     out["unrolled_rpca"] = bench_unrolled(dev)
@@ -717,16 +717,20 @@ def bench_weather():
 
 def bench_recovery(args, O, lam, dev, flush):
     """The headline workload in the BF16-shadow and FP8-shadow (E4M3, per-128 x 128-tile power-of-two
-    scales) modes: sketch and first power step on the shadow, FP32-accurate last power step and
-    projection.  Iterations per second from a captured graph and per-phase device times."""
+    scales) modes (sketch and first power step on the shadow, FP32-accurate last power step and
+    projection), and at FP32 with range propagation (Alg. 1 steps 8-11) or with the intermediate
+    power step left unnormalised (Sec. 2.5).  Iterations per second from a captured graph and
+    per-phase device times (the "orth" phase shows the Cholesky QR each variant saves or keeps)."""
     import torch
     from paper_1509_00296_gb300 import frsvt
     out = {"workload": RWORKLOAD, "unit": UNIT, "hbm_floor_ms_fp32": 11 * 4.0 * RN * RN / (peaks()[0] * 1e9) * 1e3}
     S = torch.empty_like(O)
     A = torch.empty_like(O)
-    for name, prec in (("bf16", frsvt.PREC_BF16), ("fp8", frsvt.PREC_FP8)):
-        h = frsvt.Handle(RN, RN, RL, q=RQ, range_prop=False, seed=ROMEGA_SEED, stream=torch.cuda.current_stream(),
-                         precision=prec)
+    variants = (("bf16", frsvt.PREC_BF16, False, False), ("fp8", frsvt.PREC_FP8, False, False),
+                ("fp32_range_prop", frsvt.PREC_FP32, True, False), ("fp32_orth_last", frsvt.PREC_FP32, False, True))
+    for name, prec, rp, ol in variants:
+        h = frsvt.Handle(RN, RN, RL, q=RQ, range_prop=rp, seed=ROMEGA_SEED, stream=torch.cuda.current_stream(),
+                         precision=prec, orth_last=ol)
         h.rpca_init(O, S, A, lam, 1.5, 1e7)
         for _ in range(3):
             h.ialm_step(O, S, A, RL)
@@ -744,6 +748,8 @@ def bench_recovery(args, O, lam, dev, flush):
                      "phases_ms_per_step": {k: v[0] / K for k, v in tm.items() if v[1] > 0},
                      "launch_groups_per_step": sum(v[1] for v in tm.values()) / K, "jacobi_sweeps": info.sweeps,
                      "rank": info.r, "basis": info.s, "device_status": info.device_status}
+        if rp:
+            out[name]["propagated_columns"] = info.keep
         h.close()
     return out
 

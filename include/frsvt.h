@@ -76,8 +76,8 @@ typedef enum frsvt_precision {
 #define FRSVT_CFG_ORTH_LAST 2    /* orthonormalise only after the last power step (Sec. 2.5): the
                                     intermediate steps of Alg. 1 step 14 pass A A^T Q on unnormalised.
                                     X is the same in exact arithmetic (only span(Q) enters it); honoured
-                                    by the FP32 tensor-core path of the narrow basis, the other paths
-                                    orthonormalise every step. */
+                                    by the wide basis and by the FP32 tensor-core path of the narrow
+                                    basis, the other paths orthonormalise every step. */
 
 typedef struct frsvt_config {
   int64_t m_max;                 /* largest row count served by the handle */
@@ -119,9 +119,11 @@ typedef struct frsvt_handle frsvt_handle;
  * cfg.l_max <= 32 builds the narrow-basis handle (16- or 32-column panels);
  * 32 < cfg.l_max <= 128 the wide-basis handle (128-column panels, any short
  * side, grid-wide Cholesky QR and core), which serves frsvt_svt,
- * frsvt_spectral_norm, rpca_init and rpca_ialm_step; for it range_prop,
- * FRSVT_CFG_ADJOINT and m_max >= 2^31 return FRSVT_ERR_UNSUPPORTED, and the
- * batched WSVT and debug entry points return FRSVT_ERR_UNSUPPORTED.
+ * frsvt_svt_factors, frsvt_spectral_norm, rpca_init and rpca_ialm_step, with
+ * range propagation and FRSVT_CFG_ORTH_LAST; for it FRSVT_CFG_ADJOINT and
+ * m_max >= 2^31 return FRSVT_ERR_UNSUPPORTED, and the batched WSVT and debug
+ * entry points return FRSVT_ERR_UNSUPPORTED.  The wide handle computes no
+ * Prop. 4 residual (frsvt_info.rp_residual stays -1).
  * Returns FRSVT_ERR_INVALID_ARG for out-of-range sizes, FRSVT_ERR_ALLOC if
  * the device allocation fails.
  */

@@ -120,6 +120,9 @@ int wide_tile();
 cudaError_t prepare_wide_kernels();
 int wide_gram_grid();
 int wide_gram_count();
+cudaError_t launch_wd_rp_insert(float* YT, const float* QtT, int64_t ld, int64_t ns, int l, const DevState* dst,
+                               cudaStream_t st);
+cudaError_t launch_wd_identity(float* T, cudaStream_t st);
 int wide_splits(int64_t nlong, int64_t nk, int sms);
 cudaError_t launch_wd_omega(float* OT, float* OTl, void* OTb, void* OTbl, int64_t ldo, int64_t m, int l, int use_rp,
                             uint64_t seed, uint64_t ctr, const DevState* dst, cudaStream_t st);
@@ -241,7 +244,7 @@ struct frsvt_handle {
   int64_t w_ldl = 0, w_lds = 0, w_ldp = 0;      // long-side / short-side / partial row strides
   float *wOT = nullptr, *wOTl = nullptr, *wZT = nullptr, *wZTl = nullptr, *wZ = nullptr, *wZl = nullptr;
   float *wYT = nullptr, *wQT = nullptr, *wQTl = nullptr, *wQp = nullptr, *wRf = nullptr, *wRfl = nullptr;
-  float *wT1 = nullptr, *wT2 = nullptr, *wpart = nullptr;
+  float *wT1 = nullptr, *wT2 = nullptr, *wI = nullptr, *wpart = nullptr;
   void *wOTb = nullptr, *wOTbl = nullptr, *wZTb = nullptr, *wZTbl = nullptr, *wQTb = nullptr, *wQTbl = nullptr;
   void* A8 = nullptr;              // E4M3 shadow of A (FRSVT_PREC_FP8), row stride ld8 bytes
   float* w8s = nullptr;            // its per-128 x 128-tile scales
@@ -605,7 +608,7 @@ void free_all(frsvt_handle* h) {
                   h->rpart, h->pmax,   h->psum,     h->cpart_sc,  h->cpart_lr, h->cpart_alm, h->Gfin, h->rsum,
                   h->tickets, h->wsvt_next, h->ad_ws, h->Ab,
                   h->wOT, h->wOTl, h->wZT, h->wZTl, h->wZ, h->wZl, h->wYT, h->wQT, h->wQTl, h->wQp, h->wRf,
-                  h->wRfl, h->wT1, h->wT2, h->wpart, h->wgc, h->wGpk, h->wac, h->wtick,
+                  h->wRfl, h->wT1, h->wT2, h->wI, h->wpart, h->wgc, h->wGpk, h->wac, h->wtick,
                   h->wOTb, h->wOTbl, h->wZTb, h->wZTbl, h->wQTb, h->wQTbl, h->A8, h->w8s};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -646,8 +649,11 @@ int wide_lowp(const frsvt_handle* h) { return h->A8 != nullptr ? 2 : (h->Ab != n
 // Reduced precision (lowp, see wide_lowp): the sketch and the first q - 1 power steps
 // read the shadow with BF16 copies of the narrow factors; the last power step and the projection
 // stay FP32-accurate.
+// use_rp: range propagation (Alg. 1 steps 8-11): the sketch takes l - keep new columns and the
+// propagated basis Q~ of the previous call (wQp, Q~^T), and the core leaves the next Q~.
 frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int l, int q,
-                                 uint64_t ctr, float tau_host, int tau_from_mu, int advance_counter, int lowp = 0) {
+                                 uint64_t ctr, float tau_host, int tau_from_mu, int advance_counter, int lowp = 0,
+                                 int use_rp = 0) {
   cudaStream_t st = h->stream;
   const int64_t LW = wide_lp();
   const bool tall = m >= n;
@@ -691,7 +697,7 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
   const CUtensorMap& tmLb = short_col ? tmBr : tmBc;
   const int Ss = wide_splits(ns, nl, h->sms), Sl = wide_splits(nl, ns, h->sms);
   FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_omega(h->wOT, h->wOTl, bf ? h->wOTb : nullptr, bf ? h->wOTbl : nullptr,
-                                                   ldl, nl, l, 0, h->cfg.seed, ctr, h->dst, st));
+                                                   ldl, nl, l, use_rp, h->cfg.seed, ctr, h->dst, st));
   if (bf)
     FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(short_col, lowp, tmSb, tmOTb, tmOTbl, ns, nl, Ss, h->wpart,
                                                     h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr, lds, nullptr,
@@ -700,8 +706,10 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
     FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(short_col, 0, tmS, tmOT, tmOTl, ns, nl, Ss, h->wpart, h->w_ldp,
                                                     h->wtick, h->wYT, nullptr, nullptr, nullptr, lds, nullptr,
                                                     nullptr, h->dst, st));
+  if (use_rp) FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_rp_insert(h->wYT, h->wQp, lds, ns, l, h->dst, st));
   frsvt_status s = wide_orth(h, ns, l, q == 0 ? 2 : 1, bf && q > 1);
   if (s != FRSVT_OK) return s;
+  const bool orth_last = (h->cfg.flags & FRSVT_CFG_ORTH_LAST) != 0;
   for (int it = 0; it < q; ++it) {
     if (bf && it < q - 1) {
       FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(!short_col, lowp, tmLb, tmQTb, tmQTbl, nl, ns, Sl, h->wpart,
@@ -718,6 +726,14 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
                                                          h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr, lds,
                                                          nullptr, nullptr, h->dst, st));
     }
+    if (orth_last && it < q - 1) {
+      // Sec. 2.5: the intermediate power step passes Y = A A^T Q on unnormalised (same span): Q = Y,
+      // split into its TF32 parts (and BF16 copies) by the substitution kernel with T = I
+      const bool bfn = bf && it + 1 < q - 1;
+      FRSVT_LAUNCH(FRSVT_PHASE_APPLY, launch_wd_trsm(h->wYT, lds, ns, h->wI, h->wQT, h->wQTl, bfn ? h->wQTb : nullptr,
+                                                    bfn ? h->wQTbl : nullptr, lds, st));
+      continue;
+    }
     if ((s = wide_orth(h, ns, l, it == q - 1 ? 2 : 1, bf && it + 1 < q - 1)) != FRSVT_OK) return s;
   }
   // projection B^T = Z (step 16), then B B^T = Z^T Z and the core (steps 16-19)
@@ -725,11 +741,14 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
                                                    h->wtick, h->wZT, nullptr, nullptr, nullptr, ldl, h->wZ, h->wZl,
                                                    h->dst, st));
   FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_wd_gram(true, h->wZT, ldl, nl, h->w_gram_grid, h->wgc, h->wGpk,
-                                                l, h->cfg.rank_tol, l, tau_host, tau_from_mu, 0,
+                                                l, h->cfg.rank_tol, l, tau_host, tau_from_mu, use_rp,
                                                 advance_counter, h->cfg.max_jacobi_sweeps, h->wT1, h->wT2, h->dst,
                                                 st));
   FRSVT_LAUNCH(FRSVT_PHASE_APPLY, launch_wd_apply(h->wQT, lds, ns, h->wT1, nullptr, nullptr, 0, h->wRf, h->wRfl,
                                                  st));
+  if (use_rp)                                    // step 21: Q~ = Q U_B[:, :keep], kept as Q~^T
+    FRSVT_LAUNCH(FRSVT_PHASE_APPLY, launch_wd_apply(h->wQT, lds, ns, h->wT2, h->wQp, nullptr, lds, nullptr, nullptr,
+                                                   st));
   return FRSVT_OK;
 }
 
@@ -788,6 +807,7 @@ bool wide_alloc(frsvt_handle* h) {
   alloc(reinterpret_cast<void**>(&h->wRfl), fn);
   alloc(reinterpret_cast<void**>(&h->wT1), sizeof(float) * LW * LW);
   alloc(reinterpret_cast<void**>(&h->wT2), sizeof(float) * LW * LW);
+  alloc(reinterpret_cast<void**>(&h->wI), sizeof(float) * LW * LW);
   alloc(reinterpret_cast<void**>(&h->wpart), sizeof(float) * 8 * LW * h->w_ldp);
   alloc(reinterpret_cast<void**>(&h->wgc), sizeof(double) * h->w_gram_grid * wide_gram_count());
   alloc(reinterpret_cast<void**>(&h->wGpk), sizeof(double) * wide_gram_count());
@@ -816,7 +836,8 @@ bool wide_alloc(frsvt_handle* h) {
   }
   if (!ok) return false;
   return cudaMemsetAsync(h->wtick, 0, sizeof(unsigned) * (h->w_ntiles + 2), h->stream) == cudaSuccess &&
-         cudaMemsetAsync(h->wT2, 0, sizeof(float) * LW * LW, h->stream) == cudaSuccess;
+         cudaMemsetAsync(h->wT2, 0, sizeof(float) * LW * LW, h->stream) == cudaSuccess &&
+         launch_wd_identity(h->wI, h->stream) == cudaSuccess;
 }
 
 // Adjoint workspace (floats): L (m x K), R (n x K), P, T, Z (m x LP each), Yb, Y, RQ (n x LP
@@ -933,8 +954,7 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   h->wide = cfg->l_max > 32;
   h->LP = cfg->l_max <= 16 ? 16 : (cfg->l_max <= 32 ? 32 : wide_lp());
   const int64_t nsmax = cfg->n_max < cfg->m_max ? cfg->n_max : cfg->m_max;
-  if (h->wide ? (cfg->range_prop || (cfg->flags & FRSVT_CFG_ADJOINT) ||
-                 cfg->m_max >= (int64_t(1) << 31))
+  if (h->wide ? ((cfg->flags & FRSVT_CFG_ADJOINT) || cfg->m_max >= (int64_t(1) << 31))
               : nsmax > ns_limit(h->LP)) {
     delete h;
     return FRSVT_ERR_UNSUPPORTED;
@@ -1118,7 +1138,8 @@ static frsvt_status svt_range_and_core(frsvt_handle* h, const float* A, int64_t 
   if ((s = sync_rp_shape(h, m, n, l)) != FRSVT_OK) return s;
   if (h->wide) {
     if (h->Ab != nullptr) FRSVT_CK(launch_to_bf16(A, lda, m, n, h->Ab, h->ldb, h->stream));
-    return wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1, wide_lowp(h));
+    return wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1, wide_lowp(h),
+                               h->cfg.range_prop ? 1 : 0);
   }
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;
@@ -1245,7 +1266,7 @@ static frsvt_status ialm_launches(frsvt_handle* h, const frsvt_handle::StepKey& 
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;   // the shadow is kept current by rpca_init / the epilogue
   if (h->wide) {
-    if ((s = wide_range_and_core(h, A, m, n, ld, l, h->cfg.q, kCounterFromState, 0.f, 1, 1, wide_lowp(h))) !=
+    if ((s = wide_range_and_core(h, A, m, n, ld, l, h->cfg.q, kCounterFromState, 0.f, 1, 1, wide_lowp(h), rp)) !=
         FRSVT_OK)
       return s;
     if ((s = wide_epilogue(h, true, m, n, O, S, A, ld, L, ldl)) != FRSVT_OK) return s;

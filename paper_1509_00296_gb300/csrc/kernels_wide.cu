@@ -116,6 +116,31 @@ __global__ void k_wd_omega(float* __restrict__ OT, float* __restrict__ OTl, __nv
   }
 }
 
+// ---------------------------------------------------------------- range propagation
+// Alg. 1 steps 8-11 on the wide basis: the sketch Y^T = Omega_p^T A filled rows 0 .. p - 1
+// (p = l - keep, Omega_p the first p columns of the stream's Omega); rows p .. l - 1 take the
+// propagated basis Q~^T (rows 0 .. keep - 1 of QtT, keep from the device state).  The span of
+// [Y_p, Q~] is that of the paper's [Q~, Y_p orthogonalised against Q~], which the Cholesky QR
+// that follows makes orthonormal.
+__global__ void k_wd_rp_insert(float* __restrict__ YT, const float* __restrict__ QtT, int64_t ld, int64_t ns, int l,
+                               const DevState* __restrict__ dst) {
+  const int keep = max(0, min(dst->keep, l));
+  if (keep == 0) return;
+  const int p = l - keep;
+  const int64_t total = static_cast<int64_t>(keep) * ns;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t j = e / ns, x = e % ns;
+    YT[(p + j) * ld + x] = QtT[j * ld + x];
+  }
+}
+
+// T = the identity (the triangular operand of k_wd_trsm for Q = Y, the unnormalised power steps).
+__global__ void k_wd_identity(float* __restrict__ T) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kWL * kWL; e += gridDim.x * blockDim.x)
+    T[e] = (e / kWL == e % kWL) ? 1.f : 0.f;
+}
+
 // ---------------------------------------------------------------- FP8 shadow of A
 // One CTA per 128 x 128 tile of A: s = the smallest power of two with max|A_tile| / s <= 448 (the
 // E4M3 range), A8 = e4m3(A / s) (round to nearest, saturating), scales[tile] = s.  The tile is
@@ -770,6 +795,11 @@ __device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, dou
     }
   }
   __syncthreads();
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned start, bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // Entry e of the packed Gram (a df64 pair stored where a double is declared).
@@ -1467,6 +1497,19 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
       const int64_t rbase = 128 * static_cast<int64_t>(tr) + 32 * q;   // the warp's 32 rows
       for (int cg = 0; cg < 4; ++cg) {
         const int colt = 128 * half + 32 * cg;
+        if (ALM) {                                     // the next chunk's rows of O, S, A into L2
+          const bool same = cg < 3;
+          const int tn = tl + static_cast<int>(gridDim.x);
+          const int64_t prow = same ? rbase + lane : 128 * static_cast<int64_t>(tn / ntc) + 32 * q + lane;
+          const int64_t pcol = same ? static_cast<int64_t>(kWN) * tc + colt + 32
+                                    : static_cast<int64_t>(kWN) * (tn % ntc) + 128 * half;
+          if ((same || k + 1 < mine) && prow < m && pcol < n) {
+            const uint32_t bytes = static_cast<uint32_t>(imin64(128, ((n - pcol) * 4 + 15) / 16 * 16));
+            prefetch_l2_bulk(O + prow * ld + pcol, bytes);
+            prefetch_l2_bulk(S + prow * ld + pcol, bytes);
+            prefetch_l2_bulk(A + prow * ld + pcol, bytes);
+          }
+        }
         {                                              // the 32 x 32 chunk of X, staged row-major
           float x[16];
           const uint32_t ta = tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(buf * kWN + colt);
@@ -1707,6 +1750,21 @@ cudaError_t launch_wd_quant8(const float* A, int64_t lda, int64_t m, int64_t n, 
   const int ntr = static_cast<int>((m + kQT - 1) / kQT), ntc = static_cast<int>((n + kQT - 1) / kQT);
   if (ntr == 0 || ntc == 0) return cudaSuccess;
   k_wd_quant8<<<ntr * ntc, kQThr, 0, st>>>(A, lda, m, n, static_cast<uint8_t*>(A8), ld8, scales, ntc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wd_rp_insert(float* YT, const float* QtT, int64_t ld, int64_t ns, int l, const DevState* dst,
+                               cudaStream_t st) {
+  const int64_t total = static_cast<int64_t>(l) * ns;
+  int64_t grid = (total + 255) / 256;
+  if (grid > 1024) grid = 1024;
+  if (grid == 0) return cudaSuccess;
+  k_wd_rp_insert<<<static_cast<int>(grid), 256, 0, st>>>(YT, QtT, ld, ns, l, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wd_identity(float* T, cudaStream_t st) {
+  k_wd_identity<<<16, 256, 0, st>>>(T);
   return cudaGetLastError();
 }
 

@@ -52,7 +52,7 @@ def test_invalid_arguments_rejected_on_host(libpath):
     assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
     bad = frsvt.Config(10, 10, 129, 1, 1, 0, 0, 30, 0, 1e-10)        # l_max > 128
     assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
-    bad = frsvt.Config(10, 10, 33, 1, 1, 0, 0, 30, 0, 1e-10)         # wide basis with range propagation
+    bad = frsvt.Config(10, 10, 33, 1, 0, 0, 0, 30, 1, 1e-10)         # wide basis with the adjoint workspace
     assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 2
     bad = frsvt.Config(10, 10, 8, 1, 1, 7, 0, 30, 0, 1e-10)          # unknown precision
     assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 2

@@ -167,6 +167,80 @@ def test_wide_recovery_8192_full_size(fr, recovery_ref, prec):
     assert np.allclose(hist, ref.history, rtol=1e-3 if prec != "fp8" else 1e-2)
 
 
+@pytest.mark.parametrize("variant", ["range_prop", "orth_last"])
+def test_wide_recovery_8192_variants(fr, recovery_ref, variant):
+    """The large low-rank recovery with range propagation (Alg. 1 steps 8-11: each iteration
+    sketches l - keep new columns next to the previous iteration's Q~) or with the intermediate
+    power step left unnormalised (Sec. 2.5): three iALM iterations at full size against the oracle
+    running the same variant."""
+    import torch
+    O, nrm, _ = recovery_ref
+    m, n = O.shape
+    rp, ol = variant == "range_prop", variant == "orth_last"
+    ref = orpca.ialm_rpca(O, method="frsvt", l=120, q=2, seed=2004, range_prop=rp, orth_last=ol, fixed_iters=3,
+                          normO2=nrm)
+    Og = torch.from_numpy(np.ascontiguousarray(O, dtype=np.float32)).cuda()
+    S, A, L = torch.empty_like(Og), torch.empty_like(Og), torch.empty_like(Og)
+    h = fr.Handle(m, n, 120, q=2, range_prop=rp, seed=2004, orth_last=ol)
+    h.rpca_init(Og, S, A, 1.0 / np.sqrt(max(m, n)), 1.5, 1e7, normO2=nrm)
+    hist = [h.ialm_step(Og, S, A, 120, L=L if k == 2 else None, sync_residual=True) for k in range(3)]
+    info = h.info()
+    h.close()
+    eL = rel_fro(L.cpu().numpy(), ref.L)
+    eS = rel_fro(S.cpu().numpy(), ref.S)
+    print(f"recovery 8192 {variant}: rel err L {eL:.3e} S {eS:.3e}, keep {info.keep}")
+    assert info.device_status == 0, info
+    if rp:
+        assert info.keep == min(info.r, 118) and info.keep > 0
+    assert eL <= TOL
+    assert eS <= TOL
+    assert np.allclose(hist, ref.history, rtol=1e-3)
+
+
+@pytest.mark.parametrize("m,n", [(2048, 1024), (1024, 2048)])
+def test_wide_range_propagation_sequence(fr, m, n):
+    """Range propagation on the wide basis, both orientations: three calls on a slowly moving
+    iterate, each X against the oracle given the previous oracle call's Q~ (keep = min(r, l - 2)
+    columns carried over, on the short side)."""
+    l, q = 64, 1
+    A0, s = spectrum_matrix(m, n, 80, 0.95, 0.001, seed=201)
+    rng = np.random.default_rng(202)
+    D = rng.standard_normal((m, n)) * 0.01
+    tau = float(0.5 * (s[30] + s[31]))
+    h = fr.Handle(max(m, n), max(m, n), l, q=q, range_prop=True, seed=23)
+    Qp = None
+    for t in range(3):
+        A = (A0 + t * D).astype(np.float32).astype(np.float64)
+        ref = osvt.frsvt(A, tau, l, q, seed=23, stream=t, Q_prev=Qp)
+        Qp = ref.Q_tilde
+        X = h.svt(to_gpu(A), tau, l).cpu().numpy()
+        info = h.info()
+        assert info.r == ref.r and info.keep == ref.Q_tilde.shape[1], (t, info.r, ref.r, info.keep)
+        assert info.counter == t + 1
+        assert info.rp_residual == -1.0                 # the wide basis computes no Prop. 4 residual
+        assert rel_fro(X, ref.X) <= TOL, t
+    h.close()
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_wide_orth_last_matches_oracle(fr, q):
+    """FRSVT_CFG_ORTH_LAST on the wide basis: the intermediate power steps are not orthonormalised;
+    X matches the oracle's same variant over a range-propagated sequence of two calls."""
+    m, n, l = 2048, 1024, 64
+    A, s = spectrum_matrix(m, n, 80, 0.95, 0.001, seed=211)
+    A = A.astype(np.float32).astype(np.float64)
+    tau = float(0.5 * (s[20] + s[21]))
+    h = fr.Handle(m, n, l, q=q, range_prop=True, seed=37, orth_last=True)
+    Qp = None
+    for t in range(2):
+        ref = osvt.frsvt(A, tau, l, q, seed=37, stream=t, Q_prev=Qp, orth_last=True)
+        Qp = ref.Q_tilde
+        X = h.svt(to_gpu(A), tau, l).cpu().numpy()
+        assert h.info().r == ref.r, t
+        assert rel_fro(X, ref.X) <= TOL, t
+    h.close()
+
+
 @pytest.mark.parametrize("m,n,l,q", [(2048, 1024, 64, 2), (1500, 700, 120, 2), (1200, 600, 40, 3)])
 def test_wide_bf16_svt_matches_oracle(fr, m, n, l, q):
     """BF16 shadow on the wide basis: X against the oracle's FP32-free Alg. 1 at the 1e-4 bar."""
