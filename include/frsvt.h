@@ -318,6 +318,38 @@ frsvt_status frsvt_svt_noalloc(const float* A, int64_t m, int64_t n, int64_t lda
                                int32_t l, int32_t q, uint64_t seed, uint64_t counter,
                                float* X, int64_t ldx, void* stream);
 
+/*
+ * Low-rank representation (Table 6, Type A; the robust-LRR application of Sec. 4): min ||L||_* + lam ||S||_{2,1}
+ * s.t. O = Z L + S with the dictionary Z = O (d x n), by the inexact ALM with the splitting J = L:
+ * per iteration J = FRSVT_{1/mu}(L + Y2 / mu) (Alg. 1, Omega stream = iteration index, range
+ * propagation across iterations when asked), L = (I + Z^T Z)^{-1} (Z^T (O - S + Y1 / mu) + J -
+ * Y2 / mu), S = the column shrinkage of O - Z L + Y1 / mu by lam / mu (column i scaled by
+ * max(0, 1 - (lam / mu) / ||q_i||)), Y1 += mu (O - Z L - S), Y2 += mu (L - J),
+ * mu = min(rho mu, mu_max).
+ *
+ * frsvt_lrr_create: workspace for d <= d_max, 2 <= n <= n_max (<= 16384), FRSVT rank l
+ *   (1 <= l <= min(128, n_max)) and q power steps; owns an frsvt handle for the n x n J step
+ *   (l > 32: the wide basis).  Allocates all device memory.  stream: a cudaStream_t.
+ * frsvt_lrr_init: O is a caller-owned device matrix (d x n, row-major, ldo >= n) that must stay
+ *   valid while the handle iterates; zeroes L, S, J, Y1, Y2, sets mu = mu0, and forms
+ *   (I + O^T O)^{-1} on the device by Newton-Schulz iterations (synchronizes the stream once).
+ *   Needs lam > 0, mu0 > 0, rho >= 1, mu0 <= mu_max < inf (FRSVT_ERR_INVALID_ARG otherwise).
+ * frsvt_lrr_step: one iteration, enqueued on the stream; with err != NULL it synchronizes and
+ *   writes max(||O - Z L - S||_inf, ||L - J||_inf) (the stopping quantity) to *err (host).
+ * frsvt_lrr_get: copies L (n x n) and S (d x n) into caller-owned device buffers (either may be
+ *   NULL), and the next mu and the iteration count to host pointers (either may be NULL).
+ * Errors of the J step are returned as the frsvt status; frsvt_lrr_last_error explains.
+ */
+typedef struct frsvt_lrr frsvt_lrr;
+frsvt_status frsvt_lrr_create(frsvt_lrr** h, int64_t d_max, int64_t n_max, int32_t l, int32_t q, uint64_t seed,
+                              int32_t range_prop, void* stream);
+frsvt_status frsvt_lrr_destroy(frsvt_lrr* h);
+frsvt_status frsvt_lrr_init(frsvt_lrr* h, const float* O, int64_t d, int64_t n, int64_t ldo, double lam, double mu0,
+                            double rho, double mu_max);
+frsvt_status frsvt_lrr_step(frsvt_lrr* h, double* err);
+frsvt_status frsvt_lrr_get(frsvt_lrr* h, float* L, int64_t ldl, float* S, int64_t lds, double* mu, int32_t* iters);
+const char* frsvt_lrr_last_error(const frsvt_lrr* h);
+
 const char* frsvt_status_string(frsvt_status s);
 const char* frsvt_last_error(const frsvt_handle* h);
 

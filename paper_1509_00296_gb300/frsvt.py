@@ -71,6 +71,14 @@ _SIGS = {
     "frsvt_enable_timing": [_P, ctypes.c_int32],
     "frsvt_get_timings": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
     "frsvt_step_kernels": [_P, ctypes.POINTER(ctypes.c_int32)],
+    "frsvt_lrr_create": [ctypes.POINTER(_P), _I64, _I64, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                         ctypes.c_int32, _P],
+    "frsvt_lrr_destroy": [_P],
+    "frsvt_lrr_init": [_P, _P, _I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                       ctypes.c_double],
+    "frsvt_lrr_step": [_P, ctypes.POINTER(ctypes.c_double)],
+    "frsvt_lrr_get": [_P, _P, _I64, _P, _I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
+    "frsvt_lrr_last_error": [_P],
     "frsvt_phase_name": [ctypes.c_int32],
     "frsvt_svt_save": [_P, _P, _I64, _I64, _I64, ctypes.c_float, ctypes.c_int32, ctypes.c_uint64, _P, _I64, _P],
     "frsvt_backward": [_P, _P, _P, _I64, _I64, _I64, ctypes.c_float, ctypes.c_int32, ctypes.c_uint64, _P, _I64, _P,
@@ -103,7 +111,8 @@ def lib():
         for name, args in _SIGS.items():
             fn = getattr(L, name)
             fn.argtypes = args
-            fn.restype = (ctypes.c_char_p if name in ("frsvt_status_string", "frsvt_last_error", "frsvt_phase_name")
+            fn.restype = (ctypes.c_char_p if name in ("frsvt_status_string", "frsvt_last_error", "frsvt_phase_name",
+                                                      "frsvt_lrr_last_error")
                           else ctypes.c_int)
         L.frsvt_adjoint_saved_bytes.argtypes = [_P, _I64, _I64]
         L.frsvt_adjoint_saved_bytes.restype = ctypes.c_size_t
@@ -481,3 +490,56 @@ def _autograd_function():
 def frsvt_svt_autograd(A, tau, handle, l: int, omega_stream: int = 0):
     """Differentiable X = FRSVT_tau(A): gradients with respect to A and tau by the library's adjoint."""
     return _autograd_function().apply(A, tau, handle, l, omega_stream)
+
+
+class LRR:
+    """Low-rank representation (Table 6, Type A) by the inexact ALM on the GPU, the J step by
+    FRSVT (include/frsvt.h, frsvt_lrr_*).  O: d x n float32 CUDA tensor, kept referenced."""
+
+    def __init__(self, d_max: int, n_max: int, l: int, q: int = 1, seed: int = 0, range_prop: bool = True,
+                 stream=None):
+        h = _P()
+        st = lib().frsvt_lrr_create(ctypes.byref(h), d_max, n_max, l, q, seed, 1 if range_prop else 0,
+                                     _stream_ptr(stream))
+        if st != FRSVT_OK:
+            raise FrsvtError(st, "frsvt_lrr_create failed")
+        self._h = h
+        self._O = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().frsvt_lrr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        if st != FRSVT_OK:
+            raise FrsvtError(st, lib().frsvt_lrr_last_error(self._h).decode())
+
+    def init(self, O, lam: float, mu0: float = 1e-6, rho: float = 1.1, mu_max: float = 1e10):
+        _check_f32_cuda(O, "O")
+        self._O = O
+        d, n = O.shape
+        self._chk(lib().frsvt_lrr_init(self._h, _ptr(O), d, n, O.stride(0), lam, mu0, rho, mu_max))
+
+    def step(self, sync_err: bool = False):
+        """One iteration; with sync_err the max-norm residual (synchronizes)."""
+        e = ctypes.c_double(0.0)
+        self._chk(lib().frsvt_lrr_step(self._h, ctypes.byref(e) if sync_err else None))
+        return e.value if sync_err else None
+
+    def result(self):
+        """(L, S, next mu, iterations) with L and S as new float32 CUDA tensors."""
+        import torch
+        d, n = self._O.shape
+        L = torch.empty((n, n), dtype=torch.float32, device=self._O.device)
+        S = torch.empty((d, n), dtype=torch.float32, device=self._O.device)
+        mu = ctypes.c_double(0.0)
+        it = ctypes.c_int32(0)
+        self._chk(lib().frsvt_lrr_get(self._h, _ptr(L), n, _ptr(S), n, ctypes.byref(mu), ctypes.byref(it)))
+        return L, S, mu.value, it.value
