@@ -76,8 +76,10 @@ typedef enum frsvt_precision {
 #define FRSVT_CFG_ORTH_LAST 2    /* orthonormalise only after the last power step (Sec. 2.5): the
                                     intermediate steps of Alg. 1 step 14 pass A A^T Q on unnormalised.
                                     X is the same in exact arithmetic (only span(Q) enters it); honoured
-                                    by the wide basis and by the FP32 tensor-core path of the narrow
-                                    basis, the other paths orthonormalise every step. */
+                                    by frsvt_svt and rpca_ialm_step on the wide basis and on the FP32
+                                    tensor-core path of the narrow basis (both scale the unnormalised
+                                    step by powers of two, exactly), the other paths orthonormalise
+                                    every step; frsvt_spectral_norm always orthonormalises. */
 
 typedef struct frsvt_config {
   int64_t m_max;                 /* largest row count served by the handle */

@@ -123,6 +123,7 @@ int wide_gram_count();
 cudaError_t launch_wd_rp_insert(float* YT, const float* QtT, int64_t ld, int64_t ns, int l, const DevState* dst,
                                cudaStream_t st);
 cudaError_t launch_wd_identity(float* T, cudaStream_t st);
+cudaError_t launch_wd_colscale(const float* YT, int64_t ld, int64_t ns, float* T, cudaStream_t st);
 int wide_splits(int64_t nlong, int64_t nk, int sms);
 cudaError_t launch_wd_omega(float* OT, float* OTl, void* OTb, void* OTbl, int64_t ldo, int64_t m, int l, int use_rp,
                             uint64_t seed, uint64_t ctr, const DevState* dst, cudaStream_t st);
@@ -244,7 +245,8 @@ struct frsvt_handle {
   int64_t w_ldl = 0, w_lds = 0, w_ldp = 0;      // long-side / short-side / partial row strides
   float *wOT = nullptr, *wOTl = nullptr, *wZT = nullptr, *wZTl = nullptr, *wZ = nullptr, *wZl = nullptr;
   float *wYT = nullptr, *wQT = nullptr, *wQTl = nullptr, *wQp = nullptr, *wRf = nullptr, *wRfl = nullptr;
-  float *wT1 = nullptr, *wT2 = nullptr, *wI = nullptr, *wpart = nullptr;
+  float *wT1 = nullptr, *wT2 = nullptr, *wpart = nullptr;
+  float* wI = nullptr;             // diagonal T of the unnormalised power steps (identity off the diagonal)
   void *wOTb = nullptr, *wOTbl = nullptr, *wZTb = nullptr, *wZTbl = nullptr, *wQTb = nullptr, *wQTbl = nullptr;
   void* A8 = nullptr;              // E4M3 shadow of A (FRSVT_PREC_FP8), row stride ld8 bytes
   float* w8s = nullptr;            // its per-128 x 128-tile scales
@@ -651,9 +653,12 @@ int wide_lowp(const frsvt_handle* h) { return h->A8 != nullptr ? 2 : (h->Ab != n
 // stay FP32-accurate.
 // use_rp: range propagation (Alg. 1 steps 8-11): the sketch takes l - keep new columns and the
 // propagated basis Q~ of the previous call (wQp, Q~^T), and the core leaves the next Q~.
+// orth_last_ok: the SVT calls honour FRSVT_CFG_ORTH_LAST; the spectral-norm estimate (up to 64
+// power steps, whose unnormalised growth sigma_1^(2 q) would overflow FP32) always
+// orthonormalises.
 frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int l, int q,
                                  uint64_t ctr, float tau_host, int tau_from_mu, int advance_counter, int lowp = 0,
-                                 int use_rp = 0) {
+                                 int use_rp = 0, bool orth_last_ok = false) {
   cudaStream_t st = h->stream;
   const int64_t LW = wide_lp();
   const bool tall = m >= n;
@@ -709,7 +714,7 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
   if (use_rp) FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_rp_insert(h->wYT, h->wQp, lds, ns, l, h->dst, st));
   frsvt_status s = wide_orth(h, ns, l, q == 0 ? 2 : 1, bf && q > 1);
   if (s != FRSVT_OK) return s;
-  const bool orth_last = (h->cfg.flags & FRSVT_CFG_ORTH_LAST) != 0;
+  const bool orth_last = orth_last_ok && (h->cfg.flags & FRSVT_CFG_ORTH_LAST) != 0;
   for (int it = 0; it < q; ++it) {
     if (bf && it < q - 1) {
       FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(!short_col, lowp, tmLb, tmQTb, tmQTbl, nl, ns, Sl, h->wpart,
@@ -727,9 +732,11 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
                                                          nullptr, nullptr, h->dst, st));
     }
     if (orth_last && it < q - 1) {
-      // Sec. 2.5: the intermediate power step passes Y = A A^T Q on unnormalised (same span): Q = Y,
-      // split into its TF32 parts (and BF16 copies) by the substitution kernel with T = I
+      // Sec. 2.5: the intermediate power step passes Y = A A^T Q on without orthonormalising it (same
+      // span): Q = Y with each column scaled by a power of two (exact; keeps FP32 in range), split
+      // into its TF32 parts (and BF16 copies) by the substitution kernel with that diagonal T
       const bool bfn = bf && it + 1 < q - 1;
+      FRSVT_LAUNCH(FRSVT_PHASE_APPLY, launch_wd_colscale(h->wYT, lds, ns, h->wI, st));
       FRSVT_LAUNCH(FRSVT_PHASE_APPLY, launch_wd_trsm(h->wYT, lds, ns, h->wI, h->wQT, h->wQTl, bfn ? h->wQTb : nullptr,
                                                     bfn ? h->wQTbl : nullptr, lds, st));
       continue;
@@ -1139,7 +1146,7 @@ static frsvt_status svt_range_and_core(frsvt_handle* h, const float* A, int64_t 
   if (h->wide) {
     if (h->Ab != nullptr) FRSVT_CK(launch_to_bf16(A, lda, m, n, h->Ab, h->ldb, h->stream));
     return wide_range_and_core(h, A, m, n, lda, l, h->cfg.q, kCounterFromState, tau, 0, 1, wide_lowp(h),
-                               h->cfg.range_prop ? 1 : 0);
+                               h->cfg.range_prop ? 1 : 0, true);
   }
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;
@@ -1266,8 +1273,8 @@ static frsvt_status ialm_launches(frsvt_handle* h, const frsvt_handle::StepKey& 
   const int rp = h->cfg.range_prop ? 1 : 0;
   const bool bf = h->Ab != nullptr && h->tma && n <= 256;   // the shadow is kept current by rpca_init / the epilogue
   if (h->wide) {
-    if ((s = wide_range_and_core(h, A, m, n, ld, l, h->cfg.q, kCounterFromState, 0.f, 1, 1, wide_lowp(h), rp)) !=
-        FRSVT_OK)
+    if ((s = wide_range_and_core(h, A, m, n, ld, l, h->cfg.q, kCounterFromState, 0.f, 1, 1, wide_lowp(h), rp,
+                                 true)) != FRSVT_OK)
       return s;
     if ((s = wide_epilogue(h, true, m, n, O, S, A, ld, L, ldl)) != FRSVT_OK) return s;
   } else {

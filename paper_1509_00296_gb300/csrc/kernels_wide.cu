@@ -135,6 +135,32 @@ __global__ void k_wd_rp_insert(float* __restrict__ YT, const float* __restrict__
   }
 }
 
+// Diagonal of T (otherwise the identity) for an unnormalised power step: T_aa = 2^-e with
+// ||row a of Y^T|| = f 2^e, f in [1/2, 1) (1 for a zero row), so that k_wd_trsm with T writes
+// Q = Y diag(T) exactly (a power-of-two scaling: same span, and no overflow however many
+// unnormalised steps follow).  One CTA per row.
+__global__ void k_wd_colscale(const float* __restrict__ YT, int64_t ld, int64_t ns, float* __restrict__ T) {
+  __shared__ float red[256];
+  const int a = blockIdx.x;
+  float ss = 0.f;
+  for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) {
+    const float v = YT[a * ld + x];
+    ss = fmaf(v, v, ss);
+  }
+  red[threadIdx.x] = ss;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const float nrm = sqrtf(red[0]);
+    int e = 0;
+    if (nrm > 0.f && isfinite(nrm)) frexpf(nrm, &e);
+    T[a * kWL + a] = ldexpf(1.f, -e);
+  }
+}
+
 // T = the identity (the triangular operand of k_wd_trsm for Q = Y, the unnormalised power steps).
 __global__ void k_wd_identity(float* __restrict__ T) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kWL * kWL; e += gridDim.x * blockDim.x)
@@ -1760,6 +1786,11 @@ cudaError_t launch_wd_rp_insert(float* YT, const float* QtT, int64_t ld, int64_t
   if (grid > 1024) grid = 1024;
   if (grid == 0) return cudaSuccess;
   k_wd_rp_insert<<<static_cast<int>(grid), 256, 0, st>>>(YT, QtT, ld, ns, l, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wd_colscale(const float* YT, int64_t ld, int64_t ns, float* T, cudaStream_t st) {
+  k_wd_colscale<<<kWL, 256, 0, st>>>(YT, ld, ns, T);
   return cudaGetLastError();
 }
 

@@ -68,7 +68,10 @@ def test_lrr_wide_basis_parity(fr):
     eL, eS = rel_fro(L, ref.L), rel_fro(S, ref.S)
     print(f"lrr 200x320 l=64: rel err L {eL:.3e} S {eS:.3e}")
     assert eL <= TOL and eS <= TOL
-    assert np.allclose(hist, ref.history, rtol=1e-3, atol=1e-6 * max(ref.history))
+    # the stopping quantity is a max-norm residual, O - Z L - S or L - J: an FP32 difference of
+    # entries of O's size, so the bound is 1e-3 of it plus 1e-4 of max |O|
+    gap = np.abs(np.asarray(hist) - np.asarray(ref.history))
+    assert np.all(gap <= 1e-3 * np.abs(ref.history) + 1e-4 * np.abs(O).max()), gap.max()
 
 
 def test_lrr_invalid_arguments(fr):
