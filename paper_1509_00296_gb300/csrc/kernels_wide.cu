@@ -823,11 +823,6 @@ __device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, dou
   __syncthreads();
 }
 
-// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned start, bytes a multiple of 16).
-__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 // Entry e of the packed Gram (a df64 pair stored where a double is declared).
 __device__ __forceinline__ df64 gram_entry(const double* Gpk, int e) {
   const float2 w = __ldcg(reinterpret_cast<const float2*>(Gpk) + e);
@@ -1523,19 +1518,6 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
       const int64_t rbase = 128 * static_cast<int64_t>(tr) + 32 * q;   // the warp's 32 rows
       for (int cg = 0; cg < 4; ++cg) {
         const int colt = 128 * half + 32 * cg;
-        if (ALM) {                                     // the next chunk's rows of O, S, A into L2
-          const bool same = cg < 3;
-          const int tn = tl + static_cast<int>(gridDim.x);
-          const int64_t prow = same ? rbase + lane : 128 * static_cast<int64_t>(tn / ntc) + 32 * q + lane;
-          const int64_t pcol = same ? static_cast<int64_t>(kWN) * tc + colt + 32
-                                    : static_cast<int64_t>(kWN) * (tn % ntc) + 128 * half;
-          if ((same || k + 1 < mine) && prow < m && pcol < n) {
-            const uint32_t bytes = static_cast<uint32_t>(imin64(128, ((n - pcol) * 4 + 15) / 16 * 16));
-            prefetch_l2_bulk(O + prow * ld + pcol, bytes);
-            prefetch_l2_bulk(S + prow * ld + pcol, bytes);
-            prefetch_l2_bulk(A + prow * ld + pcol, bytes);
-          }
-        }
         {                                              // the 32 x 32 chunk of X, staged row-major
           float x[16];
           const uint32_t ta = tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(buf * kWN + colt);
