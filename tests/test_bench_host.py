@@ -14,14 +14,17 @@ import bench  # noqa: E402
 def test_ncu_figures_match_committed_profile():
     text = open(os.path.join(ROOT, bench.NCU_PROFILE)).read()
     table = text[text.index("Figures bench.py reports"):]
-    rows = dict((m.group(1), (float(m.group(2)), float(m.group(3))))
-                for m in re.finditer(r"^\| (k_\S+) \| ([\d.]+) \| ([\d.]+) \|$", table, flags=re.M))
+    rows = dict((m.group(1), (float(m.group(2)), None if m.group(3) == "-" else float(m.group(3))))
+                for m in re.finditer(r"^\| (k_\S+) \| ([\d.]+) \| ([\d.]+|-) \|$", table, flags=re.M))
     for k, v in bench.NCU_WIDE.items():
         if v["traffic"] is None and v["tensor_pct"] is None:
             continue
         assert k in rows, k
         assert abs(rows[k][0] * 1e6 - v["traffic"]) < 0.05e6, (k, rows[k], v)
-        assert abs(rows[k][1] - v["tensor_pct"]) < 0.05, (k, rows[k], v)
+        if v["tensor_pct"] is None:
+            assert rows[k][1] is None, (k, rows[k])
+        else:
+            assert abs(rows[k][1] - v["tensor_pct"]) < 0.05, (k, rows[k], v)
 
 
 def test_both_arms_print_the_same_config():
