@@ -92,6 +92,11 @@ typedef struct frsvt_config {
   int32_t max_jacobi_sweeps;     /* cap of the l x l Jacobi SVD (<= 0: 30) */
   int32_t flags;                 /* FRSVT_CFG_* bits (other bits: FRSVT_ERR_INVALID_ARG) */
   double rank_tol;               /* relative pivot cut of the Cholesky QR (<= 0: 1e-12) */
+  int32_t problem_streams;       /* 0 or 1: one stream; 2..16 (with FRSVT_CFG_ADJOINT): frsvt_create
+                                    also makes that many child handles, each with its own stream and
+                                    workspace, and rpca_unrolled_forward / rpca_unrolled_backward run
+                                    the batch's problems on them concurrently (problem b on child
+                                    b mod problem_streams), joined back into the handle's stream */
 } frsvt_config;
 
 typedef struct frsvt_info {

@@ -155,6 +155,7 @@ cudaError_t launch_ur_bwd_pre(const float* O, const float* Y, float ys, const fl
                               cudaStream_t st);
 cudaError_t launch_ur_sum(const double* part, int count, float* out, int accumulate, cudaStream_t st);
 cudaError_t launch_ur_addf(const float* in, float* out, cudaStream_t st);
+cudaError_t launch_ur_addv(const float* in, float* out, int count, cudaStream_t st);
 cudaError_t launch_absmax_sumsq(const float* O, int64_t m, int64_t n, int64_t ld, float* pmax, float2* psum, int nblk,
                                 cudaStream_t st);
 cudaError_t launch_wd_alm(bool alm, const CUtensorMap& tmZ, const CUtensorMap& tmZl, const CUtensorMap& tmR,
@@ -232,6 +233,12 @@ struct frsvt_handle {
   };
   uint64_t epoch = 1;
   cudaStream_t capture_stream = nullptr;
+  // child handles (cfg.problem_streams): independent problems of an unrolled batch run on them,
+  // each on its own stream, forked from and joined back into `stream`
+  std::vector<frsvt_handle*> kids;
+  std::vector<cudaStream_t> kid_streams;
+  std::vector<cudaEvent_t> kid_events;
+  cudaEvent_t fork_event = nullptr;
   static constexpr int kGraphSlots = 4;          // graphs kept for the most recent argument tuples
   cudaGraphExec_t step_exec[kGraphSlots] = {};
   StepKey step_key[kGraphSlots] = {};
@@ -598,6 +605,14 @@ frsvt_status sync_rp_shape(frsvt_handle* h, int64_t m, int64_t n, int l) {
 }
 
 void free_all(frsvt_handle* h) {
+  for (frsvt_handle* k : h->kids) frsvt_destroy(k);
+  h->kids.clear();
+  for (cudaStream_t s : h->kid_streams) cudaStreamDestroy(s);
+  h->kid_streams.clear();
+  for (cudaEvent_t e : h->kid_events) cudaEventDestroy(e);
+  h->kid_events.clear();
+  if (h->fork_event) cudaEventDestroy(h->fork_event);
+  h->fork_event = nullptr;
   for (auto& g : h->step_exec) {
     if (g) cudaGraphExecDestroy(g);
     g = nullptr;
@@ -949,6 +964,9 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
   if (cfg->m_max < 1 || cfg->n_max < 1 || cfg->l_max < 1 || cfg->l_max > kMaxL || cfg->q < 0 || cfg->q > 64)
     return FRSVT_ERR_INVALID_ARG;
   if ((cfg->flags & ~(FRSVT_CFG_ADJOINT | FRSVT_CFG_ORTH_LAST)) != 0) return FRSVT_ERR_INVALID_ARG;
+  if (cfg->problem_streams < 0 || cfg->problem_streams > 16 ||
+      (cfg->problem_streams > 1 && !(cfg->flags & FRSVT_CFG_ADJOINT)))
+    return FRSVT_ERR_INVALID_ARG;
   if (cfg->precision != FRSVT_PREC_FP32 && cfg->precision != FRSVT_PREC_BF16 &&
       !(cfg->precision == FRSVT_PREC_FP8 && cfg->l_max > 32))
     return FRSVT_ERR_UNSUPPORTED;
@@ -1099,6 +1117,28 @@ frsvt_status frsvt_create(frsvt_handle** out, const frsvt_config* cfg, void* str
     free_all(h);
     delete h;
     return FRSVT_ERR_CUDA;
+  }
+  if (cfg->problem_streams > 1) {                   // child handles for concurrent problems
+    frsvt_config kc = *cfg;
+    kc.problem_streams = 0;
+    bool ok = cudaEventCreateWithFlags(&h->fork_event, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < cfg->problem_streams; ++i) {
+      cudaStream_t ks = nullptr;
+      cudaEvent_t ke = nullptr;
+      ok = cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking) == cudaSuccess;
+      if (ok) h->kid_streams.push_back(ks);
+      ok = ok && cudaEventCreateWithFlags(&ke, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) h->kid_events.push_back(ke);
+      frsvt_handle* kid = nullptr;
+      const frsvt_status ks2 = ok ? frsvt_create(&kid, &kc, ks) : FRSVT_ERR_CUDA;
+      if (ks2 == FRSVT_OK) h->kids.push_back(kid);
+      ok = ok && ks2 == FRSVT_OK;
+    }
+    if (!ok) {
+      free_all(h);
+      delete h;
+      return FRSVT_ERR_ALLOC;
+    }
   }
   *out = h;
   return FRSVT_OK;
@@ -1805,8 +1845,8 @@ frsvt_status frsvt_debug_cols_tc(frsvt_handle* h, const float* A, int64_t m, int
 // of step k (frsvt_adjoint_saved_bytes), then the backward scratch: Sb, Yb, Lb, Tb, Ab (m x ld
 // each) and two arrays of per-CTA partial sums.
 struct UrLayout {
-  size_t mat, blob, per_step, scratch_off, part_off, total;
-  int grid;
+  size_t mat, blob, per_step, scratch_off, part_off, acc_off, kid_block, total;
+  int grid, kids;
 };
 
 static size_t ur_align(size_t x) { return (x + 255) / 256 * 256; }
@@ -1818,8 +1858,13 @@ static UrLayout ur_layout(const frsvt_handle* h, int32_t batch, int32_t steps, i
   u.per_step = 3 * u.mat + u.blob;
   u.scratch_off = static_cast<size_t>(batch) * static_cast<size_t>(steps) * u.per_step;
   u.grid = unrolled_grid(m, n, h->sms);
-  u.part_off = u.scratch_off + 5 * u.mat;
-  u.total = u.part_off + ur_align(sizeof(double) * 2 * static_cast<size_t>(u.grid) + 64);
+  u.kids = h->kids.empty() ? 1 : static_cast<int>(h->kids.size());
+  // per child (or the handle alone): five scratch matrices, two partial arrays and the tt slot,
+  // then the child's dtau / dmu accumulators (2 x steps floats)
+  u.part_off = 5 * u.mat;
+  u.acc_off = u.part_off + ur_align(sizeof(double) * 2 * static_cast<size_t>(u.grid) + 64);
+  u.kid_block = u.acc_off + ur_align(sizeof(float) * 2 * static_cast<size_t>(steps));
+  u.total = u.scratch_off + static_cast<size_t>(u.kids) * u.kid_block;
   return u;
 }
 
@@ -1832,6 +1877,28 @@ static frsvt_status ur_check(frsvt_handle* h, int32_t batch, int32_t steps, cons
   if (s != FRSVT_OK) return s;
   if ((n % 4) != 0) return fail(h, FRSVT_ERR_INVALID_ARG, "the unrolled steps need n % 4 == 0");
   if (!(lambda > 0.f) || !std::isfinite(lambda)) return fail(h, FRSVT_ERR_INVALID_ARG, "lambda must be finite and > 0");
+  return FRSVT_OK;
+}
+
+// The handle (or child j of it) that runs problem b, and fork / join of the children's streams
+// around a batch (the children start after everything enqueued so far on the handle's stream,
+// and the handle's stream resumes after all of them).
+static frsvt_handle* ur_worker(frsvt_handle* h, int32_t b) {
+  return h->kids.empty() ? h : h->kids[static_cast<size_t>(b) % h->kids.size()];
+}
+
+static frsvt_status ur_fork(frsvt_handle* h) {
+  if (h->kids.empty()) return FRSVT_OK;
+  FRSVT_CK(cudaEventRecord(h->fork_event, h->stream));
+  for (cudaStream_t ks : h->kid_streams) FRSVT_CK(cudaStreamWaitEvent(ks, h->fork_event, 0));
+  return FRSVT_OK;
+}
+
+static frsvt_status ur_join(frsvt_handle* h) {
+  for (size_t i = 0; i < h->kids.size(); ++i) {
+    FRSVT_CK(cudaEventRecord(h->kid_events[i], h->kid_streams[i]));
+    FRSVT_CK(cudaStreamWaitEvent(h->stream, h->kid_events[i], 0));
+  }
   return FRSVT_OK;
 }
 
@@ -1878,10 +1945,12 @@ frsvt_status rpca_unrolled_forward(frsvt_handle* h, int32_t batch, int32_t steps
   if (batch == 0 || m == 0 || n == 0) return FRSVT_OK;
   const UrLayout u = ur_layout(h, batch, steps, m, n, ld);
   unsigned char* base = static_cast<unsigned char*>(saved);
-  float* Sw = reinterpret_cast<float*>(base + u.scratch_off);          // S_k of the running step
   const size_t step = static_cast<size_t>(m) * static_cast<size_t>(ld);
-  cudaStream_t st = h->stream;
+  if ((s = ur_fork(h)) != FRSVT_OK) return s;
   for (int32_t b = 0; b < batch; ++b) {
+    frsvt_handle* hw = ur_worker(h, b);
+    cudaStream_t st = hw->stream;
+    float* Sw = reinterpret_cast<float*>(base + u.scratch_off + (b % u.kids) * u.kid_block);   // S_k of the running step
     const float* Ob = O + step * b;
     for (int32_t k = 0; k < steps; ++k) {
       unsigned char* slot = base + (static_cast<size_t>(b) * steps + k) * u.per_step;
@@ -1891,8 +1960,8 @@ frsvt_status rpca_unrolled_forward(frsvt_handle* h, int32_t batch, int32_t steps
       void* blob = slot + 3 * u.mat;
       if (k == 0) FRSVT_CK(launch_ur_pre(Ob, nullptr, nullptr, y0_scale[b], Ak, m, n, ld, mu[0], u.grid, st));
       float* Lout = (k == steps - 1) ? L + step * b : Lk;
-      if ((s = frsvt_svt_save(h, Ak, m, n, ld, tau[k], l, static_cast<uint64_t>(k), Lout, ld, blob)) != FRSVT_OK)
-        return s;
+      if ((s = frsvt_svt_save(hw, Ak, m, n, ld, tau[k], l, static_cast<uint64_t>(k), Lout, ld, blob)) != FRSVT_OK)
+        return fail(h, s, frsvt_last_error(hw));
       if (k == steps - 1) {
         FRSVT_CK(cudaMemcpy2DAsync(Lk, sizeof(float) * ld, Lout, sizeof(float) * ld, sizeof(float) * n, m,
                                    cudaMemcpyDeviceToDevice, st));
@@ -1904,7 +1973,7 @@ frsvt_status rpca_unrolled_forward(frsvt_handle* h, int32_t batch, int32_t steps
                               mu[k], mu[k + 1], lambda, u.grid, st));
     }
   }
-  return FRSVT_OK;
+  return ur_join(h);
 }
 
 frsvt_status rpca_unrolled_backward(frsvt_handle* h, int32_t batch, int32_t steps, const float* O, int64_t m,
@@ -1916,23 +1985,30 @@ frsvt_status rpca_unrolled_backward(frsvt_handle* h, int32_t batch, int32_t step
   if ((s = check_matrix(h, dL, m, n, ld, "dL")) != FRSVT_OK) return s;
   if (y0_scale == nullptr || tau == nullptr || mu == nullptr || saved == nullptr || dtau == nullptr || dmu == nullptr)
     return fail(h, FRSVT_ERR_INVALID_ARG, "y0_scale, tau, mu, saved, dtau and dmu are required");
-  cudaStream_t st = h->stream;
-  FRSVT_CK(cudaMemsetAsync(dtau, 0, sizeof(float) * steps, st));
-  FRSVT_CK(cudaMemsetAsync(dmu, 0, sizeof(float) * steps, st));
+  FRSVT_CK(cudaMemsetAsync(dtau, 0, sizeof(float) * steps, h->stream));
+  FRSVT_CK(cudaMemsetAsync(dmu, 0, sizeof(float) * steps, h->stream));
   if (batch == 0 || m == 0 || n == 0) return FRSVT_OK;
   const UrLayout u = ur_layout(h, batch, steps, m, n, ld);
   unsigned char* base = static_cast<unsigned char*>(const_cast<void*>(saved));
-  unsigned char* sc = base + u.scratch_off;
-  float* Sb = reinterpret_cast<float*>(sc);
-  float* Yb = reinterpret_cast<float*>(sc + u.mat);
-  float* Lb = reinterpret_cast<float*>(sc + 2 * u.mat);
-  float* Tb = reinterpret_cast<float*>(sc + 3 * u.mat);
-  float* Ab = reinterpret_cast<float*>(sc + 4 * u.mat);
-  double* part = reinterpret_cast<double*>(base + u.part_off);
-  double* part2 = part + u.grid;
-  float* tt = reinterpret_cast<float*>(part2 + u.grid);                // dtau of one FRSVT adjoint
+  for (int j = 0; j < u.kids; ++j)                 // the per-worker dtau / dmu accumulators
+    FRSVT_CK(cudaMemsetAsync(base + u.scratch_off + j * u.kid_block + u.acc_off, 0, sizeof(float) * 2 * steps,
+                             h->stream));
   const size_t step = static_cast<size_t>(m) * static_cast<size_t>(ld);
+  if ((s = ur_fork(h)) != FRSVT_OK) return s;
   for (int32_t b = 0; b < batch; ++b) {
+    frsvt_handle* hw = ur_worker(h, b);
+    cudaStream_t st = hw->stream;
+    unsigned char* sc = base + u.scratch_off + (b % u.kids) * u.kid_block;
+    float* Sb = reinterpret_cast<float*>(sc);
+    float* Yb = reinterpret_cast<float*>(sc + u.mat);
+    float* Lb = reinterpret_cast<float*>(sc + 2 * u.mat);
+    float* Tb = reinterpret_cast<float*>(sc + 3 * u.mat);
+    float* Ab = reinterpret_cast<float*>(sc + 4 * u.mat);
+    double* part = reinterpret_cast<double*>(sc + u.part_off);
+    double* part2 = part + u.grid;
+    float* tt = reinterpret_cast<float*>(part2 + u.grid);              // dtau of one FRSVT adjoint
+    float* kdtau = reinterpret_cast<float*>(sc + u.acc_off);
+    float* kdmu = kdtau + steps;
     const float* Ob = O + step * b;
     for (int32_t k = steps - 1; k >= 0; --k) {
       unsigned char* slot = base + (static_cast<size_t>(b) * steps + k) * u.per_step;
@@ -1945,14 +2021,20 @@ frsvt_status rpca_unrolled_backward(frsvt_handle* h, int32_t batch, int32_t step
       FRSVT_CK(launch_ur_bwd_post(Ob, Lk, Yp, y0_scale[b], last ? nullptr : Sb, last ? nullptr : Yb,
                                   last ? dL + step * b : nullptr, Lb, Yb, Tb, m, n, ld, mu[k], lambda, part, u.grid,
                                   st));
-      if ((s = frsvt_backward(h, blob, Ak, m, n, ld, tau[k], l, static_cast<uint64_t>(k), Lb, ld, Ab, ld, tt)) !=
+      if ((s = frsvt_backward(hw, blob, Ak, m, n, ld, tau[k], l, static_cast<uint64_t>(k), Lb, ld, Ab, ld, tt)) !=
           FRSVT_OK)
-        return s;
+        return fail(h, s, frsvt_last_error(hw));
       FRSVT_CK(launch_ur_bwd_pre(Ob, Yp, y0_scale[b], Ab, Tb, Sb, Yb, m, n, ld, mu[k], part2, u.grid, st));
-      FRSVT_CK(launch_ur_sum(part, u.grid, dmu + k, 1, st));
-      FRSVT_CK(launch_ur_sum(part2, u.grid, dmu + k, 1, st));
-      FRSVT_CK(launch_ur_addf(tt, dtau + k, st));
+      FRSVT_CK(launch_ur_sum(part, u.grid, kdmu + k, 1, st));
+      FRSVT_CK(launch_ur_sum(part2, u.grid, kdmu + k, 1, st));
+      FRSVT_CK(launch_ur_addf(tt, kdtau + k, st));
     }
+  }
+  if ((s = ur_join(h)) != FRSVT_OK) return s;
+  for (int j = 0; j < u.kids; ++j) {               // the workers' sums, in worker order
+    const float* acc = reinterpret_cast<const float*>(base + u.scratch_off + j * u.kid_block + u.acc_off);
+    FRSVT_CK(launch_ur_addv(acc, dtau, steps, h->stream));
+    FRSVT_CK(launch_ur_addv(acc + steps, dmu, steps, h->stream));
   }
   return FRSVT_OK;
 }

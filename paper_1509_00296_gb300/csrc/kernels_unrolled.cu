@@ -182,6 +182,10 @@ __global__ void k_ur_addf(const float* __restrict__ in, float* __restrict__ out)
   if (threadIdx.x == 0 && blockIdx.x == 0) *out += *in;
 }
 
+__global__ void k_ur_addv(const float* __restrict__ in, float* __restrict__ out, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) out[i] += in[i];
+}
+
 int ur_grid(int64_t m, int64_t n4, int sms) {
   const int64_t want = (m * n4 + kUThr - 1) / kUThr;
   const int64_t cap = 4LL * sms;
@@ -221,6 +225,11 @@ cudaError_t launch_ur_bwd_pre(const float* O, const float* Y, float ys, const fl
 
 cudaError_t launch_ur_addf(const float* in, float* out, cudaStream_t st) {
   k_ur_addf<<<1, 32, 0, st>>>(in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ur_addv(const float* in, float* out, int count, cudaStream_t st) {
+  k_ur_addv<<<1, 256, 0, st>>>(in, out, count);
   return cudaGetLastError();
 }
 

@@ -37,7 +37,7 @@ class Config(ctypes.Structure):
     _fields_ = [("m_max", ctypes.c_int64), ("n_max", ctypes.c_int64), ("l_max", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("range_prop", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("max_jacobi_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("rank_tol", ctypes.c_double)]
+                ("rank_tol", ctypes.c_double), ("problem_streams", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -166,10 +166,10 @@ class Handle:
 
     def __init__(self, m_max: int, n_max: int, l_max: int, q: int = 2, range_prop: bool = True,
                  seed: int = 0, max_jacobi_sweeps: int = 30, rank_tol: float = 1e-12, stream=None,
-                 adjoint: bool = False, precision: int = 0, orth_last: bool = False):
+                 adjoint: bool = False, precision: int = 0, orth_last: bool = False, problem_streams: int = 0):
         flags = (CFG_ADJOINT if adjoint else 0) | (CFG_ORTH_LAST if orth_last else 0)
         cfg = Config(m_max, n_max, l_max, q, 1 if range_prop else 0, precision, seed, max_jacobi_sweeps,
-                     flags, rank_tol)
+                     flags, rank_tol, problem_streams)
         h = _P()
         self._stream = stream
         st = lib().frsvt_create(ctypes.byref(h), ctypes.byref(cfg), _stream_ptr(stream))

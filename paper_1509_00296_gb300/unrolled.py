@@ -58,11 +58,14 @@ class RPCAUnrolled:
     """
 
     def __init__(self, m: int, n: int, steps: int = 10, l: int = 16, q: int = 1, lam: float | None = None,
-                 mu0: float = 1.0, rho: float = 1.5, seed: int = 0, device="cuda"):
+                 mu0: float = 1.0, rho: float = 1.5, seed: int = 0, device="cuda", streams: int = 8):
+        """streams: concurrent problems of a batch (child handles of the library, each with its own
+        CUDA stream and workspace); 0 or 1 runs them one after another."""
         torch = _torch()
         self.m, self.n, self.K, self.l = m, n, steps, l
         self.lam = lam if lam is not None else 1.0 / math.sqrt(max(m, n))
-        self.handle = fr.Handle(m, n, l, q=q, seed=seed, adjoint=True, range_prop=False)
+        self.handle = fr.Handle(m, n, l, q=q, seed=seed, adjoint=True, range_prop=False,
+                                problem_streams=streams if streams > 1 else 0)
         mu = torch.tensor([mu0 * rho ** k for k in range(steps)], dtype=torch.float32, device=device)
         self.mu = mu.clone().requires_grad_(True)
         self.tau = (1.0 / mu).clone().requires_grad_(True)

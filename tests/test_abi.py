@@ -58,6 +58,10 @@ def test_invalid_arguments_rejected_on_host(libpath):
     assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 2
     bad = frsvt.Config(10, 10, 8, 1, 1, 0, 0, 30, 4, 1e-10)          # unknown flag bit
     assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
+    bad = frsvt.Config(10, 10, 8, 1, 0, 0, 0, 30, 0, 1e-10, 4)       # child streams without the adjoint
+    assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
+    bad = frsvt.Config(10, 10, 8, 1, 0, 0, 0, 30, 1, 1e-10, 17)      # more than 16 child streams
+    assert L.frsvt_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
     assert L.frsvt_create(None, None, None) == 1
     assert L.frsvt_svt(None, None, 1, 1, 4, ctypes.c_float(1.0), 1, None, 4) == 1
 
