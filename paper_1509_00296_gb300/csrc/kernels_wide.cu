@@ -1406,6 +1406,36 @@ constexpr uint32_t kEZ = 128 * kWK * 4;                  // 16 KB
 constexpr uint32_t kER = kWN * kWK * 4;                  // 32 KB
 constexpr uint32_t kEStage = 2 * kEZ + 2 * kER;          // 96 KB
 constexpr int kEXs = 33;                                  // staged X chunk row stride (floats)
+constexpr int kEBatch = 4;                                // row groups whose O, S, A loads are in flight together
+
+// O, S, A at rows rbase + 4 (i0 + ii) + rr (ii < kEBatch), columns colg .. colg + 3, for the
+// transposed epilogue read; full[ii]: the whole float4 is inside the matrix.
+__device__ __forceinline__ void epi_load(const float* O, const float* S, const float* A, int64_t ld, int64_t m,
+                                         int64_t n, int64_t rbase, int64_t colg, int i0, int rr,
+                                         float (&ov)[kEBatch][4], float (&sv)[kEBatch][4], float (&av)[kEBatch][4],
+                                         bool (&full)[kEBatch]) {
+#pragma unroll
+  for (int ii = 0; ii < kEBatch; ++ii) {
+    const int64_t rowg = rbase + 4 * (i0 + ii) + rr;
+    full[ii] = rowg < m && colg + 4 <= n;
+    if (full[ii]) {
+      const float4 o = __ldcs(reinterpret_cast<const float4*>(O + rowg * ld + colg));
+      const float4 s4 = __ldcs(reinterpret_cast<const float4*>(S + rowg * ld + colg));
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(A + rowg * ld + colg));
+      ov[ii][0] = o.x; ov[ii][1] = o.y; ov[ii][2] = o.z; ov[ii][3] = o.w;
+      sv[ii][0] = s4.x; sv[ii][1] = s4.y; sv[ii][2] = s4.z; sv[ii][3] = s4.w;
+      av[ii][0] = a.x; av[ii][1] = a.y; av[ii][2] = a.z; av[ii][3] = a.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool in = rowg < m && colg + e < n;
+        ov[ii][e] = in ? O[rowg * ld + colg + e] : 0.f;
+        sv[ii][e] = in ? S[rowg * ld + colg + e] : 0.f;
+        av[ii][e] = in ? A[rowg * ld + colg + e] : 0.f;
+      }
+    }
+  }
+}
 constexpr uint32_t kESmem = kEStages * kEStage + kEW * 32 * kEXs * 4;   // + 8 x 4.2 KB for the transpose
 
 template <bool ALM>
@@ -1518,6 +1548,14 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
       const int64_t rbase = 128 * static_cast<int64_t>(tr) + 32 * q;   // the warp's 32 rows
       for (int cg = 0; cg < 4; ++cg) {
         const int colt = 128 * half + 32 * cg;
+        const int64_t col0 = static_cast<int64_t>(kWN) * tc + colt;
+        const bool act = ok && rbase < m && col0 < n;  // warp-uniform
+        const int64_t colg = col0 + c4;
+        float ov[kEBatch][4], sv[kEBatch][4], av[kEBatch][4];
+        bool full[kEBatch];
+        // the first row groups' O, S, A loads go out before the tensor-memory read (they do not
+        // depend on X), so that their latency overlaps it
+        if (ALM && act) epi_load(O, S, A, ld, m, n, rbase, colg, 0, rr, ov, sv, av, full);
         {                                              // the 32 x 32 chunk of X, staged row-major
           float x[16];
           const uint32_t ta = tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(buf * kWN + colt);
@@ -1529,39 +1567,24 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
           for (int j = 0; j < 16; ++j) sX[lane * kEXs + 16 + j] = x[j];
         }
         __syncwarp();
-        const int64_t col0 = static_cast<int64_t>(kWN) * tc + colt;
-        if (ok && rbase < m && col0 < n) {
+        if (act) {
           // lane (rr, c4) takes rows 4 i + rr, columns c4 .. c4 + 3: every load and store below
           // covers four rows x 128 contiguous bytes per warp
-          const int64_t colg = col0 + c4;
 #pragma unroll
-          for (int i0 = 0; i0 < 8; i0 += 4) {
-            float ov[4][4], sv[4][4], av[4][4];
-            bool full[4];
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii) {
-              const int64_t rowg = rbase + 4 * (i0 + ii) + rr;
-              full[ii] = rowg < m && colg + 4 <= n;
-              if (!ALM) continue;
-              if (full[ii]) {
-                const float4 o = __ldcs(reinterpret_cast<const float4*>(O + rowg * ld + colg));
-                const float4 s4 = __ldcs(reinterpret_cast<const float4*>(S + rowg * ld + colg));
-                const float4 a = __ldcs(reinterpret_cast<const float4*>(A + rowg * ld + colg));
-                ov[ii][0] = o.x; ov[ii][1] = o.y; ov[ii][2] = o.z; ov[ii][3] = o.w;
-                sv[ii][0] = s4.x; sv[ii][1] = s4.y; sv[ii][2] = s4.z; sv[ii][3] = s4.w;
-                av[ii][0] = a.x; av[ii][1] = a.y; av[ii][2] = a.z; av[ii][3] = a.w;
+          for (int i0 = 0; i0 < 8; i0 += kEBatch) {
+            if (i0 > 0) {
+              if (ALM) {
+                epi_load(O, S, A, ld, m, n, rbase, colg, i0, rr, ov, sv, av, full);
               } else {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  const bool in = rowg < m && colg + e < n;
-                  ov[ii][e] = in ? O[rowg * ld + colg + e] : 0.f;
-                  sv[ii][e] = in ? S[rowg * ld + colg + e] : 0.f;
-                  av[ii][e] = in ? A[rowg * ld + colg + e] : 0.f;
-                }
+                for (int ii = 0; ii < kEBatch; ++ii) full[ii] = rbase + 4 * (i0 + ii) + rr < m && colg + 4 <= n;
               }
+            } else if (!ALM) {
+#pragma unroll
+              for (int ii = 0; ii < kEBatch; ++ii) full[ii] = rbase + 4 * ii + rr < m && colg + 4 <= n;
             }
 #pragma unroll
-            for (int ii = 0; ii < 4; ++ii) {
+            for (int ii = 0; ii < kEBatch; ++ii) {
               const int r = 4 * (i0 + ii) + rr;
               const int64_t rowg = rbase + r;
               float xv[4];
