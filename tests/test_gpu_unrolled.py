@@ -123,3 +123,24 @@ def test_unrolled_full_basis_equals_exact_svd_gradient():
     """l = n: FRSVT is the exact SVT, so the gradient matches central differences of the
     exact-SVT pipeline (the FP64 oracle's exact-SVD reference gradient) at 1e-3."""
     assert _run(128, 32, 3, 32, 1, batch=1, batch_seed=97, rho=1.2, exact_ref=True) == 6
+
+
+def test_unrolled_concurrent_batch_matches_serial():
+    """The batch run on child handles with their own streams (problem_streams) gives the loss and
+    gradients of the one-stream run: the same kernels per problem, only the order of the
+    per-problem gradient sums differs."""
+    import torch
+    from paper_1509_00296_gb300.unrolled import RPCAUnrolled
+    O3, L3, _ = synth.unrolled_batch(seed=77, batch=3, m=512, n=128)
+    Od = torch.from_numpy(O3.astype(np.float32)).cuda()
+    Lt = torch.from_numpy(L3.astype(np.float32)).cuda()
+    out = []
+    for streams in (0, 2):
+        net = RPCAUnrolled(512, 128, steps=4, l=8, q=1, mu0=0.01, rho=1.2, seed=SEED, streams=streams)
+        loss = net.loss(Od, Lt)
+        loss.backward()
+        out.append((float(loss.detach()), net.tau.grad.cpu().numpy(), net.mu.grad.cpu().numpy()))
+    (l0, t0, m0), (l1, t1, m1) = out
+    assert abs(l0 - l1) <= 1e-6 * abs(l0)
+    assert np.allclose(t0, t1, rtol=1e-5, atol=1e-7 * np.abs(t0).max())
+    assert np.allclose(m0, m1, rtol=1e-5, atol=1e-7 * np.abs(m0).max())
