@@ -207,7 +207,7 @@ __device__ void block_cholesky(SmallWs<LP>& w, int p, double rank_tol, uint32_t*
       const bool drop = !(d.hi > tolf * g0j) || !(g0j > 1e-15f * maxdiag) || !(d.hi > 1e-30f) || !(d.hi < 1e30f);
       df64 inv{0.f, 0.f}, rjj{0.f, 0.f};
       if (!drop) {
-        inv = df_rsqrt(d);
+        inv = df_rsqrt_fma(d);
         rjj = df_mul(d, inv);
       }
       df64 rjb{0.f, 0.f};
@@ -219,9 +219,20 @@ __device__ void block_cholesky(SmallWs<LP>& w, int p, double rank_tol, uint32_t*
       }
       __syncwarp();
       if (!drop && lane > j && lane < p) {
-#pragma unroll 4
-        for (int a = j + 1; a <= lane; ++a)
-          Gd[a * LP + lane] = df_add(Gd[a * LP + lane], df_neg(df_mul(Rd[j * LP + a], rjb)));
+        // four independent updates at a time: every load first, then the fused multiply-subtracts,
+        // then the stores (the dependent chain per column is what sets the pace of this warp)
+        int a = j + 1;
+        for (; a + 3 <= lane; a += 4) {
+          df64 r4[4], g4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            r4[u] = Rd[j * LP + a + u];
+            g4[u] = Gd[(a + u) * LP + lane];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) Gd[(a + u) * LP + lane] = df_fms(g4[u], r4[u], rjb);
+        }
+        for (; a <= lane; ++a) Gd[a * LP + lane] = df_fms(Gd[a * LP + lane], Rd[j * LP + a], rjb);
       }
       __syncwarp();
     }
