@@ -61,7 +61,7 @@ WIDE_PHASE_KERNEL = {"sketch": "k_wd_pass<1,0>", "power_AQ": "k_wd_pass<0,0>", "
 NCU_PROFILE = "profiles/wide_passes_recovery_8192x8192.md"
 NCU_WIDE = {"k_wd_pass<1,0>": {"traffic": 280.1e6, "tensor_pct": 46.2},
             "k_wd_pass<0,0>": {"traffic": 280.6e6, "tensor_pct": 41.2},
-            "k_wd_alm<true>": {"traffic": 1299.4e6, "tensor_pct": None}}
+            "k_wd_alm<true>": {"traffic": 1299.1e6, "tensor_pct": None}}
 
 
 def config_dict(ws: int):
