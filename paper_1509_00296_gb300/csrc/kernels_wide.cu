@@ -1273,10 +1273,17 @@ k_wd_trsm(const float* in, int64_t ldi, int64_t len, const float* __restrict__ T
   float* Ys = RT + kWL * kTS;                                 // kWL x kTX: Ys[c][x]
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTThr;
   const int nx = static_cast<int>(imin64(kTThr, len - x0));
-  for (int e = threadIdx.x; e < kWL * kWL; e += kTThr) {
-    const int a = e / kWL, c = e % kWL;
-    RT[c * kTS + a] = __ldcg(T + e);
+  // staging: float4 loads, eight in flight per thread (T transposed into RT on the way)
+#pragma unroll 8
+  for (int e = threadIdx.x; e < kWL * kWL / 4; e += kTThr) {
+    const int a = e % kWL, c4 = e / kWL;                  // consecutive threads: consecutive rows of RT
+    const float4 t = __ldcg(reinterpret_cast<const float4*>(T + a * kWL) + c4);
+    RT[(4 * c4) * kTS + a] = t.x;
+    RT[(4 * c4 + 1) * kTS + a] = t.y;
+    RT[(4 * c4 + 2) * kTS + a] = t.z;
+    RT[(4 * c4 + 3) * kTS + a] = t.w;
   }
+#pragma unroll 8
   for (int e = threadIdx.x; e < kWL * (kTThr / 4); e += kTThr) {
     const int c = e / (kTThr / 4), x4 = e % (kTThr / 4);
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1351,8 +1358,10 @@ k_wd_apply(const float* in, int64_t ldi, int64_t len, const float* __restrict__ 
   float* Is = Ts + kWL * kWL;                             // 128 x 64
   const int64_t xs = static_cast<int64_t>(blockIdx.x) * kACols;
   const int nx = static_cast<int>(imin64(kACols, len - xs));
+#pragma unroll 8                                           // eight loads in flight per thread
   for (int e = threadIdx.x; e < kWL * kWL / 4; e += kAThr)
     reinterpret_cast<float4*>(Ts)[e] = __ldcg(reinterpret_cast<const float4*>(T) + e);
+#pragma unroll 8
   for (int e = threadIdx.x; e < kWL * kACols; e += kAThr) {
     const int a = e / kACols, x = e % kACols;
     Is[e] = (x < nx) ? __ldcg(in + a * ldi + xs + x) : 0.f;
