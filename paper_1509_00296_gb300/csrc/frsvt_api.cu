@@ -124,13 +124,12 @@ cudaError_t launch_wd_rp_insert(float* YT, const float* QtT, int64_t ld, int64_t
                                cudaStream_t st);
 cudaError_t launch_wd_identity(float* T, cudaStream_t st);
 cudaError_t launch_wd_colscale(const float* YT, int64_t ld, int64_t ns, float* T, cudaStream_t st);
-int wide_splits(int64_t nlong, int64_t nk, int sms);
 cudaError_t launch_wd_omega(float* OT, float* OTl, void* OTb, void* OTbl, int64_t ldo, int64_t m, int l, int use_rp,
                             uint64_t seed, uint64_t ctr, const DevState* dst, cudaStream_t st);
 cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
-                           int64_t nlong, int64_t nk, int S, float* part, int64_t ldp, unsigned* tickets, float* outT,
-                           float* outTl, void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl,
-                           DevState* dst, cudaStream_t st, const float* scales = nullptr, int ntr8 = 0, int ntc8 = 0);
+                           int64_t nlong, int64_t nk, int sms, float* part, int64_t ldp, float* outT, float* outTl,
+                           void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl, DevState* dst,
+                           cudaStream_t st, const float* scales = nullptr, int ntr8 = 0, int ntc8 = 0);
 cudaError_t launch_wd_quant8(const float* A, int64_t lda, int64_t m, int64_t n, void* A8, int64_t ld8, float* scales,
                              cudaStream_t st);
 cudaError_t launch_wd_gram(bool core, const float* XT, int64_t ldx, int64_t len, int grid, double* cpart, double* Gpk,
@@ -259,8 +258,7 @@ struct frsvt_handle {
   float* w8s = nullptr;            // its per-128 x 128-tile scales
   int64_t ld8 = 0;
   double *wgc = nullptr, *wGpk = nullptr, *wac = nullptr;
-  unsigned* wtick = nullptr;       // pass tiles, then the Gram ticket, then the epilogue ticket
-  int64_t w_ntiles = 0;
+  unsigned* wtick = nullptr;       // the epilogue ticket
   int w_gram_grid = 8;
   // adaptive rank prediction (Eq. 7): parameters; the state lives in DevState
   int ap_a = 0;
@@ -715,16 +713,15 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
   const CUtensorMap& tmL = short_col ? tmAr : tmAc;
   const CUtensorMap& tmSb = short_col ? tmBc : tmBr;
   const CUtensorMap& tmLb = short_col ? tmBr : tmBc;
-  const int Ss = wide_splits(ns, nl, h->sms), Sl = wide_splits(nl, ns, h->sms);
   FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_omega(h->wOT, h->wOTl, bf ? h->wOTb : nullptr, bf ? h->wOTbl : nullptr,
                                                    ldl, nl, l, use_rp, h->cfg.seed, ctr, h->dst, st));
   if (bf)
-    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(short_col, lowp, tmSb, tmOTb, tmOTbl, ns, nl, Ss, h->wpart,
-                                                    h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr, lds, nullptr,
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(short_col, lowp, tmSb, tmOTb, tmOTbl, ns, nl, h->sms, h->wpart,
+                                                    h->w_ldp, h->wYT, nullptr, nullptr, nullptr, lds, nullptr,
                                                     nullptr, h->dst, st, sc8, ntr8, ntc8));
   else
-    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(short_col, 0, tmS, tmOT, tmOTl, ns, nl, Ss, h->wpart, h->w_ldp,
-                                                    h->wtick, h->wYT, nullptr, nullptr, nullptr, lds, nullptr,
+    FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_pass(short_col, 0, tmS, tmOT, tmOTl, ns, nl, h->sms, h->wpart, h->w_ldp,
+                                                    h->wYT, nullptr, nullptr, nullptr, lds, nullptr,
                                                     nullptr, h->dst, st));
   if (use_rp) FRSVT_LAUNCH(FRSVT_PHASE_SKETCH, launch_wd_rp_insert(h->wYT, h->wQp, lds, ns, l, h->dst, st));
   frsvt_status s = wide_orth(h, ns, l, q == 0 ? 2 : 1, bf && q > 1);
@@ -732,18 +729,18 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
   const bool orth_last = orth_last_ok && (h->cfg.flags & FRSVT_CFG_ORTH_LAST) != 0;
   for (int it = 0; it < q; ++it) {
     if (bf && it < q - 1) {
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(!short_col, lowp, tmLb, tmQTb, tmQTbl, nl, ns, Sl, h->wpart,
-                                                        h->w_ldp, h->wtick, nullptr, nullptr, h->wZTb, h->wZTbl, ldl,
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(!short_col, lowp, tmLb, tmQTb, tmQTbl, nl, ns, h->sms, h->wpart,
+                                                        h->w_ldp, nullptr, nullptr, h->wZTb, h->wZTbl, ldl,
                                                         nullptr, nullptr, h->dst, st, sc8, ntr8, ntc8));
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(short_col, lowp, tmSb, tmZTb, tmZTbl, ns, nl, Ss, h->wpart,
-                                                         h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr, lds,
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(short_col, lowp, tmSb, tmZTb, tmZTbl, ns, nl, h->sms, h->wpart,
+                                                         h->w_ldp, h->wYT, nullptr, nullptr, nullptr, lds,
                                                          nullptr, nullptr, h->dst, st, sc8, ntr8, ntc8));
     } else {
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(!short_col, 0, tmL, tmQT, tmQTl, nl, ns, Sl, h->wpart,
-                                                        h->w_ldp, h->wtick, h->wZT, h->wZTl, nullptr, nullptr, ldl,
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_AQ, launch_wd_pass(!short_col, 0, tmL, tmQT, tmQTl, nl, ns, h->sms, h->wpart,
+                                                        h->w_ldp, h->wZT, h->wZTl, nullptr, nullptr, ldl,
                                                         nullptr, nullptr, h->dst, st));
-      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(short_col, 0, tmS, tmZT, tmZTl, ns, nl, Ss, h->wpart,
-                                                         h->w_ldp, h->wtick, h->wYT, nullptr, nullptr, nullptr, lds,
+      FRSVT_LAUNCH(FRSVT_PHASE_POWER_ATZ, launch_wd_pass(short_col, 0, tmS, tmZT, tmZTl, ns, nl, h->sms, h->wpart,
+                                                         h->w_ldp, h->wYT, nullptr, nullptr, nullptr, lds,
                                                          nullptr, nullptr, h->dst, st));
     }
     if (orth_last && it < q - 1) {
@@ -759,8 +756,8 @@ frsvt_status wide_range_and_core(frsvt_handle* h, const float* A, int64_t m, int
     if ((s = wide_orth(h, ns, l, it == q - 1 ? 2 : 1, bf && it + 1 < q - 1)) != FRSVT_OK) return s;
   }
   // projection B^T = Z (step 16), then B B^T = Z^T Z and the core (steps 16-19)
-  FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_wd_pass(!short_col, 0, tmL, tmQT, tmQTl, nl, ns, Sl, h->wpart, h->w_ldp,
-                                                   h->wtick, h->wZT, nullptr, nullptr, nullptr, ldl, h->wZ, h->wZl,
+  FRSVT_LAUNCH(FRSVT_PHASE_PROJECT, launch_wd_pass(!short_col, 0, tmL, tmQT, tmQTl, nl, ns, h->sms, h->wpart, h->w_ldp,
+                                                   h->wZT, nullptr, nullptr, nullptr, ldl, h->wZ, h->wZl,
                                                    h->dst, st));
   FRSVT_LAUNCH(FRSVT_PHASE_CORE, launch_wd_gram(true, h->wZT, ldl, nl, h->w_gram_grid, h->wgc, h->wGpk,
                                                 l, h->cfg.rank_tol, l, tau_host, tau_from_mu, use_rp,
@@ -793,7 +790,7 @@ frsvt_status wide_epilogue(frsvt_handle* h, bool alm, int64_t m, int64_t n, cons
   const int64_t ntiles = cdiv(m, 128) * cdiv(n, wide_tile());
   const int grid = static_cast<int>(ntiles < h->sms ? ntiles : h->sms);
   FRSVT_LAUNCH(FRSVT_PHASE_EPILOGUE, launch_wd_alm(alm, tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, h->dst,
-                                                   h->wac, h->wtick + h->w_ntiles + 1, grid, alm ? h->Ab : nullptr,
+                                                   h->wac, h->wtick, grid, alm ? h->Ab : nullptr,
                                                    h->ldb, h->stream));
   return FRSVT_OK;
 }
@@ -807,7 +804,6 @@ bool wide_alloc(frsvt_handle* h) {
   h->w_ldl = cdiv(lmax, T) * T;
   h->w_lds = cdiv(smax, T) * T;
   h->w_ldp = h->w_ldl;
-  h->w_ntiles = h->w_ldp / T;
   h->w_gram_grid = wide_gram_grid();
   if (h->w_gram_grid < 1) h->w_gram_grid = 1;
   bool ok = true;
@@ -830,11 +826,11 @@ bool wide_alloc(frsvt_handle* h) {
   alloc(reinterpret_cast<void**>(&h->wT1), sizeof(float) * LW * LW);
   alloc(reinterpret_cast<void**>(&h->wT2), sizeof(float) * LW * LW);
   alloc(reinterpret_cast<void**>(&h->wI), sizeof(float) * LW * LW);
-  alloc(reinterpret_cast<void**>(&h->wpart), sizeof(float) * 8 * LW * h->w_ldp);
+  alloc(reinterpret_cast<void**>(&h->wpart), sizeof(float) * 8 * LW * h->w_ldp);   // 8 partial planes per pass tile
   alloc(reinterpret_cast<void**>(&h->wgc), sizeof(double) * h->w_gram_grid * wide_gram_count());
   alloc(reinterpret_cast<void**>(&h->wGpk), sizeof(double) * wide_gram_count());
   alloc(reinterpret_cast<void**>(&h->wac), sizeof(double) * (h->sms > 0 ? h->sms : 1));
-  alloc(reinterpret_cast<void**>(&h->wtick), sizeof(unsigned) * (h->w_ntiles + 2));
+  alloc(reinterpret_cast<void**>(&h->wtick), sizeof(unsigned));
   alloc(reinterpret_cast<void**>(&h->dst), sizeof(DevState));
   alloc(reinterpret_cast<void**>(&h->pmax), sizeof(float) * h->absmax_blocks);
   alloc(reinterpret_cast<void**>(&h->psum), sizeof(float2) * h->absmax_blocks);
@@ -857,7 +853,7 @@ bool wide_alloc(frsvt_handle* h) {
     alloc(&h->wQTbl, bn);
   }
   if (!ok) return false;
-  return cudaMemsetAsync(h->wtick, 0, sizeof(unsigned) * (h->w_ntiles + 2), h->stream) == cudaSuccess &&
+  return cudaMemsetAsync(h->wtick, 0, sizeof(unsigned), h->stream) == cudaSuccess &&
          cudaMemsetAsync(h->wT2, 0, sizeof(float) * LW * LW, h->stream) == cudaSuccess &&
          launch_wd_identity(h->wI, h->stream) == cudaSuccess;
 }

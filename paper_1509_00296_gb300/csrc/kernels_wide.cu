@@ -43,6 +43,7 @@ constexpr int kWN = 256;                       // long-side extent of a pass til
 constexpr int kWK = 32;                        // floats per K-chunk (128 bytes)
 constexpr int kWStages = 3;
 constexpr int kWSplit = 8;                     // split warps of the pass
+constexpr int kWParts = 8;                     // partial planes of the pass workspace
 constexpr int kWThr = 64 + 32 * (4 + kWSplit); // 448
 constexpr uint32_t kWABytes = kWN * kWK * 4;   // 32 KB
 constexpr uint32_t kWMBytes = kWL * kWK * 4;   // 16 KB
@@ -256,6 +257,41 @@ __device__ __forceinline__ void fp8x16_to_bf16(const uint4 q, float sc, uint4& l
   hi8 = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
+// The CTA whose range holds unit x when U units are cut into G contiguous ranges
+// [b U / G, (b + 1) U / G): the largest b with floor(b U / G) <= x.
+__device__ __forceinline__ int pass_cta_of(int64_t x, int64_t U, int G) {
+  return static_cast<int>(((x + 1) * G + U - 1) / U) - 1;
+}
+
+// Stores of one float4 of a reduced pass tile (row k, long-side columns x0 + 4 x4 .. + 3): the
+// TF32 hi / lo and BF16 hi / lo layouts, and the shared-memory staging of the row-major outputs.
+__device__ __forceinline__ void pass_store_out(const float4 v, int k, int x4, int x0, float* __restrict__ outT,
+                                               float* __restrict__ outTl, __nv_bfloat16* __restrict__ outTb,
+                                               __nv_bfloat16* __restrict__ outTbl, int64_t ldo, float* sm) {
+  constexpr int kSt = kWL + 1;
+  if (outT != nullptr) reinterpret_cast<float4*>(outT + k * ldo + x0)[x4] = v;
+  if (outTl != nullptr) reinterpret_cast<float4*>(outTl + k * ldo + x0)[x4] = f4_lo(v);
+  if (outTb != nullptr) {
+    __nv_bfloat16 h[4], l[4];
+    bf16_split(v.x, h[0], l[0]);
+    bf16_split(v.y, h[1], l[1]);
+    bf16_split(v.z, h[2], l[2]);
+    bf16_split(v.w, h[3], l[3]);
+    __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(outTb + k * ldo + x0 + 4 * x4);
+    __nv_bfloat162* lb = reinterpret_cast<__nv_bfloat162*>(outTbl + k * ldo + x0 + 4 * x4);
+    hb[0] = __halves2bfloat162(h[0], h[1]);
+    hb[1] = __halves2bfloat162(h[2], h[3]);
+    lb[0] = __halves2bfloat162(l[0], l[1]);
+    lb[1] = __halves2bfloat162(l[2], l[3]);
+  }
+  if (sm != nullptr) {
+    sm[(4 * x4 + 0) * kSt + k] = v.x;
+    sm[(4 * x4 + 1) * kSt + k] = v.y;
+    sm[(4 * x4 + 2) * kSt + k] = v.z;
+    sm[(4 * x4 + 3) * kSt + k] = v.w;
+  }
+}
+
 // ---------------------------------------------------------------- passes over A
 // COL = false (row pass): D[k][i] = sum_j M[k][j] A[i][j] for the 256 rows i of the tile, K = n,
 //   A tiles 256 rows x one K-chunk (K-major, 128-byte swizzle).
@@ -268,32 +304,35 @@ __device__ __forceinline__ void fp8x16_to_bf16(const uint4 q, float sc, uint4& l
 // PR = 1 (BF16 shadow of A): K-chunks of 64 BF16; M arrives as BF16 hi / lo parts, so only A's
 //   BF16 rounding remains: kind::f16 MMAs M_hi A + M_lo A (the column pass reads A MN-major in
 //   the plain 128-byte swizzle, 4 boxes of 64 x 64); no split.
-// Warps: 0 TMA, 1 tensor memory + MMA, 2-5 drain, 6-13 split (PR = 0).  The last CTA of a tile
-// sums the S partials in split order and writes the outputs: outT / outTl (128 x ldo, TF32 hi /
-// lo parts), outTb / outTbl (the same as BF16 hi / lo parts), outR / outRl (row-major).
+// Work split: the ntiles x nkc (tile, K-chunk) units, tile-major, are cut into G contiguous
+// ranges, one per CTA (G CTAs cover the SMs once, G >= ntiles), so a CTA ends one tile and starts
+// at most one more: a segment per tile, each with its own TMEM accumulator (columns 0-255 and
+// 256-511) and its own partial, slot = its index among the tile's segments.  The last CTA to
+// finish a tile sums that tile's partials in slot order (a fixed order) and writes the outputs:
+// outT / outTl (128 x ldo, TF32 hi / lo parts), outTb / outTbl (the same as BF16 hi / lo parts),
+// outR / outRl (row-major).
+// Warps: 0 TMA, 1 tensor memory + MMA, 2-5 drain, 6-13 split (PR = 0).
 template <bool COL, int PR>
 __global__ void __launch_bounds__(kWThr, 1)
 k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmM,
-          const __grid_constant__ CUtensorMap tmMl, int64_t nlong, int64_t nk, int S, float* __restrict__ part,
-          int64_t ldp, unsigned* __restrict__ tickets, float* __restrict__ outT, float* __restrict__ outTl,
-          __nv_bfloat16* __restrict__ outTb, __nv_bfloat16* __restrict__ outTbl, int64_t ldo,
-          float* __restrict__ outR, float* __restrict__ outRl, DevState* __restrict__ dst,
-          const float* __restrict__ scales, int ntr8, int ntc8) {
+          const __grid_constant__ CUtensorMap tmMl, int64_t nlong, int64_t nk, int G, float* __restrict__ part,
+          int64_t ldp, DevState* __restrict__ dst, const float* __restrict__ scales, int ntr8, int ntc8) {
   constexpr int KC = PR ? 64 : kWK;                         // elements of K per chunk (128-byte rows)
   constexpr int NS = (PR == 2) ? 2 : kWStages;              // pipeline stages
   constexpr uint32_t SB = (PR == 2) ? kWStage + 16384u : kWStage;   // stage bytes (+ the FP8 tile)
   constexpr uint32_t TX = (PR == 2) ? 16384u + 2 * kWMBytes : kWStage;   // bytes the TMA brings per stage
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t full[kWStages], hidone[kWStages], lo_ready[kWStages], empty[kWStages], acc_full;
+  __shared__ __align__(8) uint64_t full[kWStages], hidone[kWStages], lo_ready[kWStages], empty[kWStages], acc_full[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x / S, split = blockIdx.x % S;
-  const int nkc = static_cast<int>((nk + KC - 1) / KC);
-  const int c0 = static_cast<int>(static_cast<int64_t>(split) * nkc / S);
-  const int c1 = static_cast<int>(static_cast<int64_t>(split + 1) * nkc / S);
-  const int nc = c1 - c0;
-  const int x0 = tile * kWN;
+  const int64_t nkc = (nk + KC - 1) / KC;
+  const int64_t U = ((nlong + kWN - 1) / kWN) * nkc;
+  const int64_t u0 = static_cast<int64_t>(blockIdx.x) * U / G;
+  const int nc = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * U / G - u0);   // units of this CTA
+  const int t0 = static_cast<int>(u0 / nkc);                                                // its first tile
+  const int nseg = (nc > 0 && (u0 + nc - 1) / nkc > t0) ? 2 : 1;
+  const int gsplit = nseg == 2 ? static_cast<int>((t0 + 1) * nkc - u0) : nc;              // first unit of tile t0 + 1
+  const uint32_t tcols = nseg == 2 ? 512u : 256u;
   // every block-scope declaration of dsm in this file asks for 1024-byte alignment (one entity);
   // the swizzled TMA destinations need it, so a misplaced base is reported and nothing is issued
   if ((smem_addr(dsm) & 1023u) != 0u) {
@@ -307,10 +346,11 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       mbar_init(&lo_ready[s], kWSplit);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&acc_full, 1);
+    mbar_init(&acc_full[0], 1);
+    mbar_init(&acc_full[1], 1);
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(&tmem_base, 256);
+  if (warp == 1) tmem_alloc(&tmem_base, tcols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -329,7 +369,9 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           break;
         }
         unsigned char* st = dsm + s * SB;
-        const int c = c0 + g;
+        const int tg = t0 + (g >= gsplit ? 1 : 0);
+        const int c = static_cast<int>(u0 + g - static_cast<int64_t>(tg) * nkc);
+        const int x0 = tg * kWN;
         mbar_arrive_expect_tx(&full[s], TX);
         if (PR == 2) {
           if (COL) tma_load_2d(st + kWABytes + 2 * kWMBytes, &tmA, x0, KC * c, &full[s]);
@@ -358,15 +400,18 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           if (ok && !mbar_wait(PR == 2 ? &lo_ready[s] : &full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
           tc_fence_after();
           const unsigned char* st = dsm + s * SB;
+          const uint32_t dacc = tbase + (g >= gsplit ? 256u : 0u);
+          const bool first = g == 0 || g == gsplit;
 #pragma unroll
           for (int ks = 0; ks < KC / 16; ++ks) {
             const uint64_t bd = COL ? smem_desc_sw128(st + ks * 2048, 8192, 1024) : smem_desc_sw128(st + 32 * ks, 16, 1024);
-            tc_mma_bf16w(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bd, idesc, g > 0 || ks > 0);
-            tc_mma_bf16w(tbase, smem_desc_sw128(st + kWABytes + kWMBytes + 32 * ks, 16, 1024), bd, idesc, true);
+            tc_mma_bf16w(dacc, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bd, idesc, !first || ks > 0);
+            tc_mma_bf16w(dacc, smem_desc_sw128(st + kWABytes + kWMBytes + 32 * ks, 16, 1024), bd, idesc, true);
           }
           tc_commit(&empty[s]);
+          if (g == gsplit - 1 && nseg == 2) tc_commit(&acc_full[0]);
         }
-        tc_commit(&acc_full);
+        tc_commit(&acc_full[nseg - 1]);
       } else {
         constexpr uint32_t idesc = idesc_tf32(128, kWN, false, COL);
         auto bdesc = [&](const unsigned char* a, int ks) -> uint64_t {
@@ -377,52 +422,44 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           if (ok && !mbar_wait(&lo_ready[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
           tc_fence_after();
           const unsigned char* st = dsm + s * SB;
+          const uint32_t dacc = tbase + (g >= gsplit ? 256u : 0u);
 #pragma unroll
           for (int ks = 0; ks < kWK / 8; ++ks)
-            tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc, true);
+            tc_mma_tf32(dacc, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc, true);
           tc_commit(&empty[s]);
+          if (g == gsplit - 1 && nseg == 2) tc_commit(&acc_full[0]);
         };
         for (int g = 0; g < nc; ++g) {
           const int s = g % NS, u = g / NS;
           if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
           tc_fence_after();
           const unsigned char* st = dsm + s * SB;
+          const uint32_t dacc = tbase + (g >= gsplit ? 256u : 0u);
+          const bool first = g == 0 || g == gsplit;
 #pragma unroll
           for (int ks = 0; ks < kWK / 8; ++ks) {
-            tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
-                        g > 0 || ks > 0);
-            tc_mma_tf32(tbase, smem_desc_sw128(st + kWABytes + kWMBytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
+            tc_mma_tf32(dacc, smem_desc_sw128(st + kWABytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
+                        !first || ks > 0);
+            tc_mma_tf32(dacc, smem_desc_sw128(st + kWABytes + kWMBytes + 32 * ks, 16, 1024), bdesc(st, ks), idesc,
                         true);
           }
           tc_commit(&hidone[s]);
           if (g > 0) issue_lo(g - 1);
         }
         if (nc > 0) issue_lo(nc - 1);
-        tc_commit(&acc_full);
+        tc_commit(&acc_full[nseg - 1]);
       }
     }
   } else if (warp < 6) {
-    // drain: TMEM lane 32 q + L is row k of D, column x its long-side index; partial of split s
-    // goes to part[s][k][x0 + x].
-    const int q = warp & 3;
-    if (!mbar_wait(&acc_full, 0u)) flag_timeout(ok, dst);
-    tc_fence_after();
-    const int k = 32 * q + lane;
-    float* dstp = part + (static_cast<int64_t>(split) * kWL + k) * ldp + x0;
-    for (int grp = 0; grp < kWN / 16; ++grp) {
-      float v[16];
-      tmem_ld16(tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(16 * grp), v);
-      float4* d4 = reinterpret_cast<float4*>(dstp + 16 * grp);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        d4[u] = (nc > 0 && ok) ? make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3])
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    // drain only (below)
   } else if (PR == 2) {
     // FP8 tile (plain rows) -> BF16 tile in the layout the MMA reads, times the tile scales
     const int t = threadIdx.x - 32 * 6;
     for (int g = 0; g < nc; ++g) {
-      const int s = g % NS, u = g / NS, c = c0 + g;
+      const int s = g % NS, u = g / NS;
+      const int tg = t0 + (g >= gsplit ? 1 : 0);
+      const int c = static_cast<int>(u0 + g - static_cast<int64_t>(tg) * nkc);
+      const int x0 = tg * kWN;
       if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
       unsigned char* ab = dsm + s * SB;
       const uint4* a8 = reinterpret_cast<const uint4*>(ab + kWABytes + 2 * kWMBytes);
@@ -466,60 +503,86 @@ k_wd_pass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       if (lane == 0) mbar_arrive(&lo_ready[s]);
     }
   }
+  if (warp >= 2) {
+    // drain by warps 2-13: warp w reads the TMEM lanes of its quarter q = w mod 4 (lane 32 q + L is
+    // row k of D, column x its long-side index), column groups i, i + 3, ... with i = (w - 2) / 4;
+    // the segment in slot j of tile t goes to part[j][k][t kWN + x].
+    const int q = warp & 3, i0 = (warp - 2) >> 2;
+    const int k = 32 * q + lane;
+    for (int sg = 0; sg < nseg; ++sg) {
+      if (!mbar_wait(&acc_full[sg], 0u)) flag_timeout(ok, dst);
+      tc_fence_after();
+      const int t = t0 + sg;
+      const int j = static_cast<int>(blockIdx.x) - pass_cta_of(static_cast<int64_t>(t) * nkc, U, G);
+      float* dstp = part + (static_cast<int64_t>(j) * kWL + k) * ldp + static_cast<int64_t>(t) * kWN;
+      for (int grp = i0; grp < kWN / 16; grp += 3) {
+        float v[16];
+        tmem_ld16(tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(256 * sg + 16 * grp), v);
+        float4* d4 = reinterpret_cast<float4*>(dstp + 16 * grp);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          d4[u] = (nc > 0 && ok) ? make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3])
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tbase, 256);
+  if (warp == 1) tmem_dealloc(tbase, tcols);
+}
 
-  // last CTA of the tile: sum the S partials in split order, write the outputs
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned old = atomicAdd(&tickets[tile], 1u);
-    flag = (old == static_cast<unsigned>(S - 1)) ? 1 : 0;
-    if (flag) tickets[tile] = 0;
+// The pass outputs: the partials of each tile summed in slot order (a fixed order).  CTA (t, kb)
+// takes rows k = kPsRows kb .. + kPsRows - 1 of tile t, thread (r, c) row r and the float4 columns
+// c, c + 16, c + 32, c + 48; the row-major outputs go through a shared-memory transpose.
+constexpr int kPsRows = 16;
+constexpr int kPsThr = kPsRows * 16;
+__global__ void __launch_bounds__(kPsThr)
+k_wd_psum(const float* __restrict__ part, int64_t ldp, int64_t nlong, int64_t nkc, int G, float* __restrict__ outT,
+          float* __restrict__ outTl, __nv_bfloat16* __restrict__ outTb, __nv_bfloat16* __restrict__ outTbl, int64_t ldo,
+          float* __restrict__ outR, float* __restrict__ outRl) {
+  __shared__ float sm[kWN * (kPsRows + 1)];
+  const int t = blockIdx.x / (kWL / kPsRows), kb = blockIdx.x % (kWL / kPsRows);
+  const int64_t U = ((nlong + kWN - 1) / kWN) * nkc;
+  const int jf = pass_cta_of(static_cast<int64_t>(t) * nkc, U, G);
+  const int nparts = pass_cta_of(static_cast<int64_t>(t + 1) * nkc - 1, U, G) - jf + 1;
+  const int x0 = t * kWN;
+  const int r = threadIdx.x >> 4, c = threadIdx.x & 15;
+  const int k = kb * kPsRows + r;
+  float4 v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+  for (int s = 0; s < nparts; ++s) {
+    const float4* ps = reinterpret_cast<const float4*>(part + (static_cast<int64_t>(s) * kWL + k) * ldp + x0);
+    float4 w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = __ldcg(ps + c + 16 * j);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = f4_add(v[j], w[j]);
   }
-  __syncthreads();
-  if (!flag) return;
-  __threadfence();
-  constexpr int kSt = kWL + 1;
-  float* sm = reinterpret_cast<float*>(dsm);               // kWN x kSt staging for the row-major outputs
-  for (int e = threadIdx.x; e < kWL * (kWN / 4); e += kWThr) {
-    const int k = e / (kWN / 4), x4 = e % (kWN / 4);
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int s = 0; s < S; ++s)
-      v = f4_add(v, __ldcg(reinterpret_cast<const float4*>(part + (static_cast<int64_t>(s) * kWL + k) * ldp + x0) + x4));
-    if (outT != nullptr) reinterpret_cast<float4*>(outT + k * ldo + x0)[x4] = v;
-    if (outTl != nullptr) reinterpret_cast<float4*>(outTl + k * ldo + x0)[x4] = f4_lo(v);
-    if (outTb != nullptr) {
-      __nv_bfloat16 h[4], l[4];
-      bf16_split(v.x, h[0], l[0]);
-      bf16_split(v.y, h[1], l[1]);
-      bf16_split(v.z, h[2], l[2]);
-      bf16_split(v.w, h[3], l[3]);
-      __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(outTb + k * ldo + x0 + 4 * x4);
-      __nv_bfloat162* lb = reinterpret_cast<__nv_bfloat162*>(outTbl + k * ldo + x0 + 4 * x4);
-      hb[0] = __halves2bfloat162(h[0], h[1]);
-      hb[1] = __halves2bfloat162(h[2], h[3]);
-      lb[0] = __halves2bfloat162(l[0], l[1]);
-      lb[1] = __halves2bfloat162(l[2], l[3]);
-    }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int x4 = c + 16 * j;
+    pass_store_out(v[j], k, x4, x0, outT, outTl, outTb, outTbl, ldo, nullptr);
     if (outR != nullptr) {
-      sm[(4 * x4 + 0) * kSt + k] = v.x;
-      sm[(4 * x4 + 1) * kSt + k] = v.y;
-      sm[(4 * x4 + 2) * kSt + k] = v.z;
-      sm[(4 * x4 + 3) * kSt + k] = v.w;
+      sm[(4 * x4 + 0) * (kPsRows + 1) + r] = v[j].x;
+      sm[(4 * x4 + 1) * (kPsRows + 1) + r] = v[j].y;
+      sm[(4 * x4 + 2) * (kPsRows + 1) + r] = v[j].z;
+      sm[(4 * x4 + 3) * (kPsRows + 1) + r] = v[j].w;
     }
   }
   if (outR == nullptr) return;
   __syncthreads();
   const int nx = static_cast<int>(imin64(kWN, nlong - x0));
-  for (int e = threadIdx.x; e < nx * (kWL / 4); e += kWThr) {
-    const int x = e / (kWL / 4), k4 = e % (kWL / 4);
-    const float* r = sm + x * kSt + 4 * k4;
-    const float4 v = make_float4(r[0], r[1], r[2], r[3]);
-    reinterpret_cast<float4*>(outR + (x0 + x) * static_cast<int64_t>(kWL))[k4] = v;
-    if (outRl != nullptr) reinterpret_cast<float4*>(outRl + (x0 + x) * static_cast<int64_t>(kWL))[k4] = f4_lo(v);
+  for (int e = threadIdx.x; e < nx * (kPsRows / 4); e += kPsThr) {
+    const int x = e / (kPsRows / 4), k4 = e % (kPsRows / 4);
+    const float* rr = sm + x * (kPsRows + 1) + 4 * k4;
+    const float4 o = make_float4(rr[0], rr[1], rr[2], rr[3]);
+    float4* d = reinterpret_cast<float4*>(outR + (x0 + x) * static_cast<int64_t>(kWL) + kb * kPsRows) + k4;
+    *d = o;
+    if (outRl != nullptr)
+      reinterpret_cast<float4*>(outRl + (x0 + x) * static_cast<int64_t>(kWL) + kb * kPsRows)[k4] = f4_lo(o);
   }
 }
 
@@ -1723,38 +1786,54 @@ cudaError_t launch_wd_omega(float* OT, float* OTl, void* OTb, void* OTbl, int64_
   return cudaGetLastError();
 }
 
-// Splits of K per tile so that ntiles * S covers the SMs once (S <= 8, at least 2 chunks each).
-int wide_splits(int64_t nlong, int64_t nk, int sms) {
+// CTAs of a pass: the ntiles x nkc units cut into G ranges, G = the SM count (at least two units
+// per CTA, at least one CTA per tile), lowered until no tile is cut into more than kWParts
+// segments (the partial planes of the workspace).  Host copy of pass_cta_of.
+static int64_t pass_cta_of_host(int64_t x, int64_t U, int64_t G) { return ((x + 1) * G + U - 1) / U - 1; }
+
+int wide_pass_grid(int64_t nlong, int64_t nk, int prec, int sms) {
   const int64_t ntiles = (nlong + kWN - 1) / kWN;
-  const int64_t nkc = (nk + 64 - 1) / 64;
-  int64_t S = sms / (ntiles > 0 ? ntiles : 1);
-  if (S > 8) S = 8;
-  if (S > nkc / 2) S = nkc / 2;
-  if (S < 1) S = 1;
-  return static_cast<int>(S);
+  const int64_t nkc = (nk + (prec ? 64 : kWK) - 1) / (prec ? 64 : kWK);
+  const int64_t U = ntiles * nkc;
+  if (ntiles < 1 || nkc < 1) return 0;
+  int64_t G = sms < U / 2 ? sms : U / 2;
+  if (G < ntiles) G = ntiles;
+  for (; G > ntiles; --G) {
+    int64_t worst = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+      const int64_t n = pass_cta_of_host((t + 1) * nkc - 1, U, G) - pass_cta_of_host(t * nkc, U, G) + 1;
+      worst = n > worst ? n : worst;
+    }
+    if (worst <= kWParts) break;
+  }
+  return static_cast<int>(G);
 }
 
 cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
-                           int64_t nlong, int64_t nk, int S, float* part, int64_t ldp, unsigned* tickets, float* outT,
-                           float* outTl, void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl,
-                           DevState* dst, cudaStream_t st, const float* scales, int ntr8, int ntc8) {
-  const int ntiles = static_cast<int>((nlong + kWN - 1) / kWN);
+                           int64_t nlong, int64_t nk, int sms, float* part, int64_t ldp, float* outT, float* outTl,
+                           void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl, DevState* dst,
+                           cudaStream_t st, const float* scales, int ntr8, int ntc8) {
+  const int G = wide_pass_grid(nlong, nk, prec, sms);
+  if (G < 1) return cudaErrorInvalidValue;
   const size_t smem = prec == 2 ? 2 * (kWStage + 16384) : kWStages * kWStage;
   __nv_bfloat16* tb = static_cast<__nv_bfloat16*>(outTb);
   __nv_bfloat16* tbl = static_cast<__nv_bfloat16*>(outTbl);
-#define ARGS tmA, tmM, tmMl, nlong, nk, S, part, ldp, tickets, outT, outTl, tb, tbl, ldo, outR, outRl, dst, scales, \
-             ntr8, ntc8
+#define ARGS tmA, tmM, tmMl, nlong, nk, G, part, ldp, dst, scales, ntr8, ntc8
   if (prec == 0) {
-    if (col) k_wd_pass<true, 0><<<ntiles * S, kWThr, smem, st>>>(ARGS);
-    else k_wd_pass<false, 0><<<ntiles * S, kWThr, smem, st>>>(ARGS);
+    if (col) k_wd_pass<true, 0><<<G, kWThr, smem, st>>>(ARGS);
+    else k_wd_pass<false, 0><<<G, kWThr, smem, st>>>(ARGS);
   } else if (prec == 1) {
-    if (col) k_wd_pass<true, 1><<<ntiles * S, kWThr, smem, st>>>(ARGS);
-    else k_wd_pass<false, 1><<<ntiles * S, kWThr, smem, st>>>(ARGS);
+    if (col) k_wd_pass<true, 1><<<G, kWThr, smem, st>>>(ARGS);
+    else k_wd_pass<false, 1><<<G, kWThr, smem, st>>>(ARGS);
   } else {
-    if (col) k_wd_pass<true, 2><<<ntiles * S, kWThr, smem, st>>>(ARGS);
-    else k_wd_pass<false, 2><<<ntiles * S, kWThr, smem, st>>>(ARGS);
+    if (col) k_wd_pass<true, 2><<<G, kWThr, smem, st>>>(ARGS);
+    else k_wd_pass<false, 2><<<G, kWThr, smem, st>>>(ARGS);
   }
 #undef ARGS
+  const int64_t ntiles = (nlong + kWN - 1) / kWN;
+  const int64_t nkc = (nk + (prec ? 64 : kWK) - 1) / (prec ? 64 : kWK);
+  k_wd_psum<<<static_cast<int>(ntiles * (kWL / kPsRows)), kPsThr, 0, st>>>(part, ldp, nlong, nkc, G, outT, outTl, tb,
+                                                                           tbl, ldo, outR, outRl);
   return cudaGetLastError();
 }
 
