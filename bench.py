@@ -59,8 +59,8 @@ WIDE_PHASE_KERNEL = {"sketch": "k_wd_pass<1,0>", "power_AQ": "k_wd_pass<0,0>", "
 # kernel exists).  traffic:
 # dram__bytes_read.sum + dram__bytes_write.sum; tensor_pct: sm__pipe_tensor_cycles_active (percent of elapsed).
 NCU_PROFILE = "profiles/wide_passes_recovery_8192x8192.md"
-NCU_WIDE = {"k_wd_pass<1,0>": {"traffic": 280.1e6, "tensor_pct": 46.2},
-            "k_wd_pass<0,0>": {"traffic": 280.6e6, "tensor_pct": 41.2},
+NCU_WIDE = {"k_wd_pass<1,0>": {"traffic": 286.4e6, "tensor_pct": 55.2},
+            "k_wd_pass<0,0>": {"traffic": 291.4e6, "tensor_pct": 57.4},
             "k_wd_alm<true>": {"traffic": 1299.1e6, "tensor_pct": None}}
 
 
@@ -347,8 +347,8 @@ def main():
 
 
 def profile_svt(prec: str):
-    """Three frsvt_svt calls (18 launches each in FP32 / BF16 mode, 19 in FP8 mode) on the
-    large low-rank recovery matrix: a fixed, short launch sequence for ncu captures."""
+    """Three frsvt_svt calls on the large low-rank recovery matrix: a fixed, short launch sequence
+    for ncu captures (per call: six passes, each followed by its partial sum)."""
     import numpy as np
     import torch
     from paper_1509_00296_gb300 import build, frsvt, synth
@@ -389,7 +389,8 @@ def fp32_issue_peak_tops() -> float:
 def wide_roofline(tm, K, n, sweeps):
     """Rooflines of the wide-basis iALM step's kernel groups from the tracing hook's per-phase
     times (CUDA events on the launching stream), and the dominant one.  HBM-bound groups:
-    algorithmic bytes per launch over the average launch time.  The small dense tails (Gram,
+    algorithmic bytes per launch over the average launch time (a pass's launch group is the pass
+    and its partial sum, k_wd_psum; the ncu traffic is the pass kernel's).  The small dense tails (Gram,
     Cholesky, Jacobi): FP32-pipe lane instructions per launch over time, against the GPU's FP32
     issue peak (a df64 product-accumulate is 9 FP32 instructions; a Jacobi pair rotation on
     128-long columns ~1000)."""
