@@ -51,7 +51,7 @@ WORKLOAD = "video-background RPCA 76800x200 (320x240 px x 200 frames), FRSVT l=1
 # Kernels that serve each phase of the wide-basis FP32 path: one kernel, except the sketch (Omega
 # generation, a few percent of it) and the small dense tails (the Gram of a basis-side matrix on all
 # SMs, then the Cholesky QR operand on one SM or the core on an 8-CTA cluster).
-WIDE_PHASE_KERNEL = {"sketch": "k_wd_pass<1,0>", "power_AQ": "k_wd_pass<0,0>", "power_AtZ": "k_wd_pass<1,0>",
+WIDE_PHASE_KERNEL = {"sketch": "k_wd_omega + k_wd_pass<1,0>", "power_AQ": "k_wd_pass<0,0>", "power_AtZ": "k_wd_pass<1,0>",
                      "project": "k_wd_pass<0,0>", "orth": "k_wd_gram + k_wd_orth", "apply": "k_wd_trsm / k_wd_apply",
                      "core": "k_wd_gram + k_wd_core", "epilogue": "k_wd_alm<true>"}
 # ncu counters of the wide-basis kernels on this workload, per launch (NCU_PROFILE records the capture command
@@ -405,6 +405,7 @@ def wide_roofline(tm, K, n, sweeps):
             t[0] += ms / K
             t[1] += cnt / K
     hbm_bytes = {"k_wd_pass<1,0>": e + 3 * z, "k_wd_pass<0,0>": e + 4 * z, "k_wd_alm<true>": 5 * e + 4 * z,
+                 "k_wd_omega + k_wd_pass<1,0>": e + 5 * z,
                  "k_wd_trsm / k_wd_apply": 3 * z}
     gram_ops = 9.0 * n * 128 * 129 / 2
     chol_ops = 4.5e6
@@ -412,8 +413,10 @@ def wide_roofline(tm, K, n, sweeps):
                "k_wd_gram + k_wd_core": gram_ops + chol_ops + sweeps * (128 * 127 / 2) * 1000.0}
     pk = fp32_issue_peak_tops()
     all_roofs = {}
+    # the sketch phase is two launch groups (Omega^T, then the pass with its sum): one unit of work
+    units_per_group = {"k_wd_omega + k_wd_pass<1,0>": 0.5}
     for k, (ms, cnt) in kern.items():
-        per_launch_ms = ms / cnt
+        per_launch_ms = ms / (cnt * units_per_group.get(k, 1.0))
         ncu = NCU_WIDE.get(k, {})
         if k in hbm_bytes:
             ach = hbm_bytes[k] / (per_launch_ms / 1e3) / 1e9
