@@ -1509,6 +1509,11 @@ __device__ __forceinline__ void epi_load(const float* O, const float* S, const f
   }
 }
 constexpr uint32_t kESmem = kEStages * kEStage + kEW * 32 * kEXs * 4;   // + 8 x 4.2 KB for the transpose
+// The iALM form keeps one operand stage (a tile's four K-chunks are loaded and multiplied well
+// within the time its epilogue takes) and gives the other 96 KB to a per-warp ring of O, S, A:
+// two slots of 16 rows x 32 columns of each, filled by cp.async two half-chunks ahead.
+constexpr int kESlot = 3 * 16 * 32;                                      // floats per ring slot
+constexpr uint32_t kESmemAlm = kEStage + kEW * 32 * kEXs * 4 + kEW * 2 * kESlot * 4;
 
 template <bool ALM>
 __global__ void __launch_bounds__(kEThr, 1)
@@ -1517,6 +1522,7 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
          const float* __restrict__ O, float* __restrict__ S, float* __restrict__ A, int64_t ld, float* __restrict__ L,
          int64_t ldl, DevState* __restrict__ dst, double* __restrict__ cpart, unsigned* __restrict__ ticket,
          __nv_bfloat16* __restrict__ Ab, int64_t ldb) {
+  constexpr int NS = ALM ? 1 : kEStages;              // operand stages
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[kEStages], empty[kEStages], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
@@ -1531,7 +1537,7 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
     return;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kEStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -1555,7 +1561,7 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
       prefetch_tensormap(&tmR);
       prefetch_tensormap(&tmRl);
       for (int g = 0; g < 4 * mine && ok; ++g) {
-        const int s = g % kEStages, u = g / kEStages;
+        const int s = g % NS, u = g / NS;
         const int tl = static_cast<int>(blockIdx.x) + (g / 4) * static_cast<int>(gridDim.x);
         const int tr = tl / ntc, tc = tl % ntc, c = g % 4;
         if (u > 0 && !mbar_wait(&empty[s], static_cast<uint32_t>(u - 1) & 1u)) {
@@ -1580,7 +1586,7 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
         const uint32_t d = tbase + static_cast<uint32_t>(buf * kWN);
         for (int c = 0; c < 4; ++c) {
           const int g = 4 * k + c;
-          const int s = g % kEStages, u = g / kEStages;
+          const int s = g % NS, u = g / NS;
           if (ok && !mbar_wait(&full[s], static_cast<uint32_t>(u) & 1u)) flag_timeout(ok, dst);
           tc_fence_after();
           const unsigned char* st = dsm + s * kEStage;
@@ -1599,6 +1605,124 @@ k_wd_alm(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtens
         tc_commit(&acc_full[buf]);
       }
     }
+  } else if (ALM) {
+    // epilogue warps, iALM form: lane (rr, c4) takes rows 4 i + rr and columns c4 .. c4 + 3 of
+    // each 16-row half of the warp's 32 x 32 chunk of X; its O, S, A come from the ring slot that
+    // cp.async filled two half-chunks earlier.  Step s = 8 k + 2 cg + hh: tile k of this CTA,
+    // column group cg, row half hh.
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const double mu = dst->mu;
+    const double mu_next = fmin(dst->rho * mu, dst->mu_bar);
+    const float thr = static_cast<float>(dst->lambda / mu);
+    const float ratio = static_cast<float>(mu / mu_next);
+    float* sX = reinterpret_cast<float*>(dsm + NS * kEStage) + (warp - 2) * (32 * kEXs);
+    float* ring = reinterpret_cast<float*>(dsm + NS * kEStage + kEW * 32 * kEXs * 4) + (warp - 2) * (2 * kESlot);
+    const int rr = lane >> 3, c4 = 4 * (lane & 7);
+    auto fill = [&](int s) {                           // one cp.async group per step, empty past the end
+      if (s < 8 * mine) {
+        const int k = s >> 3, cg = (s >> 1) & 3, hh = s & 1;
+        const int tl = static_cast<int>(blockIdx.x) + k * static_cast<int>(gridDim.x);
+        const int64_t rbase = 128 * static_cast<int64_t>(tl / ntc) + 32 * q + 16 * hh;
+        const int64_t colg = static_cast<int64_t>(kWN) * (tl % ntc) + 128 * half + 32 * cg + c4;
+        float* slot = ring + (s & 1) * kESlot;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t rowg = rbase + 4 * i + rr;
+          const bool in = rowg < m && colg < n;
+          const int bytes = in ? 4 * static_cast<int>(imin64(4, n - colg)) : 0;
+          const int64_t off = in ? rowg * ld + colg : 0;
+          float* d = slot + (4 * i + rr) * 32 + c4;
+          cp_async16(d, O + off, bytes);
+          cp_async16(d + 512, S + off, bytes);
+          cp_async16(d + 1024, A + off, bytes);
+        }
+      }
+      cp_async_commit();
+    };
+    fill(0);
+    fill(1);
+    for (int k = 0; k < mine; ++k) {
+      const int buf = k & 1;
+      const int tl = static_cast<int>(blockIdx.x) + k * static_cast<int>(gridDim.x);
+      const int tr = tl / ntc, tc = tl % ntc;
+      if (ok && !mbar_wait(&acc_full[buf], static_cast<uint32_t>(k / 2) & 1u)) flag_timeout(ok, dst);
+      tc_fence_after();
+      const int64_t rbase = 128 * static_cast<int64_t>(tr) + 32 * q;   // the warp's 32 rows
+      for (int cg = 0; cg < 4; ++cg) {
+        const int colt = 128 * half + 32 * cg;
+        const int64_t colg = static_cast<int64_t>(kWN) * tc + colt + c4;
+        {                                              // the 32 x 32 chunk of X, staged row-major
+          float x[16];
+          const uint32_t ta = tbase + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(buf * kWN + colt);
+          tmem_ld16(ta, x);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sX[lane * kEXs + j] = x[j];
+          tmem_ld16(ta + 16, x);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sX[lane * kEXs + 16 + j] = x[j];
+        }
+        for (int hh = 0; hh < 2; ++hh) {
+          const int s = 8 * k + 2 * cg + hh;
+          cp_async_wait<1>();                          // step s's group has landed (s + 1 may be in flight)
+          __syncwarp();                                // ... for every lane, and sX is complete
+          const float* slot = ring + (s & 1) * kESlot;
+          float4 ov[4], sv[4], av[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float* src = slot + (4 * i + rr) * 32 + c4;
+            ov[i] = *reinterpret_cast<const float4*>(src);
+            sv[i] = *reinterpret_cast<const float4*>(src + 512);
+            av[i] = *reinterpret_cast<const float4*>(src + 1024);
+          }
+          __syncwarp();                                // the slot is free again
+          fill(s + 2);
+          if (!ok) continue;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = 16 * hh + 4 * i + rr;
+            const int64_t rowg = rbase + r;
+            const float o4[4] = {ov[i].x, ov[i].y, ov[i].z, ov[i].w};
+            const float s4[4] = {sv[i].x, sv[i].y, sv[i].z, sv[i].w};
+            const float a4[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
+            float sn[4], an[4], xv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              xv[e] = sX[r * kEXs + c4 + e];
+              const float t = a4[e] + s4[e] - xv[e];                            // O - L + Y / mu
+              sn[e] = (t > thr) ? (t - thr) : ((t < -thr) ? (t + thr) : 0.f);
+              an[e] = o4[e] - sn[e] + ratio * (t - sn[e]);                      // O - S' + Y' / mu'
+              const float rz = o4[e] - xv[e] - sn[e];                           // O - L - S'
+              if (rowg < m && colg + e < n) res2 = fmaf(rz, rz, res2);
+            }
+            if (rowg < m && colg + 4 <= n) {
+              __stcs(reinterpret_cast<float4*>(S + rowg * ld + colg), make_float4(sn[0], sn[1], sn[2], sn[3]));
+              __stcs(reinterpret_cast<float4*>(A + rowg * ld + colg), make_float4(an[0], an[1], an[2], an[3]));
+              if (L != nullptr)
+                *reinterpret_cast<float4*>(L + rowg * ldl + colg) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+              if (Ab != nullptr) {                                              // BF16 shadow of A'
+                const __nv_bfloat162 b0 = __floats2bfloat162_rn(an[0], an[1]);
+                const __nv_bfloat162 b1 = __floats2bfloat162_rn(an[2], an[3]);
+                __stcs(reinterpret_cast<uint2*>(Ab + rowg * ldb + colg),
+                       make_uint2(*reinterpret_cast<const uint32_t*>(&b0), *reinterpret_cast<const uint32_t*>(&b1)));
+              }
+            } else {
+              for (int e = 0; e < 4; ++e)
+                if (rowg < m && colg + e < n) {
+                  S[rowg * ld + colg + e] = sn[e];
+                  A[rowg * ld + colg + e] = an[e];
+                  if (L != nullptr) L[rowg * ldl + colg + e] = xv[e];
+                  if (Ab != nullptr) Ab[rowg * ldb + colg + e] = __float2bfloat16_rn(an[e]);
+                }
+            }
+          }
+        }
+        __syncwarp();                                  // sX is rewritten by the next chunk
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+    cp_async_wait<0>();
   } else {
     const int q = warp & 3, half = (warp - 2) >> 2;
     double mu = 0.0, mu_next = 0.0;
@@ -1759,7 +1883,7 @@ cudaError_t prepare_wide_kernels() {
   if (e == cudaSuccess) e = set_dyn(k_wd_core, kTSmem);
   if (e == cudaSuccess) e = set_dyn(k_wd_apply, sizeof(float) * kWL * (kWL + kACols));
   if (e == cudaSuccess) e = set_dyn(k_wd_trsm, sizeof(float) * kWL * (kTS + kTX));
-  if (e == cudaSuccess) e = set_dyn(k_wd_alm<true>, kESmem);
+  if (e == cudaSuccess) e = set_dyn(k_wd_alm<true>, kESmemAlm);
   if (e == cudaSuccess) e = set_dyn(k_wd_alm<false>, kESmem);
   return e;
 }
@@ -1906,7 +2030,7 @@ cudaError_t launch_wd_alm(bool alm, const CUtensorMap& tmZ, const CUtensorMap& t
                           const CUtensorMap& tmRl, int64_t m, int64_t n, const float* O, float* S, float* A, int64_t ld,
                           float* L, int64_t ldl, DevState* dst, double* cpart, unsigned* ticket, int grid,
                           void* Ab, int64_t ldb, cudaStream_t st) {
-  const size_t smem = kESmem;
+  const size_t smem = alm ? kESmemAlm : kESmem;
   __nv_bfloat16* ab = static_cast<__nv_bfloat16*>(Ab);
   if (alm)
     k_wd_alm<true><<<grid, kEThr, smem, st>>>(tmZ, tmZl, tmR, tmRl, m, n, O, S, A, ld, L, ldl, dst, cpart, ticket, ab,
