@@ -61,7 +61,7 @@ WIDE_PHASE_KERNEL = {"sketch": "k_wd_omega + k_wd_pass<1,0>", "power_AQ": "k_wd_
 NCU_PROFILE = "profiles/wide_passes_recovery_8192x8192.md"
 NCU_WIDE = {"k_wd_pass<1,0>": {"traffic": 286.4e6, "tensor_pct": 55.2},
             "k_wd_pass<0,0>": {"traffic": 291.4e6, "tensor_pct": 57.4},
-            "k_wd_alm<true>": {"traffic": 1299.1e6, "tensor_pct": None}}
+            "k_wd_alm<true>": {"traffic": 1328.4e6, "tensor_pct": None}}
 
 
 def config_dict(ws: int):
