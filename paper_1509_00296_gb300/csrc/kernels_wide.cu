@@ -612,13 +612,13 @@ constexpr size_t kGSmem = sizeof(float) * kGCols * kGSt + sizeof(df64) * kGCount
 constexpr size_t kTSmem = kTEnd;                                                          // tail kernel
 
 __device__ __forceinline__ void block_of(int t, int& bi, int& bj) {
-  bi = 0;
-  int rem = t;
-  while (rem >= 32 - bi) {
-    rem -= 32 - bi;
-    ++bi;
-  }
-  bj = bi + rem;
+  // row bi of the 32 x 32 block triangle starts at S(bi) = bi (65 - bi) / 2: bi is the largest
+  // root bound (65 - sqrt(4225 - 8 t)) / 2, made exact by one integer check each way
+  int b = static_cast<int>((65.f - sqrtf(static_cast<float>(4225 - 8 * t))) * 0.5f);
+  if (b < 31 && (b + 1) * (64 - b) / 2 <= t) ++b;
+  if (b * (65 - b) / 2 > t) --b;
+  bi = b;
+  bj = b + t - b * (65 - b) / 2;
 }
 
 struct TailVec {
@@ -886,10 +886,28 @@ __device__ void wide_cholesky(df64* G, const TailVec& v, float* Rout, int p, dou
   __syncthreads();
 }
 
-// Entry e of the packed Gram (a df64 pair stored where a double is declared).
-__device__ __forceinline__ df64 gram_entry(const double* Gpk, int e) {
-  const float2 w = __ldcg(reinterpret_cast<const float2*>(Gpk) + e);
-  return df64{w.x, w.y};
+// The packed Gram (4 x 4 blocks, bi <= bj) unpacked into G (128 x 128 df64, upper blocks): two
+// entries of a block row per 16-byte load, all of a thread's loads issued before any store.
+template <int NT>
+__device__ __forceinline__ void unpack_gram(const double* __restrict__ Gpk, df64* G) {
+  constexpr int kPairs = kGCount / 2;
+  constexpr int kPer = (kPairs + NT - 1) / NT;
+  float4 w[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int e2 = static_cast<int>(threadIdx.x) + j * NT;
+    w[j] = e2 < kPairs ? __ldcg(reinterpret_cast<const float4*>(Gpk) + e2) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int e2 = static_cast<int>(threadIdx.x) + j * NT;
+    if (e2 < kPairs) {
+      const int t = e2 >> 3, u = (2 * e2) & 15;
+      int bi, bj;
+      block_of(t, bi, bj);
+      *reinterpret_cast<float4*>(G + (4 * bi + (u >> 2)) * kWL + 4 * bj + (u & 3)) = w[j];
+    }
+  }
 }
 
 struct CoreArgs {
@@ -1024,12 +1042,7 @@ k_wd_orth(const double* __restrict__ Gpk, int p, double rank_tol, float* __restr
   df64* G = reinterpret_cast<df64*>(dsm + kTG);                 // 128 x 128 (upper triangle used)
   float* R = reinterpret_cast<float*>(dsm + kTR);               // R (FP32, upper)
   const TailVec v = carve_vec(dsm);
-  for (int e = tid; e < kGCount; e += nt) {                     // unpack the 4 x 4 blocks
-    const int t = e >> 4, u = e & 15;
-    int bi, bj;
-    block_of(t, bi, bj);
-    G[(4 * bi + (u >> 2)) * kWL + 4 * bj + (u & 3)] = gram_entry(Gpk, e);
-  }
+  unpack_gram<kTW>(Gpk, G);
   __syncthreads();
   wide_cholesky(G, v, R, p, rank_tol, &dst->status, reinterpret_cast<df64*>(dsm + kTP));
   for (int e = tid; e < kWL * kWL; e += nt) {
@@ -1302,12 +1315,7 @@ k_wd_core(const double* __restrict__ Gpk, int p, double rank_tol, CoreArgs ca, f
   float* R = reinterpret_cast<float*>(dsm + kTR);
   const TailVec v = carve_vec(dsm);
   if (rank == 0) {
-    for (int e = tid; e < kGCount; e += nt) {
-      const int t = e >> 4, u = e & 15;
-      int bi, bj;
-      block_of(t, bi, bj);
-      G[(4 * bi + (u >> 2)) * kWL + 4 * bj + (u & 3)] = gram_entry(Gpk, e);
-    }
+    unpack_gram<kCW>(Gpk, G);
     __syncthreads();
     wide_cholesky(G, v, R, p, rank_tol, &dst->status, reinterpret_cast<df64*>(dsm + kTP));
   }
