@@ -597,7 +597,9 @@ constexpr int kGCount = kGB * 16;        // packed partial (df64 entries)
 constexpr int kGCols = 64;               // long-side columns staged per step
 constexpr int kGSt = kWL + 4;            // staging row stride (floats)
 constexpr int kGSumE = 64;               // entries per CTA of the partial sum
-constexpr int kGSumT = 256;              // its threads: 4 quarters of the partials per entry
+constexpr int kGSumQ = 8;                // groups of threads per entry, each summing every 8th partial
+constexpr int kGSumB = 20;               // partials a thread has in flight
+constexpr int kGSumT = kGSumQ * kGSumE;  // threads of a partial-sum CTA
 // threads of the one-CTA orthonormalisation tail after a Gram matrix
 constexpr int kTW = 512;
 
@@ -999,35 +1001,38 @@ k_wd_gram(const float* __restrict__ XT, int64_t ldx, int64_t len, int64_t per_ct
 }
 
 // Gpk = the sum of the nparts partials, entry by entry in a fixed order: each CTA takes kGSumE
-// entries; quarter q of its threads sums partials q, q + 4, q + 8, ... (16 loads in flight,
-// pairwise within a group), then the four quarter sums are added in quarter order.
+// entries; group q of its threads sums partials q, q + kGSumQ, q + 2 kGSumQ, ... (kGSumB loads in
+// flight, one batch for 152 partials; pairwise within a batch), then the group sums are added in
+// group order.
 __global__ void __launch_bounds__(kGSumT)
 k_wd_gsum(const double* __restrict__ cpart, int nparts, double* __restrict__ Gpk) {
-  __shared__ df64 red[4][kGSumE];
+  __shared__ df64 red[kGSumQ][kGSumE];
   const int t = threadIdx.x, el = t % kGSumE, q = t / kGSumE;
   const int e = blockIdx.x * kGSumE + el;
   const float2* cp = reinterpret_cast<const float2*>(cpart);
   df64 sum{0.f, 0.f};
   if (e < kGCount) {
-    for (int k0 = q; k0 < nparts; k0 += 4 * 16) {
-      df64 v[16];
+    for (int k0 = q; k0 < nparts; k0 += kGSumQ * kGSumB) {
+      df64 v[kGSumB];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int k = k0 + 4 * u;
+      for (int u = 0; u < kGSumB; ++u) {
+        const int k = k0 + kGSumQ * u;
         const float2 w = k < nparts ? __ldcg(cp + static_cast<int64_t>(k) * kGCount + e) : make_float2(0.f, 0.f);
         v[u] = df64{w.x, w.y};
       }
 #pragma unroll
-      for (int h = 1; h < 16; h *= 2)
+      for (int h = 1; h < kGSumB; h *= 2)
 #pragma unroll
-        for (int u = 0; u + h < 16; u += 2 * h) v[u] = df_add(v[u], v[u + h]);
+        for (int u = 0; u + h < kGSumB; u += 2 * h) v[u] = df_add(v[u], v[u + h]);
       sum = df_add(sum, v[0]);
     }
   }
   red[q][el] = sum;
   __syncthreads();
   if (q == 0 && e < kGCount) {
-    const df64 g = df_add(df_add(red[0][el], red[1][el]), df_add(red[2][el], red[3][el]));
+    df64 g = red[0][el];
+#pragma unroll
+    for (int r = 1; r < kGSumQ; ++r) g = df_add(g, red[r][el]);
     reinterpret_cast<float2*>(Gpk)[e] = make_float2(g.hi, g.lo);
   }
 }
