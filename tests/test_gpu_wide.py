@@ -334,6 +334,31 @@ def test_wide_basis_serves_m_less_than_n(fr, m, n, l, q):
     h.close()
 
 
+def test_wide_ialm_ragged_columns(fr):
+    """iALM on 1031 x 517 (neither side a multiple of 4 or of a tile) stored with ld = 520: the
+    fused epilogue's last column group reads one float of each row and zero-fills the rest;
+    4 iterations against the oracle."""
+    import torch
+    O, _, _ = synth.lowrank_sparse(1031, 517, 12, 0.10, 10.0, seed=79, scale=1.0 / np.sqrt(12.0))
+    O = O.astype(np.float32).astype(np.float64)
+    m, n, l, iters = 1031, 517, 40, 4
+    nrm = power_norm2(O)
+    ref = orpca.ialm_rpca(O, method="frsvt", l=l, q=1, seed=2006, range_prop=False, fixed_iters=iters, normO2=nrm)
+    Og = to_gpu(O, ld=520)
+    S, A, L = to_gpu(np.zeros_like(O), ld=520), to_gpu(np.zeros_like(O), ld=520), to_gpu(np.zeros_like(O), ld=520)
+    h = fr.Handle(m, n, l, q=1, range_prop=False, seed=2006)
+    h.rpca_init(Og, S, A, 1.0 / np.sqrt(max(m, n)), 1.5, 1e7, normO2=nrm)
+    hist = [h.ialm_step(Og, S, A, l, L=L if k == iters - 1 else None, sync_residual=True) for k in range(iters)]
+    info = h.info()
+    h.close()
+    assert info.alm_iter == iters and info.device_status == 0, info
+    assert rel_fro(L.cpu().numpy(), ref.L) <= TOL
+    assert rel_fro(S.cpu().numpy(), ref.S) <= TOL
+    assert np.allclose(hist, ref.history, rtol=1e-3)
+    Sp = S.as_strided((m, 520), (520, 1)).cpu().numpy()
+    assert np.all(Sp[:, n:] == 0.0)                                  # the padding is never written
+
+
 def test_wide_ialm_m_less_than_n(fr):
     """iALM on a wide O (512 x 1500, rank 20 + 10 % corruption): 4 iterations against the oracle."""
     O, _, _ = synth.lowrank_sparse(512, 1500, 20, 0.10, 10.0, seed=78, scale=1.0 / np.sqrt(20.0))
