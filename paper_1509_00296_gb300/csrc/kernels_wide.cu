@@ -6,17 +6,21 @@
 // each pass streams from L2 next to the tiles of A:
 //
 //   k_wd_omega  Omega^T (128 x m) from the Philox stream (steps 4 / 8), split into TF32 hi / lo.
-//   k_wd_pass   the passes over A on tcgen05, FP32-accurate (3xTF32):
+//   k_wd_pass   the passes over A on tcgen05, FP32-accurate (3xTF32), or on a BF16 / FP8 shadow:
 //                 row pass    Z^T = Q^T A^T   (steps 14 and 16: Z = A Q = B^T)
 //                 column pass Y^T = M^T A     (steps 5 / 9 with M = Omega, step 14 with M = Z)
 //               D (128 x 256) accumulates in tensor memory, the M = 128 operand being the
-//               basis side (k = 0..127) and N = 256 the long side of the tile; K is split over
-//               S CTAs per tile whose partials the last CTA of the tile sums in a fixed order.
-//   k_wd_gram   X^T X (128 x 128) of a basis-side matrix in double-float arithmetic, cluster
-//               split-K reduction, then in one CTA either the orthonormalisation tail
-//               (Cholesky with the rank cut, R^{-1}: Cholesky QR, steps 6 / 11 / 14) or the core
-//               tail (Cholesky of B B^T, one-sided Jacobi SVD, shrinkage: steps 16-19, Eq. 6).
-//   k_wd_apply  Out = T^T In for a 128 x 128 T: Q = Y R^{-1}, Rf = Q M, Q~ = Q U.
+//               basis side (k = 0..127) and N = 256 the long side of the tile; the (tile,
+//               K-chunk) units are cut into one contiguous range per SM, each range writing a
+//               partial per tile it touches.
+//   k_wd_psum   the partials of each tile summed in a fixed order into the pass outputs.
+//   k_wd_gram   X^T X (128 x 128) of a basis-side matrix in double-float arithmetic, one partial
+//               per SM; k_wd_gsum adds the partials in a fixed order.
+//   k_wd_orth   one CTA: Cholesky of the Gram with the rank cut (Cholesky QR, steps 6 / 11 / 14);
+//   k_wd_trsm   Q^T = R^{-T} Y^T by forward substitution.
+//   k_wd_core   the core (steps 16-19, Eq. 6): Cholesky of B B^T, one-sided Jacobi SVD on an
+//               8-CTA cluster, shrinkage, M and the propagated basis factor.
+//   k_wd_apply  Out = T^T In for a 128 x 128 T: Rf = Q M, Q~ = Q U.
 //   k_wd_alm    X = Z Rf^T on tcgen05 (3xTF32) fused with the iALM sparse shrinkage, dual update
 //               and residual (or X written out for a plain SVT).
 //
