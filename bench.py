@@ -602,6 +602,11 @@ def bench_video(args, dev, flush):
 def graph_rate(h, O, S, A, l, steps, flush):
     """Capture one iALM iteration in a CUDA graph and time `steps` replays (device time, L2 flushed
     between replays outside the events); returns ms per iteration."""
+    return statistics.fmean(graph_replay_ms(h, O, S, A, l, steps, flush))
+
+
+def graph_replay_ms(h, O, S, A, l, steps, flush):
+    """The device time (ms) of each of `steps` replays of one captured iALM iteration."""
     import torch
     cap = torch.cuda.Stream()
     st = torch.cuda.current_stream()
@@ -620,7 +625,7 @@ def graph_rate(h, O, S, A, l, steps, flush):
         g.replay()
         evs[k][1].record()
     torch.cuda.synchronize()
-    return sum(a.elapsed_time(b) for a, b in evs) / steps
+    return [a.elapsed_time(b) for a, b in evs]
 
 
 def bench_video_bf16(args, O, O_np, lam, dev, flush):
@@ -803,9 +808,11 @@ def bench_recovery(args, O, lam, dev, flush):
             h.ialm_step(O, S, A, RL)
         tm = h.timings()
         h.enable_timing(False)
-        ms = graph_rate(h, O, S, A, RL, 10, flush)
+        reps = graph_replay_ms(h, O, S, A, RL, 10, flush)
+        ms = statistics.fmean(reps)
         info = h.info()
         out[name] = {"ms_per_step": ms, "value": 1e3 / ms,
+                     "replay_ms_median": statistics.median(reps), "replay_ms_max": max(reps),
                      "phases_ms_per_step": {k: v[0] / K for k, v in tm.items() if v[1] > 0},
                      "launch_groups_per_step": sum(v[1] for v in tm.values()) / K, "jacobi_sweeps": info.sweeps,
                      "rank": info.r, "basis": info.s, "device_status": info.device_status}
