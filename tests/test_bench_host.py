@@ -38,3 +38,25 @@ def test_wide_phase_kernels_cover_the_roofline_candidates():
     for k in ("k_wd_pass<1,0>", "k_wd_pass<0,0>", "k_wd_alm<true>"):
         assert k in bench.WIDE_PHASE_KERNEL.values()
     assert 70.0 < bench.fp32_alu_peak_tflops() < 90.0
+
+
+def test_wide_roofline_groups_from_phase_times():
+    """The roofline groups computed from per-phase times: a pass's launch group is the pass with its
+    partial sum, the sketch phase (Omega^T, then the first pass) is one unit of two launch groups,
+    and the core group is reported against the FP32 issue rate."""
+    K = 4
+    ph = {"sketch": (0.100, 2), "power_AQ": (0.180, 2), "power_AtZ": (0.176, 2), "orth": (0.440, 4),
+          "project": (0.090, 1), "core": (0.500, 1), "epilogue": (0.240, 1), "apply": (0.108, 5)}
+    tm = {k: (ms * K, cnt * K) for k, (ms, cnt) in ph.items()}
+    r = bench.wide_roofline(tm, K, 8192, 8)
+    assert r["kernel"] == "k_wd_gram + k_wd_core" and r["bound"] == "alu"
+    other = r["other_kernels"]
+    e, z = 4.0 * 8192 * 8192, 4.0 * 128 * 8192
+    peak, _ = bench.peaks()
+    # sketch: 0.100 ms for one unit of e + 5 z bytes
+    assert abs(other["k_wd_omega + k_wd_pass<1,0>"]["achieved"] - (e + 5 * z) / 0.100e-3 / 1e9) < 1e-6
+    # row pass: (0.180 + 0.090) ms over 3 launch groups of e + 4 z bytes
+    assert abs(other["k_wd_pass<0,0>"]["achieved"] - (e + 4 * z) / 0.090e-3 / 1e9) < 1e-6
+    assert abs(other["k_wd_pass<1,0>"]["achieved"] - (e + 3 * z) / 0.088e-3 / 1e9) < 1e-6
+    assert abs(other["k_wd_alm<true>"]["frac"] - (5 * e + 4 * z) / 0.240e-3 / 1e9 / peak) < 1e-9
+    assert 0.0 < r["frac"] < 0.1
