@@ -1318,7 +1318,6 @@ k_wd_core(const double* __restrict__ Gpk, int p, double rank_tol, CoreArgs ca, f
           float* __restrict__ T2, DevState* __restrict__ dst) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ int rotflag[2 * kJC];
-  const int tid = threadIdx.x, nt = blockDim.x;
   const int rank = static_cast<int>(cooperative_groups::this_cluster().block_rank());
   df64* G = reinterpret_cast<df64*>(dsm + kTG);
   float* R = reinterpret_cast<float*>(dsm + kTR);
