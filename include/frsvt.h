@@ -290,6 +290,20 @@ const char* frsvt_phase_name(int32_t phase);
 frsvt_status frsvt_step_kernels(frsvt_handle* h, int32_t* kernels);
 
 /*
+ * Work split of one pass over A on the wide basis (Alg. 1 steps 5, 9, 14, 16: Y^T = M^T A or
+ * Z^T = Q^T A^T with a 128-row basis side).  The long side (nlong) is cut into tiles of 256, the
+ * contracted side (nk) into K-chunks of 32 columns for an FP32-accurate pass
+ * (precision = FRSVT_PREC_FP32) or of 64 for a BF16 / FP8 shadow pass; the tile-major
+ * (tile, K-chunk) units are cut into *grid contiguous ranges, one CTA each, for a GPU of `sms`
+ * SMs.  *max_parts = the most CTA ranges that touch one tile (the partials its fixed-order sum
+ * adds; the workspace holds 8), *max_tiles = the most tiles one range touches (its TMEM
+ * accumulators; at most 2).  Host-only arithmetic, no device work; FRSVT_ERR_INVALID_ARG for
+ * null outputs, nlong, nk or sms below 1, or an unknown precision.
+ */
+frsvt_status frsvt_wide_pass_plan(int64_t nlong, int64_t nk, int32_t precision, int32_t sms, int32_t* grid,
+                                  int32_t* max_parts, int32_t* max_tiles);
+
+/*
  * Allocation-free FRSVT (the paper has no counterpart: this is a deployment
  * entry point, not part of the method).
  *

@@ -126,6 +126,7 @@ cudaError_t launch_wd_identity(float* T, cudaStream_t st);
 cudaError_t launch_wd_colscale(const float* YT, int64_t ld, int64_t ns, float* T, cudaStream_t st);
 cudaError_t launch_wd_omega(float* OT, float* OTl, void* OTb, void* OTbl, int64_t ldo, int64_t m, int l, int use_rp,
                             uint64_t seed, uint64_t ctr, const DevState* dst, cudaStream_t st);
+void wide_pass_plan(int64_t nlong, int64_t nk, int prec, int sms, int* grid, int* max_parts, int* max_tiles);
 cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
                            int64_t nlong, int64_t nk, int sms, float* part, int64_t ldp, float* outT, float* outTl,
                            void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl, DevState* dst,
@@ -1742,6 +1743,20 @@ frsvt_status frsvt_enable_timing(frsvt_handle* h, int32_t enable) {
 frsvt_status frsvt_step_kernels(frsvt_handle* h, int32_t* kernels) {
   if (h == nullptr || kernels == nullptr) return FRSVT_ERR_INVALID_ARG;
   *kernels = h->last_step_kernels;
+  return FRSVT_OK;
+}
+
+frsvt_status frsvt_wide_pass_plan(int64_t nlong, int64_t nk, int32_t precision, int32_t sms, int32_t* grid,
+                                  int32_t* max_parts, int32_t* max_tiles) {
+  if (grid == nullptr || max_parts == nullptr || max_tiles == nullptr) return FRSVT_ERR_INVALID_ARG;
+  if (nlong < 1 || nk < 1 || sms < 1 || precision < FRSVT_PREC_FP32 || precision > FRSVT_PREC_FP8)
+    return FRSVT_ERR_INVALID_ARG;
+  int g = 0, mp = 0, mt = 0;
+  wide_pass_plan(nlong, nk, precision == FRSVT_PREC_FP32 ? 0 : (precision == FRSVT_PREC_BF16 ? 1 : 2), sms, &g, &mp,
+                 &mt);
+  *grid = g;
+  *max_parts = mp;
+  *max_tiles = mt;
   return FRSVT_OK;
 }
 

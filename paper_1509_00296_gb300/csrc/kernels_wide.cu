@@ -1949,6 +1949,30 @@ int wide_pass_grid(int64_t nlong, int64_t nk, int prec, int sms) {
   return static_cast<int>(G);
 }
 
+// The plan wide_pass_grid gives a pass: its CTA count, the most segments (partials) of one tile
+// and the most tiles one CTA's range touches.
+void wide_pass_plan(int64_t nlong, int64_t nk, int prec, int sms, int* grid, int* max_parts, int* max_tiles) {
+  const int64_t ntiles = (nlong + kWN - 1) / kWN;
+  const int64_t nkc = (nk + (prec ? 64 : kWK) - 1) / (prec ? 64 : kWK);
+  const int64_t U = ntiles * nkc;
+  const int G = wide_pass_grid(nlong, nk, prec, sms);
+  int mp = 0, mt = 0;
+  if (G > 0) {
+    for (int64_t t = 0; t < ntiles; ++t) {
+      const int64_t n = pass_cta_of_host((t + 1) * nkc - 1, U, G) - pass_cta_of_host(t * nkc, U, G) + 1;
+      mp = n > mp ? static_cast<int>(n) : mp;
+    }
+    for (int64_t b = 0; b < G; ++b) {
+      const int64_t u0 = b * U / G, u1 = (b + 1) * U / G;
+      const int64_t n = u1 > u0 ? (u1 - 1) / nkc - u0 / nkc + 1 : 0;
+      mt = n > mt ? static_cast<int>(n) : mt;
+    }
+  }
+  *grid = G;
+  *max_parts = mp;
+  *max_tiles = mt;
+}
+
 cudaError_t launch_wd_pass(bool col, int prec, const CUtensorMap& tmA, const CUtensorMap& tmM, const CUtensorMap& tmMl,
                            int64_t nlong, int64_t nk, int sms, float* part, int64_t ldp, float* outT, float* outTl,
                            void* outTb, void* outTbl, int64_t ldo, float* outR, float* outRl, DevState* dst,

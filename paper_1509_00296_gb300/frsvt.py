@@ -71,6 +71,8 @@ _SIGS = {
     "frsvt_enable_timing": [_P, ctypes.c_int32],
     "frsvt_get_timings": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
     "frsvt_step_kernels": [_P, ctypes.POINTER(ctypes.c_int32)],
+    "frsvt_wide_pass_plan": [_I64, _I64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "frsvt_lrr_create": [ctypes.POINTER(_P), _I64, _I64, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                          ctypes.c_int32, _P],
     "frsvt_lrr_destroy": [_P],
@@ -411,6 +413,17 @@ class Handle:
         cnt = ctypes.c_int32()
         self._chk(lib().frsvt_get_sigma(self._h, buf, 128, ctypes.byref(cnt)))
         return [buf[i] for i in range(cnt.value)]
+
+
+def wide_pass_plan(nlong: int, nk: int, precision: int = 0, sms: int = 152):
+    """(grid, max_parts, max_tiles) of one wide-basis pass over A (frsvt_wide_pass_plan): the CTA
+    count, the most partials of one tile, the most tiles of one CTA's range.  Host arithmetic."""
+    g, mp, mt = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    st = lib().frsvt_wide_pass_plan(int(nlong), int(nk), int(precision), int(sms), ctypes.byref(g), ctypes.byref(mp),
+                                    ctypes.byref(mt))
+    if st != 0:
+        raise FrsvtError(st, "frsvt_wide_pass_plan")
+    return g.value, mp.value, mt.value
 
 
 def debug_omega(rows: int, cols: int, seed: int, stream: int, problem: int = 0):
